@@ -1,0 +1,573 @@
+/*
+ * brmppi_oracle.c -- plain FP64 CPU oracle for one BR-MPPI control solve.
+ *
+ * TEST INFRASTRUCTURE ONLY (see brmppi_oracle.h).  Slow on purpose: plain
+ * loops, libm, a dense Cholesky solve for the projection, no blocking, no
+ * fusion.  Each function names the passage of the paper it restates.
+ *
+ * Readings of the paper where it is silent or garbled (the same readings the
+ * CUDA path takes):
+ *   - model: accel a is an input, progress psi is a state driven by nu
+ *     (psi' = nu, Sec. IV-B); explicit Euler with every right-hand side at
+ *     step k (Sec. III-A); angles are never wrapped, delta is not clamped.
+ *   - barrier-rate row: L_f h + L_g h u is the second-order Taylor increment
+ *     Ts*hdot + Ts^2/2*hddot along the continuous vector field with the input
+ *     held (Eq. barrier_function_approx, Sec. IV-C), for obstacles and hitch.
+ *   - sign of the CBF equality as printed in Eq. cbf_equality.
+ *   - alpha_i starts at alpha0 each rollout; its nominal input is 0; the
+ *     sampled u^alpha is clipped to [ua_lo, ua_hi]; alpha itself is unclipped.
+ *   - A's alpha column uses h_tilde = sgn(h) max(|h|, h_floor), sgn(0) = +1.
+ *   - z_des is clipped to the box before projection; after projection only
+ *     the physical input u is clipped (the applied input).
+ *   - the applied input drives dynamics, cost and the weighted update.
+ *   - J = sum_{tau=0}^{H-1} r(x_{tau+1}, u_tau), no terminal cost, no
+ *     lambda u^T Sigma^-1 u term; heading errors wrapped into (-pi, pi];
+ *     theta2r = theta1r (one heading column).
+ */
+#include "brmppi_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ------------------------------------------------------------------ */
+/* Philox4x32-10.  Salmon et al., SC'11: each round multiplies words 0 and 2
+   by the two round constants, and the next counter is
+   (hi(M1*c2) ^ c1 ^ k0, lo(M1*c2), hi(M0*c0) ^ c3 ^ k1, lo(M0*c0));
+   the key is bumped by the two Weyl constants before every round but the
+   first. */
+#define PHILOX_M0 0xD2511F53u
+#define PHILOX_M1 0xCD9E8D57u
+#define PHILOX_W0 0x9E3779B9u
+#define PHILOX_W1 0xBB67AE85u
+
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {
+  uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+  uint32_t k0 = key[0], k1 = key[1];
+  for (int round = 0; round < 10; ++round) {
+    if (round > 0) {
+      k0 += PHILOX_W0;
+      k1 += PHILOX_W1;
+    }
+    uint64_t p0 = (uint64_t)PHILOX_M0 * (uint64_t)c0;
+    uint64_t p1 = (uint64_t)PHILOX_M1 * (uint64_t)c2;
+    uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+    uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+    uint32_t n0 = hi1 ^ c1 ^ k0;
+    uint32_t n1 = lo1;
+    uint32_t n2 = hi0 ^ c3 ^ k1;
+    uint32_t n3 = lo0;
+    c0 = n0;
+    c1 = n1;
+    c2 = n2;
+    c3 = n3;
+  }
+  out[0] = c0;
+  out[1] = c1;
+  out[2] = c2;
+  out[3] = c3;
+}
+
+/* 32-bit word -> uniform in (0, 1): the top 23 bits plus one half, scaled by
+   2^-23 (exact in binary32 and binary64). */
+static double word_to_uniform(uint32_t w) { return ((double)(w >> 9) + 0.5) * (1.0 / 8388608.0); }
+
+/* Noise of the MPPI sampling step (Sec. II-B: w ~ N(0, Sigma)), drawn from
+   the counter-based stream: normal q is lane q%4 of Philox block q/4 at
+   counter (q/4, tau, s, counter_lo32), key (seed_lo32, seed_hi32); lanes
+   (0,1) and (2,3) are Box-Muller pairs. */
+void orc_normals(uint64_t seed, uint64_t counter, uint32_t s, uint32_t tau, int d, double *n) {
+  const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+  for (int blk = 0; 4 * blk < d; ++blk) {
+    const uint32_t ctr[4] = {(uint32_t)blk, tau, s, (uint32_t)counter};
+    uint32_t w[4];
+    orc_philox4x32_10(ctr, key, w);
+    double g[4];
+    for (int pair = 0; pair < 2; ++pair) {
+      double ua = word_to_uniform(w[2 * pair]);
+      double ub = word_to_uniform(w[2 * pair + 1]);
+      double radius = sqrt(-2.0 * log(ua));
+      double angle = 2.0 * M_PI * ub;
+      g[2 * pair] = radius * cos(angle);
+      g[2 * pair + 1] = radius * sin(angle);
+    }
+    for (int lane = 0; lane < 4 && 4 * blk + lane < d; ++lane) n[4 * blk + lane] = g[lane];
+  }
+}
+
+/* ------------------------------------------------------------------ */
+/* Tractor-trailer kinematics, explicit Euler (Sec. III-A,
+   Eq. tt_discrete_kinematics), with acceleration a as input and the path
+   progress psi integrated from nu. */
+void orc_dynamics_step(const orc_params *P, const double x[7], const double u[3], double xn[7]) {
+  const double px = x[0], py = x[1], th1 = x[2], th2 = x[3], v = x[4], delta = x[5], psi = x[6];
+  const double a = u[0], omega = u[1], nu = u[2];
+  const double Ts = P->Ts;
+  xn[0] = px + Ts * v * cos(th1);
+  xn[1] = py + Ts * v * sin(th1);
+  xn[2] = th1 + Ts * v / P->l1 * tan(delta);
+  xn[3] = th2 + Ts * v / P->l2 *
+                    (sin(th1 - th2) - (P->lh / P->l1) * cos(th1 - th2) * tan(delta));
+  xn[4] = v + Ts * a;
+  xn[5] = delta + Ts * omega;
+  xn[6] = psi + Ts * nu;
+}
+
+void orc_integrate(const orc_params *P, const double x0[7], const double *U, int H, double *traj) {
+  memcpy(traj, x0, 7 * sizeof(double));
+  for (int k = 0; k < H; ++k) orc_dynamics_step(P, traj + 7 * k, U + 3 * k, traj + 7 * (k + 1));
+}
+
+/* ------------------------------------------------------------------ */
+/* Integer power for the super-ellipse exponent. */
+static double ipow(double base, int e) {
+  double r = 1.0;
+  for (int i = 0; i < e; ++i) r *= base;
+  return r;
+}
+
+static int obstacle_exponent(const double obs[6]) {
+  double e = obs[5];
+  int ei = (int)e;
+  if ((double)ei != e || ei < 2 || (ei % 2) != 0) return -1;
+  return ei;
+}
+
+/* Super-ellipse barrier (Sec. IV-C, Eq. barrier_function): semi-axes
+   inflated by the footprint disc radius, coordinates rotated into the
+   obstacle frame. */
+double orc_obstacle_h(const orc_params *P, const double obs[6], const double x[7]) {
+  const int e = obstacle_exponent(obs);
+  if (e < 0) return NAN;
+  const double cx = obs[0], cy = obs[1], Ax = obs[2] + P->r_inflate, Ay = obs[3] + P->r_inflate;
+  const double th_o = obs[4];
+  const double xp = cos(th_o) * (x[0] - cx) + sin(th_o) * (x[1] - cy);
+  const double yp = -sin(th_o) * (x[0] - cx) + cos(th_o) * (x[1] - cy);
+  return ipow(xp / Ax, e) + ipow(yp / Ay, e) - 1.0;
+}
+
+/* Barrier-rate equality row for one obstacle (Eq. cbf_equality with the
+   second-order expansion of Eq. barrier_function_approx).
+   Along the continuous field with the input held, the rear-axle point
+   moves with  pdot = v (cos th1, sin th1)  and
+   pddot = a (cos th1, sin th1) + v * th1dot * (-sin th1, cos th1),
+   th1dot = v tan(delta) / l1.  With h = h(x', y'):
+   hdot  = grad h . pdot',  hddot = grad h . pddot' + pdot'^T Hess h pdot'.
+   hddot is affine in a; steer rate and progress rate do not enter at second
+   order.  Row: A_u = (Ts^2/2 * dhddot/da, 0, 0) and
+   b = -alpha h - Ts hdot - Ts^2/2 hddot|_{a=0}. */
+void orc_obstacle_row(const orc_params *P, const double obs[6], const double x[7],
+                      double A_u[3], double *h, double *b_rest) {
+  const int e = obstacle_exponent(obs);
+  const double cx = obs[0], cy = obs[1], Ax = obs[2] + P->r_inflate, Ay = obs[3] + P->r_inflate;
+  const double th_o = obs[4];
+  const double co = cos(th_o), so = sin(th_o);
+  const double px = x[0], py = x[1], th1 = x[2], v = x[4], delta = x[5];
+  const double Ts = P->Ts;
+
+  /* rotate a world vector into the obstacle frame */
+#define ROT_X(wx, wy) (co * (wx) + so * (wy))
+#define ROT_Y(wx, wy) (-so * (wx) + co * (wy))
+  const double xp = ROT_X(px - cx, py - cy);
+  const double yp = ROT_Y(px - cx, py - cy);
+
+  /* derivatives of h in obstacle-frame coordinates */
+  const double Axe = ipow(Ax, e), Aye = ipow(Ay, e);
+  const double hval = ipow(xp, e) / Axe + ipow(yp, e) / Aye - 1.0;
+  const double hx = e * ipow(xp, e - 1) / Axe;
+  const double hy = e * ipow(yp, e - 1) / Aye;
+  const double hxx = e * (e - 1) * ipow(xp, e - 2) / Axe;
+  const double hyy = e * (e - 1) * ipow(yp, e - 2) / Aye;
+
+  const double c1 = cos(th1), s1 = sin(th1);
+  const double th1dot = v * tan(delta) / P->l1;
+  /* velocity, and the two parts of the acceleration */
+  const double vel_x = ROT_X(v * c1, v * s1), vel_y = ROT_Y(v * c1, v * s1);
+  const double dir_x = ROT_X(c1, s1), dir_y = ROT_Y(c1, s1); /* multiplies a */
+  const double cen_x = ROT_X(-v * th1dot * s1, v * th1dot * c1);
+  const double cen_y = ROT_Y(-v * th1dot * s1, v * th1dot * c1);
+#undef ROT_X
+#undef ROT_Y
+
+  const double hdot = hx * vel_x + hy * vel_y;
+  const double hddot_0 = hx * cen_x + hy * cen_y + hxx * vel_x * vel_x + hyy * vel_y * vel_y;
+  const double dhddot_da = hx * dir_x + hy * dir_y;
+
+  A_u[0] = 0.5 * Ts * Ts * dhddot_da;
+  A_u[1] = 0.0;
+  A_u[2] = 0.0;
+  *h = hval;
+  *b_rest = -Ts * hdot - 0.5 * Ts * Ts * hddot_0;
+}
+
+/* Hitch-angle barrier (Sec. IV-D, Eq. hitch_angle_barrier):
+   h_h = dtheta_max - kappa v - |th2 - th1|. */
+double orc_hitch_h(const orc_params *P, const double x[7]) {
+  return P->dtheta_max - P->kappa * x[4] - fabs(x[3] - x[2]);
+}
+
+/* Barrier-rate row of the hitch barrier, second-order expansion as for the
+   obstacles.  With Delta = th2 - th1, sigma = sgn(Delta) (sgn(0) = +1),
+   phi = th1 - th2, t = tan(delta), k = lh/l1:
+     th1dot = v t / l1,  G = sin(phi) - k cos(phi) t,  th2dot = v G / l2,
+     hdot   = -kappa a - sigma (th2dot - th1dot),
+     hddot  = -sigma (th2ddot - th1ddot)          (a held: vddot = 0)
+     th1ddot = (a t + v (1 + t^2) omega) / l1
+     th2ddot = a G / l2 + v / l2 * ((cos(phi) + k t sin(phi)) phidot
+                                    - k cos(phi) (1 + t^2) omega)
+   which is affine in (a, omega).  The row coefficients are read off by
+   evaluating Ts hdot + Ts^2/2 hddot at unit inputs. */
+static double hitch_increment(const orc_params *P, const double x[7], double a, double omega) {
+  const double th1 = x[2], th2 = x[3], v = x[4], delta = x[5];
+  const double Delta = th2 - th1;
+  const double sigma = (Delta >= 0.0) ? 1.0 : -1.0;
+  const double phi = th1 - th2;
+  const double t = tan(delta);
+  const double k = P->lh / P->l1;
+  const double G = sin(phi) - k * cos(phi) * t;
+  const double th1dot = v * t / P->l1;
+  const double th2dot = v * G / P->l2;
+  const double phidot = th1dot - th2dot;
+  const double th1ddot = (a * t + v * (1.0 + t * t) * omega) / P->l1;
+  const double th2ddot =
+      a * G / P->l2 +
+      v / P->l2 * ((cos(phi) + k * t * sin(phi)) * phidot - k * cos(phi) * (1.0 + t * t) * omega);
+  const double hdot = -P->kappa * a - sigma * (th2dot - th1dot);
+  const double hddot = -sigma * (th2ddot - th1ddot);
+  return P->Ts * hdot + 0.5 * P->Ts * P->Ts * hddot;
+}
+
+void orc_hitch_row(const orc_params *P, const double x[7], double A_u[3], double *h, double *b_rest) {
+  const double c0 = hitch_increment(P, x, 0.0, 0.0);
+  const double ca = hitch_increment(P, x, 1.0, 0.0) - c0;
+  const double cw = hitch_increment(P, x, 0.0, 1.0) - c0;
+  A_u[0] = ca;
+  A_u[1] = cw;
+  A_u[2] = 0.0;
+  *h = orc_hitch_h(P, x);
+  *b_rest = -c0;
+}
+
+/* ------------------------------------------------------------------ */
+/* Dense linear algebra for the projection: Cholesky, with Gaussian
+   elimination (partial pivoting) as the fallback. */
+static int cholesky_solve(int n, double *K, double *rhs) {
+  for (int j = 0; j < n; ++j) {
+    double s = K[j * n + j];
+    for (int k = 0; k < j; ++k) s -= K[j * n + k] * K[j * n + k];
+    if (!(s > 0.0)) return -1;
+    const double Ljj = sqrt(s);
+    K[j * n + j] = Ljj;
+    for (int i = j + 1; i < n; ++i) {
+      double t = K[i * n + j];
+      for (int k = 0; k < j; ++k) t -= K[i * n + k] * K[j * n + k];
+      K[i * n + j] = t / Ljj;
+    }
+  }
+  for (int i = 0; i < n; ++i) { /* L y = rhs */
+    double t = rhs[i];
+    for (int k = 0; k < i; ++k) t -= K[i * n + k] * rhs[k];
+    rhs[i] = t / K[i * n + i];
+  }
+  for (int i = n - 1; i >= 0; --i) { /* L^T x = y */
+    double t = rhs[i];
+    for (int k = i + 1; k < n; ++k) t -= K[k * n + i] * rhs[k];
+    rhs[i] = t / K[i * n + i];
+  }
+  return 0;
+}
+
+static int gauss_solve(int n, double *K, double *rhs) {
+  for (int c = 0; c < n; ++c) {
+    int piv = c;
+    for (int r = c + 1; r < n; ++r)
+      if (fabs(K[r * n + c]) > fabs(K[piv * n + c])) piv = r;
+    if (K[piv * n + c] == 0.0) return -1;
+    if (piv != c) {
+      for (int k = 0; k < n; ++k) {
+        double t = K[c * n + k];
+        K[c * n + k] = K[piv * n + k];
+        K[piv * n + k] = t;
+      }
+      double t = rhs[c];
+      rhs[c] = rhs[piv];
+      rhs[piv] = t;
+    }
+    for (int r = c + 1; r < n; ++r) {
+      double f = K[r * n + c] / K[c * n + c];
+      for (int k = c; k < n; ++k) K[r * n + k] -= f * K[c * n + k];
+      rhs[r] -= f * rhs[c];
+    }
+  }
+  for (int r = n - 1; r >= 0; --r) {
+    double t = rhs[r];
+    for (int k = r + 1; k < n; ++k) t -= K[r * n + k] * rhs[k];
+    rhs[r] = t / K[r * n + r];
+  }
+  return 0;
+}
+
+/* Soft-bound projection (Sec. IV-A, Eq. softproj), closed form
+   (Eq. closed-form_projection):
+     M = W + rho I,   p = W z_des + rho/2 (z_hi + z_lo),
+     z* = M^-1 [ p - A^T (A M^-1 A^T)^-1 (A M^-1 p - b) ]. */
+int orc_project(int d, int nc, const double *A, const double *b, const double *w, double rho,
+                const double *z_lo, const double *z_hi, const double *z_des, double *z_star) {
+  double *Minv = (double *)malloc(sizeof(double) * (size_t)d);
+  double *p = (double *)malloc(sizeof(double) * (size_t)d);
+  double *K = (double *)malloc(sizeof(double) * (size_t)(nc * nc + 1));
+  double *K2 = (double *)malloc(sizeof(double) * (size_t)(nc * nc + 1));
+  double *lam = (double *)malloc(sizeof(double) * (size_t)(nc + 1));
+  double *lam2 = (double *)malloc(sizeof(double) * (size_t)(nc + 1));
+  int status = ORC_OK;
+  for (int j = 0; j < d; ++j) {
+    Minv[j] = 1.0 / (w[j] + rho);
+    p[j] = w[j] * z_des[j] + 0.5 * rho * (z_hi[j] + z_lo[j]);
+  }
+  for (int i = 0; i < nc; ++i) {
+    double t = 0.0;
+    for (int j = 0; j < d; ++j) t += A[i * d + j] * Minv[j] * p[j];
+    lam[i] = t - b[i]; /* A M^-1 p - b */
+    for (int r = 0; r < nc; ++r) {
+      double kk = 0.0;
+      for (int j = 0; j < d; ++j) kk += A[i * d + j] * Minv[j] * A[r * d + j];
+      K[i * nc + r] = kk; /* A M^-1 A^T */
+    }
+  }
+  memcpy(K2, K, sizeof(double) * (size_t)(nc * nc));
+  memcpy(lam2, lam, sizeof(double) * (size_t)nc);
+  if (nc > 0 && cholesky_solve(nc, K, lam) != 0) {
+    memcpy(lam, lam2, sizeof(double) * (size_t)nc);
+    if (gauss_solve(nc, K2, lam) != 0) status = ORC_EINVAL;
+  }
+  if (status == ORC_OK) {
+    for (int j = 0; j < d; ++j) {
+      double t = p[j];
+      for (int i = 0; i < nc; ++i) t -= A[i * d + j] * lam[i];
+      z_star[j] = Minv[j] * t;
+    }
+  }
+  free(Minv);
+  free(p);
+  free(K);
+  free(K2);
+  free(lam);
+  free(lam2);
+  return status;
+}
+
+/* ------------------------------------------------------------------ */
+/* Reference path zeta(psi) parameterised by arc length (Sec. IV-B), read
+   from a table sampled every ds: psi clamped to the table, linear
+   interpolation of (x, y, theta). */
+void orc_path_lookup(const double *path, int n, double ds, double psi, double *xr, double *yr,
+                     double *thr) {
+  const double psi_max = (double)(n - 1) * ds;
+  double q = psi;
+  if (q < 0.0) q = 0.0;
+  if (q > psi_max) q = psi_max;
+  int i = (int)floor(q / ds);
+  if (i > n - 2) i = n - 2;
+  if (i < 0) i = 0;
+  const double f = q / ds - (double)i;
+  const double *r0 = path + 3 * i, *r1 = path + 3 * (i + 1);
+  *xr = r0[0] + f * (r1[0] - r0[0]);
+  *yr = r0[1] + f * (r1[1] - r0[1]);
+  *thr = r0[2] + f * (r1[2] - r0[2]);
+}
+
+static double wrap_angle(double a) {
+  /* into (-pi, pi] */
+  double r = fmod(a + M_PI, 2.0 * M_PI);
+  if (r < 0.0) r += 2.0 * M_PI;
+  r -= M_PI;
+  if (r == -M_PI) r = M_PI;
+  return r;
+}
+
+/* Contouring stage cost (Sec. IV-B, Eq. cost_function_contour with the
+   errors of Eq. contour_lag_errors):
+   r = Qc e_c^2 + Ql e_l^2 + Qth |e_theta|^2 + u^T R u + mu (nu_bar - nu)^2. */
+double orc_stage_cost(const orc_params *P, const double x[7], const double u[3], const double *path,
+                      int n, double ds) {
+  double xr, yr, thr;
+  orc_path_lookup(path, n, ds, x[6], &xr, &yr, &thr);
+  const double e_c = sin(thr) * (x[0] - xr) - cos(thr) * (x[1] - yr);
+  const double e_l = -cos(thr) * (x[0] - xr) - sin(thr) * (x[1] - yr);
+  const double e_th1 = wrap_angle(x[2] - thr);
+  const double e_th2 = wrap_angle(x[3] - thr);
+  double r = P->Qc * e_c * e_c + P->Ql * e_l * e_l + P->Qth * (e_th1 * e_th1 + e_th2 * e_th2);
+  for (int j = 0; j < 3; ++j) r += P->R[j] * u[j] * u[j];
+  r += P->mu * (P->nu_bar - u[2]) * (P->nu_bar - u[2]);
+  return r;
+}
+
+/* Importance weights of MPPI (Sec. II-B):
+   gamma_s = exp(-(J_s - min J)/lambda), gamma_bar = gamma / sum gamma. */
+int orc_softmin(int S, const double *J, double lambda, double *gamma_bar) {
+  double Jmin = INFINITY;
+  for (int s = 0; s < S; ++s)
+    if (isfinite(J[s]) && J[s] < Jmin) Jmin = J[s];
+  if (!isfinite(Jmin)) {
+    for (int s = 0; s < S; ++s) gamma_bar[s] = 0.0;
+    return ORC_ENONFINITE;
+  }
+  double sum = 0.0;
+  for (int s = 0; s < S; ++s) {
+    gamma_bar[s] = isfinite(J[s]) ? exp(-(J[s] - Jmin) / lambda) : 0.0;
+    sum += gamma_bar[s];
+  }
+  for (int s = 0; s < S; ++s) gamma_bar[s] /= sum;
+  return ORC_OK;
+}
+
+static double clip(double v, double lo, double hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
+/* ------------------------------------------------------------------ */
+/* One BR-MPPI rollout (Sec. IV-A): at every step sample z_des, build the
+   barrier-rate rows at the current state, project, apply the clipped input,
+   update the barrier rates alpha_{tau+1} = alpha_tau + u^alpha, step the
+   kinematics and accumulate the stage cost. */
+int orc_rollout_sample(const orc_params *P, const double x0[7], const double *U_nom,
+                       const double *obs, int n_obs, const double *path, int n_pts, double ds,
+                       uint64_t seed, uint64_t counter, uint32_t s, double *states, double *u_out,
+                       double *alpha_out, double *z_des_out, double *z_star_out, double *J_out) {
+  const int H = P->H;
+  const int Nc = 1 + n_obs;
+  const int d = 3 + Nc;
+  const int proj = !(P->flags & ORC_PROJ_NONE);
+  for (int o = 0; o < n_obs; ++o)
+    if (obstacle_exponent(obs + 6 * o) < 0) return ORC_EINVAL;
+  if (n_pts < 2 || !(ds > 0.0)) return ORC_EINVAL;
+
+  double *n = (double *)malloc(sizeof(double) * (size_t)d);
+  double *alpha = (double *)malloc(sizeof(double) * (size_t)Nc);
+  double *A = (double *)calloc((size_t)(Nc * d), sizeof(double));
+  double *b = (double *)malloc(sizeof(double) * (size_t)Nc);
+  double *w = (double *)malloc(sizeof(double) * (size_t)d);
+  double *zlo = (double *)malloc(sizeof(double) * (size_t)d);
+  double *zhi = (double *)malloc(sizeof(double) * (size_t)d);
+  double *zdes = (double *)malloc(sizeof(double) * (size_t)d);
+  double *zs = (double *)malloc(sizeof(double) * (size_t)d);
+  for (int j = 0; j < 3; ++j) {
+    w[j] = P->w_u[j];
+    zlo[j] = P->z_lo[j];
+    zhi[j] = P->z_hi[j];
+  }
+  for (int i = 0; i < Nc; ++i) {
+    w[3 + i] = P->w_alpha;
+    zlo[3 + i] = P->ua_lo;
+    zhi[3 + i] = P->ua_hi;
+    alpha[i] = P->alpha0;
+  }
+  double x[7], xn[7], u[3];
+  memcpy(x, x0, sizeof(x));
+  if (states) memcpy(states, x0, sizeof(x));
+  if (alpha_out)
+    for (int i = 0; i < Nc; ++i) alpha_out[i] = alpha[i];
+  double J = 0.0;
+  int status = ORC_OK;
+
+  for (int tau = 0; tau < H; ++tau) {
+    /* 1. noise and the sampled augmented input (perturbed nominal) */
+    orc_normals(seed, counter, s, (uint32_t)tau, proj ? d : 3, n);
+    for (int j = 0; j < 3; ++j)
+      zdes[j] = clip(U_nom[3 * tau + j] + P->sigma[j] * n[j], P->z_lo[j], P->z_hi[j]);
+    for (int i = 0; i < Nc; ++i)
+      zdes[3 + i] = proj ? clip(P->sigma_alpha * n[3 + i], P->ua_lo, P->ua_hi) : 0.0;
+
+    if (proj) {
+      /* 2. barrier-rate equality rows A z = b at the current state */
+      for (int i = 0; i < Nc; ++i) {
+        double Au[3], h, b_rest;
+        if (i == 0)
+          orc_hitch_row(P, x, Au, &h, &b_rest);
+        else
+          orc_obstacle_row(P, obs + 6 * (i - 1), x, Au, &h, &b_rest);
+        const double hmag = fabs(h) > P->h_floor ? fabs(h) : P->h_floor;
+        const double h_tilde = (h >= 0.0) ? hmag : -hmag;
+        for (int j = 0; j < d; ++j) A[i * d + j] = 0.0;
+        A[i * d + 0] = Au[0];
+        A[i * d + 1] = Au[1];
+        A[i * d + 2] = Au[2];
+        A[i * d + 3 + i] = h_tilde;
+        b[i] = -alpha[i] * h + b_rest;
+      }
+      /* 3. soft-bound projection */
+      if (orc_project(d, Nc, A, b, w, P->rho, zlo, zhi, zdes, zs) != ORC_OK) {
+        status = ORC_EINVAL;
+        break;
+      }
+    } else {
+      for (int j = 0; j < d; ++j) zs[j] = zdes[j];
+    }
+    if (z_des_out) memcpy(z_des_out + (size_t)d * tau, zdes, sizeof(double) * (size_t)d);
+    if (z_star_out) memcpy(z_star_out + (size_t)d * tau, zs, sizeof(double) * (size_t)d);
+
+    /* 4. applied input (clipped) and barrier-rate update */
+    for (int j = 0; j < 3; ++j) u[j] = clip(zs[j], P->z_lo[j], P->z_hi[j]);
+    if (proj)
+      for (int i = 0; i < Nc; ++i) alpha[i] += zs[3 + i];
+
+    /* 5. kinematics and stage cost at the new state */
+    orc_dynamics_step(P, x, u, xn);
+    memcpy(x, xn, sizeof(x));
+    J += orc_stage_cost(P, x, u, path, n_pts, ds);
+
+    if (states) memcpy(states + 7 * (tau + 1), x, sizeof(x));
+    if (u_out) memcpy(u_out + 3 * tau, u, sizeof(u));
+    if (alpha_out)
+      for (int i = 0; i < Nc; ++i) alpha_out[(size_t)Nc * (tau + 1) + i] = alpha[i];
+  }
+  if (J_out) *J_out = J;
+  free(n);
+  free(alpha);
+  free(A);
+  free(b);
+  free(w);
+  free(zlo);
+  free(zhi);
+  free(zdes);
+  free(zs);
+  return status;
+}
+
+/* ------------------------------------------------------------------ */
+/* The solve: S rollouts, softmin weights, and the update of
+   Eq. MPPI_update_rule over the applied inputs; then the optimal
+   trajectory, x0 integrated with U*. */
+int orc_solve(const orc_params *P, const double x0[7], const double *U_nom, const double *obs,
+              int n_obs, const double *path, int n_pts, double ds, uint64_t seed,
+              uint64_t counter, double *U_out, double *traj_out, double *J_out, double *u_hist,
+              double *states_out) {
+  const int S = P->S, H = P->H;
+  if (S <= 0 || H <= 0 || n_obs < 0 || n_pts < 2) return ORC_EINVAL;
+  double *J = (double *)malloc(sizeof(double) * (size_t)S);
+  double *uh = u_hist ? u_hist : (double *)malloc(sizeof(double) * (size_t)S * (size_t)H * 3);
+  double *gb = (double *)malloc(sizeof(double) * (size_t)S);
+  int status = ORC_OK;
+  for (int s = 0; s < S && status == ORC_OK; ++s) {
+    status = orc_rollout_sample(P, x0, U_nom, obs, n_obs, path, n_pts, ds, seed, counter,
+                                (uint32_t)s,
+                                states_out ? states_out + (size_t)s * (size_t)(H + 1) * 7 : NULL,
+                                uh + (size_t)s * (size_t)H * 3, NULL, NULL, NULL, &J[s]);
+  }
+  if (status == ORC_OK) {
+    status = orc_softmin(S, J, P->lambda, gb);
+    if (status == ORC_OK) {
+      for (int k = 0; k < 3 * H; ++k) {
+        double acc = 0.0;
+        for (int s = 0; s < S; ++s) acc += gb[s] * uh[(size_t)s * (size_t)H * 3 + (size_t)k];
+        U_out[k] = acc;
+      }
+    } else {
+      for (int k = 0; k < 3 * H; ++k) U_out[k] = U_nom[k];
+    }
+    if (traj_out) orc_integrate(P, x0, U_out, H, traj_out);
+    if (J_out) memcpy(J_out, J, sizeof(double) * (size_t)S);
+  }
+  free(J);
+  free(gb);
+  if (!u_hist) free(uh);
+  return status;
+}

@@ -1,0 +1,117 @@
+/*
+ * brmppi_oracle.h -- plain FP64 CPU oracle for one BR-MPPI control solve.
+ *
+ * TEST INFRASTRUCTURE ONLY.  This is the slow, step-by-step restatement of
+ * the method that the CUDA path is checked against.  Only the test suite,
+ * the smoke check and the CPU-baseline leg of the benchmark may load it.
+ * It shares no source, header, helper or constant table with the CUDA
+ * library: every formula here is written out again from the paper.
+ *
+ * Paper: "GPU-Accelerated Barrier-Rate Guided MPPI Control for
+ * Tractor-Trailer Systems" (arXiv 2508.05773).  Section / equation labels
+ * below are the paper's.
+ *
+ * Conventions (identical to the CUDA path's inputs, not its code):
+ *   state  x = (px, py, th1, th2, v, delta, psi)             7 doubles
+ *   input  u = (a, omega, nu)                                3 doubles
+ *   augmented z = (a, omega, nu, ua_0 .. ua_{Nc-1})          d = 3 + Nc
+ *   constraint 0 is the hitch-angle barrier, 1..No the obstacles
+ *   obstacle row  (cx, cy, mx, my, theta_o, e)                6 doubles
+ *   path row      (x, y, theta_unwrapped) at arc length j*ds  3 doubles
+ *
+ * All functions are pure; none keeps state between calls.
+ */
+#ifndef BRMPPI_ORACLE_H
+#define BRMPPI_ORACLE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ORC_OK 0
+#define ORC_EINVAL (-1)
+#define ORC_ENONFINITE (-5)
+
+/* flags */
+#define ORC_PROJ_NONE 1 /* standard MPPI: skip the barrier-rate projection */
+
+typedef struct {
+  int32_t S, H, flags;
+  double Ts, lambda;                  /* sample time, softmin temperature */
+  double l1, lh, l2;                  /* wheelbase, hitch offset, trailer length */
+  double dtheta_max, kappa;           /* hitch limit  dtheta_max - kappa * v */
+  double r_inflate;                   /* footprint disc radius added to semi-axes */
+  double Qc, Ql, Qth, R[3], mu, nu_bar; /* contouring cost weights */
+  double z_lo[3], z_hi[3], sigma[3];  /* input bounds and noise std */
+  double alpha0, sigma_alpha, ua_lo, ua_hi; /* barrier-rate variables */
+  double w_u[3], w_alpha, rho, h_floor;     /* projection weights */
+} orc_params;
+
+/* Philox4x32 with 10 rounds (Salmon, Moraes, Dror, Shaw, SC'11). */
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+
+/* Standard normals n[0..d) of sample s at step tau (noise mapping of the
+   solve: key = seed, counter = (q/4, tau, s, counter mod 2^32), Box-Muller on
+   word pairs). */
+void orc_normals(uint64_t seed, uint64_t counter, uint32_t s, uint32_t tau, int d, double *n);
+
+/* One explicit-Euler step of the tractor-trailer kinematics. */
+void orc_dynamics_step(const orc_params *P, const double x[7], const double u[3], double xn[7]);
+
+/* Super-ellipse obstacle barrier h_o(x) (Sec. IV-C).  Returns NaN when the
+   exponent is not an even integer >= 2. */
+double orc_obstacle_h(const orc_params *P, const double obs[6], const double x[7]);
+
+/* Barrier-rate equality row of one obstacle: A_u (3 entries), h, and the
+   part of b that does not depend on alpha, b = -alpha*h + b_rest. */
+void orc_obstacle_row(const orc_params *P, const double obs[6], const double x[7],
+                      double A_u[3], double *h, double *b_rest);
+
+/* Hitch-angle barrier h_h(x) (Sec. IV-D) and its barrier-rate row. */
+double orc_hitch_h(const orc_params *P, const double x[7]);
+void orc_hitch_row(const orc_params *P, const double x[7], double A_u[3], double *h, double *b_rest);
+
+/* Soft-bound equality projection, closed form (Sec. IV-A), dense.
+   A is nc x d row-major, w the diagonal of W (d entries).  Returns ORC_OK or
+   ORC_EINVAL if A M^-1 A^T is singular. nc may be 0. */
+int orc_project(int d, int nc, const double *A, const double *b, const double *w, double rho,
+                const double *z_lo, const double *z_hi, const double *z_des, double *z_star);
+
+/* Reference path lookup at arc length psi: linear interpolation in a table of
+   n >= 2 rows sampled every ds. */
+void orc_path_lookup(const double *path, int n, double ds, double psi, double *xr, double *yr,
+                     double *thr);
+
+/* Contouring stage cost r(x, u, psi) (Sec. IV-B). */
+double orc_stage_cost(const orc_params *P, const double x[7], const double u[3], const double *path,
+                      int n, double ds);
+
+/* Softmin weights gamma_bar_s (Sec. II-B); non-finite J gets weight 0.
+   Returns ORC_ENONFINITE if no J is finite. */
+int orc_softmin(int S, const double *J, double lambda, double *gamma_bar);
+
+/* One rollout of sample s.  Any output pointer may be NULL:
+   states (H+1)*7, u (H)*3 applied inputs, alpha (H+1)*Nc, z_des H*d,
+   z_star H*d, J scalar. Returns ORC_OK or ORC_EINVAL. */
+int orc_rollout_sample(const orc_params *P, const double x0[7], const double *U_nom,
+                       const double *obs, int n_obs, const double *path, int n_pts, double ds,
+                       uint64_t seed, uint64_t counter, uint32_t s, double *states, double *u,
+                       double *alpha, double *z_des, double *z_star, double *J);
+
+/* The full solve.  U_out H*3 (required); traj_out (H+1)*7, J_out S,
+   u_hist S*H*3, states_out S*(H+1)*7 optional.  On ORC_ENONFINITE U_out is
+   the nominal sequence. */
+int orc_solve(const orc_params *P, const double x0[7], const double *U_nom, const double *obs,
+              int n_obs, const double *path, int n_pts, double ds, uint64_t seed,
+              uint64_t counter, double *U_out, double *traj_out, double *J_out, double *u_hist,
+              double *states_out);
+
+/* Euler rollout of a fixed input sequence (no projection): traj (H+1)*7. */
+void orc_integrate(const orc_params *P, const double x0[7], const double *U, int H, double *traj);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
