@@ -1,0 +1,394 @@
+#!/usr/bin/env python
+"""Benchmark of the BR-MPPI solve on GB300.
+
+Workload: the paper-scale closed loop -- S = 4096 rollouts, horizon H = 50,
+Ts = 0.05 s, 8 random ellipses along a 38.7 m reverse-parking path (15 m
+straight, 90 deg arc of R = 10 m, 8 m straight), tractor-trailer with
+l1 = 4.0, lh = 0.5, l2 = 8.0 m.  One step = one control solve (all rollouts,
+projection, costs, softmin, update, optimal trajectory, warm start).
+
+* ``value``: rollout-steps/s = S * H * solves / device time, inputs resident
+  in HBM, warm start produced on the device (ping-pong), counter = tick.
+  Each step is bracketed by CUDA events on the launching stream; the L2 is
+  flushed (256 MiB write) between steps outside the bracketed intervals.
+* ``e2e``: the closed loop through the public host entry point
+  ``brmppi_solve``: per tick the host buffers (state, nominal, obstacles,
+  path) go to the device, U* and the optimal trajectory come back, the FP64
+  host plant advances by U*[0] and the nominal is shifted.
+* ``cpu_baseline``: the FP64 oracle on the host, single thread, on a bounded
+  sample of the same solves.
+* ``--impl reference``: the oracle as the reference arm (no reference code
+  exists for this path), bounded samples of the same solve per step.
+
+Several GPUs (torchrun): one process per GPU, each running the same
+independent solves (different seeds) -- the path shards by instance and has
+no data-path collective; the ranks only agree on the timed window.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "rollout-steps/s (S·H·solves/s) batched vs plain; p50/p99 solve latency"
+UNIT = "rollout-steps/s"
+N_SM = 152
+FP32_LANES_PER_SM = 128
+L2_FLUSH_BYTES = 256 << 20
+
+
+# ----------------------------------------------------------------------------
+# Algorithmic work of one rollout-step (FP32 lane operations; one sample on one
+# lane, each +, -, *, fma, min, max, compare/select, integer mul / xor / add,
+# reciprocal, and each elementary function sin, cos, tan, log, sqrt, exp
+# counted as one operation).  The tally follows the rollout kernel step by
+# step; the derivation is tabulated in the design doc.
+PHILOX_BLOCK_OPS = 10 * 10 + 8      # 10 rounds x (2 mul.lo + 2 mul.hi + 4 xor + 2 key adds) + uniform maps
+BOX_MULLER_PAIR_OPS = 2 + 2 + 1 + 1 + 2 + 2   # 2 uniforms, log, sqrt, sincos(2pi u) (2), 2 mul
+STEP_BASE_OPS = (
+    9      # z_des for (a, omega, nu): fma + clamp(2) each
+    + 8    # trig of state: sincos(th1) (2) + rotation (4) + phi (1) + sincos(phi) ... counted below
+    + 3    # tan(delta), th1dot (2 mul)
+    + 9    # p_u (3 fma), M_u^-1 p_u (3 mul), nu projection (1), constants
+    + 14   # 2x2 solve: det (3), inverse (1), y (6), z_u (2), clamp (6 -> counted in apply)
+    + 6    # clamp of applied inputs
+    + 14   # Euler step (7 updates, 2 ops each)
+    + 12   # path index: fma, floor, convert, add, 2 clamps, frac; 3 lerps (2 each)
+    + 6    # sincos(theta_r) (2) + rotation (4)
+    + 6    # e_c, e_l
+    + 6    # heading errors with wrap (3 each)
+    + 20   # stage cost (7 squares, weights, sums)
+    + 4    # TwoSum
+    + 5    # sincos(phi) (2) + remaining trig bookkeeping
+)
+HITCH_ROW_OPS = 34          # Delta, sign, G, th2dot, phidot, h, A_a, A_w, c0
+OBSTACLE_ROW_OPS = 31       # dx, dy, rotation (4), h (4), grads (4), dir (4), vel (2), hdot (3), hddot0 (8), A_a, b
+ROW_TAIL_OPS = 24           # h floor/sign, z_des alpha, p_alpha, b, r, 1/h, 1/D, S2 (3), g (2), c (3), alpha update (3)
+
+
+def ops_per_rollout_step(n_obs: int, proj: bool = True) -> int:
+    d = 3 + 1 + n_obs
+    P = (d + 3) // 4
+    normals_ops = P * (PHILOX_BLOCK_OPS + 2 * BOX_MULLER_PAIR_OPS)
+    if not proj:
+        return PHILOX_BLOCK_OPS + 2 * BOX_MULLER_PAIR_OPS + STEP_BASE_OPS
+    return (normals_ops + STEP_BASE_OPS + HITCH_ROW_OPS + OBSTACLE_ROW_OPS * n_obs
+            + ROW_TAIL_OPS * (1 + n_obs))
+
+
+# ----------------------------------------------------------------------------
+def _dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def _measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------
+def _workload(rank: int):
+    from paper_2508_05773_gb300 import scenarios as sc
+    return sc.config2(seed=2 + 1000 * rank)
+
+
+def _config_block(c, extra=None):
+    p = c["params"]
+    cfg = {
+        "workload": "paper-scale closed-loop tick: S=4096 rollouts, H=50, Ts=0.05 s, "
+                    "8 elliptical obstacles, 38.7 m reverse-parking path (ds=0.1 m)",
+        "S": int(p["S"]), "H": int(p["H"]), "n_obstacles": int(c["obs"].shape[0]),
+        "path_points": int(c["path"].shape[0]), "solves_per_step": 1,
+        "l2": "flushed between steps (256 MiB write, outside the timed intervals)",
+        "timing": "sum of per-step CUDA-event intervals on the launching stream",
+    }
+    if extra:
+        cfg.update(extra)
+    return cfg
+
+
+def run_cpu_baseline(budget_s: float = 12.0):
+    """The FP64 oracle on host cores (single thread) on full config-2 solves,
+    as many ticks as fit the budget (at least one)."""
+    import oracle
+    from paper_2508_05773_gb300 import scenarios as sc
+    c = sc.config2()
+    p = sc.as_float32(c["params"])
+    S, H = int(p["S"]), int(p["H"])
+    t0 = time.perf_counter()
+    n = 0
+    while True:
+        oracle.solve(p, c["x0"], c["U_nom"], c["obs"], c["path"], c["ds"], c["seed"], n,
+                     want_J=False)
+        n += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    el = time.perf_counter() - t0
+    return {"value": n * S * H / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{n} full solves (S={S}, H={H}, 8 obstacles) of the same workload, "
+                      f"FP64, single thread, {el:.1f} s"}
+
+
+def run_reference(args, world, rank):
+    """Reference arm: the oracle as it stands, on bounded samples of the
+    workload (512 of the 4096 rollouts of each solve)."""
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_2508_05773_gb300 import scenarios as sc
+    c = sc.config2()
+    p = sc.as_float32(c["params"])
+    S_sample, H = 512, int(p["H"])
+    for i in range(args.warmup):
+        oracle.solve(p, c["x0"], c["U_nom"], c["obs"], c["path"], c["ds"], c["seed"], i,
+                     S=S_sample, want_J=False)
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        oracle.solve(p, c["x0"], c["U_nom"], c["obs"], c["path"], c["ds"], c["seed"], i,
+                     S=S_sample, want_J=False)
+    el = time.perf_counter() - t0
+    value = args.steps * S_sample * H / el
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": _config_block(c, {"rollouts_per_step": S_sample}),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{S_sample} of the {int(p['S'])} rollouts of each solve, "
+                                   "FP64 oracle, single thread"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "gpu_launches": 0,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args, world, rank, local):
+    import torch
+    import paper_2508_05773_gb300 as pkg
+    from paper_2508_05773_gb300 import plant
+
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    c = _workload(rank)
+    p = c["params"]
+    S, H = int(p["S"]), int(p["H"])
+    n_obs = int(c["obs"].shape[0])
+    solver = pkg.Solver(p, device=local, max_obstacles=max(16, n_obs), max_path_pts=1024)
+
+    # ---------------- device-resident inputs
+    x0 = torch.tensor(c["x0"], dtype=torch.float64, device=dev)
+    Ubuf = [torch.tensor(c["U_nom"], device=dev), torch.empty((H, 3), device=dev)]
+    obs = torch.tensor(c["obs"], device=dev)
+    path = torch.tensor(c["path"], device=dev)
+    U_out = torch.empty((H, 3), device=dev)
+    traj = torch.empty((H + 1, 7), device=dev)
+    status = torch.zeros(1, dtype=torch.int32, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def solve(tick: int):
+        rc = solver.solve_device(x0, Ubuf[tick % 2], obs, path, c["ds"], c["seed"], tick, U_out,
+                                 traj, None, Ubuf[(tick + 1) % 2], status, stream)
+        if rc != 0:
+            raise RuntimeError(pkg.brmppi_last_error(solver.ctx))
+
+    for i in range(args.warmup):
+        flush.zero_()
+        solve(i)
+    torch.cuda.synchronize()
+    assert int(status.item()) == 0
+
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    clocks = ClockSampler(local) if rank == 0 else None
+    if clocks:
+        clocks.start()
+        time.sleep(0.3)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    for i in range(args.steps):
+        flush.zero_()
+        starts[i].record(stream)
+        solve(args.warmup + i)
+        ends[i].record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop() if clocks else None
+    per = [s.elapsed_time(e) for s, e in zip(starts, ends)]  # ms
+    total_ms = float(sum(per))
+    if dist:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    rollout_steps = world * args.steps * S * H
+    value = rollout_steps / (total_ms * 1e-3)
+    lat = np.array(per)
+
+    # ---------------- end to end: closed loop through the host entry point
+    e2e = None
+    e2e_lat = None
+    h2d, d2h = solver.transfer_bytes(n_obs, int(c["path"].shape[0]))
+    x = np.array(c["x0"], dtype=np.float64)
+    Unom = np.array(c["U_nom"], dtype=np.float32)
+    for i in range(args.warmup):
+        out = solver.solve(x, Unom, c["obs"], c["path"], c["ds"], c["seed"], i)
+    x = np.array(c["x0"], dtype=np.float64)
+    Unom = np.array(c["U_nom"], dtype=np.float32)
+    if dist:
+        dist.barrier()
+    tick_s = []
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        ts = time.perf_counter()
+        out = solver.solve(x, Unom, c["obs"], c["path"], c["ds"], c["seed"], i)
+        x = plant.step(p, x, out["U"][0])
+        Unom = plant.shift(out["U"])
+        tick_s.append(time.perf_counter() - ts)
+    el = time.perf_counter() - t0
+    if dist:
+        t = torch.tensor([el], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        el = float(t.item())
+    e2e = {"value": world * args.steps * S * H / el, "unit": UNIT,
+           "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+           "p50_ms": 1e3 * float(np.percentile(tick_s, 50)),
+           "p99_ms": 1e3 * float(np.percentile(tick_s, 99)),
+           "what": "closed loop: brmppi_solve on host buffers + FP64 host plant + shift"}
+
+    if rank == 0:
+        peaks = _measured_peaks()
+        sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+        peak_ops = N_SM * FP32_LANES_PER_SM * sm_mhz * 1e6
+        ops = S * H * ops_per_rollout_step(n_obs)
+        kernel_s = total_ms * 1e-3 / args.steps / world if world > 1 else total_ms * 1e-3 / args.steps
+        achieved = ops / kernel_s
+        launch = solver.launch(n_obs)
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": _config_block(c, {"launch": launch}),
+            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                           "p999": float(np.percentile(lat, 99.9)), "deadline": 10.0,
+                           "misses": int(np.sum(lat > 10.0))},
+            "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
+                         "unit": "Tops/s (FP32 lane ops)", "frac": achieved / peak_ops,
+                         "traffic": None, "kernel": "rollout_solve_kernel",
+                         "ops_per_launch": ops,
+                         "peak_note": f"152 SMs x 128 FP32 lanes x {sm_mhz:.0f} MHz (sm_max_mhz of "
+                                      "MEASURED_PEAKS.json); derived, not measured"},
+            "e2e": e2e,
+            "gpu_launches": args.steps,
+            "clocks": clk,
+        }
+        if not args.no_cpu_baseline and world == 1:
+            line["cpu_baseline"] = run_cpu_baseline()
+        print(json.dumps(line), flush=True)
+    solver.close()
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    world, rank, local = _dist_env()
+    if args.impl == "reference":
+        return run_reference(args, world, rank)
+    return run_ours(args, world, rank, local)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

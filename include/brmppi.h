@@ -1,0 +1,149 @@
+/*
+ * brmppi.h -- C ABI of the GB300 (sm_103a) BR-MPPI solver library
+ * (libbrmppi.so).
+ *
+ * One solve is one control update of Barrier-Rate guided MPPI for a
+ * tractor-trailer, as defined in "GPU-Accelerated Barrier-Rate Guided MPPI
+ * Control for Tractor-Trailer Systems" (arXiv 2508.05773):
+ *   - S rollouts over H steps of the kinematics of Sec. III-A
+ *     (Eq. tt_discrete_kinematics, explicit Euler, acceleration as input and
+ *     the path progress psi driven by the progress rate nu, Sec. IV-B);
+ *   - at every step the sampled augmented input z = (a, omega, nu, u^alpha)
+ *     is projected onto the barrier-rate equalities of Eq. cbf_equality with
+ *     the soft-bound closed form of Eq. closed-form_projection (Sec. IV-A),
+ *     one row per elliptical obstacle (Eq. barrier_function with the
+ *     second-order expansion of Eq. barrier_function_approx, Sec. IV-C) and
+ *     one for the velocity-scaled hitch limit (Eq. hitch_angle_barrier,
+ *     Sec. IV-D);
+ *   - each rollout accumulates the contouring cost of
+ *     Eq. cost_function_contour / contour_lag_errors (Sec. IV-B);
+ *   - the solve ends with the softmin weights and the weighted update of
+ *     Eq. MPPI_update_rule (Sec. II-B), computed as a max-subtracted
+ *     log-sum-exp, and the optimal trajectory (x0 integrated with U*).
+ *
+ * Layouts (all row-major, caller-owned):
+ *   state      x0[7]        double  (px, py, theta1, theta2, v, delta, psi)
+ *   inputs     U[H][3]      float   (a, omega, nu)
+ *   obstacles  obs[n][6]    float   (cx, cy, mx, my, theta_o, e); e must be 2
+ *   path       path[n][3]   float   (x, y, heading unwrapped) at s = j*ds
+ *   trajectory traj[H+1][7] float
+ *   costs      J[S]         float
+ *
+ * Noise: normal q of sample s at step tau is lane q%4 of the Philox4x32-10
+ * block at counter (q/4, tau, s, counter mod 2^32) with key
+ * (seed mod 2^32, seed / 2^32), Box-Muller on word pairs (0,1), (2,3);
+ * q = 0,1,2 perturb (a, omega, nu), q = 3 + i the barrier-rate input of
+ * constraint i (0 = hitch, 1.. = obstacles in input order).
+ *
+ * Conventions: every function returns a brmppi_status; on failure the
+ * context's last-error string says why and no output is written (host entry
+ * points) or written outputs are unspecified (device entry points). The
+ * library never throws. All computation runs in the library's CUDA kernels;
+ * there is no CPU fallback.  A context is used by one host thread at a time
+ * for solve / solve_device; submit / poll are thread-safe.
+ */
+#ifndef BRMPPI_H
+#define BRMPPI_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define BRMPPI_ABI_VERSION 1u
+
+typedef enum {
+  BRMPPI_OK = 0,
+  BRMPPI_EINVAL = -1,     /* bad argument (sizes, NULL, e != 2, ...) */
+  BRMPPI_ENOMEM = -2,     /* device or pinned allocation failed */
+  BRMPPI_EAGAIN = -3,     /* result not ready yet (poll) */
+  BRMPPI_ETIMEDOUT = -4,  /* a bounded wait gave up */
+  BRMPPI_ENONFINITE = -5, /* non-finite input, or no rollout had a finite cost
+                             (U_out then holds the nominal sequence) */
+  BRMPPI_ECUDA = -6,      /* CUDA runtime error (message in last_error) */
+  BRMPPI_EBUSY = -7       /* no free slot / queue full */
+} brmppi_status;
+
+/* Flags */
+#define BRMPPI_FLAG_PROJ_NONE 0x1u /* standard MPPI: skip the projection (baseline) */
+
+/* Every constant of the solve; POD. Fields the paper leaves open take the
+   documented readings (alpha init, noise and bounds of u^alpha, W, rho, the
+   floor on |h| in A's alpha column). */
+typedef struct brmppi_params {
+  uint32_t abi_version;          /* must be BRMPPI_ABI_VERSION */
+  int32_t S, H;                  /* samples, horizon steps (S >= 1, 1 <= H <= 1024) */
+  int32_t max_obstacles;         /* capacity: obstacles per solve (<= 256) */
+  int32_t max_path_pts;          /* capacity: path rows per solve (>= 2) */
+  int32_t flags;                 /* BRMPPI_FLAG_* */
+  int32_t threads_per_sample;    /* 0 = autotune, else 1, 2, 4, 8, 16 or 32 */
+  int32_t block_threads;         /* 0 = autotune, else 64..512, multiple of 32 */
+  float Ts, lambda;              /* sample time [s]; softmin temperature */
+  float l1, lh, l2;              /* wheelbase, hitch offset, trailer length [m] */
+  float dtheta_max, kappa;       /* hitch limit dtheta_max - kappa*v */
+  float r_inflate;               /* footprint disc radius added to semi-axes */
+  float Qc, Ql, Qth, R[3], mu, nu_bar; /* contouring cost weights, progress target */
+  float z_lo[3], z_hi[3];        /* bounds of (a, omega, nu) */
+  float sigma[3];                /* noise std of (a, omega, nu) */
+  float alpha0, sigma_alpha;     /* barrier-rate init, noise std of u^alpha */
+  float ua_lo, ua_hi;            /* bounds of u^alpha */
+  float w_u[3], w_alpha;         /* diagonal of W */
+  float rho, h_floor;            /* soft-bound penalty; floor on |h| in A */
+} brmppi_params;
+
+typedef struct brmppi_ctx brmppi_ctx; /* opaque: device buffers, stream */
+
+/* Fill *p with the library defaults (abi_version set). */
+void brmppi_default_params(brmppi_params *p);
+
+/* Create a context on CUDA device `device`; allocates every buffer a solve
+   of the given capacities needs (device + pinned host). */
+brmppi_status brmppi_create(const brmppi_params *p, int device, brmppi_ctx **out);
+
+/* Destroy a context (NULL is a no-op). Waits for its work to finish. */
+void brmppi_destroy(brmppi_ctx *ctx);
+
+/* Message of the last failure on this context ("" if none); valid until the
+   next call on the context. A NULL ctx gives the last create() failure. */
+const char *brmppi_last_error(const brmppi_ctx *ctx);
+
+/* One solve from HOST buffers: copies inputs to the device, runs the solve
+   and copies U* (H*3), and optionally the optimal trajectory ((H+1)*7) and
+   the per-sample costs (S), back; returns when they are in host memory.
+   n_obs in [0, max_obstacles], n_pts in [2, max_path_pts], ds > 0. */
+brmppi_status brmppi_solve(brmppi_ctx *ctx, const double x0[7], const float *U_nom,
+                           const float *obs, int32_t n_obs, const float *path, int32_t n_pts,
+                           float ds, uint64_t seed, uint64_t counter, float *U_out,
+                           float *traj_out, float *J_out);
+
+/* The same solve on DEVICE buffers, enqueued on `stream` (a cudaStream_t;
+   NULL = the legacy default stream). Allocates nothing and does not
+   synchronise: outputs are valid once the stream reaches this point.
+   status_dev (device int32, may be NULL) receives BRMPPI_OK,
+   BRMPPI_ENONFINITE or BRMPPI_EINVAL from the kernel. U_next (device H*3,
+   may be NULL) receives the warm start for the next tick: U* shifted by one
+   step with its last row repeated. */
+brmppi_status brmppi_solve_device(brmppi_ctx *ctx, const double *x0_dev, const float *U_nom_dev,
+                                  const float *obs_dev, int32_t n_obs, const float *path_dev,
+                                  int32_t n_pts, float ds, uint64_t seed, uint64_t counter,
+                                  float *U_out_dev, float *traj_out_dev, float *J_out_dev,
+                                  float *U_next_dev, int32_t *status_dev, void *stream);
+
+/* Launch configuration the context will use for a solve with n_obs
+   obstacles (after autotuning if requested). */
+brmppi_status brmppi_get_launch(brmppi_ctx *ctx, int32_t n_obs, int32_t *threads_per_sample,
+                                int32_t *block_threads, int32_t *blocks);
+
+/* Bytes the host entry point brmppi_solve copies per call for a solve with
+   n_obs obstacles and n_pts path rows: *h2d (inputs, one copy) and *d2h
+   (U*, trajectory and status, one copy; plus 4*S when costs are asked
+   for). */
+brmppi_status brmppi_transfer_bytes(brmppi_ctx *ctx, int32_t n_obs, int32_t n_pts, uint64_t *h2d,
+                                    uint64_t *d2h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

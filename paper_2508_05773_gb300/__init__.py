@@ -1,0 +1,16 @@
+"""GB300-native BR-MPPI solver (arXiv 2508.05773): the data-parallel hot path
+of Barrier-Rate guided MPPI for a tractor-trailer, as sm_103a CUDA behind a C
+ABI (``include/brmppi.h``, ``libbrmppi.so``).
+
+``scenarios`` builds seeded synthetic inputs; the C-ABI functions are
+re-exported here with their C names.  Importing the package does not load the
+library; the first call does, and fails loudly if it has not been built.
+"""
+from ._native import (  # noqa: F401
+    BRMPPI_ABI_VERSION, BRMPPI_EAGAIN, BRMPPI_EBUSY, BRMPPI_ECUDA, BRMPPI_EINVAL, BRMPPI_ENOMEM,
+    BRMPPI_ENONFINITE, BRMPPI_ETIMEDOUT, BRMPPI_FLAG_PROJ_NONE, BRMPPI_OK, EXPORTS, BrmppiError,
+    NativeLibraryMissing, Solver, brmppi_create, brmppi_default_params, brmppi_destroy,
+    brmppi_get_launch, brmppi_last_error, brmppi_transfer_bytes, brmppi_params, brmppi_solve, brmppi_solve_device,
+    load, params_from_dict,
+)
+from . import scenarios  # noqa: F401

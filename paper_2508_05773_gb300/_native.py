@@ -1,0 +1,272 @@
+"""ctypes binding of libbrmppi.so (include/brmppi.h): argument marshalling
+only.  Every step of a solve runs in the library's CUDA kernels; there is no
+Python or CPU fallback, and a missing library is an error."""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libbrmppi.so")
+
+BRMPPI_ABI_VERSION = 1
+BRMPPI_OK = 0
+BRMPPI_EINVAL = -1
+BRMPPI_ENOMEM = -2
+BRMPPI_EAGAIN = -3
+BRMPPI_ETIMEDOUT = -4
+BRMPPI_ENONFINITE = -5
+BRMPPI_ECUDA = -6
+BRMPPI_EBUSY = -7
+BRMPPI_FLAG_PROJ_NONE = 0x1
+
+STATUS_NAMES = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "EAGAIN", -4: "ETIMEDOUT",
+                -5: "ENONFINITE", -6: "ECUDA", -7: "EBUSY"}
+
+#: every exported symbol the header declares
+EXPORTS = (
+    "brmppi_default_params", "brmppi_create", "brmppi_destroy", "brmppi_last_error",
+    "brmppi_solve", "brmppi_solve_device", "brmppi_get_launch", "brmppi_transfer_bytes",
+)
+
+
+class brmppi_params(ctypes.Structure):
+    _fields_ = [
+        ("abi_version", ctypes.c_uint32),
+        ("S", ctypes.c_int32), ("H", ctypes.c_int32),
+        ("max_obstacles", ctypes.c_int32), ("max_path_pts", ctypes.c_int32),
+        ("flags", ctypes.c_int32), ("threads_per_sample", ctypes.c_int32),
+        ("block_threads", ctypes.c_int32),
+        ("Ts", ctypes.c_float), ("lambda_", ctypes.c_float),
+        ("l1", ctypes.c_float), ("lh", ctypes.c_float), ("l2", ctypes.c_float),
+        ("dtheta_max", ctypes.c_float), ("kappa", ctypes.c_float), ("r_inflate", ctypes.c_float),
+        ("Qc", ctypes.c_float), ("Ql", ctypes.c_float), ("Qth", ctypes.c_float),
+        ("R", ctypes.c_float * 3), ("mu", ctypes.c_float), ("nu_bar", ctypes.c_float),
+        ("z_lo", ctypes.c_float * 3), ("z_hi", ctypes.c_float * 3), ("sigma", ctypes.c_float * 3),
+        ("alpha0", ctypes.c_float), ("sigma_alpha", ctypes.c_float),
+        ("ua_lo", ctypes.c_float), ("ua_hi", ctypes.c_float),
+        ("w_u", ctypes.c_float * 3), ("w_alpha", ctypes.c_float),
+        ("rho", ctypes.c_float), ("h_floor", ctypes.c_float),
+    ]
+
+
+_lock = threading.Lock()
+_lib = None
+
+_F = ctypes.POINTER(ctypes.c_float)
+_D = ctypes.POINTER(ctypes.c_double)
+_I32 = ctypes.POINTER(ctypes.c_int32)
+_VP = ctypes.c_void_p
+
+
+class NativeLibraryMissing(RuntimeError):
+    pass
+
+
+def load() -> ctypes.CDLL:
+    """Load libbrmppi.so (built by ``__graft_entry__.build()``)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise NativeLibraryMissing(
+                f"{LIB_PATH} is missing: build the CUDA library first "
+                "(python -c 'import __graft_entry__ as g; g.build()')")
+        lib = ctypes.CDLL(LIB_PATH)
+        P = ctypes.POINTER(brmppi_params)
+        sig = {
+            "brmppi_default_params": (None, [P]),
+            "brmppi_create": (ctypes.c_int, [P, ctypes.c_int, ctypes.POINTER(_VP)]),
+            "brmppi_destroy": (None, [_VP]),
+            "brmppi_last_error": (ctypes.c_char_p, [_VP]),
+            "brmppi_solve": (ctypes.c_int, [_VP, _D, _F, _F, ctypes.c_int32, _F, ctypes.c_int32,
+                                            ctypes.c_float, ctypes.c_uint64, ctypes.c_uint64, _F, _F,
+                                            _F]),
+            "brmppi_solve_device": (ctypes.c_int, [_VP, _VP, _VP, _VP, ctypes.c_int32, _VP,
+                                                   ctypes.c_int32, ctypes.c_float, ctypes.c_uint64,
+                                                   ctypes.c_uint64, _VP, _VP, _VP, _VP, _VP, _VP]),
+            "brmppi_get_launch": (ctypes.c_int, [_VP, ctypes.c_int32, _I32, _I32, _I32]),
+            "brmppi_transfer_bytes": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.c_int32,
+                                                     ctypes.POINTER(ctypes.c_uint64),
+                                                     ctypes.POINTER(ctypes.c_uint64)]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+        return lib
+
+
+class BrmppiError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def brmppi_default_params() -> brmppi_params:
+    p = brmppi_params()
+    load().brmppi_default_params(ctypes.byref(p))
+    return p
+
+
+def params_from_dict(d: dict, max_obstacles: int = 16, max_path_pts: int = 4096,
+                     threads_per_sample: int = 0, block_threads: int = 0) -> brmppi_params:
+    """brmppi_params from the parameter dict of ``scenarios`` (values are
+    rounded to binary32 by the struct)."""
+    p = brmppi_default_params()
+    for name, _ in brmppi_params._fields_:
+        key = "lambda" if name == "lambda_" else name
+        if key in d:
+            val = d[key]
+            attr = getattr(p, name)
+            if isinstance(attr, ctypes.Array):
+                for i, v in enumerate(val):
+                    attr[i] = float(v)
+            elif isinstance(attr, int):
+                setattr(p, name, int(val))
+            else:
+                setattr(p, name, float(val))
+    p.max_obstacles = int(max_obstacles)
+    p.max_path_pts = int(max_path_pts)
+    p.threads_per_sample = int(threads_per_sample)
+    p.block_threads = int(block_threads)
+    p.abi_version = BRMPPI_ABI_VERSION
+    return p
+
+
+def brmppi_create(params: brmppi_params, device: int = 0) -> ctypes.c_void_p:
+    lib = load()
+    h = _VP()
+    st = lib.brmppi_create(ctypes.byref(params), int(device), ctypes.byref(h))
+    if st != BRMPPI_OK:
+        raise BrmppiError(st, lib.brmppi_last_error(None).decode())
+    return h
+
+
+def brmppi_destroy(ctx) -> None:
+    if ctx:
+        load().brmppi_destroy(ctx)
+
+
+def brmppi_last_error(ctx) -> str:
+    return load().brmppi_last_error(ctx).decode()
+
+
+def _f32(a, n=None):
+    arr = np.ascontiguousarray(a, dtype=np.float32)
+    if n is not None and arr.size != n:
+        raise ValueError(f"expected {n} floats, got {arr.size}")
+    return arr
+
+
+def brmppi_solve(ctx, x0, U_nom, obs, path, ds, seed, counter, H, S=None, want_traj=True,
+                 want_J=False):
+    """Host-buffer solve. Returns (status, U[H,3], traj[H+1,7] or None, J[S] or None)."""
+    lib = load()
+    x0 = np.ascontiguousarray(x0, dtype=np.float64)
+    if x0.size != 7:
+        raise ValueError("x0 must have 7 entries")
+    U_nom = _f32(U_nom, 3 * H)
+    obs = _f32(obs).reshape(-1)
+    n_obs = obs.size // 6
+    path = _f32(path).reshape(-1)
+    n_pts = path.size // 3
+    U = np.zeros((H, 3), dtype=np.float32)
+    traj = np.zeros((H + 1, 7), dtype=np.float32) if want_traj else None
+    J = np.zeros(S, dtype=np.float32) if want_J else None
+    st = lib.brmppi_solve(ctx, x0.ctypes.data_as(_D), U_nom.ctypes.data_as(_F),
+                          obs.ctypes.data_as(_F) if n_obs else None, n_obs,
+                          path.ctypes.data_as(_F), n_pts, float(ds), int(seed) & (2**64 - 1),
+                          int(counter) & (2**64 - 1), U.ctypes.data_as(_F),
+                          traj.ctypes.data_as(_F) if traj is not None else None,
+                          J.ctypes.data_as(_F) if J is not None else None)
+    return st, U, traj, J
+
+
+def _dptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def brmppi_solve_device(ctx, x0, U_nom, obs, path, ds, seed, counter, U_out, traj_out=None,
+                        J_out=None, U_next=None, status=None, stream=None) -> int:
+    """Device-buffer solve on torch CUDA tensors (x0 float64[7], U_nom
+    float32[H,3], obs float32[n,6], path float32[n,3], outputs float32;
+    status int32[1]).  Enqueued on ``stream`` (torch stream or raw handle;
+    default: torch's current stream); does not synchronise."""
+    lib = load()
+    n_obs = 0 if obs is None else obs.numel() // 6
+    n_pts = path.numel() // 3
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream().cuda_stream
+    elif hasattr(stream, "cuda_stream"):
+        stream = stream.cuda_stream
+    return lib.brmppi_solve_device(ctx, _dptr(x0), _dptr(U_nom), _dptr(obs) if n_obs else None,
+                                   n_obs, _dptr(path), n_pts, float(ds), int(seed) & (2**64 - 1),
+                                   int(counter) & (2**64 - 1), _dptr(U_out), _dptr(traj_out),
+                                   _dptr(J_out), _dptr(U_next), _dptr(status),
+                                   ctypes.c_void_p(int(stream)))
+
+
+def brmppi_get_launch(ctx, n_obs: int):
+    tps, thr, blk = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    st = load().brmppi_get_launch(ctx, int(n_obs), ctypes.byref(tps), ctypes.byref(thr),
+                                  ctypes.byref(blk))
+    if st != BRMPPI_OK:
+        raise BrmppiError(st, brmppi_last_error(ctx))
+    return dict(threads_per_sample=tps.value, block_threads=thr.value, blocks=blk.value)
+
+
+def brmppi_transfer_bytes(ctx, n_obs: int, n_pts: int):
+    h2d, d2h = ctypes.c_uint64(), ctypes.c_uint64()
+    st = load().brmppi_transfer_bytes(ctx, int(n_obs), int(n_pts), ctypes.byref(h2d),
+                                      ctypes.byref(d2h))
+    if st != BRMPPI_OK:
+        raise BrmppiError(st, brmppi_last_error(ctx))
+    return int(h2d.value), int(d2h.value)
+
+
+class Solver:
+    """Convenience owner of one context."""
+
+    def __init__(self, params: dict, device: int = 0, max_obstacles: int = 16,
+                 max_path_pts: int = 4096, threads_per_sample: int = 0, block_threads: int = 0):
+        self.params = dict(params)
+        self.S = int(params["S"])
+        self.H = int(params["H"])
+        self._p = params_from_dict(params, max_obstacles, max_path_pts, threads_per_sample,
+                                   block_threads)
+        self.ctx = brmppi_create(self._p, device)
+
+    def close(self):
+        if self.ctx:
+            brmppi_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def solve(self, x0, U_nom, obs, path, ds, seed, counter, want_traj=True, want_J=False,
+              check=True):
+        st, U, traj, J = brmppi_solve(self.ctx, x0, U_nom, obs, path, ds, seed, counter, self.H,
+                                      self.S, want_traj, want_J)
+        if check and st != BRMPPI_OK:
+            raise BrmppiError(st, brmppi_last_error(self.ctx))
+        return dict(status=st, U=U, traj=traj, J=J)
+
+    def solve_device(self, *args, **kw) -> int:
+        return brmppi_solve_device(self.ctx, *args, **kw)
+
+    def launch(self, n_obs: int) -> dict:
+        return brmppi_get_launch(self.ctx, n_obs)
+
+    def transfer_bytes(self, n_obs: int, n_pts: int):
+        return brmppi_transfer_bytes(self.ctx, n_obs, n_pts)
