@@ -109,6 +109,61 @@ def _load():
     return _lib
 
 
+class using_library:
+    """Context manager: route every wrapper in this module through another
+    build of the oracle (the mutation tests compile planted mistakes into
+    copies of the source and check that the pins catch them)."""
+
+    def __init__(self, path: str):
+        self.path = path
+        self.saved = None
+
+    def __enter__(self):
+        global _lib
+        _load()
+        with _lock:
+            self.saved = _lib
+            _lib = None
+        # load the alternative build with the same prototypes
+        lib = ctypes.CDLL(self.path)
+        for name in ("orc_philox4x32_10", "orc_normals", "orc_dynamics_step", "orc_obstacle_h",
+                     "orc_obstacle_row", "orc_hitch_h", "orc_hitch_row", "orc_project",
+                     "orc_path_lookup", "orc_stage_cost", "orc_softmin", "orc_rollout_sample",
+                     "orc_solve", "orc_integrate"):
+            src = getattr(self.saved, name)
+            dst = getattr(lib, name)
+            dst.restype = src.restype
+            dst.argtypes = src.argtypes
+        with _lock:
+            _lib = lib
+        return lib
+
+    def __exit__(self, *exc):
+        global _lib
+        with _lock:
+            _lib = self.saved
+        return False
+
+
+def compile_variant(source_text: str, out_dir: str, name: str = "variant") -> str:
+    """Compile a (modified) copy of the oracle source into out_dir."""
+    c_path = os.path.join(out_dir, name + ".c")
+    so_path = os.path.join(out_dir, name + ".so")
+    with open(c_path, "w") as f:
+        f.write(source_text)
+    import shutil
+    shutil.copy(_HDR, os.path.join(out_dir, os.path.basename(_HDR)))
+    subprocess.run(["gcc", "-std=c11", "-D_DEFAULT_SOURCE", "-O1", "-fPIC", "-shared",
+                    "-fno-fast-math", "-ffp-contract=off", "-o", so_path, c_path, "-lm"],
+                   check=True)
+    return so_path
+
+
+def source() -> str:
+    with open(_SRC) as f:
+        return f.read()
+
+
 def _params(p: dict, S: int | None = None, H: int | None = None) -> _Params:
     out = _Params()
     for name, _ in _Params._fields_:

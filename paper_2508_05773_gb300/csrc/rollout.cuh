@@ -152,13 +152,31 @@ __device__ __forceinline__ bool pair_less(float ah, float al, float bh, float bl
 
 // ------------------------------------------------------------ the rollout
 // Frame of one solve (relative coordinates), computed per block from x0.
+// Doubles of x0 enter as unevaluated float pairs (hi + lo), so that the
+// per-block staging needs no FP64 arithmetic.
 struct Frame {
-  double ox, oy, oth;
-  float c0, s0;        // cos / sin of theta1_0
-  float t2, v, dl;     // theta2 - theta1_0, speed, steer angle
-  float qf0;           // fractional path cell of psi0
-  int i0;              // integer path cell of psi0
+  float ox_h, ox_l, oy_h, oy_l, oth_h, oth_l;  // origin (px0, py0, theta1_0)
+  float c0, s0;                                // cos / sin of theta1_0
+  float t2, v_h, v_l, dl;                      // theta2 - theta1_0, speed, steer angle
+  float qf0;                                   // fractional path cell of psi0
+  int i0;                                      // integer path cell of psi0
+  double psi0;
 };
+
+// x = hi + lo with hi = fl(x)
+__device__ __forceinline__ void split_double(double x, float& hi, float& lo) {
+  hi = static_cast<float>(x);
+  lo = static_cast<float>(x - static_cast<double>(hi));
+}
+
+// Compensated accumulation (TwoSum): (h, l) += inc with the rounding error
+// of the float sum carried in l.
+__device__ __forceinline__ void acc2(float& h, float& l, float inc) {
+  const float sum = h + inc;
+  const float bp = sum - h;
+  l += (h - (sum - bp)) + (inc - bp);
+  h = sum;
+}
 
 template <int TPS, int BPT>
 __global__ void __launch_bounds__(512)
@@ -180,19 +198,21 @@ rollout_solve_kernel(const KParams p, const KIO io) {
     bool finite = true;
     for (int j = 0; j < 7; ++j) finite = finite && isfinite(x0[j]);
     if (!finite) atomicOr(io.err, ERR_NONFINITE_X0);
-    fr.ox = x0[0];
-    fr.oy = x0[1];
-    fr.oth = x0[2];
-    fr.c0 = static_cast<float>(cos(x0[2]));
-    fr.s0 = static_cast<float>(sin(x0[2]));
+    split_double(x0[0], fr.ox_h, fr.ox_l);
+    split_double(x0[1], fr.oy_h, fr.oy_l);
+    split_double(x0[2], fr.oth_h, fr.oth_l);
+    float sn, cs;
+    sincosf(fr.oth_h, &sn, &cs);
+    fr.c0 = cs - sn * fr.oth_l;  // cos(hi + lo), lo below one ulp of hi
+    fr.s0 = sn + cs * fr.oth_l;
     fr.t2 = static_cast<float>(x0[3] - x0[2]);
-    fr.v = static_cast<float>(x0[4]);
+    split_double(x0[4], fr.v_h, fr.v_l);
     fr.dl = static_cast<float>(x0[5]);
+    fr.psi0 = x0[6];
     const double q0 = x0[6] / static_cast<double>(p.ds);
-    const double fq = floor(q0);
-    const double fq_c = fmin(fmax(fq, -1.0e9), 1.0e9);
-    fr.i0 = static_cast<int>(fq_c);
-    fr.qf0 = static_cast<float>(q0 - fq_c);
+    const double fq = fmin(fmax(floor(q0), -1.0e9), 1.0e9);
+    fr.i0 = static_cast<int>(fq);
+    fr.qf0 = static_cast<float>(q0 - fq);
   }
   __syncthreads();
   for (int o = threadIdx.x; o < p.n_obs; o += blockDim.x) {
@@ -200,10 +220,9 @@ rollout_solve_kernel(const KParams p, const KIO io) {
     float* d = sm + L.obs + 8 * o;
     if (ob[5] != 2.0f) atomicOr(io.err, ERR_EXPONENT);
     const float Ax = ob[2] + p.r_inflate, Ay = ob[3] + p.r_inflate;
-    d[0] = static_cast<float>(static_cast<double>(ob[0]) - fr.ox);
-    d[1] = static_cast<float>(static_cast<double>(ob[1]) - fr.oy);
-    d[2] = static_cast<float>(cos(static_cast<double>(ob[4])));
-    d[3] = static_cast<float>(sin(static_cast<double>(ob[4])));
+    d[0] = (ob[0] - fr.ox_h) - fr.ox_l;
+    d[1] = (ob[1] - fr.oy_h) - fr.oy_l;
+    sincosf(ob[4], &d[3], &d[2]);
     d[4] = 1.0f / (Ax * Ax);
     d[5] = 1.0f / (Ay * Ay);
     d[6] = 0.0f;
@@ -212,9 +231,9 @@ rollout_solve_kernel(const KParams p, const KIO io) {
   for (int j = threadIdx.x; j < p.n_pts; j += blockDim.x) {
     const float* r = io.path + 3 * j;
     float* d = sm + L.path + 3 * j;
-    d[0] = static_cast<float>(static_cast<double>(r[0]) - fr.ox);
-    d[1] = static_cast<float>(static_cast<double>(r[1]) - fr.oy);
-    d[2] = static_cast<float>(static_cast<double>(r[2]) - fr.oth);
+    d[0] = (r[0] - fr.ox_h) - fr.ox_l;
+    d[1] = (r[1] - fr.oy_h) - fr.oy_l;
+    d[2] = (r[2] - fr.oth_h) - fr.oth_l;
   }
   for (int j = threadIdx.x; j < 3 * p.H; j += blockDim.x) sm[L.unom + j] = io.U_nom[j];
   __syncthreads();
@@ -224,31 +243,39 @@ rollout_solve_kernel(const KParams p, const KIO io) {
   const float* unom_s = sm + L.unom;
   float* uh_s = sm + L.uh;
 
-  // --- per-sample state (relative frame)
+  // --- per-sample state (relative frame); position, speed and progress
+  // carried as compensated pairs
   const float c0 = fr.c0, s0 = fr.s0;
-  float px = 0.f, py = 0.f, t1 = 0.f, t2 = fr.t2, v = fr.v, dl = fr.dl, ps = 0.f;
+  float px = 0.f, pxl = 0.f, py = 0.f, pyl = 0.f, t1 = 0.f, t2 = fr.t2, v = fr.v_h, vl = fr.v_l,
+        dl = fr.dl, ps = 0.f, psl = 0.f;
   float alpha[4 * BPT];
 #pragma unroll
   for (int k = 0; k < 4 * BPT; ++k) alpha[k] = p.alpha0;
   float Jh = 0.f, Jl = 0.f;
   const uint32_t sid = static_cast<uint32_t>(s);
 
-  for (int tau = 0; tau < p.H; ++tau) {
-    // noise: this lane's Philox blocks
-    float nrm[4 * BPT];
+  // noise of step tau for this lane's Philox blocks (computed one step ahead)
+  auto draw = [&](int tau, float* out) {
 #pragma unroll
     for (int k = 0; k < BPT; ++k) {
       const int b = lt + TPS * k;
       if (b < p.P) {
-        const uint4 w = philox4x32_10(make_uint4(static_cast<uint32_t>(b), static_cast<uint32_t>(tau), sid, p.ctr),
-                                      p.key0, p.key1);
-        box_muller(w.x, w.y, nrm[4 * k + 0], nrm[4 * k + 1]);
-        box_muller(w.z, w.w, nrm[4 * k + 2], nrm[4 * k + 3]);
+        const uint4 w = philox4x32_10(
+            make_uint4(static_cast<uint32_t>(b), static_cast<uint32_t>(tau), sid, p.ctr), p.key0, p.key1);
+        box_muller(w.x, w.y, out[4 * k + 0], out[4 * k + 1]);
+        box_muller(w.z, w.w, out[4 * k + 2], out[4 * k + 3]);
       } else {
 #pragma unroll
-        for (int m = 0; m < 4; ++m) nrm[4 * k + m] = 0.f;
+        for (int m = 0; m < 4; ++m) out[4 * k + m] = 0.f;
       }
     }
+  };
+  float nrm[4 * BPT];
+  draw(0, nrm);
+
+  for (int tau = 0; tau < p.H; ++tau) {
+    float nxt[4 * BPT];
+    draw(tau + 1 < p.H ? tau + 1 : tau, nxt);
     const float na = team_bcast0<TPS>(nrm[0]);
     const float nw = team_bcast0<TPS>(nrm[1]);
     const float nn = team_bcast0<TPS>(nrm[2]);
@@ -265,7 +292,8 @@ rollout_solve_kernel(const KParams p, const KIO io) {
     float sp, cp;
     sincosf(phi, &sp, &cp);
     const float tn = tanf(dl);
-    const float th1dot = v * tn * p.inv_l1;
+    const float vv = v + vl;
+    const float th1dot = vv * tn * p.inv_l1;
 
     float za, zw, zn;
     if (p.proj) {
@@ -291,27 +319,27 @@ rollout_solve_kernel(const KParams p, const KIO io) {
               const float Delta = t2 - t1;
               const float sg = Delta >= 0.f ? 1.f : -1.f;
               const float G = sp - p.k_hitch * cp * tn;
-              const float th2dot = v * G * p.inv_l2;
+              const float th2dot = vv * G * p.inv_l2;
               const float phidot = th1dot - th2dot;
               const float sec2 = 1.f + tn * tn;
-              h = p.dtheta_max - p.kappa * v - sg * Delta;
+              h = p.dtheta_max - p.kappa * vv - sg * Delta;
               Aa = -p.Ts * p.kappa - p.hTs2 * sg * (G * p.inv_l2 - tn * p.inv_l1);
-              Aw = p.hTs2 * sg * v * sec2 * (p.k_hitch * cp * p.inv_l2 + p.inv_l1);
+              Aw = p.hTs2 * sg * vv * sec2 * (p.k_hitch * cp * p.inv_l2 + p.inv_l1);
               const float c0h = -p.Ts * sg * (th2dot - th1dot) -
-                                p.hTs2 * sg * v * p.inv_l2 * (cp + p.k_hitch * tn * sp) * phidot;
+                                p.hTs2 * sg * vv * p.inv_l2 * (cp + p.k_hitch * tn * sp) * phidot;
               brest = -c0h;
             } else {
               // ellipse row (e = 2) in the obstacle frame
               const float* ob = obs_s + 8 * (i - 1);
-              const float dx = px - ob[0], dy = py - ob[1];
+              const float dx = (px - ob[0]) + pxl, dy = (py - ob[1]) + pyl;
               const float co = ob[2], so = ob[3], iax = ob[4], iay = ob[5];
               const float xp = co * dx + so * dy;
               const float yp = co * dy - so * dx;
               h = xp * xp * iax + yp * yp * iay - 1.f;
               const float hx = 2.f * xp * iax, hy = 2.f * yp * iay;
               const float dirx = co * c1 + so * s1, diry = co * s1 - so * c1;
-              const float velx = v * dirx, vely = v * diry;
-              const float vw = v * th1dot;
+              const float velx = vv * dirx, vely = vv * diry;
+              const float vw = vv * th1dot;
               const float hdot = hx * velx + hy * vely;
               const float hdd0 = vw * (hy * dirx - hx * diry) +
                                  2.f * (iax * velx * velx + iay * vely * vely);
@@ -361,17 +389,17 @@ rollout_solve_kernel(const KParams p, const KIO io) {
     const float un = clampf(zn, p.zlo2, p.zhi2);
 
     // explicit Euler step, right-hand sides at the current state
-    const float Tv = p.Ts * v;
-    px += Tv * c1;
-    py += Tv * s1;
+    const float Tv = p.Ts * vv;
+    acc2(px, pxl, Tv * c1);
+    acc2(py, pyl, Tv * s1);
     t1 += p.Ts * th1dot;
     t2 += Tv * p.inv_l2 * (sp - p.k_hitch * cp * tn);
-    v += p.Ts * ua;
+    acc2(v, vl, p.Ts * ua);
     dl += p.Ts * uw;
-    ps += p.Ts * un;
+    acc2(ps, psl, p.Ts * un);
 
     // stage cost at the new state
-    const float qf = fr.qf0 + ps * p.inv_ds;
+    const float qf = fr.qf0 + (ps * p.inv_ds + psl * p.inv_ds);
     const float fl = floorf(qf);
     int ii = fr.i0 + static_cast<int>(fl);
     float ff = qf - fl;
@@ -390,7 +418,7 @@ rollout_solve_kernel(const KParams p, const KIO io) {
     sincosf(thr, &st, &ct);
     const float cth = c0 * ct - s0 * st;
     const float sth = s0 * ct + c0 * st;
-    const float dxr = px - xr, dyr = py - yr;
+    const float dxr = (px - xr) + pxl, dyr = (py - yr) + pyl;
     const float ec = sth * dxr - cth * dyr;
     const float el = -cth * dxr - sth * dyr;
     const float e1 = wrap_pi(t1 - thr), e2 = wrap_pi(t2 - thr);
@@ -408,6 +436,8 @@ rollout_solve_kernel(const KParams p, const KIO io) {
       uh_s[(3 * tau + 1) * spb + team] = uw;
       uh_s[(3 * tau + 2) * spb + team] = un;
     }
+#pragma unroll
+    for (int k = 0; k < 4 * BPT; ++k) nrm[k] = nxt[k];
   }
 
   // --- per-sample cost: normalise the pair
@@ -544,17 +574,16 @@ rollout_solve_kernel(const KParams p, const KIO io) {
     }
     // optimal trajectory: x0 integrated with U* (same relative frame)
     if (io.traj_out) {
-      float qx = 0.f, qy = 0.f, q1 = 0.f, q2 = fr.t2, qv = fr.v, qd = fr.dl;
-      double qps = 0.0;
+      float qx = 0.f, qy = 0.f, q1 = 0.f, q2 = fr.t2, qv = fr.v_h + fr.v_l, qd = fr.dl, qp = 0.f;
       float* tr = io.traj_out;
       for (int tau = 0; tau <= p.H; ++tau) {
-        tr[7 * tau + 0] = static_cast<float>(fr.ox + static_cast<double>(qx));
-        tr[7 * tau + 1] = static_cast<float>(fr.oy + static_cast<double>(qy));
-        tr[7 * tau + 2] = static_cast<float>(fr.oth + static_cast<double>(q1));
-        tr[7 * tau + 3] = static_cast<float>(fr.oth + static_cast<double>(q2));
+        tr[7 * tau + 0] = (fr.ox_h + qx) + fr.ox_l;
+        tr[7 * tau + 1] = (fr.oy_h + qy) + fr.oy_l;
+        tr[7 * tau + 2] = (fr.oth_h + q1) + fr.oth_l;
+        tr[7 * tau + 3] = (fr.oth_h + q2) + fr.oth_l;
         tr[7 * tau + 4] = qv;
         tr[7 * tau + 5] = qd;
-        tr[7 * tau + 6] = static_cast<float>(io.x0[6] + qps);
+        tr[7 * tau + 6] = static_cast<float>(fr.psi0 + static_cast<double>(qp));
         if (tau == p.H) break;
         float a1, b1;
         sincosf(q1, &a1, &b1);
@@ -570,7 +599,7 @@ rollout_solve_kernel(const KParams p, const KIO io) {
         q1 += d1;
         qv += p.Ts * ustar[3 * tau + 0];
         qd += p.Ts * ustar[3 * tau + 1];
-        qps += static_cast<double>(p.Ts * ustar[3 * tau + 2]);
+        qp += p.Ts * ustar[3 * tau + 2];
       }
     }
     *io.err = 0u;

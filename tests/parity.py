@@ -1,15 +1,34 @@
 """Tolerances of the GPU-vs-oracle comparison (FP32 CUDA path against the
 FP64 oracle), 1e-4 relative as the solve's accuracy target:
 
-* states and trajectories: |g - o| / max(|o|, 1)            <= 1e-4
-* U*: |g - o| / max(|o|, 0.01 (z_hi - z_lo))                <= 1e-4
-* per-sample costs J (diagnostic): |g - o| / |o|            <= 1e-5
+* states / optimal trajectory: |g - o| <= 1e-4 max(|o|, 1)
+* per-sample costs J:          |g - o| <= EPS_J |o| with EPS_J = 2^-18, and
+  the median relative error <= 2^-23 (about one binary32 ulp: the rollout
+  carries position, speed, progress and the cost sum as compensated pairs).
+  The worst case is a rollout grazing an ellipse: at h ~ 0 the barrier is
+  a difference of O(1) terms whose binary32 cancellation error (~1e-7) the
+  projection amplifies (D = h^2 / m_alpha becomes small), a conditioning of
+  the method itself.
+* U*: |g - o| <= 1e-4 max(|o|, 0.01 (z_hi - z_lo)) + kappa, where kappa is
+  the softmin's amplification of cost errors within EPS_J.
+
+Derivation of kappa.  U* = sum_s gb_s u_s with gb_s proportional to
+exp(-J_s / lambda).  Costs perturbed by delta_s move the update by
+  dU* = -(1/lambda) sum_s gb_s (delta_s - dbar) (u_s - U*),  dbar = sum gb delta,
+so |delta_s| <= EPS_J |J_s| bounds it by
+  kappa = (EPS_J / lambda) sum_s gb_s (|J_s| + Jbar) |u_s - U*|,
+  Jbar = sum_s gb_s |J_s|.
+kappa is computed from the oracle's own costs and applied inputs.  With
+J ~ 10^2..10^3 and lambda = 1 the weights of near-tied samples are as
+sensitive as this, whatever the implementation: a binary32 cost is only
+known to 2^-24 of its size.
 """
 import numpy as np
 
 TOL_STATE = 1e-4
 TOL_U = 1e-4
-TOL_J = 1e-5
+EPS_J = 2.0 ** -18
+EPS_J_MEDIAN = 2.0 ** -23
 
 
 def err_state(g, o):
@@ -18,24 +37,59 @@ def err_state(g, o):
     return float(np.max(np.abs(g - o) / np.maximum(np.abs(o), 1.0))) if o.size else 0.0
 
 
-def err_u(g, o, p):
-    span = np.asarray(p["z_hi"], np.float64) - np.asarray(p["z_lo"], np.float64)
-    g = np.asarray(g, np.float64).reshape(-1, 3)
-    o = np.asarray(o, np.float64).reshape(-1, 3)
-    return float(np.max(np.abs(g - o) / np.maximum(np.abs(o), 0.01 * span)))
-
-
 def err_j(g, o):
     g = np.asarray(g, np.float64)
     o = np.asarray(o, np.float64)
     return float(np.max(np.abs(g - o) / np.abs(o)))
 
 
+def err_j_median(g, o):
+    g = np.asarray(g, np.float64)
+    o = np.asarray(o, np.float64)
+    return float(np.median(np.abs(g - o) / np.abs(o)))
+
+
+def softmin_kappa(J, u_hist, U, lam, eps=EPS_J):
+    """Per-element bound on |dU*| for cost errors |delta_s| <= eps |J_s|."""
+    J = np.asarray(J, np.float64)
+    fin = np.isfinite(J)
+    g = np.zeros_like(J)
+    Jm = J[fin].min()
+    g[fin] = np.exp(-(J[fin] - Jm) / lam)
+    g /= g.sum()
+    aJ = np.where(fin, np.abs(J), 0.0)
+    Jbar = float(np.sum(g * aJ))
+    w = g * (aJ + Jbar)                                     # (S,)
+    dev = np.abs(np.asarray(u_hist, np.float64) - np.asarray(U, np.float64)[None])  # (S,H,3)
+    return (eps / lam) * np.einsum("s,shj->hj", w, dev)
+
+
+def u_scale(o, p):
+    span = np.asarray(p["z_hi"], np.float64) - np.asarray(p["z_lo"], np.float64)
+    return np.maximum(np.abs(np.asarray(o, np.float64).reshape(-1, 3)), 0.01 * span)
+
+
+def err_u(g, o, p):
+    g = np.asarray(g, np.float64).reshape(-1, 3)
+    o = np.asarray(o, np.float64).reshape(-1, 3)
+    return float(np.max(np.abs(g - o) / u_scale(o, p)))
+
+
 def assert_solve_matches(out, ref, p, label="", check_J=True):
-    eu = err_u(out["U"], ref["U"], p)
+    """out: GPU dict(U, traj, J); ref: oracle dict(U, traj, J, u_hist)."""
+    g = np.asarray(out["U"], np.float64).reshape(-1, 3)
+    o = np.asarray(ref["U"], np.float64).reshape(-1, 3)
+    kappa = softmin_kappa(ref["J"], ref["u_hist"], o, float(p["lambda"]))
+    tol = TOL_U * u_scale(o, p) + kappa
+    excess = float(np.max(np.abs(g - o) / tol))
+    eu = err_u(g, o, p)
     ex = err_state(out["traj"], ref["traj"]) if out.get("traj") is not None else 0.0
     ej = err_j(out["J"], ref["J"]) if (check_J and out.get("J") is not None) else 0.0
-    assert eu <= TOL_U, f"{label} U* rel err {eu:.3e}"
+    ejm = err_j_median(out["J"], ref["J"]) if (check_J and out.get("J") is not None) else 0.0
+    assert ej <= EPS_J, f"{label} J rel err {ej:.3e} > {EPS_J:.3e}"
+    assert ejm <= EPS_J_MEDIAN, f"{label} median J rel err {ejm:.3e} > {EPS_J_MEDIAN:.3e}"
+    assert excess <= 1.0, (f"{label} U* err {eu:.3e} (rel), {excess:.3f} of the tolerance "
+                           f"(kappa max {kappa.max():.2e})")
     assert ex <= TOL_STATE, f"{label} trajectory rel err {ex:.3e}"
-    assert ej <= TOL_J, f"{label} J rel err {ej:.3e}"
-    return eu, ex, ej
+    return dict(err_u=eu, err_traj=ex, err_J=ej, err_J_median=ejm, tol_frac=excess,
+                kappa_max=float(kappa.max()))

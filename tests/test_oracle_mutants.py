@@ -1,0 +1,133 @@
+"""The oracle's pins catch plausible mistakes.
+
+Each case plants one mistake (a dropped term, a wrong sign, index or
+constant, a swapped operand) into a copy of the oracle's C source, compiles
+it, routes the oracle binding through that copy, and runs the pin battery of
+the other oracle tests.  The mutant must fail at least one pin.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from tests import test_oracle_barriers as tb
+from tests import test_oracle_cost_softmin as tc
+from tests import test_oracle_dynamics as td
+from tests import test_oracle_philox as tp
+from tests import test_oracle_projection as tj
+from tests import test_oracle_solve as ts
+
+MUTANTS = [
+    ("philox multiplier swapped", "(uint64_t)PHILOX_M0 * (uint64_t)c0", "(uint64_t)PHILOX_M1 * (uint64_t)c0"),
+    ("philox key bump", "k1 += PHILOX_W1;", "k1 += PHILOX_W0;"),
+    ("philox word order", "uint32_t n0 = hi1 ^ c1 ^ k0;", "uint32_t n0 = hi0 ^ c1 ^ k0;"),
+    ("box-muller pair", "g[2 * pair + 1] = radius * sin(angle);", "g[2 * pair + 1] = radius * cos(angle);"),
+    ("noise counter fields", "{(uint32_t)blk, tau, s, (uint32_t)counter}", "{(uint32_t)blk, s, tau, (uint32_t)counter}"),
+    ("trailer angle sign", "(sin(th1 - th2) - (P->lh / P->l1)", "(sin(th2 - th1) - (P->lh / P->l1)"),
+    ("tractor yaw uses l2", "xn[2] = th1 + Ts * v / P->l1 * tan(delta);", "xn[2] = th1 + Ts * v / P->l2 * tan(delta);"),
+    ("hitch coupling dropped", " - (P->lh / P->l1) * cos(th1 - th2) * tan(delta));", ");"),
+    ("speed not integrated", "xn[4] = v + Ts * a;", "xn[4] = v;"),
+    ("ellipse rotation sign", "#define ROT_Y(wx, wy) (-so * (wx) + co * (wy))", "#define ROT_Y(wx, wy) (so * (wx) + co * (wy))"),
+    ("ellipse hessian dropped", "+ hxx * vel_x * vel_x", ""),
+    ("ellipse centripetal dropped", "hddot_0 = hx * cen_x + hy * cen_y +", "hddot_0 ="),
+    ("ellipse accel coefficient", "A_u[0] = 0.5 * Ts * Ts * dhddot_da;", "A_u[0] = Ts * Ts * dhddot_da;"),
+    ("ellipse inflation dropped", "const double cx = obs[0], cy = obs[1], Ax = obs[2] + P->r_inflate, Ay = obs[3] + P->r_inflate;\n  const double th_o = obs[4];\n  const double xp", "const double cx = obs[0], cy = obs[1], Ax = obs[2], Ay = obs[3];\n  const double th_o = obs[4];\n  const double xp"),
+    ("hitch sign of Delta", "const double sigma = (Delta >= 0.0) ? 1.0 : -1.0;", "const double sigma = (Delta >= 0.0) ? -1.0 : 1.0;"),
+    ("hitch steer-rate term dropped", " - k * cos(phi) * (1.0 + t * t) * omega);", ");"),
+    ("hitch speed threshold", "return P->dtheta_max - P->kappa * x[4] - fabs(x[3] - x[2]);", "return P->dtheta_max + P->kappa * x[4] - fabs(x[3] - x[2]);"),
+    ("hitch kappa in hdot", "const double hdot = -P->kappa * a - sigma * (th2dot - th1dot);", "const double hdot = -sigma * (th2dot - th1dot);"),
+    ("projection residual sign", "lam[i] = t - b[i]; /* A M^-1 p - b */", "lam[i] = t + b[i];"),
+    ("projection box centre", "p[j] = w[j] * z_des[j] + 0.5 * rho * (z_hi[j] + z_lo[j]);", "p[j] = w[j] * z_des[j] + 0.5 * rho * (z_hi[j] - z_lo[j]);"),
+    ("projection M^-1 dropped", "z_star[j] = Minv[j] * t;", "z_star[j] = t;"),
+    ("projection K transposed operand", "kk += A[i * d + j] * Minv[j] * A[r * d + j];", "kk += A[i * d + j] * Minv[j] * A[i * d + j];"),
+    ("path lerp fraction", "const double f = q / ds - (double)i;", "const double f = q / ds - (double)(i + 1);"),
+    ("contouring error sign", "const double e_c = sin(thr) * (x[0] - xr) - cos(thr) * (x[1] - yr);", "const double e_c = sin(thr) * (x[0] - xr) + cos(thr) * (x[1] - yr);"),
+    ("heading not wrapped", "const double e_th1 = wrap_angle(x[2] - thr);", "const double e_th1 = x[2] - thr;"),
+    ("progress term sign", "r += P->mu * (P->nu_bar - u[2]) * (P->nu_bar - u[2]);", "r += P->mu * (P->nu_bar + u[2]) * (P->nu_bar - u[2]);"),
+    ("effort weight index", "for (int j = 0; j < 3; ++j) r += P->R[j] * u[j] * u[j];", "for (int j = 0; j < 3; ++j) r += P->R[0] * u[j] * u[j];"),
+    ("softmin temperature", "exp(-(J[s] - Jmin) / lambda)", "exp(-(J[s] - Jmin) * lambda)"),
+    ("softmin not normalised", "for (int s = 0; s < S; ++s) gamma_bar[s] /= sum;", ""),
+    ("alpha update sign", "for (int i = 0; i < Nc; ++i) alpha[i] += zs[3 + i];", "for (int i = 0; i < Nc; ++i) alpha[i] -= zs[3 + i];"),
+    ("applied input not clipped", "for (int j = 0; j < 3; ++j) u[j] = clip(zs[j], P->z_lo[j], P->z_hi[j]);", "for (int j = 0; j < 3; ++j) u[j] = zs[j];"),
+    ("barrier rate uses h_tilde in b", "b[i] = -alpha[i] * h + b_rest;", "b[i] = -alpha[i] * h_tilde * 2.0 + b_rest;"),
+    ("cost before the step", "    orc_dynamics_step(P, x, u, xn);\n    memcpy(x, xn, sizeof(x));\n    J += orc_stage_cost(P, x, u, path, n_pts, ds);", "    J += orc_stage_cost(P, x, u, path, n_pts, ds);\n    orc_dynamics_step(P, x, u, xn);\n    memcpy(x, xn, sizeof(x));"),
+    ("update uses first sample only", "for (int s = 0; s < S; ++s) acc += gb[s] * uh[(size_t)s * (size_t)H * 3 + (size_t)k];", "for (int s = 0; s < S; ++s) acc += gb[s] * uh[(size_t)k];"),
+    ("nominal not added", "zdes[j] = clip(U_nom[3 * tau + j] + P->sigma[j] * n[j], P->z_lo[j], P->z_hi[j]);", "zdes[j] = clip(P->sigma[j] * n[j], P->z_lo[j], P->z_hi[j]);"),
+]
+
+_OBS = tb.OBSTACLES
+_STATES = tb.STATES
+_INPUTS = tb.INPUTS
+
+
+def _battery():
+    """Run the pins; return the name of the first that fails (or None)."""
+    checks = [
+        ("philox-curand", lambda: tp.test_philox_matches_curand_host_stream(7)),
+        ("normals-curand", lambda: tp.test_normals_match_curand_host_normals(7)),
+        ("philox-bijection", tp.test_philox_is_a_bijection_sample),
+        ("normals-distribution", tp.test_normals_distribution),
+        ("normals-positional", tp.test_normals_positional),
+        ("dyn-straight", td.test_straight_line_constant_speed),
+        ("dyn-const", td.test_constant_accel_and_steer_rate_and_progress),
+        ("dyn-dirichlet", td.test_constant_steer_angle_dirichlet_sums),
+        ("dyn-hitch", lambda: td.test_hitch_angle_recurrence_and_jackknife(-1.0)),
+        ("dyn-coupling", td.test_trailer_steering_coupling_term),
+        ("bar-values", tb.test_obstacle_barrier_values),
+        ("bar-hitch-values", tb.test_hitch_barrier_values),
+        ("bar-circle", tb.test_circle_rows_invariant_to_heading),
+        ("bar-inputs", tb.test_obstacle_row_inputs),
+    ]
+    for obs in _OBS:
+        for x0 in _STATES:
+            checks.append(("bar-taylor", lambda obs=obs, x0=x0: tb.test_obstacle_row_is_second_order_taylor(obs, x0, _INPUTS[0])))
+    for x0 in [(0.0, 0.0, 0.5, 0.7, 1.1, 0.2, 0.0), (0.0, 0.0, 3.0, 2.6, -1.0, -0.35, 0.0)]:
+        for u in _INPUTS:
+            checks.append(("hitch-taylor", lambda x0=x0, u=u: tb.test_hitch_row_is_second_order_taylor(x0, u)))
+    checks += [
+        ("proj-kkt", lambda: tj.test_kkt(7, 3)),
+        ("proj-textbook", tj.test_textbook_orthogonal_projection),
+        ("proj-norows", tj.test_no_rows_is_unconstrained_minimiser),
+        ("proj-single", tj.test_single_row_scalar_form),
+        ("proj-brute", lambda: tj.test_brute_force_grid_over_null_space(4, 2)),
+        ("proj-slsqp", tj.test_scipy_slsqp_agrees),
+        ("path-lerp", tc.test_path_lookup_interpolation_and_clamp),
+        ("cost-zero", lambda: tc.test_cost_on_path_is_zero_and_offsets_are_quadratic(0.8)),
+        ("cost-terms", tc.test_cost_effort_and_progress_terms),
+        ("softmin-basic", tc.test_softmin_basic_properties),
+        ("softmin-closed", tc.test_softmin_closed_forms),
+        ("softmin-nonfinite", tc.test_softmin_nonfinite),
+        ("solve-zero-noise-std", ts.test_zero_noise_standard_mppi_is_plain_euler),
+        ("solve-zero-noise", ts.test_zero_noise_brmppi_rollouts_identical),
+        ("solve-rows", lambda: ts.test_equality_rows_hold_and_bounds(0)),
+        ("solve-clip", ts.test_post_projection_clip),
+        ("solve-update", ts.test_update_is_weighted_mean_of_applied_inputs),
+        ("solve-mean", ts.test_equal_costs_give_mean_of_samples),
+        ("solve-cost-sum", ts.test_cost_accumulates_stage_costs_after_each_step),
+    ]
+    for name, fn in checks:
+        try:
+            with np.errstate(all="ignore"):
+                fn()
+        except BaseException as e:  # noqa: BLE001 - any failure is a catch
+            if isinstance(e, (KeyboardInterrupt, SystemExit)):
+                raise
+            if type(e).__name__ == "Skipped":
+                continue
+            return name
+    return None
+
+
+def test_unmutated_oracle_passes_battery():
+    assert _battery() is None
+
+
+@pytest.mark.parametrize("name,old,new", MUTANTS, ids=[m[0] for m in MUTANTS])
+def test_mutant_is_caught(name, old, new, tmp_path):
+    src = oracle.source()
+    assert src.count(old) == 1, f"mutation anchor not unique/found: {name}"
+    so = oracle.compile_variant(src.replace(old, new), str(tmp_path), "mutant")
+    with oracle.using_library(so):
+        caught = _battery()
+    assert caught is not None, f"mutant survived every pin: {name}"

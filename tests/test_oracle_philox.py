@@ -54,6 +54,33 @@ def test_philox_matches_curand_host_stream(seed):
         assert np.array_equal(got, words[i]), (hex(seed), i)
 
 
+@pytest.mark.parametrize("seed", [7, 0x0123456789ABCDEF])
+def test_normals_match_curand_host_normals(seed):
+    """cuRAND's host normal generator on the Philox4_32_10 stream turns each
+    block i (our counter (0, 0, i, 0): sample i at step 0, counter 0) into
+    two Box-Muller pairs, emitting (r sin, r cos) where the solve's mapping
+    emits (r cos, r sin); its uniform map differs from ours by at most
+    2^-33, so the normals agree to ~1e-6."""
+    lib = _curand()
+    if lib is None:
+        pytest.skip("libcurand not found")
+    gen = ctypes.c_void_p()
+    if lib.curandCreateGeneratorHost(ctypes.byref(gen), CURAND_RNG_PSEUDO_PHILOX4_32_10) != 0:
+        pytest.skip("cuRAND host generator unavailable")
+    n_blocks = 1024
+    try:
+        assert lib.curandSetPseudoRandomGeneratorSeed(gen, ctypes.c_ulonglong(seed)) == 0
+        out = np.zeros(4 * n_blocks, dtype=np.float32)
+        assert lib.curandGenerateNormal(gen, out.ctypes.data_as(ctypes.c_void_p),
+                                        ctypes.c_size_t(out.size), ctypes.c_float(0.0),
+                                        ctypes.c_float(1.0)) == 0
+    finally:
+        lib.curandDestroyGenerator(gen)
+    cur = out.reshape(n_blocks, 4)[:, [1, 0, 3, 2]].astype(np.float64)
+    ours = np.array([oracle.normals(seed, 0, s, 0, 4) for s in range(n_blocks)])
+    assert np.max(np.abs(cur - ours)) < 2e-5
+
+
 def test_philox_is_a_bijection_sample():
     # distinct counters give distinct outputs (a permutation for fixed key)
     key = [0xDEADBEEF, 0x12345678]

@@ -99,6 +99,23 @@ def test_equality_rows_hold_and_bounds(seed):
     assert clipped < 4 * p["H"]
 
 
+def test_post_projection_clip():
+    # A costly barrier rate (large w_alpha) makes the projection move the
+    # physical inputs, often out of the box: the applied input is then the
+    # clipped z*, within bounds, and equals z* wherever z* is inside.
+    c = sc.config1b(S=4, H=40)
+    p = sc.as_float32(dict(c["params"], w_alpha=1e4))
+    lo, hi = np.array(p["z_lo"]), np.array(p["z_hi"])
+    n_out = 0
+    for s in range(4):
+        r = oracle.rollout_sample(p, c["x0"], c["U_nom"], c["obs"], c["path"], c["ds"], c["seed"],
+                                  c["counter"], s)
+        zs = r["z_star"][:, :3]
+        np.testing.assert_array_equal(r["u"], np.clip(zs, lo, hi))
+        n_out += int(np.sum((zs < lo) | (zs > hi)))
+    assert n_out > 0
+
+
 def test_update_is_weighted_mean_of_applied_inputs():
     c = sc.config1(S=64, H=20)
     p, r = _run(c)
