@@ -184,6 +184,87 @@ def _config_block(c, extra=None):
     return cfg
 
 
+def measure_batched(dev, reps: int = 10):
+    """Uneven batch (256 instances: S in {1024..8192}, H in [30, 80], 0..16
+    obstacles, random paths, seed 1): one persistent launch per batch
+    replayed from a CUDA graph, against one plain launch per instance
+    (brmppi_solve_device, back to back on one stream)."""
+    import torch
+    import paper_2508_05773_gb300 as pkg
+    from paper_2508_05773_gb300 import scenarios as sc
+
+    cases = sc.config3()
+    t = lambda a, dt=torch.float32: torch.tensor(np.asarray(a), dtype=dt, device=dev)
+    insts = []
+    for c in cases:
+        H, S = int(c["params"]["H"]), int(c["params"]["S"])
+        insts.append(dict(x0=t(c["x0"], torch.float64), U_nom=t(c["U_nom"]),
+                          obs=t(c["obs"]) if c["obs"].shape[0] else None, path=t(c["path"]),
+                          ds=c["ds"], S=S, seed=c["seed"], counter=0,
+                          U_out=torch.empty((H, 3), device=dev),
+                          traj_out=torch.empty((H + 1, 7), device=dev),
+                          U_next=torch.empty((H, 3), device=dev),
+                          status=torch.zeros(1, dtype=torch.int32, device=dev)))
+    work = sum(int(c["params"]["S"]) * int(c["params"]["H"]) for c in cases)
+    Smax = max(int(c["params"]["S"]) for c in cases)
+    Hmax = max(int(c["params"]["H"]) for c in cases)
+    npts = max(c["path"].shape[0] for c in cases)
+    base = dict(cases[0]["params"], S=Smax, H=Hmax)
+    solver = pkg.Solver(base, max_obstacles=16, max_path_pts=npts, max_batch=len(cases))
+    stream = torch.cuda.current_stream(dev)
+    solver.autotune_batch(insts, reps=2, stream=stream)
+    graph = solver.capture_batch(insts)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    times = []
+    for r in range(reps + 2):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        if pkg.brmppi_graph_launch(graph, stream) != 0:
+            raise RuntimeError(pkg.brmppi_last_error(solver.ctx))
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if r >= 2:
+            times.append(e0.elapsed_time(e1))
+    assert all(int(d["status"].item()) == 0 for d in insts)
+    pkg.brmppi_graph_destroy(graph)
+    solver.close()
+    batched_ms = float(np.median(times))
+
+    # plain: one launch per instance, contexts per (S, H)
+    ctxs = {}
+    for c in cases:
+        key = (int(c["params"]["S"]), int(c["params"]["H"]))
+        if key not in ctxs:
+            ctxs[key] = pkg.Solver(c["params"], max_obstacles=16, max_path_pts=npts)
+    plain_times = []
+    for r in range(max(3, reps // 2) + 1):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for c, d in zip(cases, insts):
+            s = ctxs[(int(c["params"]["S"]), int(c["params"]["H"]))]
+            rc = s.solve_device(d["x0"], d["U_nom"], d["obs"], d["path"], d["ds"], d["seed"], 0,
+                                d["U_out"], d["traj_out"], None, d["U_next"], d["status"], stream)
+            if rc != 0:
+                raise RuntimeError(pkg.brmppi_last_error(s.ctx))
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if r >= 1:
+            plain_times.append(e0.elapsed_time(e1))
+    for s in ctxs.values():
+        s.close()
+    plain_ms = float(np.median(plain_times))
+    return {"workload": "256 uneven solves: S in {1024,2048,4096,8192}, H in [30,80], "
+                        "0-16 ellipses, random straight+arc paths (seed 1)",
+            "rollout_steps": work, "value": work / (batched_ms * 1e-3), "unit": UNIT,
+            "ms_per_batch": batched_ms, "plain_value": work / (plain_ms * 1e-3),
+            "plain_ms_per_batch": plain_ms, "speedup_vs_plain": plain_ms / batched_ms,
+            "launches_per_batch": 1, "plain_launches_per_batch": len(cases),
+            "how": "CUDA-graph replay of one persistent launch vs brmppi_solve_device per "
+                   "instance on one stream; L2 flushed between batches; median"}
+
+
 def run_cpu_baseline(budget_s: float = 12.0):
     """The FP64 oracle on host cores (single thread) on full config-2 solves,
     as many ticks as fit the budget (at least one)."""
@@ -267,6 +348,8 @@ def run_ours(args, world, rank, local):
     status = torch.zeros(1, dtype=torch.int32, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
+
+    solver.autotune(x0, Ubuf[0], obs, path, c["ds"], reps=3, stream=stream)
 
     def solve(tick: int):
         rc = solver.solve_device(x0, Ubuf[tick % 2], obs, path, c["ds"], c["seed"], tick, U_out,
@@ -365,6 +448,8 @@ def run_ours(args, world, rank, local):
             "gpu_launches": args.steps,
             "clocks": clk,
         }
+        if world == 1 and not args.no_batched:
+            line["batched"] = measure_batched(dev)
         if not args.no_cpu_baseline and world == 1:
             line["cpu_baseline"] = run_cpu_baseline()
         print(json.dumps(line), flush=True)
@@ -381,6 +466,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -52,7 +52,7 @@
 extern "C" {
 #endif
 
-#define BRMPPI_ABI_VERSION 1u
+#define BRMPPI_ABI_VERSION 2u
 
 typedef enum {
   BRMPPI_OK = 0,
@@ -75,11 +75,14 @@ typedef enum {
 typedef struct brmppi_params {
   uint32_t abi_version;          /* must be BRMPPI_ABI_VERSION */
   int32_t S, H;                  /* samples, horizon steps (S >= 1, 1 <= H <= 1024) */
-  int32_t max_obstacles;         /* capacity: obstacles per solve (<= 256) */
+  int32_t max_obstacles;         /* capacity: obstacles per solve (<= 124) */
   int32_t max_path_pts;          /* capacity: path rows per solve (>= 2) */
   int32_t flags;                 /* BRMPPI_FLAG_* */
-  int32_t threads_per_sample;    /* 0 = autotune, else 1, 2, 4, 8, 16 or 32 */
-  int32_t block_threads;         /* 0 = autotune, else 64..512, multiple of 32 */
+  int32_t threads_per_sample;    /* plain solves: 0 = tuned/heuristic, else 1, 2, 4, 8, 16, 32 */
+  int32_t block_threads;         /* plain solves: 0 = tuned/heuristic, else 64..512, multiple of 32 */
+  int32_t max_batch;             /* capacity: instances per batch (0 = no batches) */
+  int32_t batch_threads_per_sample; /* batches: 0 = tuned/heuristic, else as above */
+  int32_t batch_block_threads;   /* batches: 0 = tuned/heuristic, else as above */
   float Ts, lambda;              /* sample time [s]; softmin temperature */
   float l1, lh, l2;              /* wheelbase, hitch offset, trailer length [m] */
   float dtheta_max, kappa;       /* hitch limit dtheta_max - kappa*v */
@@ -94,6 +97,22 @@ typedef struct brmppi_params {
 } brmppi_params;
 
 typedef struct brmppi_ctx brmppi_ctx; /* opaque: device buffers, stream */
+
+/* One solve of a batch; every pointer is DEVICE memory with the layouts
+   above.  S <= params.S, H <= params.H, n_obs <= max_obstacles,
+   2 <= n_pts <= max_path_pts.  Outputs as for brmppi_solve_device. */
+typedef struct brmppi_instance {
+  const double *x0;
+  const float *U_nom, *obs, *path;
+  int32_t n_obs, n_pts;
+  float ds;
+  int32_t S, H;
+  uint64_t seed, counter;
+  float *U_out, *traj_out, *J_out, *U_next; /* U_out required; others may be NULL */
+  int32_t *status;                          /* may be NULL */
+} brmppi_instance;
+
+typedef struct brmppi_graph brmppi_graph; /* a captured batch launch */
 
 /* Fill *p with the library defaults (abi_version set). */
 void brmppi_default_params(brmppi_params *p);
@@ -130,6 +149,39 @@ brmppi_status brmppi_solve_device(brmppi_ctx *ctx, const double *x0_dev, const f
                                   int32_t n_pts, float ds, uint64_t seed, uint64_t counter,
                                   float *U_out_dev, float *traj_out_dev, float *J_out_dev,
                                   float *U_next_dev, int32_t *status_dev, void *stream);
+
+/* A batch of independent solves (uneven S, H, obstacle count, path) in ONE
+   launch of a persistent kernel: work items (instance, sample tile) are
+   taken longest-first from an atomic counter; each instance's partials are
+   merged in tile order by the CTA that finishes its last tile, so a solve
+   gives the same result alone (as a batch of one) or in any mix.  Uploads
+   the instance table and work list (host -> device, pinned) and enqueues
+   the kernel on `stream`; allocates nothing, does not synchronise (the next
+   call on this context waits for the previous upload to be consumed). */
+brmppi_status brmppi_solve_batch(brmppi_ctx *ctx, const brmppi_instance *inst, int32_t n,
+                                 void *stream);
+
+/* Capture the upload and the persistent launch of a batch into a CUDA graph
+   (the instance table is snapshotted; the instances' device buffers are
+   read at every replay, so updating their contents in place between replays
+   is the intended use). */
+brmppi_status brmppi_batch_capture(brmppi_ctx *ctx, const brmppi_instance *inst, int32_t n,
+                                   brmppi_graph **out);
+brmppi_status brmppi_graph_launch(brmppi_graph *g, void *stream);
+void brmppi_graph_destroy(brmppi_graph *g);
+
+/* Autotuner: time every supported launch shape (threads per sample x Philox
+   blocks per lane x block size) on the given device inputs, `reps` launches
+   each, and keep the fastest for later plain solves with this obstacle
+   count (used when params.threads_per_sample == 0). */
+brmppi_status brmppi_autotune(brmppi_ctx *ctx, const double *x0_dev, const float *U_nom_dev,
+                              const float *obs_dev, int32_t n_obs, const float *path_dev,
+                              int32_t n_pts, float ds, int32_t reps, void *stream);
+
+/* Autotuner for batches: as above on a batch, keeping the fastest shape for
+   later batches (used when params.batch_threads_per_sample == 0). */
+brmppi_status brmppi_autotune_batch(brmppi_ctx *ctx, const brmppi_instance *inst, int32_t n,
+                                    int32_t reps, void *stream);
 
 /* Launch configuration the context will use for a solve with n_obs
    obstacles (after autotuning if requested). */

@@ -12,7 +12,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libbrmppi.so")
 
-BRMPPI_ABI_VERSION = 1
+BRMPPI_ABI_VERSION = 2
 BRMPPI_OK = 0
 BRMPPI_EINVAL = -1
 BRMPPI_ENOMEM = -2
@@ -29,7 +29,9 @@ STATUS_NAMES = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "EAGAIN", -4: "ETIMEDOU
 #: every exported symbol the header declares
 EXPORTS = (
     "brmppi_default_params", "brmppi_create", "brmppi_destroy", "brmppi_last_error",
-    "brmppi_solve", "brmppi_solve_device", "brmppi_get_launch", "brmppi_transfer_bytes",
+    "brmppi_solve", "brmppi_solve_device", "brmppi_solve_batch", "brmppi_batch_capture",
+    "brmppi_graph_launch", "brmppi_graph_destroy", "brmppi_autotune", "brmppi_autotune_batch",
+    "brmppi_get_launch", "brmppi_transfer_bytes",
 )
 
 
@@ -39,7 +41,8 @@ class brmppi_params(ctypes.Structure):
         ("S", ctypes.c_int32), ("H", ctypes.c_int32),
         ("max_obstacles", ctypes.c_int32), ("max_path_pts", ctypes.c_int32),
         ("flags", ctypes.c_int32), ("threads_per_sample", ctypes.c_int32),
-        ("block_threads", ctypes.c_int32),
+        ("block_threads", ctypes.c_int32), ("max_batch", ctypes.c_int32),
+        ("batch_threads_per_sample", ctypes.c_int32), ("batch_block_threads", ctypes.c_int32),
         ("Ts", ctypes.c_float), ("lambda_", ctypes.c_float),
         ("l1", ctypes.c_float), ("lh", ctypes.c_float), ("l2", ctypes.c_float),
         ("dtheta_max", ctypes.c_float), ("kappa", ctypes.c_float), ("r_inflate", ctypes.c_float),
@@ -50,6 +53,17 @@ class brmppi_params(ctypes.Structure):
         ("ua_lo", ctypes.c_float), ("ua_hi", ctypes.c_float),
         ("w_u", ctypes.c_float * 3), ("w_alpha", ctypes.c_float),
         ("rho", ctypes.c_float), ("h_floor", ctypes.c_float),
+    ]
+
+
+class brmppi_instance(ctypes.Structure):
+    _fields_ = [
+        ("x0", ctypes.c_void_p), ("U_nom", ctypes.c_void_p), ("obs", ctypes.c_void_p),
+        ("path", ctypes.c_void_p), ("n_obs", ctypes.c_int32), ("n_pts", ctypes.c_int32),
+        ("ds", ctypes.c_float), ("S", ctypes.c_int32), ("H", ctypes.c_int32),
+        ("seed", ctypes.c_uint64), ("counter", ctypes.c_uint64),
+        ("U_out", ctypes.c_void_p), ("traj_out", ctypes.c_void_p), ("J_out", ctypes.c_void_p),
+        ("U_next", ctypes.c_void_p), ("status", ctypes.c_void_p),
     ]
 
 
@@ -89,6 +103,16 @@ def load() -> ctypes.CDLL:
             "brmppi_solve_device": (ctypes.c_int, [_VP, _VP, _VP, _VP, ctypes.c_int32, _VP,
                                                    ctypes.c_int32, ctypes.c_float, ctypes.c_uint64,
                                                    ctypes.c_uint64, _VP, _VP, _VP, _VP, _VP, _VP]),
+            "brmppi_solve_batch": (ctypes.c_int, [_VP, ctypes.POINTER(brmppi_instance),
+                                                  ctypes.c_int32, _VP]),
+            "brmppi_batch_capture": (ctypes.c_int, [_VP, ctypes.POINTER(brmppi_instance),
+                                                    ctypes.c_int32, ctypes.POINTER(_VP)]),
+            "brmppi_graph_launch": (ctypes.c_int, [_VP, _VP]),
+            "brmppi_graph_destroy": (None, [_VP]),
+            "brmppi_autotune": (ctypes.c_int, [_VP, _VP, _VP, _VP, ctypes.c_int32, _VP,
+                                               ctypes.c_int32, ctypes.c_float, ctypes.c_int32, _VP]),
+            "brmppi_autotune_batch": (ctypes.c_int, [_VP, ctypes.POINTER(brmppi_instance),
+                                                     ctypes.c_int32, ctypes.c_int32, _VP]),
             "brmppi_get_launch": (ctypes.c_int, [_VP, ctypes.c_int32, _I32, _I32, _I32]),
             "brmppi_transfer_bytes": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.c_int32,
                                                      ctypes.POINTER(ctypes.c_uint64),
@@ -115,7 +139,9 @@ def brmppi_default_params() -> brmppi_params:
 
 
 def params_from_dict(d: dict, max_obstacles: int = 16, max_path_pts: int = 4096,
-                     threads_per_sample: int = 0, block_threads: int = 0) -> brmppi_params:
+                     threads_per_sample: int = 0, block_threads: int = 0, max_batch: int = 0,
+                     batch_threads_per_sample: int = 0,
+                     batch_block_threads: int = 0) -> brmppi_params:
     """brmppi_params from the parameter dict of ``scenarios`` (values are
     rounded to binary32 by the struct)."""
     p = brmppi_default_params()
@@ -135,6 +161,9 @@ def params_from_dict(d: dict, max_obstacles: int = 16, max_path_pts: int = 4096,
     p.max_path_pts = int(max_path_pts)
     p.threads_per_sample = int(threads_per_sample)
     p.block_threads = int(block_threads)
+    p.max_batch = int(max_batch)
+    p.batch_threads_per_sample = int(batch_threads_per_sample)
+    p.batch_block_threads = int(batch_block_threads)
     p.abi_version = BRMPPI_ABI_VERSION
     return p
 
@@ -213,6 +242,77 @@ def brmppi_solve_device(ctx, x0, U_nom, obs, path, ds, seed, counter, U_out, tra
                                    ctypes.c_void_p(int(stream)))
 
 
+def _stream_handle(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if hasattr(stream, "cuda_stream"):
+        return stream.cuda_stream
+    return int(stream)
+
+
+def make_instances(insts) -> "ctypes.Array":
+    """ctypes array of brmppi_instance from dicts of torch CUDA tensors
+    (x0, U_nom, obs, path, U_out; optional traj_out, J_out, U_next, status)
+    and scalars (ds, seed, counter)."""
+    arr = (brmppi_instance * len(insts))()
+    for i, d in enumerate(insts):
+        q = arr[i]
+        q.x0 = d["x0"].data_ptr()
+        q.U_nom = d["U_nom"].data_ptr()
+        obs = d.get("obs")
+        q.n_obs = 0 if obs is None else obs.numel() // 6
+        q.obs = obs.data_ptr() if q.n_obs else None
+        q.path = d["path"].data_ptr()
+        q.n_pts = d["path"].numel() // 3
+        q.ds = float(d["ds"])
+        q.H = d["U_nom"].numel() // 3
+        q.S = int(d["S"])
+        q.seed = int(d["seed"]) & (2**64 - 1)
+        q.counter = int(d.get("counter", 0)) & (2**64 - 1)
+        q.U_out = d["U_out"].data_ptr()
+        for key in ("traj_out", "J_out", "U_next", "status"):
+            t = d.get(key)
+            setattr(q, key, None if t is None else t.data_ptr())
+    return arr
+
+
+def brmppi_solve_batch(ctx, insts, stream=None) -> int:
+    arr = insts if isinstance(insts, ctypes.Array) else make_instances(insts)
+    return load().brmppi_solve_batch(ctx, arr, len(arr), ctypes.c_void_p(_stream_handle(stream)))
+
+
+def brmppi_batch_capture(ctx, insts):
+    arr = insts if isinstance(insts, ctypes.Array) else make_instances(insts)
+    g = _VP()
+    st = load().brmppi_batch_capture(ctx, arr, len(arr), ctypes.byref(g))
+    if st != BRMPPI_OK:
+        raise BrmppiError(st, brmppi_last_error(ctx))
+    return g
+
+
+def brmppi_graph_launch(graph, stream=None) -> int:
+    return load().brmppi_graph_launch(graph, ctypes.c_void_p(_stream_handle(stream)))
+
+
+def brmppi_graph_destroy(graph) -> None:
+    if graph:
+        load().brmppi_graph_destroy(graph)
+
+
+def brmppi_autotune(ctx, x0, U_nom, obs, path, ds, reps=5, stream=None) -> int:
+    n_obs = 0 if obs is None else obs.numel() // 6
+    return load().brmppi_autotune(ctx, _dptr(x0), _dptr(U_nom), _dptr(obs) if n_obs else None,
+                                  n_obs, _dptr(path), path.numel() // 3, float(ds), int(reps),
+                                  ctypes.c_void_p(_stream_handle(stream)))
+
+
+def brmppi_autotune_batch(ctx, insts, reps=3, stream=None) -> int:
+    arr = insts if isinstance(insts, ctypes.Array) else make_instances(insts)
+    return load().brmppi_autotune_batch(ctx, arr, len(arr), int(reps),
+                                        ctypes.c_void_p(_stream_handle(stream)))
+
+
 def brmppi_get_launch(ctx, n_obs: int):
     tps, thr, blk = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
     st = load().brmppi_get_launch(ctx, int(n_obs), ctypes.byref(tps), ctypes.byref(thr),
@@ -235,12 +335,16 @@ class Solver:
     """Convenience owner of one context."""
 
     def __init__(self, params: dict, device: int = 0, max_obstacles: int = 16,
-                 max_path_pts: int = 4096, threads_per_sample: int = 0, block_threads: int = 0):
+                 max_path_pts: int = 4096, threads_per_sample: int = 0, block_threads: int = 0,
+                 max_batch: int = 0, batch_threads_per_sample: int = 0,
+                 batch_block_threads: int = 0):
+        self.ctx = None
         self.params = dict(params)
         self.S = int(params["S"])
         self.H = int(params["H"])
         self._p = params_from_dict(params, max_obstacles, max_path_pts, threads_per_sample,
-                                   block_threads)
+                                   block_threads, max_batch, batch_threads_per_sample,
+                                   batch_block_threads)
         self.ctx = brmppi_create(self._p, device)
 
     def close(self):
@@ -270,3 +374,22 @@ class Solver:
 
     def transfer_bytes(self, n_obs: int, n_pts: int):
         return brmppi_transfer_bytes(self.ctx, n_obs, n_pts)
+
+    def solve_batch(self, insts, stream=None, check=True) -> int:
+        st = brmppi_solve_batch(self.ctx, insts, stream)
+        if check and st != BRMPPI_OK:
+            raise BrmppiError(st, brmppi_last_error(self.ctx))
+        return st
+
+    def capture_batch(self, insts):
+        return brmppi_batch_capture(self.ctx, insts)
+
+    def autotune(self, x0, U_nom, obs, path, ds, reps=5, stream=None):
+        st = brmppi_autotune(self.ctx, x0, U_nom, obs, path, ds, reps, stream)
+        if st != BRMPPI_OK:
+            raise BrmppiError(st, brmppi_last_error(self.ctx))
+
+    def autotune_batch(self, insts, reps=3, stream=None):
+        st = brmppi_autotune_batch(self.ctx, insts, reps, stream)
+        if st != BRMPPI_OK:
+            raise BrmppiError(st, brmppi_last_error(self.ctx))

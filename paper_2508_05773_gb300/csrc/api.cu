@@ -1,38 +1,73 @@
 // api.cu -- the C ABI of libbrmppi.so (see include/brmppi.h).
 //
-// The context owns every buffer a solve needs, sized at create time for
-// the declared capacities, so the solve paths allocate nothing.  Host entry
+// The context owns every buffer a solve needs, sized at create time for the
+// declared capacities, so the solve paths allocate nothing.  Host entry
 // points stage inputs through one pinned buffer (one H2D copy), run the
-// kernel and read the outputs back (one D2H copy, plus the costs when
-// asked for).
+// kernel and read the outputs back (one D2H copy, plus the costs when asked
+// for).  Batches upload an instance table and a longest-first work list and
+// run one persistent launch.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <string>
+#include <vector>
 
 #include "brmppi.h"
 #include "launch.h"
 
+namespace {
+
+struct Shape {
+  int tps = 0, bpt = 0, threads = 0;
+};
+
+}  // namespace
+
 struct brmppi_ctx {
   brmppi_params prm{};
   int device = 0;
+  int num_sms = 0;
   cudaStream_t stream = nullptr;
-  // device
+  size_t smem_limit = 0;
+  // plain solves
   unsigned char* d_in = nullptr;  // x0 | U_nom | obs | path
   float* d_out = nullptr;         // U | traj | status
   float* d_J = nullptr;
   float* d_part = nullptr;
-  unsigned int* d_sync = nullptr;  // ticket, err
-  // pinned host
+  unsigned int* d_sync = nullptr;  // finished tiles, error bits
+  float* d_uh = nullptr;
   unsigned char* h_in = nullptr;
   float* h_out = nullptr;
-  // layout
-  size_t off_unom = 0, off_obs = 0, off_path = 0, in_bytes = 0;
-  size_t out_floats = 0;
-  size_t part_stride = 0, part_blocks = 0;
-  size_t smem_limit = 0;
+  size_t off_unom = 0, off_obs = 0, off_path = 0, in_bytes = 0, out_floats = 0;
+  size_t part_stride = 0, part_tiles = 0, uh_floats = 0;
+  std::map<int, Shape> tuned;  // obstacle count -> fastest plain shape
+  // batches
+  brmppi::Inst* d_inst = nullptr;
+  int2* d_work = nullptr;
+  unsigned int* d_work_ctr = nullptr;
+  float* d_bpart = nullptr;
+  unsigned int* d_bsync = nullptr;
+  float* d_buh = nullptr;
+  brmppi::Inst* h_inst = nullptr;
+  int2* h_work = nullptr;
+  cudaEvent_t upload_done = nullptr;  // host staging free again
+  cudaEvent_t batch_done = nullptr;   // device table free again
+  bool batch_pending = false;
+  size_t bpart_floats = 0, buh_floats = 0, max_work = 0;
+  bool batch_tuned = false;
+  Shape batch_shape;
   std::string err;
+};
+
+struct brmppi_graph {
+  brmppi_ctx* ctx = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  brmppi::Inst* h_inst = nullptr;
+  int2* h_work = nullptr;
 };
 
 namespace {
@@ -45,6 +80,8 @@ constexpr int kMaxPathPts = 12000;
 constexpr int kMaxH = 1024;
 constexpr int kMinThreads = 64;
 constexpr int kMaxThreads = 512;
+constexpr int kMinBatchSpb = 16;  // smallest tile of a batch launch
+constexpr int kMaxResidentThreads = 2048;
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
@@ -67,6 +104,8 @@ bool is_pow2_tps(int t) { return t == 1 || t == 2 || t == 4 || t == 8 || t == 16
 
 int philox_blocks(int n_obs) { return (4 + n_obs + 3) / 4; }  // d = 3 + (1 + n_obs)
 
+bool valid_threads(int t) { return t == 0 || (t >= kMinThreads && t <= kMaxThreads && t % 32 == 0); }
+
 std::string check_params(const brmppi_params* p) {
   if (!p) return "params is NULL";
   if (p->abi_version != BRMPPI_ABI_VERSION) return "abi_version mismatch";
@@ -77,9 +116,11 @@ std::string check_params(const brmppi_params* p) {
   if (p->flags & ~static_cast<int32_t>(BRMPPI_FLAG_PROJ_NONE)) return "unknown flag";
   if (p->threads_per_sample != 0 && !is_pow2_tps(p->threads_per_sample))
     return "threads_per_sample must be 0, 1, 2, 4, 8, 16 or 32";
-  if (p->block_threads != 0 &&
-      (p->block_threads < kMinThreads || p->block_threads > kMaxThreads || p->block_threads % 32 != 0))
+  if (p->batch_threads_per_sample != 0 && !is_pow2_tps(p->batch_threads_per_sample))
+    return "batch_threads_per_sample must be 0, 1, 2, 4, 8, 16 or 32";
+  if (!valid_threads(p->block_threads) || !valid_threads(p->batch_block_threads))
     return "block_threads must be 0 or a multiple of 32 in [64, 512]";
+  if (p->max_batch < 0 || p->max_batch > 65536) return "max_batch must be in [0, 65536]";
   const float pos[] = {p->Ts, p->lambda, p->l1, p->l2, p->h_floor};
   for (float v : pos)
     if (!(v > 0.f) || !std::isfinite(v)) return "Ts, lambda, l1, l2, h_floor must be positive and finite";
@@ -101,77 +142,8 @@ std::string check_params(const brmppi_params* p) {
   return "";
 }
 
-struct Launch {
-  int tps, bpt, threads, blocks;
-  size_t smem;
-};
-
-// Launch shape for a solve with n_obs obstacles: a team just wide enough
-// for the Philox blocks (one block per lane), blocks of 128 threads, halved
-// while that leaves fewer than two blocks per SM; narrower blocks (then
-// wider teams) while the shared-memory tables do not fit.
-bool pick_bpt(int tps, int P, int* bpt) {
-  for (int b : {1, 2, 4})
-    if (tps * b >= P && brmppi::variant_exists(tps, b)) {
-      *bpt = b;
-      return true;
-    }
-  return false;
-}
-
-bool choose_launch(const brmppi_ctx* c, int n_obs, int n_pts, Launch* L) {
-  const int P = philox_blocks(n_obs);
-  const bool fixed_tps = c->prm.threads_per_sample != 0;
-  int tps = c->prm.threads_per_sample;
-  if (!fixed_tps) {
-    tps = 1;
-    while (tps < P && tps < 32) tps <<= 1;
-  }
-  int bpt = 0;
-  if (!pick_bpt(tps, P, &bpt)) return false;
-  int threads = c->prm.block_threads;
-  const bool fixed_threads = threads != 0;
-  const int S = c->prm.S;
-  if (!fixed_threads) {
-    threads = 128;
-    while (threads > kMinThreads) {
-      const int spb = threads / tps;
-      const int blocks = (S + spb - 1) / spb;
-      if (blocks >= 2 * 152) break;
-      threads >>= 1;
-    }
-  }
-  if (threads < tps) return false;
-  for (;;) {
-    const size_t smem = brmppi::smem_bytes(n_obs, n_pts, c->prm.H, threads / tps);
-    if (smem <= c->smem_limit) break;
-    if (!fixed_threads && threads > kMinThreads) {
-      threads -= 32;
-    } else if (!fixed_tps && tps < 32) {
-      tps <<= 1;
-      if (!pick_bpt(tps, P, &bpt)) return false;
-    } else {
-      return false;
-    }
-  }
-  const int spb = threads / tps;
-  L->tps = tps;
-  L->bpt = bpt;
-  L->threads = threads;
-  L->blocks = (S + spb - 1) / spb;
-  L->smem = brmppi::smem_bytes(n_obs, n_pts, c->prm.H, spb);
-  return true;
-}
-
-brmppi::KParams make_kparams(const brmppi_params& q, int n_obs, int n_pts, float ds, uint64_t seed,
-                             uint64_t counter, int part_stride) {
-  brmppi::KParams k{};
-  k.S = q.S;
-  k.H = q.H;
-  k.n_obs = n_obs;
-  k.n_pts = n_pts;
-  k.Nc = 1 + n_obs;
-  k.P = philox_blocks(n_obs);
+brmppi::KConst make_kconst(const brmppi_params& q) {
+  brmppi::KConst k{};
   k.proj = (q.flags & BRMPPI_FLAG_PROJ_NONE) ? 0 : 1;
   k.Ts = q.Ts;
   k.hTs2 = 0.5f * q.Ts * q.Ts;
@@ -219,13 +191,113 @@ brmppi::KParams make_kparams(const brmppi_params& q, int n_obs, int n_pts, float
   k.m_a = q.w_alpha + q.rho;
   k.inv_m_a = 1.0f / (q.w_alpha + q.rho);
   k.h_floor = q.h_floor;
-  k.ds = ds;
-  k.inv_ds = 1.0f / ds;
-  k.key0 = static_cast<uint32_t>(seed);
-  k.key1 = static_cast<uint32_t>(seed >> 32);
-  k.ctr = static_cast<uint32_t>(counter);
-  k.part_stride = part_stride;
   return k;
+}
+
+brmppi::SmemCaps make_caps(int n_obs, int n_pts, int H) {
+  brmppi::SmemCaps c{};
+  c.obs = 8 * n_obs;
+  c.path = 3 * n_pts;
+  c.unom = 3 * H;
+  c.ustar = static_cast<int>(align_up(3 * static_cast<size_t>(H) + 1, 4));
+  return c;
+}
+
+size_t smem_bytes(const brmppi::SmemCaps& c, int spb) { return sizeof(float) * static_cast<size_t>(c.total(spb)); }
+
+bool pick_bpt(int tps, int P, int* bpt) {
+  for (int b : {1, 2, 4, 8})
+    if (tps * b >= P && brmppi::variant_exists(tps, b)) {
+      *bpt = b;
+      return true;
+    }
+  return false;
+}
+
+int part_stride_for(int H) { return static_cast<int>(align_up(3 + 3 * static_cast<size_t>(H) + 1, 4)); }
+
+// Heuristic plain shape: a team just wide enough for the Philox blocks (one
+// block per lane), 128-thread blocks while that leaves at least two CTAs per
+// SM, else 64.  Narrower blocks (then wider teams) while the shared-memory
+// tables do not fit.
+bool heuristic_plain(const brmppi_ctx* c, int n_obs, int n_pts, Shape* out) {
+  const int P = philox_blocks(n_obs);
+  const bool fixed_tps = c->prm.threads_per_sample != 0;
+  int tps = c->prm.threads_per_sample;
+  if (!fixed_tps) {
+    tps = 1;
+    while (tps < P && tps < 32) tps <<= 1;
+  }
+  int bpt = 0;
+  if (!pick_bpt(tps, P, &bpt)) return false;
+  int threads = c->prm.block_threads;
+  const bool fixed_threads = threads != 0;
+  if (!fixed_threads) {
+    threads = 128;
+    const int spb = threads / tps;
+    if ((c->prm.S + spb - 1) / spb < 2 * c->num_sms) threads = 64;
+  }
+  if (threads < tps) return false;
+  const brmppi::SmemCaps caps = make_caps(n_obs, n_pts, c->prm.H);
+  while (smem_bytes(caps, threads / tps) > c->smem_limit) {
+    if (!fixed_threads && threads > kMinThreads) {
+      threads -= 32;
+    } else if (!fixed_tps && tps < 32) {
+      tps <<= 1;
+      if (!pick_bpt(tps, P, &bpt)) return false;
+    } else {
+      return false;
+    }
+  }
+  out->tps = tps;
+  out->bpt = bpt;
+  out->threads = threads;
+  return true;
+}
+
+bool plain_shape(const brmppi_ctx* c, int n_obs, int n_pts, Shape* out) {
+  if (c->prm.threads_per_sample == 0 && c->prm.block_threads == 0) {
+    auto it = c->tuned.find(n_obs);
+    if (it != c->tuned.end()) {
+      const brmppi::SmemCaps caps = make_caps(n_obs, n_pts, c->prm.H);
+      if (smem_bytes(caps, it->second.threads / it->second.tps) <= c->smem_limit) {
+        *out = it->second;
+        return true;
+      }
+    }
+  }
+  return heuristic_plain(c, n_obs, n_pts, out);
+}
+
+brmppi::Inst make_inst(const double* x0, const float* U_nom, const float* obs, int n_obs, const float* path,
+                       int n_pts, float ds, int S, int H, uint64_t seed, uint64_t counter, float* U_out,
+                       float* traj_out, float* J_out, float* U_next, int32_t* status, float* part,
+                       unsigned int* sync, int spb) {
+  brmppi::Inst in{};
+  in.x0 = x0;
+  in.U_nom = U_nom;
+  in.obs = obs;
+  in.path = path;
+  in.U_out = U_out;
+  in.traj_out = traj_out;
+  in.J_out = J_out;
+  in.U_next = U_next;
+  in.status = status;
+  in.part = part;
+  in.sync = sync;
+  in.S = S;
+  in.H = H;
+  in.n_obs = n_obs;
+  in.n_pts = n_pts;
+  in.tiles = (S + spb - 1) / spb;
+  in.part_stride = part_stride_for(H);
+  in.ds = ds;
+  in.inv_ds = 1.0f / ds;
+  in.key0 = static_cast<uint32_t>(seed);
+  in.key1 = static_cast<uint32_t>(seed >> 32);
+  in.ctr = static_cast<uint32_t>(counter);
+  in.P = philox_blocks(n_obs);
+  return in;
 }
 
 brmppi_status check_sizes(brmppi_ctx* c, int32_t n_obs, int32_t n_pts, float ds) {
@@ -235,32 +307,149 @@ brmppi_status check_sizes(brmppi_ctx* c, int32_t n_obs, int32_t n_pts, float ds)
   return BRMPPI_OK;
 }
 
-brmppi_status enqueue(brmppi_ctx* c, const double* x0, const float* U_nom, const float* obs, int32_t n_obs,
-                      const float* path, int32_t n_pts, float ds, uint64_t seed, uint64_t counter,
-                      float* U_out, float* traj_out, float* J_out, float* U_next, int32_t* status,
-                      cudaStream_t stream) {
-  Launch L;
-  if (!choose_launch(c, n_obs, n_pts, &L)) return fail(c, BRMPPI_EINVAL, "no kernel variant for this size");
-  if (L.smem > c->smem_limit) return fail(c, BRMPPI_EINVAL, "shared memory need exceeds the context's limit");
-  if (static_cast<size_t>(L.blocks) > c->part_blocks) return fail(c, BRMPPI_EINVAL, "too many blocks");
-  const brmppi::KParams kp =
-      make_kparams(c->prm, n_obs, n_pts, ds, seed, counter, static_cast<int>(c->part_stride));
-  brmppi::KIO io{};
-  io.x0 = x0;
-  io.U_nom = U_nom;
-  io.obs = obs;
-  io.path = path;
-  io.U_out = U_out;
-  io.traj_out = traj_out;
-  io.J_out = J_out;
-  io.U_next = U_next;
-  io.status = status;
-  io.part = c->d_part;
-  io.ticket = c->d_sync;
-  io.err = c->d_sync + 1;
-  cudaError_t e = brmppi::launch_rollout(L.tps, L.bpt, L.blocks, L.threads, L.smem, stream, kp, io);
+brmppi_status enqueue_plain(brmppi_ctx* c, const Shape& sh, const double* x0, const float* U_nom,
+                            const float* obs, int32_t n_obs, const float* path, int32_t n_pts, float ds,
+                            uint64_t seed, uint64_t counter, float* U_out, float* traj_out, float* J_out,
+                            float* U_next, int32_t* status, cudaStream_t stream) {
+  const int H = c->prm.H, S = c->prm.S;
+  const int spb = sh.threads / sh.tps;
+  brmppi::LaunchDesc L{};
+  L.single = make_inst(x0, U_nom, obs, n_obs, path, n_pts, ds, S, H, seed, counter, U_out, traj_out, J_out,
+                       U_next, status, c->d_part, c->d_sync, spb);
+  L.caps = make_caps(n_obs, n_pts, H);
+  L.uh = c->d_uh;
+  L.uh_stride = 3 * H * spb;
+  const size_t smem = smem_bytes(L.caps, spb);
+  const int tiles = L.single.tiles;
+  if (smem > c->smem_limit) return fail(c, BRMPPI_EINVAL, "shared memory need exceeds the device limit");
+  if (static_cast<size_t>(tiles) > c->part_tiles ||
+      static_cast<size_t>(tiles) * static_cast<size_t>(L.uh_stride) > c->uh_floats)
+    return fail(c, BRMPPI_EINVAL, "launch shape exceeds the context's scratch");
+  cudaError_t e = brmppi::launch_solve(sh.tps, sh.bpt, tiles, sh.threads, smem, stream, make_kconst(c->prm), L);
   if (e != cudaSuccess) return cuda_fail(c, e, "kernel launch");
   return BRMPPI_OK;
+}
+
+// ------------------------------------------------------------- batches
+struct BatchPlan {
+  Shape shape;
+  int n_inst = 0, n_work = 0, grid = 0, Hmax = 0;
+  brmppi::SmemCaps caps{};
+  size_t smem = 0;
+};
+
+bool batch_shape_default(const brmppi_ctx* c, int max_P, Shape* out) {
+  Shape s;
+  s.tps = c->prm.batch_threads_per_sample;
+  s.threads = c->prm.batch_block_threads;
+  if (s.tps == 0 && s.threads == 0 && c->batch_tuned) {
+    s = c->batch_shape;
+  } else {
+    if (s.tps == 0) s.tps = 1;
+    if (s.threads == 0) s.threads = 128;
+  }
+  while (!pick_bpt(s.tps, max_P, &s.bpt)) {
+    if (s.tps >= 32) return false;
+    s.tps <<= 1;
+  }
+  if (s.threads < s.tps || s.threads / s.tps < kMinBatchSpb) return false;
+  *out = s;
+  return true;
+}
+
+// Validate the instances, fill the instance table and the longest-first
+// work list (host staging), and size the launch.
+brmppi_status plan_batch(brmppi_ctx* c, const brmppi_instance* inst, int32_t n, const Shape* forced,
+                         brmppi::Inst* h_inst, int2* h_work, BatchPlan* plan) {
+  if (c->prm.max_batch <= 0) return fail(c, BRMPPI_EINVAL, "context created without batch capacity (max_batch)");
+  if (!inst || n < 1 || n > c->prm.max_batch) return fail(c, BRMPPI_EINVAL, "n out of [1, max_batch]");
+  int max_P = 1, Hmax = 1, nobs_max = 0, npts_max = 2;
+  for (int i = 0; i < n; ++i) {
+    const brmppi_instance& q = inst[i];
+    if (!q.x0 || !q.U_nom || !q.path || !q.U_out || (q.n_obs > 0 && !q.obs))
+      return fail(c, BRMPPI_EINVAL, "instance " + std::to_string(i) + ": NULL buffer");
+    if (q.S < 1 || q.S > c->prm.S || q.H < 1 || q.H > c->prm.H)
+      return fail(c, BRMPPI_EINVAL, "instance " + std::to_string(i) + ": S or H beyond the capacity");
+    brmppi_status st = check_sizes(c, q.n_obs, q.n_pts, q.ds);
+    if (st != BRMPPI_OK) return fail(c, st, "instance " + std::to_string(i) + ": " + c->err);
+    max_P = std::max(max_P, philox_blocks(q.n_obs));
+    Hmax = std::max(Hmax, static_cast<int>(q.H));
+    nobs_max = std::max(nobs_max, static_cast<int>(q.n_obs));
+    npts_max = std::max(npts_max, static_cast<int>(q.n_pts));
+  }
+  Shape sh;
+  if (forced) {
+    sh = *forced;
+  } else if (!batch_shape_default(c, max_P, &sh)) {
+    return fail(c, BRMPPI_EINVAL, "no batch launch shape for these instances");
+  }
+  const int spb = sh.threads / sh.tps;
+  const brmppi::SmemCaps caps = make_caps(nobs_max, npts_max, Hmax);
+  const size_t smem = smem_bytes(caps, spb);
+  if (smem > c->smem_limit) return fail(c, BRMPPI_EINVAL, "batch tables exceed shared memory");
+  size_t pool = 0;
+  std::vector<std::pair<long long, int2>> items;
+  for (int i = 0; i < n; ++i) {
+    const brmppi_instance& q = inst[i];
+    const int H = q.H;
+    brmppi::Inst in = make_inst(q.x0, q.U_nom, q.obs, q.n_obs, q.path, q.n_pts, q.ds, q.S, H, q.seed, q.counter,
+                                q.U_out, q.traj_out, q.J_out, q.U_next, q.status, nullptr, c->d_bsync + 2 * i, spb);
+    in.part = c->d_bpart + pool;
+    pool += static_cast<size_t>(in.tiles) * static_cast<size_t>(in.part_stride);
+    if (pool > c->bpart_floats) return fail(c, BRMPPI_EINVAL, "batch partials exceed the context's pool");
+    h_inst[i] = in;
+    const long long cost = static_cast<long long>(H) * (8 + q.n_obs);
+    for (int t = 0; t < in.tiles; ++t) items.push_back({cost, make_int2(i, t)});
+  }
+  if (items.size() > c->max_work) return fail(c, BRMPPI_EINVAL, "too many work items");
+  std::stable_sort(items.begin(), items.end(),
+                   [](const std::pair<long long, int2>& a, const std::pair<long long, int2>& b) {
+                     return a.first > b.first;
+                   });
+  for (size_t j = 0; j < items.size(); ++j) h_work[j] = items[j].second;
+  const int occ = brmppi::variant_occupancy(sh.tps, sh.bpt, sh.threads, smem);
+  if (occ < 1) return fail(c, BRMPPI_EINVAL, "batch launch shape cannot be resident");
+  int grid = occ * c->num_sms;
+  if (grid > static_cast<int>(items.size())) grid = static_cast<int>(items.size());
+  if (static_cast<size_t>(grid) * 3 * Hmax * spb > c->buh_floats)
+    return fail(c, BRMPPI_EINVAL, "batch history scratch too small");
+  plan->shape = sh;
+  plan->n_inst = n;
+  plan->n_work = static_cast<int>(items.size());
+  plan->grid = grid;
+  plan->Hmax = Hmax;
+  plan->caps = caps;
+  plan->smem = smem;
+  return BRMPPI_OK;
+}
+
+brmppi_status launch_batch(brmppi_ctx* c, const BatchPlan& plan, cudaStream_t stream) {
+  brmppi::LaunchDesc L{};
+  L.inst = c->d_inst;
+  L.work = c->d_work;
+  L.n_work = plan.n_work;
+  L.work_ctr = c->d_work_ctr;
+  L.uh = c->d_buh;
+  L.uh_stride = 3 * plan.Hmax * (plan.shape.threads / plan.shape.tps);
+  L.caps = plan.caps;
+  cudaError_t e = brmppi::launch_solve(plan.shape.tps, plan.shape.bpt, plan.grid, plan.shape.threads, plan.smem,
+                                       stream, make_kconst(c->prm), L);
+  if (e != cudaSuccess) return cuda_fail(c, e, "batch kernel launch");
+  return BRMPPI_OK;
+}
+
+brmppi_status upload_and_launch(brmppi_ctx* c, const BatchPlan& plan, const brmppi::Inst* h_inst,
+                                const int2* h_work, cudaStream_t stream) {
+  cudaError_t e;
+  if (c->batch_pending && (e = cudaStreamWaitEvent(stream, c->batch_done, 0)) != cudaSuccess)
+    return cuda_fail(c, e, "wait for the previous batch");
+  if ((e = cudaMemcpyAsync(c->d_inst, h_inst, sizeof(brmppi::Inst) * plan.n_inst, cudaMemcpyHostToDevice,
+                           stream)) != cudaSuccess)
+    return cuda_fail(c, e, "instance table upload");
+  if ((e = cudaMemcpyAsync(c->d_work, h_work, sizeof(int2) * plan.n_work, cudaMemcpyHostToDevice, stream)) !=
+      cudaSuccess)
+    return cuda_fail(c, e, "work list upload");
+  return launch_batch(c, plan, stream);
 }
 
 }  // namespace
@@ -318,46 +507,76 @@ brmppi_status brmppi_create(const brmppi_params* p, int device, brmppi_ctx** out
   if (!c) return fail(nullptr, BRMPPI_ENOMEM, "host allocation failed");
   c->prm = *p;
   c->device = device;
-  cudaError_t e = cudaSetDevice(device);
   auto bail = [&](cudaError_t err, const char* what) {
     std::string m = std::string(what) + ": " + cudaGetErrorString(err);
     brmppi_destroy(c);
     return fail(nullptr, err == cudaErrorMemoryAllocation ? BRMPPI_ENOMEM : BRMPPI_ECUDA, m);
   };
+  cudaError_t e = cudaSetDevice(device);
   if (e != cudaSuccess) return bail(e, "cudaSetDevice");
-  const int H = p->H, S = p->S;
-  c->off_unom = 64;
-  c->off_obs = align_up(c->off_unom + sizeof(float) * 3 * H, 16);
-  c->off_path = align_up(c->off_obs + sizeof(float) * 6 * static_cast<size_t>(p->max_obstacles), 16);
-  c->in_bytes = align_up(c->off_path + sizeof(float) * 3 * static_cast<size_t>(p->max_path_pts), 16);
-  c->out_floats = 3 * static_cast<size_t>(H) + 7 * static_cast<size_t>(H + 1) + 1;
-  c->part_stride = align_up(3 + 3 * static_cast<size_t>(H) + 1, 4);
-  c->part_blocks = static_cast<size_t>((S + 1) / 2);  // at least two samples per block
-  if (c->part_blocks < 1) c->part_blocks = 1;
+  if ((e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device)) != cudaSuccess)
+    return bail(e, "cudaDeviceGetAttribute");
   int dev_smem = 0;
   if ((e = cudaDeviceGetAttribute(&dev_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, device)) != cudaSuccess)
     return bail(e, "cudaDeviceGetAttribute");
-  c->smem_limit = static_cast<size_t>(dev_smem) - 2048;  // static shared memory of the kernel
+  c->smem_limit = static_cast<size_t>(dev_smem) - 1024;  // static shared memory of the kernel
   if ((e = brmppi::set_smem_limit(c->smem_limit)) != cudaSuccess) return bail(e, "cudaFuncSetAttribute");
   {
-    Launch L;
-    if (!choose_launch(c, p->max_obstacles, p->max_path_pts, &L)) {
+    Shape s;
+    if (!heuristic_plain(c, p->max_obstacles, p->max_path_pts, &s)) {
       brmppi_destroy(c);
       return fail(nullptr, BRMPPI_EINVAL, "no launch shape fits these capacities in shared memory");
     }
   }
+  const size_t H = static_cast<size_t>(p->H), S = static_cast<size_t>(p->S);
+  c->off_unom = 64;
+  c->off_obs = align_up(c->off_unom + sizeof(float) * 3 * H, 16);
+  c->off_path = align_up(c->off_obs + sizeof(float) * 6 * static_cast<size_t>(p->max_obstacles), 16);
+  c->in_bytes = align_up(c->off_path + sizeof(float) * 3 * static_cast<size_t>(p->max_path_pts), 16);
+  c->out_floats = 3 * H + 7 * (H + 1) + 1;
+  c->part_stride = static_cast<size_t>(part_stride_for(p->H));
+  c->part_tiles = (S + 1) / 2;               // tiles of at least two samples
+  c->uh_floats = (S + kMaxThreads) * 3 * H;  // one tile slot per CTA, rounded up
   if ((e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking)) != cudaSuccess)
     return bail(e, "cudaStreamCreate");
   if ((e = cudaMalloc(&c->d_in, c->in_bytes)) != cudaSuccess) return bail(e, "cudaMalloc(in)");
   if ((e = cudaMalloc(&c->d_out, sizeof(float) * c->out_floats)) != cudaSuccess) return bail(e, "cudaMalloc(out)");
   if ((e = cudaMalloc(&c->d_J, sizeof(float) * S)) != cudaSuccess) return bail(e, "cudaMalloc(J)");
-  if ((e = cudaMalloc(&c->d_part, sizeof(float) * c->part_stride * c->part_blocks)) != cudaSuccess)
+  if ((e = cudaMalloc(&c->d_part, sizeof(float) * c->part_stride * c->part_tiles)) != cudaSuccess)
     return bail(e, "cudaMalloc(partials)");
+  if ((e = cudaMalloc(&c->d_uh, sizeof(float) * c->uh_floats)) != cudaSuccess) return bail(e, "cudaMalloc(history)");
   if ((e = cudaMalloc(&c->d_sync, sizeof(unsigned int) * 4)) != cudaSuccess) return bail(e, "cudaMalloc(sync)");
   if ((e = cudaMemset(c->d_sync, 0, sizeof(unsigned int) * 4)) != cudaSuccess) return bail(e, "cudaMemset");
   if ((e = cudaMallocHost(&c->h_in, c->in_bytes)) != cudaSuccess) return bail(e, "cudaMallocHost(in)");
   if ((e = cudaMallocHost(&c->h_out, sizeof(float) * c->out_floats)) != cudaSuccess)
     return bail(e, "cudaMallocHost(out)");
+  if (p->max_batch > 0) {
+    const size_t nb = static_cast<size_t>(p->max_batch);
+    const size_t tiles_per_inst = (S + kMinBatchSpb - 1) / kMinBatchSpb;
+    c->max_work = nb * tiles_per_inst;
+    c->bpart_floats = c->max_work * c->part_stride;
+    c->buh_floats = static_cast<size_t>(c->num_sms) * kMaxResidentThreads * 3 * H;
+    if ((e = cudaMalloc(&c->d_inst, sizeof(brmppi::Inst) * nb)) != cudaSuccess) return bail(e, "cudaMalloc(table)");
+    if ((e = cudaMalloc(&c->d_work, sizeof(int2) * c->max_work)) != cudaSuccess) return bail(e, "cudaMalloc(work)");
+    if ((e = cudaMalloc(&c->d_work_ctr, sizeof(unsigned int) * 2)) != cudaSuccess)
+      return bail(e, "cudaMalloc(work counter)");
+    if ((e = cudaMemset(c->d_work_ctr, 0, sizeof(unsigned int) * 2)) != cudaSuccess) return bail(e, "cudaMemset");
+    if ((e = cudaMalloc(&c->d_bpart, sizeof(float) * c->bpart_floats)) != cudaSuccess)
+      return bail(e, "cudaMalloc(batch partials)");
+    if ((e = cudaMalloc(&c->d_bsync, sizeof(unsigned int) * 2 * nb)) != cudaSuccess)
+      return bail(e, "cudaMalloc(batch sync)");
+    if ((e = cudaMemset(c->d_bsync, 0, sizeof(unsigned int) * 2 * nb)) != cudaSuccess) return bail(e, "cudaMemset");
+    if ((e = cudaMalloc(&c->d_buh, sizeof(float) * c->buh_floats)) != cudaSuccess)
+      return bail(e, "cudaMalloc(batch history)");
+    if ((e = cudaMallocHost(&c->h_inst, sizeof(brmppi::Inst) * nb)) != cudaSuccess)
+      return bail(e, "cudaMallocHost(table)");
+    if ((e = cudaMallocHost(&c->h_work, sizeof(int2) * c->max_work)) != cudaSuccess)
+      return bail(e, "cudaMallocHost(work)");
+    if ((e = cudaEventCreateWithFlags(&c->upload_done, cudaEventDisableTiming)) != cudaSuccess)
+      return bail(e, "cudaEventCreate");
+    if ((e = cudaEventCreateWithFlags(&c->batch_done, cudaEventDisableTiming)) != cudaSuccess)
+      return bail(e, "cudaEventCreate");
+  }
   if ((e = cudaDeviceSynchronize()) != cudaSuccess) return bail(e, "cudaDeviceSynchronize");
   *out = c;
   return BRMPPI_OK;
@@ -367,13 +586,25 @@ void brmppi_destroy(brmppi_ctx* c) {
   if (!c) return;
   cudaSetDevice(c->device);
   if (c->stream) cudaStreamSynchronize(c->stream);
+  if (c->batch_pending && c->batch_done) cudaEventSynchronize(c->batch_done);
   cudaFree(c->d_in);
   cudaFree(c->d_out);
   cudaFree(c->d_J);
   cudaFree(c->d_part);
+  cudaFree(c->d_uh);
   cudaFree(c->d_sync);
+  cudaFree(c->d_inst);
+  cudaFree(c->d_work);
+  cudaFree(c->d_work_ctr);
+  cudaFree(c->d_bpart);
+  cudaFree(c->d_bsync);
+  cudaFree(c->d_buh);
   cudaFreeHost(c->h_in);
   cudaFreeHost(c->h_out);
+  cudaFreeHost(c->h_inst);
+  cudaFreeHost(c->h_work);
+  if (c->upload_done) cudaEventDestroy(c->upload_done);
+  if (c->batch_done) cudaEventDestroy(c->batch_done);
   if (c->stream) cudaStreamDestroy(c->stream);
   delete c;
 }
@@ -398,6 +629,8 @@ brmppi_status brmppi_solve(brmppi_ctx* c, const double x0[7], const float* U_nom
     if (!std::isfinite(x0[j])) return fail(c, BRMPPI_ENONFINITE, "x0 is not finite");
   for (int o = 0; o < n_obs; ++o)
     if (obs[6 * o + 5] != 2.0f) return fail(c, BRMPPI_EINVAL, "obstacle exponent must be 2");
+  Shape sh;
+  if (!plain_shape(c, n_obs, n_pts, &sh)) return fail(c, BRMPPI_EINVAL, "no launch shape for this size");
   const int H = c->prm.H;
   cudaError_t e = cudaSetDevice(c->device);
   if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
@@ -412,16 +645,17 @@ brmppi_status brmppi_solve(brmppi_ctx* c, const double x0[7], const float* U_nom
   float* dU = c->d_out;
   float* dT = dU + 3 * H;
   int32_t* dS = reinterpret_cast<int32_t*>(dT + 7 * (H + 1));
-  st = enqueue(c, reinterpret_cast<const double*>(c->d_in), reinterpret_cast<const float*>(c->d_in + c->off_unom),
-               reinterpret_cast<const float*>(c->d_in + c->off_obs), n_obs,
-               reinterpret_cast<const float*>(c->d_in + c->off_path), n_pts, ds, seed, counter, dU, dT,
-               J_out ? c->d_J : nullptr, nullptr, dS, c->stream);
+  st = enqueue_plain(c, sh, reinterpret_cast<const double*>(c->d_in),
+                     reinterpret_cast<const float*>(c->d_in + c->off_unom),
+                     reinterpret_cast<const float*>(c->d_in + c->off_obs), n_obs,
+                     reinterpret_cast<const float*>(c->d_in + c->off_path), n_pts, ds, seed, counter, dU, dT,
+                     J_out ? c->d_J : nullptr, nullptr, dS, c->stream);
   if (st != BRMPPI_OK) return st;
   if ((e = cudaMemcpyAsync(c->h_out, c->d_out, sizeof(float) * c->out_floats, cudaMemcpyDeviceToHost,
                            c->stream)) != cudaSuccess)
     return cuda_fail(c, e, "D2H copy");
-  if (J_out && (e = cudaMemcpyAsync(J_out, c->d_J, sizeof(float) * c->prm.S, cudaMemcpyDeviceToHost,
-                                    c->stream)) != cudaSuccess)
+  if (J_out && (e = cudaMemcpyAsync(J_out, c->d_J, sizeof(float) * c->prm.S, cudaMemcpyDeviceToHost, c->stream)) !=
+                   cudaSuccess)
     return cuda_fail(c, e, "D2H copy (J)");
   if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return cuda_fail(c, e, "stream sync");
   int32_t kst;
@@ -436,26 +670,224 @@ brmppi_status brmppi_solve(brmppi_ctx* c, const double x0[7], const float* U_nom
 brmppi_status brmppi_solve_device(brmppi_ctx* c, const double* x0_dev, const float* U_nom_dev,
                                   const float* obs_dev, int32_t n_obs, const float* path_dev, int32_t n_pts,
                                   float ds, uint64_t seed, uint64_t counter, float* U_out_dev,
-                                  float* traj_out_dev, float* J_out_dev, float* U_next_dev,
-                                  int32_t* status_dev, void* stream) {
+                                  float* traj_out_dev, float* J_out_dev, float* U_next_dev, int32_t* status_dev,
+                                  void* stream) {
   if (!c) return BRMPPI_EINVAL;
   c->err.clear();
   if (!x0_dev || !U_nom_dev || !path_dev || !U_out_dev || (n_obs > 0 && !obs_dev))
     return fail(c, BRMPPI_EINVAL, "NULL buffer");
   brmppi_status st = check_sizes(c, n_obs, n_pts, ds);
   if (st != BRMPPI_OK) return st;
-  return enqueue(c, x0_dev, U_nom_dev, obs_dev, n_obs, path_dev, n_pts, ds, seed, counter, U_out_dev,
-                 traj_out_dev, J_out_dev, U_next_dev, status_dev, static_cast<cudaStream_t>(stream));
+  Shape sh;
+  if (!plain_shape(c, n_obs, n_pts, &sh)) return fail(c, BRMPPI_EINVAL, "no launch shape for this size");
+  return enqueue_plain(c, sh, x0_dev, U_nom_dev, obs_dev, n_obs, path_dev, n_pts, ds, seed, counter, U_out_dev,
+                       traj_out_dev, J_out_dev, U_next_dev, status_dev, static_cast<cudaStream_t>(stream));
+}
+
+brmppi_status brmppi_solve_batch(brmppi_ctx* c, const brmppi_instance* inst, int32_t n, void* stream) {
+  if (!c) return BRMPPI_EINVAL;
+  c->err.clear();
+  cudaError_t e;
+  if (c->batch_pending && (e = cudaEventSynchronize(c->upload_done)) != cudaSuccess)
+    return cuda_fail(c, e, "wait for the previous upload");
+  BatchPlan plan;
+  brmppi_status st = plan_batch(c, inst, n, nullptr, c->h_inst, c->h_work, &plan);
+  if (st != BRMPPI_OK) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  st = upload_and_launch(c, plan, c->h_inst, c->h_work, s);
+  if (st != BRMPPI_OK) return st;
+  // the uploads are consumed once the kernel has finished
+  if ((e = cudaEventRecord(c->upload_done, s)) != cudaSuccess) return cuda_fail(c, e, "cudaEventRecord");
+  if ((e = cudaEventRecord(c->batch_done, s)) != cudaSuccess) return cuda_fail(c, e, "cudaEventRecord");
+  c->batch_pending = true;
+  return BRMPPI_OK;
+}
+
+brmppi_status brmppi_batch_capture(brmppi_ctx* c, const brmppi_instance* inst, int32_t n, brmppi_graph** out) {
+  if (!c || !out) return BRMPPI_EINVAL;
+  c->err.clear();
+  *out = nullptr;
+  if (c->prm.max_batch <= 0) return fail(c, BRMPPI_EINVAL, "context created without batch capacity (max_batch)");
+  brmppi_graph* g = new (std::nothrow) brmppi_graph();
+  if (!g) return fail(c, BRMPPI_ENOMEM, "host allocation failed");
+  g->ctx = c;
+  cudaError_t e;
+  auto bail = [&](brmppi_status st) {
+    brmppi_graph_destroy(g);
+    return st;
+  };
+  if ((e = cudaMallocHost(&g->h_inst, sizeof(brmppi::Inst) * c->prm.max_batch)) != cudaSuccess)
+    return bail(cuda_fail(c, e, "cudaMallocHost(graph table)"));
+  if ((e = cudaMallocHost(&g->h_work, sizeof(int2) * c->max_work)) != cudaSuccess)
+    return bail(cuda_fail(c, e, "cudaMallocHost(graph work)"));
+  BatchPlan plan;
+  brmppi_status st = plan_batch(c, inst, n, nullptr, g->h_inst, g->h_work, &plan);
+  if (st != BRMPPI_OK) return bail(st);
+  if (c->batch_pending && (e = cudaEventSynchronize(c->batch_done)) != cudaSuccess)
+    return bail(cuda_fail(c, e, "wait for the previous batch"));
+  c->batch_pending = false;
+  if ((e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+    return bail(cuda_fail(c, e, "cudaStreamBeginCapture"));
+  st = upload_and_launch(c, plan, g->h_inst, g->h_work, c->stream);
+  e = cudaStreamEndCapture(c->stream, &g->graph);
+  if (st != BRMPPI_OK) return bail(st);
+  if (e != cudaSuccess) return bail(cuda_fail(c, e, "cudaStreamEndCapture"));
+  if ((e = cudaGraphInstantiate(&g->exec, g->graph, 0)) != cudaSuccess)
+    return bail(cuda_fail(c, e, "cudaGraphInstantiate"));
+  *out = g;
+  return BRMPPI_OK;
+}
+
+brmppi_status brmppi_graph_launch(brmppi_graph* g, void* stream) {
+  if (!g || !g->exec) return BRMPPI_EINVAL;
+  brmppi_ctx* c = g->ctx;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e;
+  if (c->batch_pending && (e = cudaStreamWaitEvent(s, c->batch_done, 0)) != cudaSuccess)
+    return cuda_fail(c, e, "wait for the previous batch");
+  if ((e = cudaGraphLaunch(g->exec, s)) != cudaSuccess) return cuda_fail(c, e, "cudaGraphLaunch");
+  if ((e = cudaEventRecord(c->batch_done, s)) != cudaSuccess) return cuda_fail(c, e, "cudaEventRecord");
+  if ((e = cudaEventRecord(c->upload_done, s)) != cudaSuccess) return cuda_fail(c, e, "cudaEventRecord");
+  c->batch_pending = true;
+  return BRMPPI_OK;
+}
+
+void brmppi_graph_destroy(brmppi_graph* g) {
+  if (!g) return;
+  if (g->exec) {
+    if (g->ctx->batch_pending) cudaEventSynchronize(g->ctx->batch_done);
+    cudaGraphExecDestroy(g->exec);
+  }
+  if (g->graph) cudaGraphDestroy(g->graph);
+  cudaFreeHost(g->h_inst);
+  cudaFreeHost(g->h_work);
+  delete g;
+}
+
+brmppi_status brmppi_autotune(brmppi_ctx* c, const double* x0, const float* U_nom, const float* obs, int32_t n_obs,
+                              const float* path, int32_t n_pts, float ds, int32_t reps, void* stream) {
+  if (!c) return BRMPPI_EINVAL;
+  c->err.clear();
+  if (!x0 || !U_nom || !path || (n_obs > 0 && !obs)) return fail(c, BRMPPI_EINVAL, "NULL buffer");
+  brmppi_status st = check_sizes(c, n_obs, n_pts, ds);
+  if (st != BRMPPI_OK) return st;
+  if (reps < 1) reps = 1;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  const int P = philox_blocks(n_obs);
+  const int H = c->prm.H;
+  float* dU = c->d_out;
+  float* dT = dU + 3 * H;
+  Shape best;
+  float best_ms = 1e30f;
+  const brmppi::SmemCaps caps = make_caps(n_obs, n_pts, H);
+  for (int tps : {1, 2, 4, 8, 16, 32}) {
+    int bpt;
+    if (!pick_bpt(tps, P, &bpt)) continue;
+    for (int threads : {64, 128, 256}) {
+      if (threads < tps || threads / tps < 2) continue;
+      const int spb = threads / tps;
+      if (smem_bytes(caps, spb) > c->smem_limit) continue;
+      const size_t tiles = (static_cast<size_t>(c->prm.S) + spb - 1) / spb;
+      if (tiles > c->part_tiles || tiles * 3 * H * spb > c->uh_floats) continue;
+      Shape sh;
+      sh.tps = tps;
+      sh.bpt = bpt;
+      sh.threads = threads;
+      st = enqueue_plain(c, sh, x0, U_nom, obs, n_obs, path, n_pts, ds, 0, 0, dU, dT, nullptr, nullptr, nullptr, s);
+      if (st != BRMPPI_OK) continue;
+      cudaEventRecord(e0, s);
+      for (int r = 0; r < reps; ++r)
+        enqueue_plain(c, sh, x0, U_nom, obs, n_obs, path, n_pts, ds, 0, r, dU, dT, nullptr, nullptr, nullptr, s);
+      cudaEventRecord(e1, s);
+      cudaEventSynchronize(e1);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best_ms) {
+        best_ms = ms;
+        best = sh;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(c, e, "autotune");
+  if (best.tps == 0) return fail(c, BRMPPI_EINVAL, "no launch shape could run");
+  c->err.clear();
+  c->tuned[n_obs] = best;
+  return BRMPPI_OK;
+}
+
+brmppi_status brmppi_autotune_batch(brmppi_ctx* c, const brmppi_instance* inst, int32_t n, int32_t reps,
+                                    void* stream) {
+  if (!c) return BRMPPI_EINVAL;
+  c->err.clear();
+  if (reps < 1) reps = 1;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e;
+  if (c->batch_pending && (e = cudaEventSynchronize(c->batch_done)) != cudaSuccess) return cuda_fail(c, e, "sync");
+  c->batch_pending = false;
+  int max_P = 1;
+  for (int i = 0; inst && i < n; ++i) max_P = std::max(max_P, philox_blocks(inst[i].n_obs));
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  Shape best;
+  float best_ms = 1e30f;
+  std::string last_err;
+  for (int tps : {1, 2, 4, 8}) {
+    int bpt;
+    if (!pick_bpt(tps, max_P, &bpt)) continue;
+    for (int threads : {64, 128, 256}) {
+      if (threads / tps < kMinBatchSpb) continue;
+      Shape sh;
+      sh.tps = tps;
+      sh.bpt = bpt;
+      sh.threads = threads;
+      BatchPlan plan;
+      if (plan_batch(c, inst, n, &sh, c->h_inst, c->h_work, &plan) != BRMPPI_OK) {
+        last_err = c->err;
+        continue;
+      }
+      if (upload_and_launch(c, plan, c->h_inst, c->h_work, s) != BRMPPI_OK) {
+        last_err = c->err;
+        continue;
+      }
+      cudaEventRecord(e0, s);
+      for (int r = 0; r < reps; ++r) launch_batch(c, plan, s);
+      cudaEventRecord(e1, s);
+      cudaEventSynchronize(e1);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best_ms) {
+        best_ms = ms;
+        best = sh;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(c, e, "autotune");
+  if (best.tps == 0) return fail(c, BRMPPI_EINVAL, "no batch launch shape could run: " + last_err);
+  c->err.clear();
+  c->batch_tuned = true;
+  c->batch_shape = best;
+  return BRMPPI_OK;
 }
 
 brmppi_status brmppi_get_launch(brmppi_ctx* c, int32_t n_obs, int32_t* tps, int32_t* threads, int32_t* blocks) {
   if (!c) return BRMPPI_EINVAL;
   if (n_obs < 0 || n_obs > c->prm.max_obstacles) return fail(c, BRMPPI_EINVAL, "n_obs out of range");
-  Launch L;
-  if (!choose_launch(c, n_obs, c->prm.max_path_pts, &L)) return fail(c, BRMPPI_EINVAL, "no variant");
-  if (tps) *tps = L.tps;
-  if (threads) *threads = L.threads;
-  if (blocks) *blocks = L.blocks;
+  Shape sh;
+  if (!plain_shape(c, n_obs, c->prm.max_path_pts, &sh)) return fail(c, BRMPPI_EINVAL, "no launch shape");
+  const int spb = sh.threads / sh.tps;
+  if (tps) *tps = sh.tps;
+  if (threads) *threads = sh.threads;
+  if (blocks) *blocks = (c->prm.S + spb - 1) / spb;
   return BRMPPI_OK;
 }
 
