@@ -52,7 +52,7 @@
 extern "C" {
 #endif
 
-#define BRMPPI_ABI_VERSION 2u
+#define BRMPPI_ABI_VERSION 3u
 
 typedef enum {
   BRMPPI_OK = 0,
@@ -83,6 +83,11 @@ typedef struct brmppi_params {
   int32_t max_batch;             /* capacity: instances per batch (0 = no batches) */
   int32_t batch_threads_per_sample; /* batches: 0 = tuned/heuristic, else as above */
   int32_t batch_block_threads;   /* batches: 0 = tuned/heuristic, else as above */
+  int32_t max_vehicles;          /* serving: registered vehicles (0 = no serving loop) */
+  int32_t serve_lanes;           /* serving: batches in flight at once (0 = 2) */
+  int32_t serve_max_batch;       /* serving: solves per launch (0 = 64) */
+  int32_t serve_queue;           /* serving: request slots, further capped by free
+                                    device memory at create (0 = 1024) */
   float Ts, lambda;              /* sample time [s]; softmin temperature */
   float l1, lh, l2;              /* wheelbase, hitch offset, trailer length [m] */
   float dtheta_max, kappa;       /* hitch limit dtheta_max - kappa*v */
@@ -182,6 +187,50 @@ brmppi_status brmppi_autotune(brmppi_ctx *ctx, const double *x0_dev, const float
    later batches (used when params.batch_threads_per_sample == 0). */
 brmppi_status brmppi_autotune_batch(brmppi_ctx *ctx, const brmppi_instance *inst, int32_t n,
                                     int32_t reps, void *stream);
+
+/* ---- Serving loop (contexts created with max_vehicles > 0) ----------------
+   A scheduler thread admits submitted requests into batches as request slots
+   and batch lanes free up, launches each batch (one persistent launch) on its
+   lane's stream while earlier batches still run, and a completion thread
+   publishes results.  Every vehicle keeps its path, its warm-started nominal
+   sequence (shifted in place on the device after each solve) and its noise
+   counter (+1 per solve) resident; requests of one vehicle run in
+   submission order.  Results do not depend on what else is in a batch: the
+   serving launch shape (one lane per sample, 128-thread blocks) is fixed. */
+
+/* Register (or re-register) a vehicle: its reference path (host, n_pts*3),
+   initial nominal sequence (host H*3, NULL = zeros) and noise seed; its
+   counter starts at 0.  EBUSY while the vehicle has requests in flight. */
+brmppi_status brmppi_vehicle_register(brmppi_ctx *ctx, uint32_t vehicle_id, const float *path,
+                                      int32_t n_pts, float ds, const float *U_init, uint64_t seed);
+
+/* Queue one solve for a vehicle from host buffers (state x0[7], obstacles
+   n_obs*6); copies them before returning.  *ticket identifies the result.
+   EBUSY when no request slot is free (retry after polling). */
+brmppi_status brmppi_submit(brmppi_ctx *ctx, uint32_t vehicle_id, const double x0[7],
+                            const float *obs, int32_t n_obs, uint64_t *ticket);
+
+/* Non-blocking: EAGAIN until the ticket's solve has finished, then copies
+   U* (H*3) and, if traj_out is not NULL, the optimal trajectory, reports
+   the submit-to-completion latency, releases the ticket and returns the
+   solve's status.  EINVAL for an unknown or released ticket. */
+brmppi_status brmppi_poll(brmppi_ctx *ctx, uint64_t ticket, float *U_out, float *traj_out,
+                          double *latency_s);
+
+/* Snapshot / restore a vehicle's solver state (nominal sequence, seed,
+   counter): the whole state, so a restored vehicle replays bit-identically.
+   EBUSY while the vehicle has requests in flight. */
+brmppi_status brmppi_vehicle_export(brmppi_ctx *ctx, uint32_t vehicle_id, float *U_nom,
+                                    uint64_t *seed, uint64_t *counter);
+brmppi_status brmppi_vehicle_import(brmppi_ctx *ctx, uint32_t vehicle_id, const float *U_nom,
+                                    uint64_t seed, uint64_t counter);
+
+typedef struct brmppi_server_stats {
+  uint64_t submitted, completed, batches, solves_in_batches;
+  int32_t request_slots, lanes, max_inflight_batches, max_batch;
+} brmppi_server_stats;
+
+brmppi_status brmppi_server_stats_get(brmppi_ctx *ctx, brmppi_server_stats *out);
 
 /* Launch configuration the context will use for a solve with n_obs
    obstacles (after autotuning if requested). */

@@ -12,7 +12,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libbrmppi.so")
 
-BRMPPI_ABI_VERSION = 2
+BRMPPI_ABI_VERSION = 3
 BRMPPI_OK = 0
 BRMPPI_EINVAL = -1
 BRMPPI_ENOMEM = -2
@@ -31,7 +31,8 @@ EXPORTS = (
     "brmppi_default_params", "brmppi_create", "brmppi_destroy", "brmppi_last_error",
     "brmppi_solve", "brmppi_solve_device", "brmppi_solve_batch", "brmppi_batch_capture",
     "brmppi_graph_launch", "brmppi_graph_destroy", "brmppi_autotune", "brmppi_autotune_batch",
-    "brmppi_get_launch", "brmppi_transfer_bytes",
+    "brmppi_get_launch", "brmppi_transfer_bytes", "brmppi_vehicle_register", "brmppi_submit",
+    "brmppi_poll", "brmppi_vehicle_export", "brmppi_vehicle_import", "brmppi_server_stats_get",
 )
 
 
@@ -43,6 +44,8 @@ class brmppi_params(ctypes.Structure):
         ("flags", ctypes.c_int32), ("threads_per_sample", ctypes.c_int32),
         ("block_threads", ctypes.c_int32), ("max_batch", ctypes.c_int32),
         ("batch_threads_per_sample", ctypes.c_int32), ("batch_block_threads", ctypes.c_int32),
+        ("max_vehicles", ctypes.c_int32), ("serve_lanes", ctypes.c_int32),
+        ("serve_max_batch", ctypes.c_int32), ("serve_queue", ctypes.c_int32),
         ("Ts", ctypes.c_float), ("lambda_", ctypes.c_float),
         ("l1", ctypes.c_float), ("lh", ctypes.c_float), ("l2", ctypes.c_float),
         ("dtheta_max", ctypes.c_float), ("kappa", ctypes.c_float), ("r_inflate", ctypes.c_float),
@@ -64,6 +67,15 @@ class brmppi_instance(ctypes.Structure):
         ("seed", ctypes.c_uint64), ("counter", ctypes.c_uint64),
         ("U_out", ctypes.c_void_p), ("traj_out", ctypes.c_void_p), ("J_out", ctypes.c_void_p),
         ("U_next", ctypes.c_void_p), ("status", ctypes.c_void_p),
+    ]
+
+
+class brmppi_server_stats(ctypes.Structure):
+    _fields_ = [
+        ("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64),
+        ("batches", ctypes.c_uint64), ("solves_in_batches", ctypes.c_uint64),
+        ("request_slots", ctypes.c_int32), ("lanes", ctypes.c_int32),
+        ("max_inflight_batches", ctypes.c_int32), ("max_batch", ctypes.c_int32),
     ]
 
 
@@ -114,6 +126,18 @@ def load() -> ctypes.CDLL:
             "brmppi_autotune_batch": (ctypes.c_int, [_VP, ctypes.POINTER(brmppi_instance),
                                                      ctypes.c_int32, ctypes.c_int32, _VP]),
             "brmppi_get_launch": (ctypes.c_int, [_VP, ctypes.c_int32, _I32, _I32, _I32]),
+            "brmppi_vehicle_register": (ctypes.c_int, [_VP, ctypes.c_uint32, _F, ctypes.c_int32,
+                                                       ctypes.c_float, _F, ctypes.c_uint64]),
+            "brmppi_submit": (ctypes.c_int, [_VP, ctypes.c_uint32, _D, _F, ctypes.c_int32,
+                                             ctypes.POINTER(ctypes.c_uint64)]),
+            "brmppi_poll": (ctypes.c_int, [_VP, ctypes.c_uint64, _F, _F,
+                                           ctypes.POINTER(ctypes.c_double)]),
+            "brmppi_vehicle_export": (ctypes.c_int, [_VP, ctypes.c_uint32, _F,
+                                                     ctypes.POINTER(ctypes.c_uint64),
+                                                     ctypes.POINTER(ctypes.c_uint64)]),
+            "brmppi_vehicle_import": (ctypes.c_int, [_VP, ctypes.c_uint32, _F, ctypes.c_uint64,
+                                                     ctypes.c_uint64]),
+            "brmppi_server_stats_get": (ctypes.c_int, [_VP, ctypes.POINTER(brmppi_server_stats)]),
             "brmppi_transfer_bytes": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.c_int32,
                                                      ctypes.POINTER(ctypes.c_uint64),
                                                      ctypes.POINTER(ctypes.c_uint64)]),
@@ -140,8 +164,9 @@ def brmppi_default_params() -> brmppi_params:
 
 def params_from_dict(d: dict, max_obstacles: int = 16, max_path_pts: int = 4096,
                      threads_per_sample: int = 0, block_threads: int = 0, max_batch: int = 0,
-                     batch_threads_per_sample: int = 0,
-                     batch_block_threads: int = 0) -> brmppi_params:
+                     batch_threads_per_sample: int = 0, batch_block_threads: int = 0,
+                     max_vehicles: int = 0, serve_lanes: int = 0, serve_max_batch: int = 0,
+                     serve_queue: int = 0) -> brmppi_params:
     """brmppi_params from the parameter dict of ``scenarios`` (values are
     rounded to binary32 by the struct)."""
     p = brmppi_default_params()
@@ -164,6 +189,10 @@ def params_from_dict(d: dict, max_obstacles: int = 16, max_path_pts: int = 4096,
     p.max_batch = int(max_batch)
     p.batch_threads_per_sample = int(batch_threads_per_sample)
     p.batch_block_threads = int(batch_block_threads)
+    p.max_vehicles = int(max_vehicles)
+    p.serve_lanes = int(serve_lanes)
+    p.serve_max_batch = int(serve_max_batch)
+    p.serve_queue = int(serve_queue)
     p.abi_version = BRMPPI_ABI_VERSION
     return p
 
@@ -337,14 +366,16 @@ class Solver:
     def __init__(self, params: dict, device: int = 0, max_obstacles: int = 16,
                  max_path_pts: int = 4096, threads_per_sample: int = 0, block_threads: int = 0,
                  max_batch: int = 0, batch_threads_per_sample: int = 0,
-                 batch_block_threads: int = 0):
+                 batch_block_threads: int = 0, max_vehicles: int = 0, serve_lanes: int = 0,
+                 serve_max_batch: int = 0, serve_queue: int = 0):
         self.ctx = None
         self.params = dict(params)
         self.S = int(params["S"])
         self.H = int(params["H"])
         self._p = params_from_dict(params, max_obstacles, max_path_pts, threads_per_sample,
                                    block_threads, max_batch, batch_threads_per_sample,
-                                   batch_block_threads)
+                                   batch_block_threads, max_vehicles, serve_lanes,
+                                   serve_max_batch, serve_queue)
         self.ctx = brmppi_create(self._p, device)
 
     def close(self):
@@ -388,6 +419,60 @@ class Solver:
         st = brmppi_autotune(self.ctx, x0, U_nom, obs, path, ds, reps, stream)
         if st != BRMPPI_OK:
             raise BrmppiError(st, brmppi_last_error(self.ctx))
+
+    # ---- serving loop
+    def register(self, vehicle_id: int, path, ds: float, U_init=None, seed: int = 0):
+        path = _f32(path).reshape(-1)
+        U = None if U_init is None else _f32(U_init, 3 * self.H)
+        st = load().brmppi_vehicle_register(self.ctx, int(vehicle_id), path.ctypes.data_as(_F),
+                                            path.size // 3, float(ds),
+                                            None if U is None else U.ctypes.data_as(_F),
+                                            int(seed) & (2**64 - 1))
+        if st != BRMPPI_OK:
+            raise BrmppiError(st, brmppi_last_error(self.ctx))
+
+    def submit(self, vehicle_id: int, x0, obs=None):
+        """Queue one solve; returns (status, ticket)."""
+        x0 = np.ascontiguousarray(x0, dtype=np.float64)
+        ob = np.zeros(0, np.float32) if obs is None else _f32(obs).reshape(-1)
+        t = ctypes.c_uint64()
+        st = load().brmppi_submit(self.ctx, int(vehicle_id), x0.ctypes.data_as(_D),
+                                  ob.ctypes.data_as(_F) if ob.size else None, ob.size // 6,
+                                  ctypes.byref(t))
+        return st, t.value
+
+    def poll(self, ticket: int, want_traj: bool = False):
+        """(status, U, traj, latency_s); status EAGAIN while running."""
+        U = np.empty((self.H, 3), np.float32)
+        traj = np.empty((self.H + 1, 7), np.float32) if want_traj else None
+        lat = ctypes.c_double()
+        st = load().brmppi_poll(self.ctx, int(ticket), U.ctypes.data_as(_F),
+                                traj.ctypes.data_as(_F) if traj is not None else None,
+                                ctypes.byref(lat))
+        return st, U, traj, lat.value
+
+    def vehicle_export(self, vehicle_id: int):
+        U = np.empty((self.H, 3), np.float32)
+        seed, ctr = ctypes.c_uint64(), ctypes.c_uint64()
+        st = load().brmppi_vehicle_export(self.ctx, int(vehicle_id), U.ctypes.data_as(_F),
+                                          ctypes.byref(seed), ctypes.byref(ctr))
+        if st != BRMPPI_OK:
+            raise BrmppiError(st, brmppi_last_error(self.ctx))
+        return U, seed.value, ctr.value
+
+    def vehicle_import(self, vehicle_id: int, U_nom, seed: int, counter: int):
+        U = _f32(U_nom, 3 * self.H)
+        st = load().brmppi_vehicle_import(self.ctx, int(vehicle_id), U.ctypes.data_as(_F),
+                                          int(seed) & (2**64 - 1), int(counter) & (2**64 - 1))
+        if st != BRMPPI_OK:
+            raise BrmppiError(st, brmppi_last_error(self.ctx))
+
+    def server_stats(self) -> dict:
+        out = brmppi_server_stats()
+        st = load().brmppi_server_stats_get(self.ctx, ctypes.byref(out))
+        if st != BRMPPI_OK:
+            raise BrmppiError(st, brmppi_last_error(self.ctx))
+        return {name: getattr(out, name) for name, _ in brmppi_server_stats._fields_}
 
     def autotune_batch(self, insts, reps=3, stream=None):
         st = brmppi_autotune_batch(self.ctx, insts, reps, stream)

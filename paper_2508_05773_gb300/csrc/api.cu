@@ -15,73 +15,17 @@
 #include <string>
 #include <vector>
 
-#include "brmppi.h"
-#include "launch.h"
+#include "internal.h"
+
+using namespace brmppi_host;
+
+namespace brmppi_host {
 
 namespace {
-
-struct Shape {
-  int tps = 0, bpt = 0, threads = 0;
-};
-
-}  // namespace
-
-struct brmppi_ctx {
-  brmppi_params prm{};
-  int device = 0;
-  int num_sms = 0;
-  cudaStream_t stream = nullptr;
-  size_t smem_limit = 0;
-  // plain solves
-  unsigned char* d_in = nullptr;  // x0 | U_nom | obs | path
-  float* d_out = nullptr;         // U | traj | status
-  float* d_J = nullptr;
-  float* d_part = nullptr;
-  unsigned int* d_sync = nullptr;  // finished tiles, error bits
-  float* d_uh = nullptr;
-  unsigned char* h_in = nullptr;
-  float* h_out = nullptr;
-  size_t off_unom = 0, off_obs = 0, off_path = 0, in_bytes = 0, out_floats = 0;
-  size_t part_stride = 0, part_tiles = 0, uh_floats = 0;
-  std::map<int, Shape> tuned;  // obstacle count -> fastest plain shape
-  // batches
-  brmppi::Inst* d_inst = nullptr;
-  int2* d_work = nullptr;
-  unsigned int* d_work_ctr = nullptr;
-  float* d_bpart = nullptr;
-  unsigned int* d_bsync = nullptr;
-  float* d_buh = nullptr;
-  brmppi::Inst* h_inst = nullptr;
-  int2* h_work = nullptr;
-  cudaEvent_t upload_done = nullptr;  // host staging free again
-  cudaEvent_t batch_done = nullptr;   // device table free again
-  bool batch_pending = false;
-  size_t bpart_floats = 0, buh_floats = 0, max_work = 0;
-  bool batch_tuned = false;
-  Shape batch_shape;
-  std::string err;
-};
-
-struct brmppi_graph {
-  brmppi_ctx* ctx = nullptr;
-  cudaGraph_t graph = nullptr;
-  cudaGraphExec_t exec = nullptr;
-  brmppi::Inst* h_inst = nullptr;
-  int2* h_work = nullptr;
-};
-
-namespace {
-
 std::mutex g_err_mu;
 std::string g_create_err;
 
-constexpr int kMaxObstacles = 124;  // ceil((4 + n)/4) <= 32 Philox blocks
-constexpr int kMaxPathPts = 12000;
-constexpr int kMaxH = 1024;
-constexpr int kMinThreads = 64;
-constexpr int kMaxThreads = 512;
-constexpr int kMinBatchSpb = 16;  // smallest tile of a batch launch
-constexpr int kMaxResidentThreads = 2048;
+}  // namespace
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
@@ -100,11 +44,15 @@ brmppi_status cuda_fail(brmppi_ctx* c, cudaError_t e, const char* what) {
   return fail(c, e == cudaErrorMemoryAllocation ? BRMPPI_ENOMEM : BRMPPI_ECUDA, m);
 }
 
-bool is_pow2_tps(int t) { return t == 1 || t == 2 || t == 4 || t == 8 || t == 16 || t == 32; }
-
 int philox_blocks(int n_obs) { return (4 + n_obs + 3) / 4; }  // d = 3 + (1 + n_obs)
 
+namespace {
+
+bool is_pow2_tps(int t) { return t == 1 || t == 2 || t == 4 || t == 8 || t == 16 || t == 32; }
+
 bool valid_threads(int t) { return t == 0 || (t >= kMinThreads && t <= kMaxThreads && t % 32 == 0); }
+
+}  // namespace
 
 std::string check_params(const brmppi_params* p) {
   if (!p) return "params is NULL";
@@ -121,6 +69,10 @@ std::string check_params(const brmppi_params* p) {
   if (!valid_threads(p->block_threads) || !valid_threads(p->batch_block_threads))
     return "block_threads must be 0 or a multiple of 32 in [64, 512]";
   if (p->max_batch < 0 || p->max_batch > 65536) return "max_batch must be in [0, 65536]";
+  if (p->max_vehicles < 0 || p->max_vehicles > 65536) return "max_vehicles must be in [0, 65536]";
+  if (p->serve_lanes < 0 || p->serve_lanes > 16) return "serve_lanes must be in [0, 16]";
+  if (p->serve_max_batch < 0 || p->serve_max_batch > 4096) return "serve_max_batch must be in [0, 4096]";
+  if (p->serve_queue < 0 || p->serve_queue > (1 << 20)) return "serve_queue must be in [0, 2^20]";
   const float pos[] = {p->Ts, p->lambda, p->l1, p->l2, p->h_floor};
   for (float v : pos)
     if (!(v > 0.f) || !std::isfinite(v)) return "Ts, lambda, l1, l2, h_floor must be positive and finite";
@@ -331,12 +283,46 @@ brmppi_status enqueue_plain(brmppi_ctx* c, const Shape& sh, const double* x0, co
 }
 
 // ------------------------------------------------------------- batches
-struct BatchPlan {
-  Shape shape;
-  int n_inst = 0, n_work = 0, grid = 0, Hmax = 0;
-  brmppi::SmemCaps caps{};
-  size_t smem = 0;
-};
+cudaError_t lane_alloc(Lane& L, int max_batch, size_t S, size_t H, int num_sms, size_t part_stride) {
+  const size_t nb = static_cast<size_t>(max_batch);
+  const size_t tiles_per_inst = (S + kMinBatchSpb - 1) / kMinBatchSpb;
+  L.max_batch = max_batch;
+  L.max_work = nb * tiles_per_inst;
+  L.bpart_floats = L.max_work * part_stride;
+  L.buh_floats = static_cast<size_t>(num_sms) * kMaxResidentThreads * 3 * H;
+  cudaError_t e;
+  if ((e = cudaMalloc(&L.d_inst, sizeof(brmppi::Inst) * nb)) != cudaSuccess) return e;
+  if ((e = cudaMalloc(&L.d_work, sizeof(int2) * L.max_work)) != cudaSuccess) return e;
+  if ((e = cudaMalloc(&L.d_work_ctr, sizeof(unsigned int) * 2)) != cudaSuccess) return e;
+  if ((e = cudaMemset(L.d_work_ctr, 0, sizeof(unsigned int) * 2)) != cudaSuccess) return e;
+  if ((e = cudaMalloc(&L.d_bpart, sizeof(float) * L.bpart_floats)) != cudaSuccess) return e;
+  if ((e = cudaMalloc(&L.d_bsync, sizeof(unsigned int) * 2 * nb)) != cudaSuccess) return e;
+  if ((e = cudaMemset(L.d_bsync, 0, sizeof(unsigned int) * 2 * nb)) != cudaSuccess) return e;
+  if ((e = cudaMalloc(&L.d_buh, sizeof(float) * L.buh_floats)) != cudaSuccess) return e;
+  if ((e = cudaMallocHost(&L.h_inst, sizeof(brmppi::Inst) * nb)) != cudaSuccess) return e;
+  if ((e = cudaMallocHost(&L.h_work, sizeof(int2) * L.max_work)) != cudaSuccess) return e;
+  if ((e = cudaEventCreateWithFlags(&L.upload_done, cudaEventDisableTiming)) != cudaSuccess) return e;
+  if ((e = cudaEventCreateWithFlags(&L.batch_done, cudaEventDisableTiming)) != cudaSuccess) return e;
+  return cudaSuccess;
+}
+
+void lane_free(Lane& L) {
+  if (L.pending && L.batch_done) cudaEventSynchronize(L.batch_done);
+  cudaFree(L.d_inst);
+  cudaFree(L.d_work);
+  cudaFree(L.d_work_ctr);
+  cudaFree(L.d_bpart);
+  cudaFree(L.d_bsync);
+  cudaFree(L.d_buh);
+  cudaFreeHost(L.h_inst);
+  cudaFreeHost(L.h_work);
+  if (L.upload_done) cudaEventDestroy(L.upload_done);
+  if (L.batch_done) cudaEventDestroy(L.batch_done);
+  if (L.stream) cudaStreamDestroy(L.stream);
+  L = Lane();
+}
+
+namespace {
 
 bool batch_shape_default(const brmppi_ctx* c, int max_P, Shape* out) {
   Shape s;
@@ -357,12 +343,29 @@ bool batch_shape_default(const brmppi_ctx* c, int max_P, Shape* out) {
   return true;
 }
 
+brmppi_status launch_batch(brmppi_ctx* c, Lane& L, const BatchPlan& plan, cudaStream_t stream) {
+  brmppi::LaunchDesc D{};
+  D.inst = L.d_inst;
+  D.work = L.d_work;
+  D.n_work = plan.n_work;
+  D.work_ctr = L.d_work_ctr;
+  D.uh = L.d_buh;
+  D.uh_stride = 3 * plan.Hmax * (plan.shape.threads / plan.shape.tps);
+  D.caps = plan.caps;
+  cudaError_t e = brmppi::launch_solve(plan.shape.tps, plan.shape.bpt, plan.grid, plan.shape.threads, plan.smem,
+                                       stream, make_kconst(c->prm), D);
+  if (e != cudaSuccess) return cuda_fail(c, e, "batch kernel launch");
+  return BRMPPI_OK;
+}
+
+}  // namespace
+
 // Validate the instances, fill the instance table and the longest-first
 // work list (host staging), and size the launch.
-brmppi_status plan_batch(brmppi_ctx* c, const brmppi_instance* inst, int32_t n, const Shape* forced,
+brmppi_status plan_batch(brmppi_ctx* c, Lane& L, const brmppi_instance* inst, int32_t n, const Shape* forced,
                          brmppi::Inst* h_inst, int2* h_work, BatchPlan* plan) {
-  if (c->prm.max_batch <= 0) return fail(c, BRMPPI_EINVAL, "context created without batch capacity (max_batch)");
-  if (!inst || n < 1 || n > c->prm.max_batch) return fail(c, BRMPPI_EINVAL, "n out of [1, max_batch]");
+  if (L.max_batch <= 0) return fail(c, BRMPPI_EINVAL, "context created without batch capacity (max_batch)");
+  if (!inst || n < 1 || n > L.max_batch) return fail(c, BRMPPI_EINVAL, "n out of [1, max_batch]");
   int max_P = 1, Hmax = 1, nobs_max = 0, npts_max = 2;
   for (int i = 0; i < n; ++i) {
     const brmppi_instance& q = inst[i];
@@ -380,6 +383,7 @@ brmppi_status plan_batch(brmppi_ctx* c, const brmppi_instance* inst, int32_t n, 
   Shape sh;
   if (forced) {
     sh = *forced;
+    if (!pick_bpt(sh.tps, max_P, &sh.bpt)) return fail(c, BRMPPI_EINVAL, "no variant for this team width");
   } else if (!batch_shape_default(c, max_P, &sh)) {
     return fail(c, BRMPPI_EINVAL, "no batch launch shape for these instances");
   }
@@ -389,19 +393,20 @@ brmppi_status plan_batch(brmppi_ctx* c, const brmppi_instance* inst, int32_t n, 
   if (smem > c->smem_limit) return fail(c, BRMPPI_EINVAL, "batch tables exceed shared memory");
   size_t pool = 0;
   std::vector<std::pair<long long, int2>> items;
+  items.reserve(L.max_work);
   for (int i = 0; i < n; ++i) {
     const brmppi_instance& q = inst[i];
     const int H = q.H;
     brmppi::Inst in = make_inst(q.x0, q.U_nom, q.obs, q.n_obs, q.path, q.n_pts, q.ds, q.S, H, q.seed, q.counter,
-                                q.U_out, q.traj_out, q.J_out, q.U_next, q.status, nullptr, c->d_bsync + 2 * i, spb);
-    in.part = c->d_bpart + pool;
+                                q.U_out, q.traj_out, q.J_out, q.U_next, q.status, nullptr, L.d_bsync + 2 * i, spb);
+    in.part = L.d_bpart + pool;
     pool += static_cast<size_t>(in.tiles) * static_cast<size_t>(in.part_stride);
-    if (pool > c->bpart_floats) return fail(c, BRMPPI_EINVAL, "batch partials exceed the context's pool");
+    if (pool > L.bpart_floats) return fail(c, BRMPPI_EINVAL, "batch partials exceed the context's pool");
     h_inst[i] = in;
     const long long cost = static_cast<long long>(H) * (8 + q.n_obs);
     for (int t = 0; t < in.tiles; ++t) items.push_back({cost, make_int2(i, t)});
   }
-  if (items.size() > c->max_work) return fail(c, BRMPPI_EINVAL, "too many work items");
+  if (items.size() > L.max_work) return fail(c, BRMPPI_EINVAL, "too many work items");
   std::stable_sort(items.begin(), items.end(),
                    [](const std::pair<long long, int2>& a, const std::pair<long long, int2>& b) {
                      return a.first > b.first;
@@ -411,7 +416,7 @@ brmppi_status plan_batch(brmppi_ctx* c, const brmppi_instance* inst, int32_t n, 
   if (occ < 1) return fail(c, BRMPPI_EINVAL, "batch launch shape cannot be resident");
   int grid = occ * c->num_sms;
   if (grid > static_cast<int>(items.size())) grid = static_cast<int>(items.size());
-  if (static_cast<size_t>(grid) * 3 * Hmax * spb > c->buh_floats)
+  if (static_cast<size_t>(grid) * 3 * Hmax * spb > L.buh_floats)
     return fail(c, BRMPPI_EINVAL, "batch history scratch too small");
   plan->shape = sh;
   plan->n_inst = n;
@@ -423,36 +428,21 @@ brmppi_status plan_batch(brmppi_ctx* c, const brmppi_instance* inst, int32_t n, 
   return BRMPPI_OK;
 }
 
-brmppi_status launch_batch(brmppi_ctx* c, const BatchPlan& plan, cudaStream_t stream) {
-  brmppi::LaunchDesc L{};
-  L.inst = c->d_inst;
-  L.work = c->d_work;
-  L.n_work = plan.n_work;
-  L.work_ctr = c->d_work_ctr;
-  L.uh = c->d_buh;
-  L.uh_stride = 3 * plan.Hmax * (plan.shape.threads / plan.shape.tps);
-  L.caps = plan.caps;
-  cudaError_t e = brmppi::launch_solve(plan.shape.tps, plan.shape.bpt, plan.grid, plan.shape.threads, plan.smem,
-                                       stream, make_kconst(c->prm), L);
-  if (e != cudaSuccess) return cuda_fail(c, e, "batch kernel launch");
-  return BRMPPI_OK;
-}
-
-brmppi_status upload_and_launch(brmppi_ctx* c, const BatchPlan& plan, const brmppi::Inst* h_inst,
+brmppi_status upload_and_launch(brmppi_ctx* c, Lane& L, const BatchPlan& plan, const brmppi::Inst* h_inst,
                                 const int2* h_work, cudaStream_t stream) {
   cudaError_t e;
-  if (c->batch_pending && (e = cudaStreamWaitEvent(stream, c->batch_done, 0)) != cudaSuccess)
+  if (L.pending && (e = cudaStreamWaitEvent(stream, L.batch_done, 0)) != cudaSuccess)
     return cuda_fail(c, e, "wait for the previous batch");
-  if ((e = cudaMemcpyAsync(c->d_inst, h_inst, sizeof(brmppi::Inst) * plan.n_inst, cudaMemcpyHostToDevice,
+  if ((e = cudaMemcpyAsync(L.d_inst, h_inst, sizeof(brmppi::Inst) * plan.n_inst, cudaMemcpyHostToDevice,
                            stream)) != cudaSuccess)
     return cuda_fail(c, e, "instance table upload");
-  if ((e = cudaMemcpyAsync(c->d_work, h_work, sizeof(int2) * plan.n_work, cudaMemcpyHostToDevice, stream)) !=
+  if ((e = cudaMemcpyAsync(L.d_work, h_work, sizeof(int2) * plan.n_work, cudaMemcpyHostToDevice, stream)) !=
       cudaSuccess)
     return cuda_fail(c, e, "work list upload");
-  return launch_batch(c, plan, stream);
+  return launch_batch(c, L, plan, stream);
 }
 
-}  // namespace
+}  // namespace brmppi_host
 
 extern "C" {
 
@@ -550,32 +540,16 @@ brmppi_status brmppi_create(const brmppi_params* p, int device, brmppi_ctx** out
   if ((e = cudaMallocHost(&c->h_in, c->in_bytes)) != cudaSuccess) return bail(e, "cudaMallocHost(in)");
   if ((e = cudaMallocHost(&c->h_out, sizeof(float) * c->out_floats)) != cudaSuccess)
     return bail(e, "cudaMallocHost(out)");
-  if (p->max_batch > 0) {
-    const size_t nb = static_cast<size_t>(p->max_batch);
-    const size_t tiles_per_inst = (S + kMinBatchSpb - 1) / kMinBatchSpb;
-    c->max_work = nb * tiles_per_inst;
-    c->bpart_floats = c->max_work * c->part_stride;
-    c->buh_floats = static_cast<size_t>(c->num_sms) * kMaxResidentThreads * 3 * H;
-    if ((e = cudaMalloc(&c->d_inst, sizeof(brmppi::Inst) * nb)) != cudaSuccess) return bail(e, "cudaMalloc(table)");
-    if ((e = cudaMalloc(&c->d_work, sizeof(int2) * c->max_work)) != cudaSuccess) return bail(e, "cudaMalloc(work)");
-    if ((e = cudaMalloc(&c->d_work_ctr, sizeof(unsigned int) * 2)) != cudaSuccess)
-      return bail(e, "cudaMalloc(work counter)");
-    if ((e = cudaMemset(c->d_work_ctr, 0, sizeof(unsigned int) * 2)) != cudaSuccess) return bail(e, "cudaMemset");
-    if ((e = cudaMalloc(&c->d_bpart, sizeof(float) * c->bpart_floats)) != cudaSuccess)
-      return bail(e, "cudaMalloc(batch partials)");
-    if ((e = cudaMalloc(&c->d_bsync, sizeof(unsigned int) * 2 * nb)) != cudaSuccess)
-      return bail(e, "cudaMalloc(batch sync)");
-    if ((e = cudaMemset(c->d_bsync, 0, sizeof(unsigned int) * 2 * nb)) != cudaSuccess) return bail(e, "cudaMemset");
-    if ((e = cudaMalloc(&c->d_buh, sizeof(float) * c->buh_floats)) != cudaSuccess)
-      return bail(e, "cudaMalloc(batch history)");
-    if ((e = cudaMallocHost(&c->h_inst, sizeof(brmppi::Inst) * nb)) != cudaSuccess)
-      return bail(e, "cudaMallocHost(table)");
-    if ((e = cudaMallocHost(&c->h_work, sizeof(int2) * c->max_work)) != cudaSuccess)
-      return bail(e, "cudaMallocHost(work)");
-    if ((e = cudaEventCreateWithFlags(&c->upload_done, cudaEventDisableTiming)) != cudaSuccess)
-      return bail(e, "cudaEventCreate");
-    if ((e = cudaEventCreateWithFlags(&c->batch_done, cudaEventDisableTiming)) != cudaSuccess)
-      return bail(e, "cudaEventCreate");
+  if (p->max_batch > 0 && (e = lane_alloc(c->batch, p->max_batch, S, H, c->num_sms, c->part_stride)) != cudaSuccess)
+    return bail(e, "batch buffers");
+  if (p->max_vehicles > 0) {
+    if ((e = cudaDeviceSynchronize()) != cudaSuccess) return bail(e, "cudaDeviceSynchronize");
+    brmppi_status st = server_create(c);
+    if (st != BRMPPI_OK) {
+      std::string m = c->err;
+      brmppi_destroy(c);
+      return fail(nullptr, st, "serving loop: " + m);
+    }
   }
   if ((e = cudaDeviceSynchronize()) != cudaSuccess) return bail(e, "cudaDeviceSynchronize");
   *out = c;
@@ -585,26 +559,17 @@ brmppi_status brmppi_create(const brmppi_params* p, int device, brmppi_ctx** out
 void brmppi_destroy(brmppi_ctx* c) {
   if (!c) return;
   cudaSetDevice(c->device);
+  if (c->server) server_destroy(c);
   if (c->stream) cudaStreamSynchronize(c->stream);
-  if (c->batch_pending && c->batch_done) cudaEventSynchronize(c->batch_done);
+  lane_free(c->batch);
   cudaFree(c->d_in);
   cudaFree(c->d_out);
   cudaFree(c->d_J);
   cudaFree(c->d_part);
   cudaFree(c->d_uh);
   cudaFree(c->d_sync);
-  cudaFree(c->d_inst);
-  cudaFree(c->d_work);
-  cudaFree(c->d_work_ctr);
-  cudaFree(c->d_bpart);
-  cudaFree(c->d_bsync);
-  cudaFree(c->d_buh);
   cudaFreeHost(c->h_in);
   cudaFreeHost(c->h_out);
-  cudaFreeHost(c->h_inst);
-  cudaFreeHost(c->h_work);
-  if (c->upload_done) cudaEventDestroy(c->upload_done);
-  if (c->batch_done) cudaEventDestroy(c->batch_done);
   if (c->stream) cudaStreamDestroy(c->stream);
   delete c;
 }
@@ -688,18 +653,19 @@ brmppi_status brmppi_solve_batch(brmppi_ctx* c, const brmppi_instance* inst, int
   if (!c) return BRMPPI_EINVAL;
   c->err.clear();
   cudaError_t e;
-  if (c->batch_pending && (e = cudaEventSynchronize(c->upload_done)) != cudaSuccess)
+  Lane& L = c->batch;
+  if (L.pending && (e = cudaEventSynchronize(L.upload_done)) != cudaSuccess)
     return cuda_fail(c, e, "wait for the previous upload");
   BatchPlan plan;
-  brmppi_status st = plan_batch(c, inst, n, nullptr, c->h_inst, c->h_work, &plan);
+  brmppi_status st = plan_batch(c, L, inst, n, nullptr, L.h_inst, L.h_work, &plan);
   if (st != BRMPPI_OK) return st;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  st = upload_and_launch(c, plan, c->h_inst, c->h_work, s);
+  st = upload_and_launch(c, L, plan, L.h_inst, L.h_work, s);
   if (st != BRMPPI_OK) return st;
   // the uploads are consumed once the kernel has finished
-  if ((e = cudaEventRecord(c->upload_done, s)) != cudaSuccess) return cuda_fail(c, e, "cudaEventRecord");
-  if ((e = cudaEventRecord(c->batch_done, s)) != cudaSuccess) return cuda_fail(c, e, "cudaEventRecord");
-  c->batch_pending = true;
+  if ((e = cudaEventRecord(L.upload_done, s)) != cudaSuccess) return cuda_fail(c, e, "cudaEventRecord");
+  if ((e = cudaEventRecord(L.batch_done, s)) != cudaSuccess) return cuda_fail(c, e, "cudaEventRecord");
+  L.pending = true;
   return BRMPPI_OK;
 }
 
@@ -707,7 +673,8 @@ brmppi_status brmppi_batch_capture(brmppi_ctx* c, const brmppi_instance* inst, i
   if (!c || !out) return BRMPPI_EINVAL;
   c->err.clear();
   *out = nullptr;
-  if (c->prm.max_batch <= 0) return fail(c, BRMPPI_EINVAL, "context created without batch capacity (max_batch)");
+  Lane& L = c->batch;
+  if (L.max_batch <= 0) return fail(c, BRMPPI_EINVAL, "context created without batch capacity (max_batch)");
   brmppi_graph* g = new (std::nothrow) brmppi_graph();
   if (!g) return fail(c, BRMPPI_ENOMEM, "host allocation failed");
   g->ctx = c;
@@ -716,19 +683,19 @@ brmppi_status brmppi_batch_capture(brmppi_ctx* c, const brmppi_instance* inst, i
     brmppi_graph_destroy(g);
     return st;
   };
-  if ((e = cudaMallocHost(&g->h_inst, sizeof(brmppi::Inst) * c->prm.max_batch)) != cudaSuccess)
+  if ((e = cudaMallocHost(&g->h_inst, sizeof(brmppi::Inst) * L.max_batch)) != cudaSuccess)
     return bail(cuda_fail(c, e, "cudaMallocHost(graph table)"));
-  if ((e = cudaMallocHost(&g->h_work, sizeof(int2) * c->max_work)) != cudaSuccess)
+  if ((e = cudaMallocHost(&g->h_work, sizeof(int2) * L.max_work)) != cudaSuccess)
     return bail(cuda_fail(c, e, "cudaMallocHost(graph work)"));
   BatchPlan plan;
-  brmppi_status st = plan_batch(c, inst, n, nullptr, g->h_inst, g->h_work, &plan);
+  brmppi_status st = plan_batch(c, L, inst, n, nullptr, g->h_inst, g->h_work, &plan);
   if (st != BRMPPI_OK) return bail(st);
-  if (c->batch_pending && (e = cudaEventSynchronize(c->batch_done)) != cudaSuccess)
+  if (L.pending && (e = cudaEventSynchronize(L.batch_done)) != cudaSuccess)
     return bail(cuda_fail(c, e, "wait for the previous batch"));
-  c->batch_pending = false;
+  L.pending = false;
   if ((e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
     return bail(cuda_fail(c, e, "cudaStreamBeginCapture"));
-  st = upload_and_launch(c, plan, g->h_inst, g->h_work, c->stream);
+  st = upload_and_launch(c, L, plan, g->h_inst, g->h_work, c->stream);
   e = cudaStreamEndCapture(c->stream, &g->graph);
   if (st != BRMPPI_OK) return bail(st);
   if (e != cudaSuccess) return bail(cuda_fail(c, e, "cudaStreamEndCapture"));
@@ -741,21 +708,22 @@ brmppi_status brmppi_batch_capture(brmppi_ctx* c, const brmppi_instance* inst, i
 brmppi_status brmppi_graph_launch(brmppi_graph* g, void* stream) {
   if (!g || !g->exec) return BRMPPI_EINVAL;
   brmppi_ctx* c = g->ctx;
+  Lane& L = c->batch;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   cudaError_t e;
-  if (c->batch_pending && (e = cudaStreamWaitEvent(s, c->batch_done, 0)) != cudaSuccess)
+  if (L.pending && (e = cudaStreamWaitEvent(s, L.batch_done, 0)) != cudaSuccess)
     return cuda_fail(c, e, "wait for the previous batch");
   if ((e = cudaGraphLaunch(g->exec, s)) != cudaSuccess) return cuda_fail(c, e, "cudaGraphLaunch");
-  if ((e = cudaEventRecord(c->batch_done, s)) != cudaSuccess) return cuda_fail(c, e, "cudaEventRecord");
-  if ((e = cudaEventRecord(c->upload_done, s)) != cudaSuccess) return cuda_fail(c, e, "cudaEventRecord");
-  c->batch_pending = true;
+  if ((e = cudaEventRecord(L.batch_done, s)) != cudaSuccess) return cuda_fail(c, e, "cudaEventRecord");
+  if ((e = cudaEventRecord(L.upload_done, s)) != cudaSuccess) return cuda_fail(c, e, "cudaEventRecord");
+  L.pending = true;
   return BRMPPI_OK;
 }
 
 void brmppi_graph_destroy(brmppi_graph* g) {
   if (!g) return;
   if (g->exec) {
-    if (g->ctx->batch_pending) cudaEventSynchronize(g->ctx->batch_done);
+    if (g->ctx->batch.pending) cudaEventSynchronize(g->ctx->batch.batch_done);
     cudaGraphExecDestroy(g->exec);
   }
   if (g->graph) cudaGraphDestroy(g->graph);
@@ -828,8 +796,9 @@ brmppi_status brmppi_autotune_batch(brmppi_ctx* c, const brmppi_instance* inst, 
   if (reps < 1) reps = 1;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   cudaError_t e;
-  if (c->batch_pending && (e = cudaEventSynchronize(c->batch_done)) != cudaSuccess) return cuda_fail(c, e, "sync");
-  c->batch_pending = false;
+  Lane& L = c->batch;
+  if (L.pending && (e = cudaEventSynchronize(L.batch_done)) != cudaSuccess) return cuda_fail(c, e, "sync");
+  L.pending = false;
   int max_P = 1;
   for (int i = 0; inst && i < n; ++i) max_P = std::max(max_P, philox_blocks(inst[i].n_obs));
   cudaEvent_t e0, e1;
@@ -848,16 +817,16 @@ brmppi_status brmppi_autotune_batch(brmppi_ctx* c, const brmppi_instance* inst, 
       sh.bpt = bpt;
       sh.threads = threads;
       BatchPlan plan;
-      if (plan_batch(c, inst, n, &sh, c->h_inst, c->h_work, &plan) != BRMPPI_OK) {
+      if (plan_batch(c, L, inst, n, &sh, L.h_inst, L.h_work, &plan) != BRMPPI_OK) {
         last_err = c->err;
         continue;
       }
-      if (upload_and_launch(c, plan, c->h_inst, c->h_work, s) != BRMPPI_OK) {
+      if (upload_and_launch(c, L, plan, L.h_inst, L.h_work, s) != BRMPPI_OK) {
         last_err = c->err;
         continue;
       }
       cudaEventRecord(e0, s);
-      for (int r = 0; r < reps; ++r) launch_batch(c, plan, s);
+      for (int r = 0; r < reps; ++r) launch_batch(c, L, plan, s);
       cudaEventRecord(e1, s);
       cudaEventSynchronize(e1);
       float ms = 0.f;

@@ -1,0 +1,119 @@
+// internal.h -- private host-side structures of libbrmppi.so, shared by the
+// C-ABI translation unit (api.cu) and the serving loop (serve.cu).
+#pragma once
+
+#include <cstdint>
+#include <map>
+#include <string>
+
+#include "brmppi.h"
+#include "launch.h"
+
+namespace brmppi_host {
+
+constexpr int kMaxObstacles = 124;  // ceil((4 + n)/4) <= 32 Philox blocks
+constexpr int kMaxPathPts = 12000;
+constexpr int kMaxH = 1024;
+constexpr int kMinThreads = 64;
+constexpr int kMaxThreads = 512;
+constexpr int kMinBatchSpb = 16;  // smallest tile of a batch launch
+constexpr int kMaxResidentThreads = 2048;
+
+struct Shape {
+  int tps = 0, bpt = 0, threads = 0;
+};
+
+// Everything one in-flight batch launch needs: instance table, work list,
+// per-tile partial pool, per-instance counters, per-CTA input history, host
+// staging of the table and list, and the events that guard their reuse.
+struct Lane {
+  brmppi::Inst* d_inst = nullptr;
+  int2* d_work = nullptr;
+  unsigned int* d_work_ctr = nullptr;
+  float* d_bpart = nullptr;
+  unsigned int* d_bsync = nullptr;
+  float* d_buh = nullptr;
+  brmppi::Inst* h_inst = nullptr;
+  int2* h_work = nullptr;
+  cudaEvent_t upload_done = nullptr;  // host staging free again
+  cudaEvent_t batch_done = nullptr;   // device table free again
+  cudaStream_t stream = nullptr;      // owned when the lane belongs to the server
+  bool pending = false;
+  int max_batch = 0;
+  size_t bpart_floats = 0, buh_floats = 0, max_work = 0;
+};
+
+struct BatchPlan {
+  Shape shape;
+  int n_inst = 0, n_work = 0, grid = 0, Hmax = 0;
+  brmppi::SmemCaps caps{};
+  size_t smem = 0;
+};
+
+struct Server;
+
+}  // namespace brmppi_host
+
+struct brmppi_ctx {
+  brmppi_params prm{};
+  int device = 0;
+  int num_sms = 0;
+  cudaStream_t stream = nullptr;
+  size_t smem_limit = 0;
+  // plain solves
+  unsigned char* d_in = nullptr;  // x0 | U_nom | obs | path
+  float* d_out = nullptr;         // U | traj | status
+  float* d_J = nullptr;
+  float* d_part = nullptr;
+  unsigned int* d_sync = nullptr;  // finished tiles, error bits
+  float* d_uh = nullptr;
+  unsigned char* h_in = nullptr;
+  float* h_out = nullptr;
+  size_t off_unom = 0, off_obs = 0, off_path = 0, in_bytes = 0, out_floats = 0;
+  size_t part_stride = 0, part_tiles = 0, uh_floats = 0;
+  std::map<int, brmppi_host::Shape> tuned;  // obstacle count -> fastest plain shape
+  // batches
+  brmppi_host::Lane batch;
+  bool batch_tuned = false;
+  brmppi_host::Shape batch_shape;
+  // serving
+  brmppi_host::Server* server = nullptr;
+  std::string err;
+};
+
+struct brmppi_graph {
+  brmppi_ctx* ctx = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  brmppi::Inst* h_inst = nullptr;
+  int2* h_work = nullptr;
+};
+
+namespace brmppi_host {
+
+size_t align_up(size_t v, size_t a);
+brmppi_status fail(brmppi_ctx* c, brmppi_status st, const std::string& msg);
+brmppi_status cuda_fail(brmppi_ctx* c, cudaError_t e, const char* what);
+int philox_blocks(int n_obs);
+bool pick_bpt(int tps, int P, int* bpt);
+int part_stride_for(int H);
+brmppi_status check_sizes(brmppi_ctx* c, int32_t n_obs, int32_t n_pts, float ds);
+
+// Allocate / free the buffers of a lane for max_batch instances of at most
+// S samples and H steps.
+cudaError_t lane_alloc(Lane& L, int max_batch, size_t S, size_t H, int num_sms, size_t part_stride);
+void lane_free(Lane& L);
+
+// Validate instances and fill a lane's host staging (table + longest-first
+// work list); `forced` fixes the launch shape (else the context's batch shape).
+brmppi_status plan_batch(brmppi_ctx* c, Lane& L, const brmppi_instance* inst, int32_t n, const Shape* forced,
+                         brmppi::Inst* h_inst, int2* h_work, BatchPlan* plan);
+// Upload the staging and launch on `stream` (waits for the lane's previous batch).
+brmppi_status upload_and_launch(brmppi_ctx* c, Lane& L, const BatchPlan& plan, const brmppi::Inst* h_inst,
+                                const int2* h_work, cudaStream_t stream);
+
+// Serving loop (serve.cu).
+brmppi_status server_create(brmppi_ctx* c);
+void server_destroy(brmppi_ctx* c);
+
+}  // namespace brmppi_host
