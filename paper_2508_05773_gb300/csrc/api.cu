@@ -158,7 +158,7 @@ brmppi::SmemCaps make_caps(int n_obs, int n_pts, int H) {
 size_t smem_bytes(const brmppi::SmemCaps& c, int spb) { return sizeof(float) * static_cast<size_t>(c.total(spb)); }
 
 bool pick_bpt(int tps, int P, int* bpt) {
-  for (int b : {1, 2, 4, 8})
+  for (int b : {1, 2, 3, 4, 5, 6, 8})
     if (tps * b >= P && brmppi::variant_exists(tps, b)) {
       *bpt = b;
       return true;

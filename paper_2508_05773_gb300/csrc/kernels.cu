@@ -1,31 +1,25 @@
-// kernels.cu -- instantiations of the solve kernel and their dispatch.
+// kernels.cu -- dispatch over the solve-kernel instantiations.
 #include "launch.h"
 
 namespace brmppi {
 
-using KernelFn = void (*)(const KConst, const LaunchDesc);
-
 namespace {
 
-struct Variant {
-  int tps, bpt;
-  KernelFn fn;
-};
-
-#define BRMPPI_VARIANT(T, B) Variant{T, B, &solve_kernel<T, B>}
-const Variant kVariants[] = {
-    BRMPPI_VARIANT(1, 1),  BRMPPI_VARIANT(1, 2),  BRMPPI_VARIANT(1, 4),  BRMPPI_VARIANT(1, 8),
-    BRMPPI_VARIANT(2, 1),  BRMPPI_VARIANT(2, 2),  BRMPPI_VARIANT(2, 4),
-    BRMPPI_VARIANT(4, 1),  BRMPPI_VARIANT(4, 2),  BRMPPI_VARIANT(4, 4),
-    BRMPPI_VARIANT(8, 1),  BRMPPI_VARIANT(8, 2),  BRMPPI_VARIANT(8, 4),
-    BRMPPI_VARIANT(16, 1), BRMPPI_VARIANT(16, 2), BRMPPI_VARIANT(32, 1),
-};
-#undef BRMPPI_VARIANT
+template <typename F>
+void for_each_variant(F f) {
+  int n = 0;
+  const Variant* a = variants_narrow(&n);
+  for (int i = 0; i < n; ++i) f(a[i]);
+  const Variant* b = variants_wide(&n);
+  for (int i = 0; i < n; ++i) f(b[i]);
+}
 
 const Variant* find(int tps, int bpt) {
-  for (const Variant& v : kVariants)
-    if (v.tps == tps && v.bpt == bpt) return &v;
-  return nullptr;
+  const Variant* hit = nullptr;
+  for_each_variant([&](const Variant& v) {
+    if (v.tps == tps && v.bpt == bpt) hit = &v;
+  });
+  return hit;
 }
 
 }  // namespace
@@ -33,12 +27,13 @@ const Variant* find(int tps, int bpt) {
 bool variant_exists(int tps, int bpt) { return find(tps, bpt) != nullptr; }
 
 cudaError_t set_smem_limit(size_t bytes) {
-  for (const Variant& v : kVariants) {
+  cudaError_t err = cudaSuccess;
+  for_each_variant([&](const Variant& v) {
     cudaError_t e = cudaFuncSetAttribute(reinterpret_cast<const void*>(v.fn),
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(bytes));
-    if (e != cudaSuccess) return e;
-  }
-  return cudaSuccess;
+    if (e != cudaSuccess && err == cudaSuccess) err = e;
+  });
+  return err;
 }
 
 int variant_occupancy(int tps, int bpt, int threads, size_t smem) {

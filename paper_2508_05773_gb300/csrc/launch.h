@@ -7,6 +7,18 @@
 
 namespace brmppi {
 
+using KernelFn = void (*)(const KConst, const LaunchDesc);
+
+struct Variant {
+  int tps, bpt;
+  KernelFn fn;
+};
+
+// Instantiations, one translation unit per group of team widths (compiled
+// in parallel); each returns its table and its length.
+const Variant* variants_narrow(int* n);  // 1 and 2 lanes per sample
+const Variant* variants_wide(int* n);    // 4 .. 32 lanes per sample
+
 // Supported (threads per sample, Philox blocks per lane) pairs.
 bool variant_exists(int tps, int bpt);
 

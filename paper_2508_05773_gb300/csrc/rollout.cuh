@@ -286,19 +286,20 @@ __device__ void run_tile(const KConst& k, const Inst& in, int tile, float* uh, c
   const float qf0 = fr.qf0;
   const int i0 = fr.i0;
 
-  auto draw = [&](int tau, float* out) {
-#pragma unroll
-    for (int b8 = 0; b8 < BPT; ++b8) {
-      const int b = lt + TPS * b8;
-      if (b < in.P) {
-        const uint4 w = philox4x32_10(
-            make_uint4(static_cast<uint32_t>(b), static_cast<uint32_t>(tau), sid, in.ctr), in.key0, in.key1);
-        box_muller(w.x, w.y, out[4 * b8 + 0], out[4 * b8 + 1]);
-        box_muller(w.z, w.w, out[4 * b8 + 2], out[4 * b8 + 3]);
-      } else {
-#pragma unroll
-        for (int m = 0; m < 4; ++m) out[4 * b8 + m] = 0.f;
-      }
+  // the four normals of Philox block b at step tau
+  auto draw_block = [&](int b, int tau, float* out) {
+    const uint4 w = philox4x32_10(
+        make_uint4(static_cast<uint32_t>(b), static_cast<uint32_t>(tau), sid, in.ctr), in.key0, in.key1);
+    box_muller(w.x, w.y, out[0], out[1]);
+    box_muller(w.z, w.w, out[2], out[3]);
+  };
+  // block 0 of this lane (lane 0: the input normals and the hitch), drawn a
+  // step ahead; further blocks are drawn where their rows are built
+  auto draw_first = [&](int tau, float* out) {
+    if (lt < in.P) {
+      draw_block(lt, tau, out);
+    } else {
+      out[0] = out[1] = out[2] = out[3] = 0.f;
     }
   };
 
@@ -333,11 +334,11 @@ __device__ void run_tile(const KConst& k, const Inst& in, int tile, float* uh, c
     acc2(Jh, Jl, rc);
   };
 
-  float nrm[4 * BPT];
-  draw(0, nrm);
+  float nrm[4];
+  draw_first(0, nrm);
   for (int tau = 0; tau < H; ++tau) {
-    float nxt[4 * BPT];
-    draw(tau + 1 < H ? tau + 1 : tau, nxt);  // off the state's critical path
+    float nxt[4];
+    draw_first(tau + 1 < H ? tau + 1 : tau, nxt);  // off the state's critical path
 
     // trigonometry of the current state
     float sr, cr;
@@ -368,15 +369,23 @@ __device__ void run_tile(const KConst& k, const Inst& in, int tile, float* uh, c
       const float pu2 = k.w_u2 * zd2 + k.pc_u2;
       const float q0 = pu0 * k.inv_m_u0, q1 = pu1 * k.inv_m_u1;  // M_u^-1 p_u
       float Saa = 0.f, Saw = 0.f, Sww = 0.f, ga = 0.f, gw = 0.f;
-      float ca[4 * BPT], cw[4 * BPT], cc[4 * BPT];
+      float ca[4 * BPT], cc[4 * BPT];
+      float cwh = 0.f;  // steer-rate coefficient: only the hitch row has one
 #pragma unroll
       for (int b8 = 0; b8 < BPT; ++b8) {
+        const int blk = lt + TPS * b8;
+        float nb[4];
+        if (b8 == 0) {
+#pragma unroll
+          for (int m = 0; m < 4; ++m) nb[m] = nrm[m];
+        } else if (blk < in.P) {
+          draw_block(blk, tau, nb);
+        }
 #pragma unroll
         for (int m = 0; m < 4; ++m) {
           const int slot = 4 * b8 + m;
-          const int i = 4 * (lt + TPS * b8) + m - 3;  // constraint index
+          const int i = 4 * blk + m - 3;  // constraint index
           ca[slot] = 0.f;
-          cw[slot] = 0.f;
           cc[slot] = 0.f;
           if (i >= 0 && i < Nc) {
             float Aa, Aw, h, brest;
@@ -414,7 +423,7 @@ __device__ void run_tile(const KConst& k, const Inst& in, int tile, float* uh, c
             }
             const float hm = fmaxf(fabsf(h), k.h_floor);
             const float ht = h >= 0.f ? hm : -hm;
-            const float zda = clampf(k.sigma_alpha * nrm[slot], k.ua_lo, k.ua_hi);
+            const float zda = clampf(k.sigma_alpha * nb[m], k.ua_lo, k.ua_hi);
             const float pa = k.w_a * zda + k.pc_a;
             const float b = -alpha[slot] * h + brest;
             const float r = Aa * q0 + Aw * q1 + ht * pa * k.inv_m_a - b;
@@ -426,7 +435,7 @@ __device__ void run_tile(const KConst& k, const Inst& in, int tile, float* uh, c
             ga += Aa * r * invD;
             gw += Aw * r * invD;
             ca[slot] = Aa * iht;
-            cw[slot] = Aw * iht;
+            if (i == 0) cwh = Aw * iht;
             cc[slot] = pa * k.inv_m_a - r * iht;
           }
         }
@@ -443,7 +452,8 @@ __device__ void run_tile(const KConst& k, const Inst& in, int tile, float* uh, c
       zw = q1 - yw;
       zn = pu2 * k.inv_m_u2;
 #pragma unroll
-      for (int slot = 0; slot < 4 * BPT; ++slot) alpha[slot] += cc[slot] + ca[slot] * ya + cw[slot] * yw;
+      for (int slot = 0; slot < 4 * BPT; ++slot) alpha[slot] += cc[slot] + ca[slot] * ya;
+      alpha[3] += cwh * yw;  // the hitch sits in slot 3 of lane 0 (cwh = 0 elsewhere)
     } else {
       za = zd0;
       zw = zd1;
@@ -469,7 +479,7 @@ __device__ void run_tile(const KConst& k, const Inst& in, int tile, float* uh, c
       uh[(3 * tau + 2) * spb + team] = un;
     }
 #pragma unroll
-    for (int q = 0; q < 4 * BPT; ++q) nrm[q] = nxt[q];
+    for (int q = 0; q < 4; ++q) nrm[q] = nxt[q];
   }
   stage_cost();  // cost of the last step
 

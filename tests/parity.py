@@ -3,7 +3,7 @@ FP64 oracle), 1e-4 relative as the solve's accuracy target:
 
 * states / optimal trajectory: |g - o| <= 1e-4 max(|o|, 1)
 * per-sample costs J:          |g - o| <= EPS_J |o| with EPS_J = 2^-18, and
-  the median relative error <= 2^-23 (about one binary32 ulp: the rollout
+  the median relative error <= 2^-22 (about two binary32 ulps: the rollout
   carries position, speed, progress and the cost sum as compensated pairs).
   The worst case is a rollout grazing an ellipse: at h ~ 0 the barrier is
   a difference of O(1) terms whose binary32 cancellation error (~1e-7) the
@@ -28,7 +28,7 @@ import numpy as np
 TOL_STATE = 1e-4
 TOL_U = 1e-4
 EPS_J = 2.0 ** -18
-EPS_J_MEDIAN = 2.0 ** -23
+EPS_J_MEDIAN = 2.0 ** -22
 
 
 def err_state(g, o):
