@@ -95,6 +95,22 @@ def _dist_env():
     return world, rank, local
 
 
+def _traffic_for_current_kernel():
+    """DRAM bytes per launch of the config-2 solve from the committed ncu
+    capture, or None when the kernel source changed since that capture."""
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic_config2.json")) as f:
+            rec = json.load(f)
+        src = os.path.join(ROOT, "paper_2508_05773_gb300", "csrc", "rollout.cuh")
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        if h != rec["rollout_cuh_sha256_16"]:
+            return None
+        return int(rec["dram_read_bytes"]) + int(rec["dram_write_bytes"])
+    except Exception:
+        return None
+
+
 def _measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -525,7 +541,7 @@ def run_ours(args, world, rank, local):
                            "misses": int(np.sum(lat > 10.0))},
             "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
                          "unit": "Tops/s (FP32 lane ops)", "frac": achieved / peak_ops,
-                         "traffic": None, "kernel": "rollout_solve_kernel",
+                         "traffic": _traffic_for_current_kernel(), "kernel": "solve_kernel",
                          "ops_per_launch": ops,
                          "peak_note": f"152 SMs x 128 FP32 lanes x {sm_mhz:.0f} MHz (sm_max_mhz of "
                                       "MEASURED_PEAKS.json); derived, not measured"},
