@@ -188,6 +188,28 @@ brmppi_status brmppi_autotune(brmppi_ctx *ctx, const double *x0_dev, const float
 brmppi_status brmppi_autotune_batch(brmppi_ctx *ctx, const brmppi_instance *inst, int32_t n,
                                     int32_t reps, void *stream);
 
+/* A solve that allocates nothing and needs no context.  The paper has no
+   counterpart: it serves callers that cannot call cudaMalloc once running --
+   code enqueued while a CUDA graph is being captured, and controllers whose
+   device memory is fixed at start-up -- and so cannot create a brmppi_ctx.
+   Same inputs, outputs and results as brmppi_solve_device (all pointers
+   device memory, enqueued on `stream`, no synchronisation); the launch shape
+   is fixed (4 lanes per sample, 128-thread blocks) and the scratch lives in
+   a file-scope device array of about 3.1 MiB that every device loading the
+   library keeps until exit.  Maxima: S <= 4096, H <= 64, n_obs <= 16,
+   n_pts <= 4096; larger sizes return BRMPPI_EINVAL with the reason in
+   brmppi_last_error(NULL).  The first call on a device looks up the array's
+   device address and sets the kernels' shared-memory limit for that
+   device; make that first call before any stream capture.  All calls on a
+   device share the array (counters are cleared on `stream` before each
+   launch): calls that overlap on the GPU race, so serialise them. */
+brmppi_status brmppi_solve_device_noalloc(const brmppi_params *p, const double *x0_dev,
+                                          const float *U_nom_dev, const float *obs_dev,
+                                          int32_t n_obs, const float *path_dev, int32_t n_pts,
+                                          float ds, uint64_t seed, uint64_t counter,
+                                          float *U_out_dev, float *traj_out_dev, float *J_out_dev,
+                                          float *U_next_dev, int32_t *status_dev, void *stream);
+
 /* ---- Serving loop (contexts created with max_vehicles > 0) ----------------
    A scheduler thread admits submitted requests into batches as request slots
    and batch lanes free up, launches each batch (one persistent launch) on its

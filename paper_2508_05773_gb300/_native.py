@@ -33,6 +33,7 @@ EXPORTS = (
     "brmppi_graph_launch", "brmppi_graph_destroy", "brmppi_autotune", "brmppi_autotune_batch",
     "brmppi_get_launch", "brmppi_transfer_bytes", "brmppi_vehicle_register", "brmppi_submit",
     "brmppi_poll", "brmppi_vehicle_export", "brmppi_vehicle_import", "brmppi_server_stats_get",
+    "brmppi_solve_device_noalloc",
 )
 
 
@@ -138,6 +139,10 @@ def load() -> ctypes.CDLL:
             "brmppi_vehicle_import": (ctypes.c_int, [_VP, ctypes.c_uint32, _F, ctypes.c_uint64,
                                                      ctypes.c_uint64]),
             "brmppi_server_stats_get": (ctypes.c_int, [_VP, ctypes.POINTER(brmppi_server_stats)]),
+            "brmppi_solve_device_noalloc": (ctypes.c_int, [P, _VP, _VP, _VP, ctypes.c_int32, _VP,
+                                                           ctypes.c_int32, ctypes.c_float,
+                                                           ctypes.c_uint64, ctypes.c_uint64, _VP,
+                                                           _VP, _VP, _VP, _VP, _VP]),
             "brmppi_transfer_bytes": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.c_int32,
                                                      ctypes.POINTER(ctypes.c_uint64),
                                                      ctypes.POINTER(ctypes.c_uint64)]),
@@ -340,6 +345,19 @@ def brmppi_autotune_batch(ctx, insts, reps=3, stream=None) -> int:
     arr = insts if isinstance(insts, ctypes.Array) else make_instances(insts)
     return load().brmppi_autotune_batch(ctx, arr, len(arr), int(reps),
                                         ctypes.c_void_p(_stream_handle(stream)))
+
+
+def brmppi_solve_device_noalloc(params, x0, U_nom, obs, path, ds, seed, counter, U_out,
+                                traj_out=None, J_out=None, U_next=None, status=None,
+                                stream=None) -> int:
+    """Allocation-free solve (no context) on torch CUDA tensors; see
+    include/brmppi.h for its limits.  ``params``: brmppi_params."""
+    n_obs = 0 if obs is None else obs.numel() // 6
+    return load().brmppi_solve_device_noalloc(
+        ctypes.byref(params), _dptr(x0), _dptr(U_nom), _dptr(obs) if n_obs else None, n_obs,
+        _dptr(path), path.numel() // 3, float(ds), int(seed) & (2**64 - 1),
+        int(counter) & (2**64 - 1), _dptr(U_out), _dptr(traj_out), _dptr(J_out), _dptr(U_next),
+        _dptr(status), ctypes.c_void_p(_stream_handle(stream)))
 
 
 def brmppi_get_launch(ctx, n_obs: int):
