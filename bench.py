@@ -49,42 +49,23 @@ L2_FLUSH_BYTES = 256 << 20
 
 
 # ----------------------------------------------------------------------------
-# Algorithmic work of one rollout-step (FP32 lane operations; one sample on one
-# lane, each +, -, *, fma, min, max, compare/select, integer mul / xor / add,
-# reciprocal, and each elementary function sin, cos, tan, log, sqrt, exp
-# counted as one operation).  The tally follows the rollout kernel step by
-# step; the derivation is tabulated in the design doc.
-PHILOX_BLOCK_OPS = 10 * 10 + 8      # 10 rounds x (2 mul.lo + 2 mul.hi + 4 xor + 2 key adds) + uniform maps
-BOX_MULLER_PAIR_OPS = 2 + 2 + 1 + 1 + 2 + 2   # 2 uniforms, log, sqrt, sincos(2pi u) (2), 2 mul
-STEP_BASE_OPS = (
-    9      # z_des for (a, omega, nu): fma + clamp(2) each
-    + 8    # trig of state: sincos(th1) (2) + rotation (4) + phi (1) + sincos(phi) ... counted below
-    + 3    # tan(delta), th1dot (2 mul)
-    + 9    # p_u (3 fma), M_u^-1 p_u (3 mul), nu projection (1), constants
-    + 14   # 2x2 solve: det (3), inverse (1), y (6), z_u (2), clamp (6 -> counted in apply)
-    + 6    # clamp of applied inputs
-    + 14   # Euler step (7 updates, 2 ops each)
-    + 12   # path index: fma, floor, convert, add, 2 clamps, frac; 3 lerps (2 each)
-    + 6    # sincos(theta_r) (2) + rotation (4)
-    + 6    # e_c, e_l
-    + 6    # heading errors with wrap (3 each)
-    + 20   # stage cost (7 squares, weights, sums)
-    + 4    # TwoSum
-    + 5    # sincos(phi) (2) + remaining trig bookkeeping
-)
-HITCH_ROW_OPS = 34          # Delta, sign, G, th2dot, phidot, h, A_a, A_w, c0
-OBSTACLE_ROW_OPS = 31       # dx, dy, rotation (4), h (4), grads (4), dir (4), vel (2), hdot (3), hddot0 (8), A_a, b
-ROW_TAIL_OPS = 24           # h floor/sign, z_des alpha, p_alpha, b, r, 1/h, 1/D, S2 (3), g (2), c (3), alpha update (3)
+# Algorithmic work of one rollout-step, in FP32/INT32 lane operations for one
+# sample on one lane (the Woodbury algorithm without the kernel's
+# compensated sums and without team redundancy): every +, -, *, fma, min,
+# max, compare/select, integer mul.lo / mul.hi / xor / add / shift / convert
+# and every elementary function (sin, cos, tan, log, sqrt, exp, reciprocal)
+# counts one.  Tally (the design doc lists it term by term):
+PHILOX_BLOCK_OPS = 132    # 10 rounds x 10 int ops, 4 uniform maps x 4, 2 Box-Muller pairs x 8
+STEP_BASE_OPS = 111       # z_des 9, state trig 13, p_u 6, 2x2 solve 14, clip 6, Euler 14, path + cost 49
+HITCH_OPS = 60            # row 27, projection terms 30, alpha update 3
+OBSTACLE_OPS = 64         # row 38, projection terms 24, alpha update 2
 
 
 def ops_per_rollout_step(n_obs: int, proj: bool = True) -> int:
-    d = 3 + 1 + n_obs
-    P = (d + 3) // 4
-    normals_ops = P * (PHILOX_BLOCK_OPS + 2 * BOX_MULLER_PAIR_OPS)
     if not proj:
-        return PHILOX_BLOCK_OPS + 2 * BOX_MULLER_PAIR_OPS + STEP_BASE_OPS
-    return (normals_ops + STEP_BASE_OPS + HITCH_ROW_OPS + OBSTACLE_ROW_OPS * n_obs
-            + ROW_TAIL_OPS * (1 + n_obs))
+        return PHILOX_BLOCK_OPS + STEP_BASE_OPS - 6
+    P = (3 + 1 + n_obs + 3) // 4
+    return PHILOX_BLOCK_OPS * P + STEP_BASE_OPS + HITCH_OPS + OBSTACLE_OPS * n_obs
 
 
 # ----------------------------------------------------------------------------
@@ -279,6 +260,63 @@ def measure_batched(dev, reps: int = 10):
             "launches_per_batch": 1, "plain_launches_per_batch": len(cases),
             "how": "CUDA-graph replay of one persistent launch vs brmppi_solve_device per "
                    "instance on one stream; L2 flushed between batches; median"}
+
+
+def measure_stress(dev, reps: int = 5):
+    """Config 5: S=65536, H=100, 64 ellipses in a 60x60 m lot, 120 m
+    multi-arc path at ds=0.05 (2401 rows).  One solve with and without the
+    stored-trajectory variant (every sample's states, S x (H+1) x 7 FP32 =
+    185 MB); HBM GB/s of the stored variant against the measured copy peak."""
+    import torch
+    import paper_2508_05773_gb300 as pkg
+    from paper_2508_05773_gb300 import scenarios as sc
+
+    c = sc.config5()
+    S, H = int(c["params"]["S"]), int(c["params"]["H"])
+    n_obs = int(c["obs"].shape[0])
+    t = lambda a, dt=torch.float32: torch.tensor(np.asarray(a), dtype=dt, device=dev)
+    base = dict(x0=t(c["x0"], torch.float64), U_nom=t(c["U_nom"]), obs=t(c["obs"]), path=t(c["path"]),
+                ds=c["ds"], S=S, seed=c["seed"], counter=0,
+                U_out=torch.empty((H, 3), device=dev), traj_out=torch.empty((H + 1, 7), device=dev),
+                status=torch.zeros(1, dtype=torch.int32, device=dev))
+    states = torch.empty((S, H + 1, 7), device=dev)
+    solver = pkg.Solver(c["params"], max_obstacles=n_obs, max_path_pts=c["path"].shape[0])
+    stream = torch.cuda.current_stream(dev)
+    solver.autotune(base["x0"], base["U_nom"], base["obs"], base["path"], c["ds"], reps=1,
+                    stream=stream)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    res = {}
+    for label, extra in (("plain", {}), ("stored", {"states_out": states})):
+        inst = dict(base, **extra)
+        ts = []
+        for r in range(reps + 2):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            solver.solve_device_ex(inst, stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if r >= 2:
+                ts.append(e0.elapsed_time(e1))
+        res[label] = float(np.median(ts))
+    assert int(base["status"].item()) == 0
+    launch = solver.launch(n_obs)
+    solver.close()
+    peaks = _measured_peaks()
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    peak_ops = N_SM * FP32_LANES_PER_SM * sm_mhz * 1e6
+    ops = S * H * ops_per_rollout_step(n_obs)
+    state_bytes = S * (H + 1) * 7 * 4
+    gbs = state_bytes / (res["stored"] * 1e-3) / 1e9
+    return {"workload": "S=65536, H=100, 64 ellipses (60x60 m lot), 120 m multi-arc path, ds=0.05",
+            "launch": launch, "ms_per_solve": res["plain"], "ms_per_solve_stored": res["stored"],
+            "rollout_steps_per_s": S * H / (res["plain"] * 1e-3),
+            "alu_frac": ops / (res["plain"] * 1e-3) / peak_ops,
+            "stored_bytes": state_bytes, "stored_hbm_gbs": gbs,
+            "stored_hbm_frac": gbs / hbm,
+            "note": "the stored variant writes 185 MB per solve at the solve's compute rate; "
+                    "ALU-bound, so its HBM fraction is low by construction"}
 
 
 def measure_serving(rates=(2000, 10000, 50000), duration=2.0, warm=0.5, n_vehicles=512, seed=4):
@@ -553,6 +591,8 @@ def run_ours(args, world, rank, local):
             line["batched"] = measure_batched(dev)
         if world == 1 and not args.no_serving:
             line["serving"] = measure_serving()
+        if world == 1 and not args.no_stress:
+            line["stress"] = measure_stress(dev)
         if not args.no_cpu_baseline and world == 1:
             line["cpu_baseline"] = run_cpu_baseline()
         print(json.dumps(line), flush=True)
@@ -571,6 +611,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-stress", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

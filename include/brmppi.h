@@ -52,7 +52,7 @@
 extern "C" {
 #endif
 
-#define BRMPPI_ABI_VERSION 3u
+#define BRMPPI_ABI_VERSION 4u
 
 typedef enum {
   BRMPPI_OK = 0,
@@ -115,6 +115,8 @@ typedef struct brmppi_instance {
   uint64_t seed, counter;
   float *U_out, *traj_out, *J_out, *U_next; /* U_out required; others may be NULL */
   int32_t *status;                          /* may be NULL */
+  float *states_out; /* may be NULL: stored-trajectory variant, every sample's
+                        states S x (H+1) x 7 (world frame, x0 first) */
 } brmppi_instance;
 
 typedef struct brmppi_graph brmppi_graph; /* a captured batch launch */
@@ -154,6 +156,12 @@ brmppi_status brmppi_solve_device(brmppi_ctx *ctx, const double *x0_dev, const f
                                   int32_t n_pts, float ds, uint64_t seed, uint64_t counter,
                                   float *U_out_dev, float *traj_out_dev, float *J_out_dev,
                                   float *U_next_dev, int32_t *status_dev, void *stream);
+
+/* One solve described by an instance (device pointers): as
+   brmppi_solve_device, with S <= params.S and H <= params.H per call and the
+   optional stored-trajectory output.  Allocates nothing, does not
+   synchronise. */
+brmppi_status brmppi_solve_device_ex(brmppi_ctx *ctx, const brmppi_instance *inst, void *stream);
 
 /* A batch of independent solves (uneven S, H, obstacle count, path) in ONE
    launch of a persistent kernel: work items (instance, sample tile) are

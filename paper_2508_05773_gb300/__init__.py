@@ -12,7 +12,7 @@ from ._native import (  # noqa: F401
     NativeLibraryMissing, Solver, brmppi_autotune, brmppi_autotune_batch, brmppi_batch_capture,
     brmppi_create, brmppi_default_params, brmppi_destroy, brmppi_get_launch, brmppi_graph_destroy,
     brmppi_graph_launch, brmppi_instance, brmppi_last_error, brmppi_params, brmppi_solve,
-    brmppi_solve_batch, brmppi_solve_device, brmppi_solve_device_noalloc, brmppi_transfer_bytes, load, make_instances,
+    brmppi_solve_batch, brmppi_solve_device, brmppi_solve_device_ex, brmppi_solve_device_noalloc, brmppi_transfer_bytes, load, make_instances,
     params_from_dict,
 )
 from . import scenarios  # noqa: F401

@@ -12,7 +12,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libbrmppi.so")
 
-BRMPPI_ABI_VERSION = 3
+BRMPPI_ABI_VERSION = 4
 BRMPPI_OK = 0
 BRMPPI_EINVAL = -1
 BRMPPI_ENOMEM = -2
@@ -29,7 +29,7 @@ STATUS_NAMES = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "EAGAIN", -4: "ETIMEDOU
 #: every exported symbol the header declares
 EXPORTS = (
     "brmppi_default_params", "brmppi_create", "brmppi_destroy", "brmppi_last_error",
-    "brmppi_solve", "brmppi_solve_device", "brmppi_solve_batch", "brmppi_batch_capture",
+    "brmppi_solve", "brmppi_solve_device", "brmppi_solve_device_ex", "brmppi_solve_batch", "brmppi_batch_capture",
     "brmppi_graph_launch", "brmppi_graph_destroy", "brmppi_autotune", "brmppi_autotune_batch",
     "brmppi_get_launch", "brmppi_transfer_bytes", "brmppi_vehicle_register", "brmppi_submit",
     "brmppi_poll", "brmppi_vehicle_export", "brmppi_vehicle_import", "brmppi_server_stats_get",
@@ -68,6 +68,7 @@ class brmppi_instance(ctypes.Structure):
         ("seed", ctypes.c_uint64), ("counter", ctypes.c_uint64),
         ("U_out", ctypes.c_void_p), ("traj_out", ctypes.c_void_p), ("J_out", ctypes.c_void_p),
         ("U_next", ctypes.c_void_p), ("status", ctypes.c_void_p),
+        ("states_out", ctypes.c_void_p),
     ]
 
 
@@ -116,6 +117,7 @@ def load() -> ctypes.CDLL:
             "brmppi_solve_device": (ctypes.c_int, [_VP, _VP, _VP, _VP, ctypes.c_int32, _VP,
                                                    ctypes.c_int32, ctypes.c_float, ctypes.c_uint64,
                                                    ctypes.c_uint64, _VP, _VP, _VP, _VP, _VP, _VP]),
+            "brmppi_solve_device_ex": (ctypes.c_int, [_VP, ctypes.POINTER(brmppi_instance), _VP]),
             "brmppi_solve_batch": (ctypes.c_int, [_VP, ctypes.POINTER(brmppi_instance),
                                                   ctypes.c_int32, _VP]),
             "brmppi_batch_capture": (ctypes.c_int, [_VP, ctypes.POINTER(brmppi_instance),
@@ -305,10 +307,17 @@ def make_instances(insts) -> "ctypes.Array":
         q.seed = int(d["seed"]) & (2**64 - 1)
         q.counter = int(d.get("counter", 0)) & (2**64 - 1)
         q.U_out = d["U_out"].data_ptr()
-        for key in ("traj_out", "J_out", "U_next", "status"):
+        for key in ("traj_out", "J_out", "U_next", "status", "states_out"):
             t = d.get(key)
             setattr(q, key, None if t is None else t.data_ptr())
     return arr
+
+
+def brmppi_solve_device_ex(ctx, inst, stream=None) -> int:
+    """One solve from a dict of torch CUDA tensors (as for batches; may carry
+    ``states_out`` of shape (S, H+1, 7))."""
+    arr = make_instances([inst])
+    return load().brmppi_solve_device_ex(ctx, arr, ctypes.c_void_p(_stream_handle(stream)))
 
 
 def brmppi_solve_batch(ctx, insts, stream=None) -> int:
@@ -423,6 +432,12 @@ class Solver:
 
     def transfer_bytes(self, n_obs: int, n_pts: int):
         return brmppi_transfer_bytes(self.ctx, n_obs, n_pts)
+
+    def solve_device_ex(self, inst, stream=None, check=True) -> int:
+        st = brmppi_solve_device_ex(self.ctx, inst, stream)
+        if check and st != BRMPPI_OK:
+            raise BrmppiError(st, brmppi_last_error(self.ctx))
+        return st
 
     def solve_batch(self, insts, stream=None, check=True) -> int:
         st = brmppi_solve_batch(self.ctx, insts, stream)

@@ -259,15 +259,16 @@ brmppi_status check_sizes(brmppi_ctx* c, int32_t n_obs, int32_t n_pts, float ds)
   return BRMPPI_OK;
 }
 
-brmppi_status enqueue_plain(brmppi_ctx* c, const Shape& sh, const double* x0, const float* U_nom,
-                            const float* obs, int32_t n_obs, const float* path, int32_t n_pts, float ds,
-                            uint64_t seed, uint64_t counter, float* U_out, float* traj_out, float* J_out,
-                            float* U_next, int32_t* status, cudaStream_t stream) {
-  const int H = c->prm.H, S = c->prm.S;
+brmppi_status enqueue_plain_sized(brmppi_ctx* c, const Shape& sh, int S, int H, const double* x0,
+                                  const float* U_nom, const float* obs, int32_t n_obs, const float* path,
+                                  int32_t n_pts, float ds, uint64_t seed, uint64_t counter, float* U_out,
+                                  float* traj_out, float* J_out, float* U_next, int32_t* status, float* states_out,
+                                  cudaStream_t stream) {
   const int spb = sh.threads / sh.tps;
   brmppi::LaunchDesc L{};
   L.single = make_inst(x0, U_nom, obs, n_obs, path, n_pts, ds, S, H, seed, counter, U_out, traj_out, J_out,
                        U_next, status, c->d_part, c->d_sync, spb);
+  L.single.states_out = states_out;
   L.caps = make_caps(n_obs, n_pts, H);
   L.uh = c->d_uh;
   L.uh_stride = 3 * H * spb;
@@ -280,6 +281,14 @@ brmppi_status enqueue_plain(brmppi_ctx* c, const Shape& sh, const double* x0, co
   cudaError_t e = brmppi::launch_solve(sh.tps, sh.bpt, tiles, sh.threads, smem, stream, make_kconst(c->prm), L);
   if (e != cudaSuccess) return cuda_fail(c, e, "kernel launch");
   return BRMPPI_OK;
+}
+
+brmppi_status enqueue_plain(brmppi_ctx* c, const Shape& sh, const double* x0, const float* U_nom,
+                            const float* obs, int32_t n_obs, const float* path, int32_t n_pts, float ds,
+                            uint64_t seed, uint64_t counter, float* U_out, float* traj_out, float* J_out,
+                            float* U_next, int32_t* status, cudaStream_t stream) {
+  return enqueue_plain_sized(c, sh, c->prm.S, c->prm.H, x0, U_nom, obs, n_obs, path, n_pts, ds, seed, counter,
+                             U_out, traj_out, J_out, U_next, status, nullptr, stream);
 }
 
 // ------------------------------------------------------------- batches
@@ -399,6 +408,7 @@ brmppi_status plan_batch(brmppi_ctx* c, Lane& L, const brmppi_instance* inst, in
     const int H = q.H;
     brmppi::Inst in = make_inst(q.x0, q.U_nom, q.obs, q.n_obs, q.path, q.n_pts, q.ds, q.S, H, q.seed, q.counter,
                                 q.U_out, q.traj_out, q.J_out, q.U_next, q.status, nullptr, L.d_bsync + 2 * i, spb);
+    in.states_out = q.states_out;
     in.part = L.d_bpart + pool;
     pool += static_cast<size_t>(in.tiles) * static_cast<size_t>(in.part_stride);
     if (pool > L.bpart_floats) return fail(c, BRMPPI_EINVAL, "batch partials exceed the context's pool");
@@ -647,6 +657,23 @@ brmppi_status brmppi_solve_device(brmppi_ctx* c, const double* x0_dev, const flo
   if (!plain_shape(c, n_obs, n_pts, &sh)) return fail(c, BRMPPI_EINVAL, "no launch shape for this size");
   return enqueue_plain(c, sh, x0_dev, U_nom_dev, obs_dev, n_obs, path_dev, n_pts, ds, seed, counter, U_out_dev,
                        traj_out_dev, J_out_dev, U_next_dev, status_dev, static_cast<cudaStream_t>(stream));
+}
+
+brmppi_status brmppi_solve_device_ex(brmppi_ctx* c, const brmppi_instance* q, void* stream) {
+  if (!c) return BRMPPI_EINVAL;
+  c->err.clear();
+  if (!q) return fail(c, BRMPPI_EINVAL, "NULL instance");
+  if (!q->x0 || !q->U_nom || !q->path || !q->U_out || (q->n_obs > 0 && !q->obs))
+    return fail(c, BRMPPI_EINVAL, "NULL buffer");
+  if (q->S < 1 || q->S > c->prm.S || q->H < 1 || q->H > c->prm.H)
+    return fail(c, BRMPPI_EINVAL, "S or H beyond the context's capacity");
+  brmppi_status st = check_sizes(c, q->n_obs, q->n_pts, q->ds);
+  if (st != BRMPPI_OK) return st;
+  Shape sh;
+  if (!plain_shape(c, q->n_obs, q->n_pts, &sh)) return fail(c, BRMPPI_EINVAL, "no launch shape for this size");
+  return enqueue_plain_sized(c, sh, q->S, q->H, q->x0, q->U_nom, q->obs, q->n_obs, q->path, q->n_pts, q->ds,
+                             q->seed, q->counter, q->U_out, q->traj_out, q->J_out, q->U_next, q->status,
+                             q->states_out, static_cast<cudaStream_t>(stream));
 }
 
 brmppi_status brmppi_solve_batch(brmppi_ctx* c, const brmppi_instance* inst, int32_t n, void* stream) {

@@ -79,6 +79,7 @@ struct Inst {
   float* J_out;      // may be null
   float* U_next;     // may be null
   int32_t* status;   // may be null
+  float* states_out;  // may be null: every sample's states, S x (H+1) x 7
   float* part;       // tiles * part_stride floats
   unsigned int* sync;  // [0] finished tiles, [1] error bits
   int S, H, n_obs, n_pts, tiles, part_stride;
@@ -183,6 +184,7 @@ struct Frame {
   float t2, v_h, v_l, dl;                      // theta2 - theta1_0, speed, steer angle
   float qf0;                                   // fractional path cell of psi0
   int i0;                                      // integer path cell of psi0
+  float psi_h, psi_l;                          // psi0
   double psi0;
 };
 
@@ -201,6 +203,7 @@ __device__ __forceinline__ void make_frame(const double* x0, float ds, unsigned 
   split_double(x0[4], fr.v_h, fr.v_l);
   fr.dl = static_cast<float>(x0[5]);
   fr.psi0 = x0[6];
+  split_double(x0[6], fr.psi_h, fr.psi_l);
   const double q0 = x0[6] / static_cast<double>(ds);
   const double fq = fmin(fmax(floor(q0), -1.0e9), 1.0e9);
   fr.i0 = static_cast<int>(fq);
@@ -333,6 +336,23 @@ __device__ void run_tile(const KConst& k, const Inst& in, int tile, float* uh, c
                      k.R1 * uw * uw + k.R2 * un * un + k.mu * dn * dn;
     acc2(Jh, Jl, rc);
   };
+
+  // stored-trajectory variant: the state of this sample after step tau, in
+  // world coordinates (written by the team's first lane)
+  float* st_out = (in.states_out && lt == 0 && s < in.S)
+                      ? in.states_out + static_cast<size_t>(s) * static_cast<size_t>(H + 1) * 7
+                      : nullptr;
+  auto store_state = [&](int tau) {
+    float* o = st_out + 7 * tau;
+    o[0] = (fr.ox_h + px) + (fr.ox_l + pxl);
+    o[1] = (fr.oy_h + py) + (fr.oy_l + pyl);
+    o[2] = (fr.oth_h + t1) + fr.oth_l;
+    o[3] = (fr.oth_h + t2) + fr.oth_l;
+    o[4] = v + vl;
+    o[5] = dl;
+    o[6] = (fr.psi_h + ps) + (fr.psi_l + psl);
+  };
+  if (st_out) store_state(0);
 
   float nrm[4];
   draw_first(0, nrm);
@@ -478,6 +498,7 @@ __device__ void run_tile(const KConst& k, const Inst& in, int tile, float* uh, c
       uh[(3 * tau + 1) * spb + team] = uw;
       uh[(3 * tau + 2) * spb + team] = un;
     }
+    if (st_out) store_state(tau + 1);
 #pragma unroll
     for (int q = 0; q < 4; ++q) nrm[q] = nxt[q];
   }
@@ -584,12 +605,18 @@ static __device__ void merge_instance(const KConst& k, const Inst& in, const Sme
     __syncthreads();
     const int bend = min(256, nb - b0);
     for (int q = threadIdx.x; q < nrows; q += blockDim.x) {
-      float acc = ustar[q];
-      for (int t = 0; t < bend; ++t) {
-        const float sc = S.chunk[t];
-        if (sc != 0.f) acc += sc * __ldcg(in.part + static_cast<size_t>(b0 + t) * stride + 3 + q);
+      // four independent chains (tiles t mod 4), combined in a fixed order
+      float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+      const float* col = in.part + static_cast<size_t>(b0) * stride + 3 + q;
+      int t = 0;
+      for (; t + 4 <= bend; t += 4) {
+        a0 += S.chunk[t + 0] * __ldcg(col + static_cast<size_t>(t + 0) * stride);
+        a1 += S.chunk[t + 1] * __ldcg(col + static_cast<size_t>(t + 1) * stride);
+        a2 += S.chunk[t + 2] * __ldcg(col + static_cast<size_t>(t + 2) * stride);
+        a3 += S.chunk[t + 3] * __ldcg(col + static_cast<size_t>(t + 3) * stride);
       }
-      ustar[q] = acc;
+      for (; t < bend; ++t) a0 += S.chunk[t] * __ldcg(col + static_cast<size_t>(t) * stride);
+      ustar[q] += (a0 + a1) + (a2 + a3);
     }
   }
   __syncthreads();

@@ -49,7 +49,7 @@ def test_params_struct_layout_matches(lib):
     # last fields: a shifted layout would scramble these
     assert abs(p.rho - 0.01) < 1e-9 and abs(p.h_floor - 1e-6) < 1e-12
     assert ctypes.sizeof(pkg.brmppi_params) == 4 * 15 + 4 * 35
-    assert ctypes.sizeof(pkg.brmppi_instance) == 8 * 4 + 4 * 5 + 4 + 8 * 2 + 8 * 5
+    assert ctypes.sizeof(pkg.brmppi_instance) == 8 * 4 + 4 * 5 + 4 + 8 * 2 + 8 * 6
 
 
 @pytest.mark.parametrize("field,value", [

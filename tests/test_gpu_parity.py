@@ -167,20 +167,84 @@ def test_device_entry_point_matches_host(pkg):
         s.close()
 
 
+def _dev_inst(c, dev, states=False):
+    import torch
+    S, H = int(c["params"]["S"]), int(c["params"]["H"])
+    t = lambda a, dt=torch.float32: torch.tensor(np.asarray(a), dtype=dt, device=dev)
+    d = dict(x0=t(c["x0"], torch.float64), U_nom=t(c["U_nom"]),
+             obs=t(c["obs"]) if c["obs"].shape[0] else None, path=t(c["path"]), ds=c["ds"], S=S,
+             seed=c["seed"], counter=c["counter"], U_out=torch.empty((H, 3), device=dev),
+             traj_out=torch.empty((H + 1, 7), device=dev), J_out=torch.empty(S, device=dev),
+             status=torch.full((1,), 99, dtype=torch.int32, device=dev))
+    if states:
+        d["states_out"] = torch.empty((S, H + 1, 7), device=dev)
+    return d
+
+
+def test_stored_trajectories_match_oracle(pkg):
+    import torch
+    dev = torch.device("cuda:0")
+    c = sc.small_random(12, S=300, H=16, n_obs=5)
+    p = sc.as_float32(c["params"])
+    ref = oracle.solve(p, c["x0"], c["U_nom"], c["obs"], c["path"], c["ds"], c["seed"], c["counter"],
+                       want_uhist=True, want_states=True)
+    s = pkg.Solver(c["params"], max_obstacles=8, max_path_pts=1024)
+    try:
+        a = _dev_inst(c, dev, states=True)
+        b = _dev_inst(c, dev, states=False)
+        s.solve_device_ex(a)
+        s.solve_device_ex(b)
+        torch.cuda.synchronize()
+        assert int(a["status"].item()) == 0
+        states = a["states_out"].cpu().numpy()
+        assert err_state(states, ref["states"]) <= 1e-4
+        # storing the states changes nothing else
+        for k in ("U_out", "traj_out", "J_out"):
+            assert np.array_equal(a[k].cpu().numpy(), b[k].cpu().numpy()), k
+        out = dict(U=a["U_out"].cpu().numpy(), traj=a["traj_out"].cpu().numpy(),
+                   J=a["J_out"].cpu().numpy())
+        assert_solve_matches(out, ref, p, "stored-trajectory variant")
+        # a smaller solve through the same context (S, H below the capacity)
+        c2 = sc.small_random(13, S=77, H=9, n_obs=3)
+        d = _dev_inst(c2, dev, states=True)
+        s.solve_device_ex(d)
+        torch.cuda.synchronize()
+        p2 = sc.as_float32(c2["params"])
+        ref2 = oracle.solve(p2, c2["x0"], c2["U_nom"], c2["obs"], c2["path"], c2["ds"], c2["seed"],
+                            c2["counter"], want_uhist=True, want_states=True)
+        assert err_state(d["states_out"].cpu().numpy(), ref2["states"]) <= 1e-4
+        assert_solve_matches(dict(U=d["U_out"].cpu().numpy(), traj=d["traj_out"].cpu().numpy(),
+                                  J=d["J_out"].cpu().numpy()), ref2, p2, "smaller solve")
+    finally:
+        s.close()
+
+
 @pytest.mark.slow
 def test_config5_full_size_sampled(pkg):
-    # Full-size stress solve: every sample's cost from the GPU; the oracle
-    # recomputes a spread of samples one by one.  U* is checked by its
-    # properties (bounds; convex combination of applied inputs).
+    # Full-size stress solve with the stored-trajectory variant: every
+    # sample's cost and state trajectory from the GPU; the oracle recomputes
+    # a spread of samples one by one.  U* is checked by its properties.
+    import torch
+    dev = torch.device("cuda:0")
     c = sc.config5()
     p = sc.as_float32(c["params"])
-    out = _gpu(pkg, c, max_obs=64)
-    assert np.all(np.isfinite(out["J"]))
-    for s in [0, 1, 4097, 31337, 65535]:
-        one = oracle.rollout_sample(p, c["x0"], c["U_nom"], c["obs"], c["path"], c["ds"], c["seed"],
-                                    c["counter"], s)
-        assert abs(out["J"][s] - one["J"]) / abs(one["J"]) <= EPS_J, s
-    U = out["U"]
-    assert np.all(U >= np.array(p["z_lo"]) - 1e-6) and np.all(U <= np.array(p["z_hi"]) + 1e-6)
-    tr = out["traj"]
-    assert np.all(np.isfinite(tr)) and np.array_equal(tr[0, [4, 5]], c["x0"][[4, 5]].astype(np.float32))
+    s = pkg.Solver(c["params"], max_obstacles=64, max_path_pts=c["path"].shape[0])
+    try:
+        d = _dev_inst(c, dev, states=True)
+        s.solve_device_ex(d)
+        torch.cuda.synchronize()
+        assert int(d["status"].item()) == 0
+        J = d["J_out"].cpu().numpy()
+        U = d["U_out"].cpu().numpy()
+        states = d["states_out"]
+        assert np.all(np.isfinite(J))
+        for smp in [0, 1, 4097, 31337, 65535]:
+            one = oracle.rollout_sample(p, c["x0"], c["U_nom"], c["obs"], c["path"], c["ds"], c["seed"],
+                                        c["counter"], smp)
+            assert abs(J[smp] - one["J"]) / abs(one["J"]) <= EPS_J, smp
+            assert err_state(states[smp].cpu().numpy(), one["states"]) <= 1e-4, smp
+        assert np.all(U >= np.array(p["z_lo"]) - 1e-6) and np.all(U <= np.array(p["z_hi"]) + 1e-6)
+        tr = d["traj_out"].cpu().numpy()
+        assert np.all(np.isfinite(tr))
+    finally:
+        s.close()
