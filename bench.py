@@ -92,6 +92,20 @@ def _traffic_for_current_kernel():
         return None
 
 
+def reduce_job(units: float, seconds: float, dist=None, device=None):
+    """Whole-job throughput over the ranks of a weak-scaling run: the units
+    every rank processed are summed and the time is the slowest rank's.
+    Returns (units / second, total units, max seconds)."""
+    if dist is None:
+        return units / seconds, units, seconds
+    import torch
+    t = torch.tensor([float(seconds)], dtype=torch.float64, device=device)
+    u = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(u.item()) / float(t.item()), float(u.item()), float(t.item())
+
+
 def _measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -521,13 +535,8 @@ def run_ours(args, world, rank, local):
         dist.barrier()
     clk = clocks.stop() if clocks else None
     per = [s.elapsed_time(e) for s, e in zip(starts, ends)]  # ms
-    total_ms = float(sum(per))
-    if dist:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    rollout_steps = world * args.steps * S * H
-    value = rollout_steps / (total_ms * 1e-3)
+    value, _, total_s = reduce_job(args.steps * S * H, float(sum(per)) * 1e-3, dist, dev)
+    total_ms = total_s * 1e3
     lat = np.array(per)
 
     # ---------------- end to end: closed loop through the host entry point
@@ -551,11 +560,8 @@ def run_ours(args, world, rank, local):
         Unom = plant.shift(out["U"])
         tick_s.append(time.perf_counter() - ts)
     el = time.perf_counter() - t0
-    if dist:
-        t = torch.tensor([el], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        el = float(t.item())
-    e2e = {"value": world * args.steps * S * H / el, "unit": UNIT,
+    e2e_value, _, el = reduce_job(args.steps * S * H, el, dist, dev)
+    e2e = {"value": e2e_value, "unit": UNIT,
            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
            "p50_ms": 1e3 * float(np.percentile(tick_s, 50)),
            "p99_ms": 1e3 * float(np.percentile(tick_s, 99)),
