@@ -146,12 +146,13 @@ brmppi::KConst make_kconst(const brmppi_params& q) {
   return k;
 }
 
-brmppi::SmemCaps make_caps(int n_obs, int n_pts, int H) {
+brmppi::SmemCaps make_caps(int n_obs, int n_pts, int H, int tps) {
   brmppi::SmemCaps c{};
   c.obs = 8 * n_obs;
-  c.path = 3 * n_pts;
-  c.unom = 3 * H;
-  c.ustar = static_cast<int>(align_up(3 * static_cast<size_t>(H) + 1, 4));
+  c.path = brmppi::SmemCaps::pad4(3 * n_pts);
+  c.unom = brmppi::SmemCaps::pad4(3 * H);
+  c.ustar = brmppi::SmemCaps::pad4(3 * H + 1);
+  c.noise_per_team = tps > 1 ? 8 * philox_blocks(n_obs) : 0;
   return c;
 }
 
@@ -190,8 +191,7 @@ bool heuristic_plain(const brmppi_ctx* c, int n_obs, int n_pts, Shape* out) {
     if ((c->prm.S + spb - 1) / spb < 2 * c->num_sms) threads = 64;
   }
   if (threads < tps) return false;
-  const brmppi::SmemCaps caps = make_caps(n_obs, n_pts, c->prm.H);
-  while (smem_bytes(caps, threads / tps) > c->smem_limit) {
+  while (smem_bytes(make_caps(n_obs, n_pts, c->prm.H, tps), threads / tps) > c->smem_limit) {
     if (!fixed_threads && threads > kMinThreads) {
       threads -= 32;
     } else if (!fixed_tps && tps < 32) {
@@ -211,7 +211,7 @@ bool plain_shape(const brmppi_ctx* c, int n_obs, int n_pts, Shape* out) {
   if (c->prm.threads_per_sample == 0 && c->prm.block_threads == 0) {
     auto it = c->tuned.find(n_obs);
     if (it != c->tuned.end()) {
-      const brmppi::SmemCaps caps = make_caps(n_obs, n_pts, c->prm.H);
+      const brmppi::SmemCaps caps = make_caps(n_obs, n_pts, c->prm.H, it->second.tps);
       if (smem_bytes(caps, it->second.threads / it->second.tps) <= c->smem_limit) {
         *out = it->second;
         return true;
@@ -269,7 +269,7 @@ brmppi_status enqueue_plain_sized(brmppi_ctx* c, const Shape& sh, int S, int H, 
   L.single = make_inst(x0, U_nom, obs, n_obs, path, n_pts, ds, S, H, seed, counter, U_out, traj_out, J_out,
                        U_next, status, c->d_part, c->d_sync, spb);
   L.single.states_out = states_out;
-  L.caps = make_caps(n_obs, n_pts, H);
+  L.caps = make_caps(n_obs, n_pts, H, sh.tps);
   L.uh = c->d_uh;
   L.uh_stride = 3 * H * spb;
   const size_t smem = smem_bytes(L.caps, spb);
@@ -389,15 +389,19 @@ brmppi_status plan_batch(brmppi_ctx* c, Lane& L, const brmppi_instance* inst, in
     nobs_max = std::max(nobs_max, static_cast<int>(q.n_obs));
     npts_max = std::max(npts_max, static_cast<int>(q.n_pts));
   }
+  // The kernel variant follows the context's obstacle capacity, not this
+  // batch's content: every batch on a context runs the same instantiation,
+  // so a solve gives the same bits alone and in any mix.
+  const int P_cap = std::max(max_P, philox_blocks(c->prm.max_obstacles));
   Shape sh;
   if (forced) {
     sh = *forced;
-    if (!pick_bpt(sh.tps, max_P, &sh.bpt)) return fail(c, BRMPPI_EINVAL, "no variant for this team width");
-  } else if (!batch_shape_default(c, max_P, &sh)) {
+    if (!pick_bpt(sh.tps, P_cap, &sh.bpt)) return fail(c, BRMPPI_EINVAL, "no variant for this team width");
+  } else if (!batch_shape_default(c, P_cap, &sh)) {
     return fail(c, BRMPPI_EINVAL, "no batch launch shape for these instances");
   }
   const int spb = sh.threads / sh.tps;
-  const brmppi::SmemCaps caps = make_caps(nobs_max, npts_max, Hmax);
+  const brmppi::SmemCaps caps = make_caps(nobs_max, npts_max, Hmax, sh.tps);
   const size_t smem = smem_bytes(caps, spb);
   if (smem > c->smem_limit) return fail(c, BRMPPI_EINVAL, "batch tables exceed shared memory");
   size_t pool = 0;
@@ -777,8 +781,8 @@ brmppi_status brmppi_autotune(brmppi_ctx* c, const double* x0, const float* U_no
   float* dT = dU + 3 * H;
   Shape best;
   float best_ms = 1e30f;
-  const brmppi::SmemCaps caps = make_caps(n_obs, n_pts, H);
   for (int tps : {1, 2, 4, 8, 16, 32}) {
+    const brmppi::SmemCaps caps = make_caps(n_obs, n_pts, H, tps);
     int bpt;
     if (!pick_bpt(tps, P, &bpt)) continue;
     for (int threads : {64, 128, 256}) {
@@ -826,7 +830,7 @@ brmppi_status brmppi_autotune_batch(brmppi_ctx* c, const brmppi_instance* inst, 
   Lane& L = c->batch;
   if (L.pending && (e = cudaEventSynchronize(L.batch_done)) != cudaSuccess) return cuda_fail(c, e, "sync");
   L.pending = false;
-  int max_P = 1;
+  int max_P = philox_blocks(c->prm.max_obstacles);
   for (int i = 0; inst && i < n; ++i) max_P = std::max(max_P, philox_blocks(inst[i].n_obs));
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);

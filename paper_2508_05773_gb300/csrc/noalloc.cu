@@ -25,7 +25,7 @@ namespace brmppi_host {
 // defined in api.cu
 std::string check_params(const brmppi_params* p);
 brmppi::KConst make_kconst(const brmppi_params& q);
-brmppi::SmemCaps make_caps(int n_obs, int n_pts, int H);
+brmppi::SmemCaps make_caps(int n_obs, int n_pts, int H, int tps);
 size_t smem_bytes(const brmppi::SmemCaps& c, int spb);
 brmppi::Inst make_inst(const double* x0, const float* U_nom, const float* obs, int n_obs, const float* path,
                        int n_pts, float ds, int S, int H, uint64_t seed, uint64_t counter, float* U_out,
@@ -117,7 +117,7 @@ extern "C" brmppi_status brmppi_solve_device_noalloc(const brmppi_params* p, con
   float* part = scratch + kNaSyncFloats;
   L.single = make_inst(x0_dev, U_nom_dev, obs_dev, n_obs, path_dev, n_pts, ds, p->S, p->H, seed, counter, U_out_dev,
                        traj_out_dev, J_out_dev, U_next_dev, status_dev, part, sync, kNaSpb);
-  L.caps = make_caps(n_obs, n_pts, p->H);
+  L.caps = make_caps(n_obs, n_pts, p->H, kNaTps);
   L.uh = part + kNaPartFloats;
   L.uh_stride = 3 * p->H * kNaSpb;
   const size_t smem = smem_bytes(L.caps, kNaSpb);

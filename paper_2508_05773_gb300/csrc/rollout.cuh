@@ -89,9 +89,15 @@ struct Inst {
 };
 
 // Shared-memory capacities of a launch (floats).
+// Every region is a multiple of 4 floats (16 bytes): float4 accesses stay
+// aligned.
 struct SmemCaps {
   int obs, path, unom, ustar;
-  __host__ __device__ int total(int spb) const { return obs + path + unom + ustar + 3 * spb + 256; }
+  int noise_per_team;  // teams wider than one lane: staged normals, 2 steps x P blocks x 4
+  __host__ __device__ static int pad4(int n) { return (n + 3) & ~3; }
+  __host__ __device__ int total(int spb) const {
+    return obs + path + unom + ustar + pad4(3 * spb) + 256 + noise_per_team * spb;
+  }
 };
 
 struct LaunchDesc {
@@ -220,6 +226,8 @@ struct Smem {
   float* jl;     // spb
   float* w;      // spb
   float* chunk;  // 256
+  float* noise;  // spb x noise_per_team
+  int noise_per_team;
   __device__ Smem(float* base, const SmemCaps& c, int spb) {
     obs = base;
     path = obs + c.obs;
@@ -228,7 +236,9 @@ struct Smem {
     jh = ustar + c.ustar;
     jl = jh + spb;
     w = jl + spb;
-    chunk = w + spb;
+    chunk = jh + SmemCaps::pad4(3 * spb);
+    noise = chunk + 256;
+    noise_per_team = c.noise_per_team;
   }
 };
 
@@ -279,9 +289,13 @@ __device__ void run_tile(const KConst& k, const Inst& in, int tile, float* uh, c
   const float c0 = fr.c0, s0 = fr.s0;
   float px = 0.f, pxl = 0.f, py = 0.f, pyl = 0.f, t1 = 0.f, t2 = fr.t2, v = fr.v_h, vl = fr.v_l,
         dl = fr.dl, ps = 0.f, psl = 0.f;
-  float alpha[4 * BPT];
+  // obstacle slots per lane: one lane per sample holds every obstacle of
+  // its Philox blocks 1.. ; wider teams hold obstacles lt, lt + TPS, ...
+  constexpr int OBS_SLOTS = (TPS == 1) ? (BPT > 1 ? 4 * (BPT - 1) : 1) : 4 * BPT;
+  float alpha_h = k.alpha0;  // the hitch's barrier rate (same on every lane)
+  float alpha[OBS_SLOTS];
 #pragma unroll
-  for (int q = 0; q < 4 * BPT; ++q) alpha[q] = k.alpha0;
+  for (int q = 0; q < OBS_SLOTS; ++q) alpha[q] = k.alpha0;
   float Jh = 0.f, Jl = 0.f;
   float ua = 0.f, uw = 0.f, un = 0.f;  // applied input of the previous step
   const uint32_t sid = static_cast<uint32_t>(s);
@@ -354,11 +368,35 @@ __device__ void run_tile(const KConst& k, const Inst& in, int tile, float* uh, c
   };
   if (st_out) store_state(0);
 
+  // Noise.  One lane per sample: the lane draws Philox block 0 a step ahead
+  // and the further blocks where their rows are built.  Wider teams: each
+  // lane draws the blocks b = lt, lt + TPS, ... of the next step into a
+  // per-team double buffer in shared memory, and constraint i is built by
+  // lane i % TPS, so rows spread evenly over the team.
+  float* nz = S.noise + team * S.noise_per_team;  // [2][P][4] (wide teams)
+  auto stage_step = [&](int tau_d, float* buf) {
+    for (int b = lt; b < in.P; b += TPS) {
+      float t4[4];
+      draw_block(b, tau_d, t4);
+      *reinterpret_cast<float4*>(buf + 4 * b) = make_float4(t4[0], t4[1], t4[2], t4[3]);
+    }
+  };
   float nrm[4];
-  draw_first(0, nrm);
+  if constexpr (TPS == 1) {
+    draw_first(0, nrm);
+  } else {
+    stage_step(0, nz);
+  }
   for (int tau = 0; tau < H; ++tau) {
     float nxt[4];
-    draw_first(tau + 1 < H ? tau + 1 : tau, nxt);  // off the state's critical path
+    float* cur = nz;
+    if constexpr (TPS == 1) {
+      draw_first(tau + 1 < H ? tau + 1 : tau, nxt);  // off the state's critical path
+    } else {
+      __syncwarp();  // this step's normals are staged; last step's reads are done
+      cur = nz + (tau & 1) * 4 * in.P;
+      if (tau + 1 < H) stage_step(tau + 1, nz + ((tau + 1) & 1) * 4 * in.P);
+    }
 
     // trigonometry of the current state
     float sr, cr;
@@ -375,9 +413,16 @@ __device__ void run_tile(const KConst& k, const Inst& in, int tile, float* uh, c
     // cost of the previous step, at this state (independent of the rows)
     if (tau > 0) stage_cost();
 
-    const float na = team_bcast0<TPS>(nrm[0]);
-    const float nw = team_bcast0<TPS>(nrm[1]);
-    const float nn = team_bcast0<TPS>(nrm[2]);
+    float na, nw, nn;
+    if constexpr (TPS == 1) {
+      na = nrm[0];
+      nw = nrm[1];
+      nn = nrm[2];
+    } else {
+      na = cur[0];
+      nw = cur[1];
+      nn = cur[2];
+    }
     const float zd0 = clampf(S.unom[3 * tau + 0] + k.sig0 * na, k.zlo0, k.zhi0);
     const float zd1 = clampf(S.unom[3 * tau + 1] + k.sig1 * nw, k.zlo1, k.zhi1);
     const float zd2 = clampf(S.unom[3 * tau + 2] + k.sig2 * nn, k.zlo2, k.zhi2);
@@ -388,75 +433,109 @@ __device__ void run_tile(const KConst& k, const Inst& in, int tile, float* uh, c
       const float pu1 = k.w_u1 * zd1 + k.pc_u1;
       const float pu2 = k.w_u2 * zd2 + k.pc_u2;
       const float q0 = pu0 * k.inv_m_u0, q1 = pu1 * k.inv_m_u1;  // M_u^-1 p_u
-      float Saa = 0.f, Saw = 0.f, Sww = 0.f, ga = 0.f, gw = 0.f;
-      float ca[4 * BPT], cc[4 * BPT];
-      float cwh = 0.f;  // steer-rate coefficient: only the hitch row has one
+      // hitch row: every lane of the team computes it (same state, same
+      // normal); its terms enter the team sums once (lane 0)
+      float Saa, Saw, Sww, ga, gw, ca_h, cw_h, cc_h;
+      {
+        const float n_h = (TPS == 1) ? nrm[3] : cur[3];
+        const float Delta = t2 - t1;
+        const float sg = Delta >= 0.f ? 1.f : -1.f;
+        const float G = sp - k.k_hitch * cp * tn;
+        const float th2dot = vv * G * k.inv_l2;
+        const float phidot = th1dot - th2dot;
+        const float sec2 = 1.f + tn * tn;
+        const float h = k.dtheta_max - k.kappa * vv - sg * Delta;
+        const float Aa = -k.Ts * k.kappa - k.hTs2 * sg * (G * k.inv_l2 - tn * k.inv_l1);
+        const float Aw = k.hTs2 * sg * vv * sec2 * (k.k_hitch * cp * k.inv_l2 + k.inv_l1);
+        const float c0h = -k.Ts * sg * (th2dot - th1dot) -
+                          k.hTs2 * sg * vv * k.inv_l2 * (cp + k.k_hitch * tn * sp) * phidot;
+        const float hm = fmaxf(fabsf(h), k.h_floor);
+        const float ht = h >= 0.f ? hm : -hm;
+        const float zda = clampf(k.sigma_alpha * n_h, k.ua_lo, k.ua_hi);
+        const float pa = k.w_a * zda + k.pc_a;
+        const float b = -alpha_h * h - c0h;
+        const float r = Aa * q0 + Aw * q1 + ht * pa * k.inv_m_a - b;
+        const float iht = 1.f / ht;
+        const float own = (lt == 0) ? k.m_a * iht * iht : 0.f;  // 1/D on lane 0
+        Saa = Aa * Aa * own;
+        Saw = Aa * Aw * own;
+        Sww = Aw * Aw * own;
+        ga = Aa * r * own;
+        gw = Aw * r * own;
+        ca_h = Aa * iht;
+        cw_h = Aw * iht;
+        cc_h = pa * k.inv_m_a - r * iht;
+      }
+
+      // ellipse rows (e = 2) in the obstacle frame; the steer rate does not
+      // enter at second order, and hdot shares dh/da's direction term.
+      // `live` = 0 turns a padding slot into a no-op without branching.
+      float ca[OBS_SLOTS], cc[OBS_SLOTS];
 #pragma unroll
-      for (int b8 = 0; b8 < BPT; ++b8) {
-        const int blk = lt + TPS * b8;
-        float nb[4];
-        if (b8 == 0) {
+      for (int q = 0; q < OBS_SLOTS; ++q) ca[q] = cc[q] = 0.f;
+      auto obstacle_row = [&](int j, float n_alpha, int slot, float live) {
+        const float4 o0 = *reinterpret_cast<const float4*>(S.obs + 8 * j);
+        const float2 o1 = *reinterpret_cast<const float2*>(S.obs + 8 * j + 4);
+        const float dx = (px - o0.x) + pxl, dy = (py - o0.y) + pyl;
+        const float co = o0.z, so = o0.w, iax = o1.x, iay = o1.y;
+        const float xp = co * dx + so * dy;
+        const float yp = co * dy - so * dx;
+        const float h = xp * xp * iax + yp * yp * iay - 1.f;
+        const float hx = 2.f * xp * iax, hy = 2.f * yp * iay;
+        const float dirx = co * c1 + so * s1, diry = co * s1 - so * c1;
+        const float gda = hx * dirx + hy * diry;  // dh along the heading
+        const float hdd0 = vv * th1dot * (hy * dirx - hx * diry) +
+                           2.f * vv * vv * (iax * dirx * dirx + iay * diry * diry);
+        const float Aa = k.hTs2 * gda;
+        const float brest = -k.Ts * vv * gda - k.hTs2 * hdd0;
+        const float hm = fmaxf(fabsf(h), k.h_floor);
+        const float ht = h >= 0.f ? hm : -hm;
+        const float zda = clampf(k.sigma_alpha * n_alpha, k.ua_lo, k.ua_hi);
+        const float pa = k.w_a * zda + k.pc_a;
+        const float b = -alpha[slot] * h + brest;
+        const float r = Aa * q0 + ht * pa * k.inv_m_a - b;
+        const float iht = 1.f / ht;
+        const float invD = live * k.m_a * iht * iht;
+        Saa += Aa * Aa * invD;
+        ga += Aa * r * invD;
+        ca[slot] = live * (Aa * iht);
+        cc[slot] = live * (pa * k.inv_m_a - r * iht);
+      };
+
+      if constexpr (TPS == 1) {
+        // obstacle j uses normal 4 + j: block 1 + j/4, drawn here
 #pragma unroll
-          for (int m = 0; m < 4; ++m) nb[m] = nrm[m];
-        } else if (blk < in.P) {
-          draw_block(blk, tau, nb);
+        for (int b8 = 1; b8 < BPT; ++b8) {
+          if (b8 < in.P) {
+            float nb[4];
+            draw_block(b8, tau, nb);
+#pragma unroll
+            for (int m = 0; m < 4; ++m) {
+              const int j = 4 * (b8 - 1) + m;
+              ca[j] = 0.f;
+              cc[j] = 0.f;
+              if (j < in.n_obs) obstacle_row(j, nb[m], j, 1.f);
+            }
+          } else {
+#pragma unroll
+            for (int m = 0; m < 4; ++m) {
+              ca[4 * (b8 - 1) + m] = 0.f;
+              cc[4 * (b8 - 1) + m] = 0.f;
+            }
+          }
         }
+      } else {
+        // obstacle j on lane j % TPS; every lane runs the team's slot count
+        const int per_lane = (in.n_obs + TPS - 1) / TPS;
 #pragma unroll
-        for (int m = 0; m < 4; ++m) {
-          const int slot = 4 * b8 + m;
-          const int i = 4 * blk + m - 3;  // constraint index
+        for (int slot = 0; slot < OBS_SLOTS; ++slot) {
           ca[slot] = 0.f;
           cc[slot] = 0.f;
-          if (i >= 0 && i < Nc) {
-            float Aa, Aw, h, brest;
-            if (i == 0) {
-              // hitch row: Delta = th2 - th1, sigma = sgn(Delta), sgn(0) = +1
-              const float Delta = t2 - t1;
-              const float sg = Delta >= 0.f ? 1.f : -1.f;
-              const float G = sp - k.k_hitch * cp * tn;
-              const float th2dot = vv * G * k.inv_l2;
-              const float phidot = th1dot - th2dot;
-              const float sec2 = 1.f + tn * tn;
-              h = k.dtheta_max - k.kappa * vv - sg * Delta;
-              Aa = -k.Ts * k.kappa - k.hTs2 * sg * (G * k.inv_l2 - tn * k.inv_l1);
-              Aw = k.hTs2 * sg * vv * sec2 * (k.k_hitch * cp * k.inv_l2 + k.inv_l1);
-              const float c0h = -k.Ts * sg * (th2dot - th1dot) -
-                                k.hTs2 * sg * vv * k.inv_l2 * (cp + k.k_hitch * tn * sp) * phidot;
-              brest = -c0h;
-            } else {
-              // ellipse row (e = 2) in the obstacle frame
-              const float* ob = S.obs + 8 * (i - 1);
-              const float dx = (px - ob[0]) + pxl, dy = (py - ob[1]) + pyl;
-              const float co = ob[2], so = ob[3], iax = ob[4], iay = ob[5];
-              const float xp = co * dx + so * dy;
-              const float yp = co * dy - so * dx;
-              h = xp * xp * iax + yp * yp * iay - 1.f;
-              const float hx = 2.f * xp * iax, hy = 2.f * yp * iay;
-              const float dirx = co * c1 + so * s1, diry = co * s1 - so * c1;
-              const float velx = vv * dirx, vely = vv * diry;
-              const float vw = vv * th1dot;
-              const float hdot = hx * velx + hy * vely;
-              const float hdd0 = vw * (hy * dirx - hx * diry) + 2.f * (iax * velx * velx + iay * vely * vely);
-              Aa = k.hTs2 * (hx * dirx + hy * diry);
-              Aw = 0.f;
-              brest = -k.Ts * hdot - k.hTs2 * hdd0;
-            }
-            const float hm = fmaxf(fabsf(h), k.h_floor);
-            const float ht = h >= 0.f ? hm : -hm;
-            const float zda = clampf(k.sigma_alpha * nb[m], k.ua_lo, k.ua_hi);
-            const float pa = k.w_a * zda + k.pc_a;
-            const float b = -alpha[slot] * h + brest;
-            const float r = Aa * q0 + Aw * q1 + ht * pa * k.inv_m_a - b;
-            const float iht = 1.f / ht;
-            const float invD = k.m_a * iht * iht;
-            Saa += Aa * Aa * invD;
-            Saw += Aa * Aw * invD;
-            Sww += Aw * Aw * invD;
-            ga += Aa * r * invD;
-            gw += Aw * r * invD;
-            ca[slot] = Aa * iht;
-            if (i == 0) cwh = Aw * iht;
-            cc[slot] = pa * k.inv_m_a - r * iht;
+          if (slot < per_lane) {
+            const int j = lt + TPS * slot;
+            const bool live = j < in.n_obs;
+            const int jj = live ? j : 0;
+            obstacle_row(jj, cur[4 + jj], slot, live ? 1.f : 0.f);
           }
         }
       }
@@ -471,9 +550,9 @@ __device__ void run_tile(const KConst& k, const Inst& in, int tile, float* uh, c
       za = q0 - ya;
       zw = q1 - yw;
       zn = pu2 * k.inv_m_u2;
+      alpha_h += cc_h + ca_h * ya + cw_h * yw;
 #pragma unroll
-      for (int slot = 0; slot < 4 * BPT; ++slot) alpha[slot] += cc[slot] + ca[slot] * ya;
-      alpha[3] += cwh * yw;  // the hitch sits in slot 3 of lane 0 (cwh = 0 elsewhere)
+      for (int slot = 0; slot < OBS_SLOTS; ++slot) alpha[slot] += cc[slot] + ca[slot] * ya;
     } else {
       za = zd0;
       zw = zd1;
@@ -499,8 +578,10 @@ __device__ void run_tile(const KConst& k, const Inst& in, int tile, float* uh, c
       uh[(3 * tau + 2) * spb + team] = un;
     }
     if (st_out) store_state(tau + 1);
+    if constexpr (TPS == 1) {
 #pragma unroll
-    for (int q = 0; q < 4; ++q) nrm[q] = nxt[q];
+      for (int q = 0; q < 4; ++q) nrm[q] = nxt[q];
+    }
   }
   stage_cost();  // cost of the last step
 
@@ -657,7 +738,7 @@ static __device__ void merge_instance(const KConst& k, const Inst& in, const Sme
         tr[7 * tau + 3] = (fr.oth_h + q2) + fr.oth_l;
         tr[7 * tau + 4] = qv;
         tr[7 * tau + 5] = qd;
-        tr[7 * tau + 6] = static_cast<float>(fr.psi0 + static_cast<double>(qp));
+        tr[7 * tau + 6] = (fr.psi_h + qp) + fr.psi_l;
         if (tau == H) break;
         float a1, b1, a2, b2, ad, bd;
         __sincosf(q1, &a1, &b1);
