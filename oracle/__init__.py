@@ -62,7 +62,20 @@ class _Params(ctypes.Structure):
         ("ua_lo", ctypes.c_double), ("ua_hi", ctypes.c_double),
         ("w_u", ctypes.c_double * 3), ("w_alpha", ctypes.c_double),
         ("rho", ctypes.c_double), ("h_floor", ctypes.c_double),
+        ("q_coll", ctypes.c_double),
+        ("alpha_stab", ctypes.c_double), ("q_stab", ctypes.c_double * 2),
+        ("q_abuf", ctypes.c_double), ("h_buf", ctypes.c_double),
     ]
+
+PROJ_NONE = 1
+COLLISION_COST = 2
+OBS8 = 4
+ALPHA_BUFFER = 8
+
+
+def obs_stride(p: dict) -> int:
+    """Doubles per obstacle row under the flags of p."""
+    return 8 if int(p["flags"]) & OBS8 else 6
 
 
 _DP = ctypes.POINTER(ctypes.c_double)
@@ -100,6 +113,14 @@ def _load():
                                              ctypes.c_double, ctypes.c_uint64, ctypes.c_uint64,
                                              _DP, _DP, _DP, _DP, _DP]),
                 "orc_integrate": (None, [P, _DP, _DP, ctypes.c_int, _DP]),
+                "orc_obstacle_h_at": (ctypes.c_double, [P, _DP, ctypes.c_int, ctypes.c_double,
+                                                        _DP]),
+                "orc_obstacle_row_at": (None, [P, _DP, ctypes.c_int, ctypes.c_double, _DP, _DP,
+                                               _DP, _DP]),
+                "orc_collision_cost": (ctypes.c_double, [P, _DP, ctypes.c_int, ctypes.c_int,
+                                                         ctypes.c_double, _DP]),
+                "orc_alpha_buffer_cost": (ctypes.c_double, [P, ctypes.c_int, _DP, _DP]),
+                "orc_hitch_stabilize": (ctypes.c_int, [P, _DP, _DP, _DP, _DP]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(lib, name)
@@ -129,7 +150,8 @@ class using_library:
         for name in ("orc_philox4x32_10", "orc_normals", "orc_dynamics_step", "orc_obstacle_h",
                      "orc_obstacle_row", "orc_hitch_h", "orc_hitch_row", "orc_project",
                      "orc_path_lookup", "orc_stage_cost", "orc_softmin", "orc_rollout_sample",
-                     "orc_solve", "orc_integrate"):
+                     "orc_solve", "orc_integrate", "orc_obstacle_h_at", "orc_obstacle_row_at",
+                     "orc_collision_cost", "orc_alpha_buffer_cost", "orc_hitch_stabilize"):
             src = getattr(self.saved, name)
             dst = getattr(lib, name)
             dst.restype = src.restype
@@ -251,6 +273,51 @@ def obstacle_row(p: dict, obs, x):
     return Au, h.value, br.value
 
 
+def obstacle_h_at(p: dict, obs, x, t: float) -> float:
+    """h of one obstacle row (6 or 8 entries) at time t."""
+    lib = _load()
+    o = _d(obs)
+    return lib.orc_obstacle_h_at(ctypes.byref(_params(p)), _ptr(o), o.size, float(t),
+                                 _ptr(_d(x, 7)))
+
+
+def obstacle_row_at(p: dict, obs, x, t: float):
+    """Row of one obstacle (6 or 8 entries) at time t: (A_u[3], h, b_rest)."""
+    lib = _load()
+    o = _d(obs)
+    Au = np.zeros(3)
+    h = ctypes.c_double()
+    br = ctypes.c_double()
+    lib.orc_obstacle_row_at(ctypes.byref(_params(p)), _ptr(o), o.size, float(t), _ptr(_d(x, 7)),
+                            _ptr(Au), ctypes.byref(h), ctypes.byref(br))
+    return Au, h.value, br.value
+
+
+def collision_cost(p: dict, obs, x, t: float = 0.0) -> float:
+    lib = _load()
+    stride = obs_stride(p)
+    o = _d(obs).reshape(-1, stride)
+    return lib.orc_collision_cost(ctypes.byref(_params(p)), _ptr(o) if o.size else None, stride,
+                                  o.shape[0], float(t), _ptr(_d(x, 7)))
+
+
+def alpha_buffer_cost(p: dict, h, alpha) -> float:
+    lib = _load()
+    h = _d(h)
+    return lib.orc_alpha_buffer_cost(ctypes.byref(_params(p)), h.size, _ptr(h),
+                                     _ptr(_d(alpha, h.size)))
+
+
+def hitch_stabilize(p: dict, x, u_ref):
+    """Returns (infeasible, u[3], slack)."""
+    lib = _load()
+    u = np.zeros(3)
+    sl = ctypes.c_double()
+    st = lib.orc_hitch_stabilize(ctypes.byref(_params(p)), _ptr(_d(x, 7)), _ptr(_d(u_ref, 3)),
+                                 _ptr(u), ctypes.byref(sl))
+    return st, u, sl.value
+
+
 def hitch_h(p: dict, x) -> float:
     lib = _load()
     P = _params(p)
@@ -313,7 +380,7 @@ def rollout_sample(p: dict, x0, U_nom, obs, path, ds, seed, counter, s):
     """One rollout; returns dict(states, u, alpha, z_des, z_star, J, status)."""
     lib = _load()
     H = int(p["H"])
-    obs = _d(obs).reshape(-1, 6)
+    obs = _d(obs).reshape(-1, obs_stride(p))
     n_obs = obs.shape[0]
     Nc = 1 + n_obs
     d = 3 + Nc
@@ -338,7 +405,7 @@ def solve(p: dict, x0, U_nom, obs, path, ds, seed, counter, *, want_J=True, want
     lib = _load()
     S = int(p["S"]) if S is None else int(S)
     H = int(p["H"])
-    obs = _d(obs).reshape(-1, 6)
+    obs = _d(obs).reshape(-1, obs_stride(p))
     n_obs = obs.shape[0]
     path = _d(path)
     U = np.zeros((H, 3))

@@ -118,6 +118,8 @@ void orc_integrate(const orc_params *P, const double x0[7], const double *U, int
   for (int k = 0; k < H; ++k) orc_dynamics_step(P, traj + 7 * k, U + 3 * k, traj + 7 * (k + 1));
 }
 
+static double clip(double v, double lo, double hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
 /* ------------------------------------------------------------------ */
 /* Integer power for the super-ellipse exponent. */
 static double ipow(double base, int e) {
@@ -126,24 +128,39 @@ static double ipow(double base, int e) {
   return r;
 }
 
-static int obstacle_exponent(const double obs[6]) {
+static int obstacle_exponent(const double *obs) {
   double e = obs[5];
   int ei = (int)e;
   if ((double)ei != e || ei < 2 || (ei % 2) != 0) return -1;
   return ei;
 }
 
+/* Velocity of an obstacle row: zero for rows of 6, (vx, vy) for rows of 8. */
+static void obstacle_velocity(const double *obs, int stride, double *vx, double *vy) {
+  *vx = (stride >= 8) ? obs[6] : 0.0;
+  *vy = (stride >= 8) ? obs[7] : 0.0;
+}
+
 /* Super-ellipse barrier (Sec. IV-C, Eq. barrier_function): semi-axes
    inflated by the footprint disc radius, coordinates rotated into the
-   obstacle frame. */
-double orc_obstacle_h(const orc_params *P, const double obs[6], const double x[7]) {
+   obstacle frame; a moving obstacle (predicted pedestrian) has its centre at
+   c + t v at time t. */
+double orc_obstacle_h_at(const orc_params *P, const double *obs, int stride, double t,
+                         const double x[7]) {
   const int e = obstacle_exponent(obs);
   if (e < 0) return NAN;
-  const double cx = obs[0], cy = obs[1], Ax = obs[2] + P->r_inflate, Ay = obs[3] + P->r_inflate;
+  double vx, vy;
+  obstacle_velocity(obs, stride, &vx, &vy);
+  const double cx = obs[0] + t * vx, cy = obs[1] + t * vy;
+  const double Ax = obs[2] + P->r_inflate, Ay = obs[3] + P->r_inflate;
   const double th_o = obs[4];
   const double xp = cos(th_o) * (x[0] - cx) + sin(th_o) * (x[1] - cy);
   const double yp = -sin(th_o) * (x[0] - cx) + cos(th_o) * (x[1] - cy);
   return ipow(xp / Ax, e) + ipow(yp / Ay, e) - 1.0;
+}
+
+double orc_obstacle_h(const orc_params *P, const double obs[6], const double x[7]) {
+  return orc_obstacle_h_at(P, obs, 6, 0.0, x);
 }
 
 /* Barrier-rate equality row for one obstacle (Eq. cbf_equality with the
@@ -151,15 +168,21 @@ double orc_obstacle_h(const orc_params *P, const double obs[6], const double x[7
    Along the continuous field with the input held, the rear-axle point
    moves with  pdot = v (cos th1, sin th1)  and
    pddot = a (cos th1, sin th1) + v * th1dot * (-sin th1, cos th1),
-   th1dot = v tan(delta) / l1.  With h = h(x', y'):
-   hdot  = grad h . pdot',  hddot = grad h . pddot' + pdot'^T Hess h pdot'.
+   th1dot = v tan(delta) / l1, while the obstacle centre moves at the
+   constant velocity c_dot (zero for a parked vehicle).  With h = h(x', y')
+   of the relative position p - c:
+   hdot  = grad h . (pdot - c_dot)',
+   hddot = grad h . pddot' + (pdot - c_dot)'^T Hess h (pdot - c_dot)'.
    hddot is affine in a; steer rate and progress rate do not enter at second
    order.  Row: A_u = (Ts^2/2 * dhddot/da, 0, 0) and
    b = -alpha h - Ts hdot - Ts^2/2 hddot|_{a=0}. */
-void orc_obstacle_row(const orc_params *P, const double obs[6], const double x[7],
-                      double A_u[3], double *h, double *b_rest) {
+void orc_obstacle_row_at(const orc_params *P, const double *obs, int stride, double t,
+                         const double x[7], double A_u[3], double *h, double *b_rest) {
   const int e = obstacle_exponent(obs);
-  const double cx = obs[0], cy = obs[1], Ax = obs[2] + P->r_inflate, Ay = obs[3] + P->r_inflate;
+  double vx, vy;
+  obstacle_velocity(obs, stride, &vx, &vy);
+  const double cx = obs[0] + t * vx, cy = obs[1] + t * vy;
+  const double Ax = obs[2] + P->r_inflate, Ay = obs[3] + P->r_inflate;
   const double th_o = obs[4];
   const double co = cos(th_o), so = sin(th_o);
   const double px = x[0], py = x[1], th1 = x[2], v = x[4], delta = x[5];
@@ -181,8 +204,8 @@ void orc_obstacle_row(const orc_params *P, const double obs[6], const double x[7
 
   const double c1 = cos(th1), s1 = sin(th1);
   const double th1dot = v * tan(delta) / P->l1;
-  /* velocity, and the two parts of the acceleration */
-  const double vel_x = ROT_X(v * c1, v * s1), vel_y = ROT_Y(v * c1, v * s1);
+  /* relative velocity, and the two parts of the acceleration */
+  const double vel_x = ROT_X(v * c1 - vx, v * s1 - vy), vel_y = ROT_Y(v * c1 - vx, v * s1 - vy);
   const double dir_x = ROT_X(c1, s1), dir_y = ROT_Y(c1, s1); /* multiplies a */
   const double cen_x = ROT_X(-v * th1dot * s1, v * th1dot * c1);
   const double cen_y = ROT_Y(-v * th1dot * s1, v * th1dot * c1);
@@ -198,6 +221,40 @@ void orc_obstacle_row(const orc_params *P, const double obs[6], const double x[7
   A_u[2] = 0.0;
   *h = hval;
   *b_rest = -Ts * hdot - 0.5 * Ts * Ts * hddot_0;
+}
+
+void orc_obstacle_row(const orc_params *P, const double obs[6], const double x[7],
+                      double A_u[3], double *h, double *b_rest) {
+  orc_obstacle_row_at(P, obs, 6, 0.0, x, A_u, h, b_rest);
+}
+
+/* Standard MPPI with a collision cost (the comparison method of Sec. V):
+   each obstacle the state penetrates adds q_coll times its depth -h_o (a
+   hinge, zero outside). */
+double orc_collision_cost(const orc_params *P, const double *obs, int stride, int n_obs, double t,
+                          const double x[7]) {
+  double c = 0.0;
+  for (int o = 0; o < n_obs; ++o) {
+    const double h = orc_obstacle_h_at(P, obs + (size_t)stride * (size_t)o, stride, t, x);
+    if (h < 0.0) c += -h;
+  }
+  return P->q_coll * c;
+}
+
+/* Buffer-zone cost of BR-MPPI (Sec. IV-A): positive barrier rates are
+   charged near an obstacle, pushing the sampled rates negative there (hdot
+   >= 0 close to the boundary).  The zone weight falls linearly from 1 at
+   h = 0 to 0 at h = h_buf. */
+double orc_alpha_buffer_cost(const orc_params *P, int n, const double *h, const double *alpha) {
+  double c = 0.0;
+  for (int i = 0; i < n; ++i) {
+    double w = 1.0 - h[i] / P->h_buf;
+    if (w < 0.0) w = 0.0;
+    if (w > 1.0) w = 1.0;
+    const double ap = alpha[i] > 0.0 ? alpha[i] : 0.0;
+    c += w * ap * ap;
+  }
+  return P->q_abuf * c;
 }
 
 /* Hitch-angle barrier (Sec. IV-D, Eq. hitch_angle_barrier):
@@ -246,6 +303,67 @@ void orc_hitch_row(const orc_params *P, const double x[7], double A_u[3], double
   A_u[2] = 0.0;
   *h = orc_hitch_h(P, x);
   *b_rest = -c0;
+}
+
+/* Hitch-angle stabilizer (Sec. IV-D, Eq. hitch_angle_qp): after BR-MPPI,
+   the reference input u_ref = (a, omega, nu) is moved to
+     argmin (u - u_ref)^T Q_h (u - u_ref)  over (a, omega) in the input box
+     s.t.  Ts hdot + Ts^2/2 hddot >= -alpha_stab h_h(x),
+   the discrete CBF condition (Eq. barrier_constraint_prelim, with the sign
+   of Eq. cbf_equality and the same second-order increment as the rollout's
+   hitch row, g . u + c0).  nu does not move the vehicle and passes through.
+   KKT for a diagonal Q_h and a box: if the box projection of u_ref meets the
+   condition it is the minimiser; otherwise the condition is active and
+   u(mu) = clip(u_ref + mu Q_h^-1 g) with the smallest mu >= 0 that meets it.
+   g . u(mu) is continuous and non-decreasing in mu, so mu is found by
+   bisection. */
+int orc_hitch_stabilize(const orc_params *P, const double x[7], const double u_ref[3],
+                        double u_out[3], double *slack) {
+  double A_u[3], h, b_rest;
+  orc_hitch_row(P, x, A_u, &h, &b_rest);
+  const double g[2] = {A_u[0], A_u[1]};
+  const double c0 = -b_rest;
+  const double rhs = -P->alpha_stab * h - c0; /* need g . u >= rhs */
+  double u[2];
+  int infeasible = 0;
+  for (int j = 0; j < 2; ++j) u[j] = clip(u_ref[j], P->z_lo[j], P->z_hi[j]);
+  if (g[0] * u[0] + g[1] * u[1] < rhs) {
+    double lo = 0.0, hi = 1.0, cand[2];
+#define U_OF_MU(mu, out)                                                             \
+  for (int j = 0; j < 2; ++j)                                                        \
+    (out)[j] = clip(u_ref[j] + (mu) * g[j] / P->q_stab[j], P->z_lo[j], P->z_hi[j]);
+    for (;;) {
+      U_OF_MU(hi, cand);
+      if (g[0] * cand[0] + g[1] * cand[1] >= rhs) break;
+      lo = hi;
+      hi *= 2.0;
+      if (hi > 1e300) {
+        infeasible = 1;
+        break;
+      }
+    }
+    if (infeasible) {
+      /* no input in the box meets the condition: the one that comes closest */
+      for (int j = 0; j < 2; ++j)
+        u[j] = g[j] > 0.0 ? P->z_hi[j] : (g[j] < 0.0 ? P->z_lo[j] : clip(u_ref[j], P->z_lo[j], P->z_hi[j]));
+    } else {
+      for (int it = 0; it < 2000 && hi - lo > 1e-17 * hi; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        U_OF_MU(mid, cand);
+        if (g[0] * cand[0] + g[1] * cand[1] >= rhs)
+          hi = mid;
+        else
+          lo = mid;
+      }
+      U_OF_MU(hi, u);
+    }
+#undef U_OF_MU
+  }
+  u_out[0] = u[0];
+  u_out[1] = u[1];
+  u_out[2] = u_ref[2];
+  if (slack) *slack = g[0] * u[0] + g[1] * u[1] - rhs;
+  return infeasible;
 }
 
 /* ------------------------------------------------------------------ */
@@ -421,7 +539,6 @@ int orc_softmin(int S, const double *J, double lambda, double *gamma_bar) {
   return ORC_OK;
 }
 
-static double clip(double v, double lo, double hi) { return v < lo ? lo : (v > hi ? hi : v); }
 
 /* ------------------------------------------------------------------ */
 /* One BR-MPPI rollout (Sec. IV-A): at every step sample z_des, build the
@@ -436,8 +553,9 @@ int orc_rollout_sample(const orc_params *P, const double x0[7], const double *U_
   const int Nc = 1 + n_obs;
   const int d = 3 + Nc;
   const int proj = !(P->flags & ORC_PROJ_NONE);
+  const int stride = (P->flags & ORC_OBS8) ? 8 : 6;
   for (int o = 0; o < n_obs; ++o)
-    if (obstacle_exponent(obs + 6 * o) < 0) return ORC_EINVAL;
+    if (obstacle_exponent(obs + (size_t)stride * (size_t)o) < 0) return ORC_EINVAL;
   if (n_pts < 2 || !(ds > 0.0)) return ORC_EINVAL;
 
   double *n = (double *)malloc(sizeof(double) * (size_t)d);
@@ -449,6 +567,7 @@ int orc_rollout_sample(const orc_params *P, const double x0[7], const double *U_
   double *zhi = (double *)malloc(sizeof(double) * (size_t)d);
   double *zdes = (double *)malloc(sizeof(double) * (size_t)d);
   double *zs = (double *)malloc(sizeof(double) * (size_t)d);
+  double *hrow = (double *)malloc(sizeof(double) * (size_t)Nc);
   for (int j = 0; j < 3; ++j) {
     w[j] = P->w_u[j];
     zlo[j] = P->z_lo[j];
@@ -483,7 +602,9 @@ int orc_rollout_sample(const orc_params *P, const double x0[7], const double *U_
         if (i == 0)
           orc_hitch_row(P, x, Au, &h, &b_rest);
         else
-          orc_obstacle_row(P, obs + 6 * (i - 1), x, Au, &h, &b_rest);
+          orc_obstacle_row_at(P, obs + (size_t)stride * (size_t)(i - 1), stride, tau * P->Ts, x,
+                              Au, &h, &b_rest);
+        hrow[i] = h;
         const double hmag = fabs(h) > P->h_floor ? fabs(h) : P->h_floor;
         const double h_tilde = (h >= 0.0) ? hmag : -hmag;
         for (int j = 0; j < d; ++j) A[i * d + j] = 0.0;
@@ -509,10 +630,16 @@ int orc_rollout_sample(const orc_params *P, const double x0[7], const double *U_
     if (proj)
       for (int i = 0; i < Nc; ++i) alpha[i] += zs[3 + i];
 
-    /* 5. kinematics and stage cost at the new state */
+    /* 5. kinematics and stage cost at the new state; the comparison
+       method's collision cost there, and the buffer cost of the obstacle
+       rates just updated against the rows' h */
     orc_dynamics_step(P, x, u, xn);
     memcpy(x, xn, sizeof(x));
     J += orc_stage_cost(P, x, u, path, n_pts, ds);
+    if (P->flags & ORC_COLLISION_COST)
+      J += orc_collision_cost(P, obs, stride, n_obs, (tau + 1) * P->Ts, x);
+    if (proj && (P->flags & ORC_ALPHA_BUFFER))
+      J += orc_alpha_buffer_cost(P, n_obs, hrow + 1, alpha + 1);
 
     if (states) memcpy(states + 7 * (tau + 1), x, sizeof(x));
     if (u_out) memcpy(u_out + 3 * tau, u, sizeof(u));
@@ -529,6 +656,7 @@ int orc_rollout_sample(const orc_params *P, const double x0[7], const double *U_
   free(zhi);
   free(zdes);
   free(zs);
+  free(hrow);
   return status;
 }
 

@@ -35,7 +35,11 @@ extern "C" {
 #define ORC_ENONFINITE (-5)
 
 /* flags */
-#define ORC_PROJ_NONE 1 /* standard MPPI: skip the barrier-rate projection */
+#define ORC_PROJ_NONE 1      /* standard MPPI: skip the barrier-rate projection */
+#define ORC_COLLISION_COST 2 /* add q_coll * sum_o max(0, -h_o) to the stage cost */
+#define ORC_OBS8 4           /* obstacle rows of 8: (cx, cy, mx, my, theta_o, e, vx, vy),
+                                the centre moving at (vx, vy) from t = 0 */
+#define ORC_ALPHA_BUFFER 8   /* barrier-rate buffer cost on the obstacle rows */
 
 typedef struct {
   int32_t S, H, flags;
@@ -47,6 +51,9 @@ typedef struct {
   double z_lo[3], z_hi[3], sigma[3];  /* input bounds and noise std */
   double alpha0, sigma_alpha, ua_lo, ua_hi; /* barrier-rate variables */
   double w_u[3], w_alpha, rho, h_floor;     /* projection weights */
+  double q_coll;                      /* collision-cost weight (ORC_COLLISION_COST) */
+  double alpha_stab, q_stab[2];       /* hitch stabilizer: CBF rate, Q_h on (a, omega) */
+  double q_abuf, h_buf;               /* buffer cost weight and zone width (ORC_ALPHA_BUFFER) */
 } orc_params;
 
 /* Philox4x32 with 10 rounds (Salmon, Moraes, Dror, Shaw, SC'11). */
@@ -69,9 +76,33 @@ double orc_obstacle_h(const orc_params *P, const double obs[6], const double x[7
 void orc_obstacle_row(const orc_params *P, const double obs[6], const double x[7],
                       double A_u[3], double *h, double *b_rest);
 
+/* Time-varying obstacles (predicted pedestrians, Sec. IV-C): a row of
+   `stride` (6 or 8) doubles; with 8 the centre at time t is
+   (cx + t vx, cy + t vy).  h and the barrier-rate row at time t. */
+double orc_obstacle_h_at(const orc_params *P, const double *obs, int stride, double t,
+                         const double x[7]);
+void orc_obstacle_row_at(const orc_params *P, const double *obs, int stride, double t,
+                         const double x[7], double A_u[3], double *h, double *b_rest);
+
+/* MPPI + collision cost baseline: q_coll * sum_o max(0, -h_o(x, t)). */
+double orc_collision_cost(const orc_params *P, const double *obs, int stride, int n_obs, double t,
+                          const double x[7]);
+
+/* Barrier-rate buffer cost: q_abuf * sum_i w(h_i) max(0, alpha_i)^2 with the
+   ramp w(h) = clip(1 - h/h_buf, 0, 1) for h >= 0 and 1 for h < 0. */
+double orc_alpha_buffer_cost(const orc_params *P, int n, const double *h, const double *alpha);
+
 /* Hitch-angle barrier h_h(x) (Sec. IV-D) and its barrier-rate row. */
 double orc_hitch_h(const orc_params *P, const double x[7]);
 void orc_hitch_row(const orc_params *P, const double x[7], double A_u[3], double *h, double *b_rest);
+
+/* Hitch-angle stabilizer CBF-QP (Sec. IV-D, Eq. hitch_angle_qp): u_out[0..2]
+   is the (a, omega) nearest u_ref in the Q_h norm inside the input box whose
+   hitch increment meets the discrete CBF condition, nu passed through;
+   *slack = increment + alpha_stab h (>= 0 when met).  Returns 0, or 1 when
+   no input in the box meets it (u_out then maximises the increment). */
+int orc_hitch_stabilize(const orc_params *P, const double x[7], const double u_ref[3],
+                        double u_out[3], double *slack);
 
 /* Soft-bound equality projection, closed form (Sec. IV-A), dense.
    A is nc x d row-major, w the diagonal of W (d entries).  Returns ORC_OK or

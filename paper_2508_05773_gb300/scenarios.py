@@ -35,9 +35,13 @@ DEFAULT_PARAMS = dict(
     z_lo=(-2.0, -0.6, 0.0), z_hi=(2.0, 0.6, 3.0), sigma=(0.5, 0.3, 0.5),
     alpha0=0.5, sigma_alpha=0.1, ua_lo=-0.5, ua_hi=0.5,
     w_u=(1.0, 1.0, 1.0), w_alpha=1.0, rho=0.01, h_floor=1e-6,
+    q_coll=100.0, alpha_stab=0.5, q_stab=(1.0, 1.0), q_abuf=10.0, h_buf=0.5,
 )
 
 FLAG_PROJ_NONE = 1
+FLAG_COLLISION_COST = 2
+FLAG_OBS8 = 4
+FLAG_ALPHA_BUFFER = 8
 
 
 def params(**overrides) -> dict:

@@ -17,6 +17,8 @@ from tests import test_oracle_dynamics as td
 from tests import test_oracle_philox as tp
 from tests import test_oracle_projection as tj
 from tests import test_oracle_solve as ts
+from tests import test_oracle_obstacle_variants as tv
+from tests import test_oracle_stabilizer as tz
 
 MUTANTS = [
     ("philox multiplier swapped", "(uint64_t)PHILOX_M0 * (uint64_t)c0", "(uint64_t)PHILOX_M1 * (uint64_t)c0"),
@@ -32,7 +34,17 @@ MUTANTS = [
     ("ellipse hessian dropped", "+ hxx * vel_x * vel_x", ""),
     ("ellipse centripetal dropped", "hddot_0 = hx * cen_x + hy * cen_y +", "hddot_0 ="),
     ("ellipse accel coefficient", "A_u[0] = 0.5 * Ts * Ts * dhddot_da;", "A_u[0] = Ts * Ts * dhddot_da;"),
-    ("ellipse inflation dropped", "const double cx = obs[0], cy = obs[1], Ax = obs[2] + P->r_inflate, Ay = obs[3] + P->r_inflate;\n  const double th_o = obs[4];\n  const double xp", "const double cx = obs[0], cy = obs[1], Ax = obs[2], Ay = obs[3];\n  const double th_o = obs[4];\n  const double xp"),
+    ("ellipse inflation dropped", "const double Ax = obs[2] + P->r_inflate, Ay = obs[3] + P->r_inflate;\n  const double th_o = obs[4];\n  const double xp", "const double Ax = obs[2], Ay = obs[3];\n  const double th_o = obs[4];\n  const double xp"),
+    ("moving centre sign", "const double cx = obs[0] + t * vx, cy = obs[1] + t * vy;\n  const double Ax = obs[2] + P->r_inflate, Ay = obs[3] + P->r_inflate;\n  const double th_o = obs[4];\n  const double xp", "const double cx = obs[0] - t * vx, cy = obs[1] + t * vy;\n  const double Ax = obs[2] + P->r_inflate, Ay = obs[3] + P->r_inflate;\n  const double th_o = obs[4];\n  const double xp"),
+    ("moving row ignores obstacle velocity", "const double vel_x = ROT_X(v * c1 - vx, v * s1 - vy)", "const double vel_x = ROT_X(v * c1, v * s1 - vy)"),
+    ("moving rows at time zero", "stride, tau * P->Ts, x,", "stride, 0.0, x,"),
+    ("collision penalty sign", "if (h < 0.0) c += -h;", "if (h < 0.0) c += h;"),
+    ("collision cost at the step's start time", "(tau + 1) * P->Ts, x);", "tau * P->Ts, x);"),
+    ("buffer ramp reversed", "double w = 1.0 - h[i] / P->h_buf;", "double w = h[i] / P->h_buf;"),
+    ("buffer charges negative rates", "const double ap = alpha[i] > 0.0 ? alpha[i] : 0.0;", "const double ap = alpha[i];"),
+    ("stabilizer CBF sign", "const double rhs = -P->alpha_stab * h - c0;", "const double rhs = P->alpha_stab * h - c0;"),
+    ("stabilizer ignores Q_h", "(out)[j] = clip(u_ref[j] + (mu) * g[j] / P->q_stab[j], P->z_lo[j], P->z_hi[j]);", "(out)[j] = clip(u_ref[j] + (mu) * g[j], P->z_lo[j], P->z_hi[j]);"),
+    ("stabilizer infeasible corner swapped", "u[j] = g[j] > 0.0 ? P->z_hi[j] : (g[j] < 0.0 ? P->z_lo[j]", "u[j] = g[j] > 0.0 ? P->z_lo[j] : (g[j] < 0.0 ? P->z_hi[j]"),
     ("hitch sign of Delta", "const double sigma = (Delta >= 0.0) ? 1.0 : -1.0;", "const double sigma = (Delta >= 0.0) ? -1.0 : 1.0;"),
     ("hitch steer-rate term dropped", " - k * cos(phi) * (1.0 + t * t) * omega);", ");"),
     ("hitch speed threshold", "return P->dtheta_max - P->kappa * x[4] - fabs(x[3] - x[2]);", "return P->dtheta_max + P->kappa * x[4] - fabs(x[3] - x[2]);"),
@@ -105,6 +117,20 @@ def _battery():
         ("solve-update", ts.test_update_is_weighted_mean_of_applied_inputs),
         ("solve-mean", ts.test_equal_costs_give_mean_of_samples),
         ("solve-cost-sum", ts.test_cost_accumulates_stage_costs_after_each_step),
+        ("moving-taylor", lambda: tv.test_moving_row_is_second_order_taylor(tv.MOVING[2], tb.STATES[0], 0.35)),
+        ("moving-static", tv.test_zero_velocity_rows_equal_static_rows),
+        ("moving-centre", tv.test_centre_moves_with_time),
+        ("moving-comoving", tv.test_comoving_vehicle_sees_a_frozen_obstacle),
+        ("moving-rows-time", tv.test_moving_rows_used_at_step_time),
+        ("coll-values", tv.test_collision_cost_values),
+        ("coll-wiring", tv.test_collision_cost_enters_after_each_step),
+        ("buffer-values", tv.test_alpha_buffer_cost_values),
+        ("buffer-wiring", tv.test_alpha_buffer_cost_enters_with_updated_rates),
+        ("stab-admissible", tz.test_admissible_reference_is_unchanged),
+        ("stab-closed-form", lambda: tz.test_closed_form_without_active_bounds(0)),
+        ("stab-brute", lambda: tz.test_brute_force_grid(0)),
+        ("stab-infeasible", tz.test_infeasible_returns_increment_maximiser),
+        ("stab-closed-loop", lambda: tz.test_keeps_hitch_inside_its_limit_in_closed_loop(0.5)),
     ]
     for name, fn in checks:
         try:
