@@ -625,21 +625,23 @@ int orc_rollout_sample(const orc_params *P, const double x0[7], const double *U_
     if (z_des_out) memcpy(z_des_out + (size_t)d * tau, zdes, sizeof(double) * (size_t)d);
     if (z_star_out) memcpy(z_star_out + (size_t)d * tau, zs, sizeof(double) * (size_t)d);
 
+    /* buffer cost of the obstacle rows just built: their h at this state
+       and the rates alpha_tau they were built with */
+    if (proj && (P->flags & ORC_ALPHA_BUFFER))
+      J += orc_alpha_buffer_cost(P, n_obs, hrow + 1, alpha + 1);
+
     /* 4. applied input (clipped) and barrier-rate update */
     for (int j = 0; j < 3; ++j) u[j] = clip(zs[j], P->z_lo[j], P->z_hi[j]);
     if (proj)
       for (int i = 0; i < Nc; ++i) alpha[i] += zs[3 + i];
 
-    /* 5. kinematics and stage cost at the new state; the comparison
-       method's collision cost there, and the buffer cost of the obstacle
-       rates just updated against the rows' h */
+    /* 5. kinematics and stage cost at the new state, and the comparison
+       method's collision cost there */
     orc_dynamics_step(P, x, u, xn);
     memcpy(x, xn, sizeof(x));
     J += orc_stage_cost(P, x, u, path, n_pts, ds);
     if (P->flags & ORC_COLLISION_COST)
       J += orc_collision_cost(P, obs, stride, n_obs, (tau + 1) * P->Ts, x);
-    if (proj && (P->flags & ORC_ALPHA_BUFFER))
-      J += orc_alpha_buffer_cost(P, n_obs, hrow + 1, alpha + 1);
 
     if (states) memcpy(states + 7 * (tau + 1), x, sizeof(x));
     if (u_out) memcpy(u_out + 3 * tau, u, sizeof(u));

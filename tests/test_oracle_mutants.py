@@ -41,6 +41,7 @@ MUTANTS = [
     ("collision penalty sign", "if (h < 0.0) c += -h;", "if (h < 0.0) c += h;"),
     ("collision cost at the step's start time", "(tau + 1) * P->Ts, x);", "tau * P->Ts, x);"),
     ("buffer ramp reversed", "double w = 1.0 - h[i] / P->h_buf;", "double w = h[i] / P->h_buf;"),
+    ("buffer charged with updated rates", "    if (proj && (P->flags & ORC_ALPHA_BUFFER))\n      J += orc_alpha_buffer_cost(P, n_obs, hrow + 1, alpha + 1);\n\n    /* 4. applied input (clipped) and barrier-rate update */\n    for (int j = 0; j < 3; ++j) u[j] = clip(zs[j], P->z_lo[j], P->z_hi[j]);\n    if (proj)\n      for (int i = 0; i < Nc; ++i) alpha[i] += zs[3 + i];\n", "    for (int j = 0; j < 3; ++j) u[j] = clip(zs[j], P->z_lo[j], P->z_hi[j]);\n    if (proj)\n      for (int i = 0; i < Nc; ++i) alpha[i] += zs[3 + i];\n    if (proj && (P->flags & ORC_ALPHA_BUFFER))\n      J += orc_alpha_buffer_cost(P, n_obs, hrow + 1, alpha + 1);\n"),
     ("buffer charges negative rates", "const double ap = alpha[i] > 0.0 ? alpha[i] : 0.0;", "const double ap = alpha[i];"),
     ("stabilizer CBF sign", "const double rhs = -P->alpha_stab * h - c0;", "const double rhs = P->alpha_stab * h - c0;"),
     ("stabilizer ignores Q_h", "(out)[j] = clip(u_ref[j] + (mu) * g[j] / P->q_stab[j], P->z_lo[j], P->z_hi[j]);", "(out)[j] = clip(u_ref[j] + (mu) * g[j], P->z_lo[j], P->z_hi[j]);"),

@@ -137,7 +137,7 @@ def test_collision_cost_enters_after_each_step():
 
 def test_alpha_buffer_cost_enters_with_updated_rates():
     """J(buffer) - J(plain) = sum over steps of the buffer cost of the rows'
-    h at the step's state and the rates after that step's update."""
+    h at the step's state and the rates alpha_tau the rows were built with."""
     c, p0 = _case(0, seed=5)
     p1 = dict(p0, flags=sc.FLAG_ALPHA_BUFFER, h_buf=1e3)
     n = len(c["obs"])
@@ -152,7 +152,7 @@ def test_alpha_buffer_cost_enters_with_updated_rates():
         e = 0.0
         for k in range(p0["H"]):
             h = [oracle.obstacle_h(p1, c["obs"][o], r0["states"][k]) for o in range(n)]
-            e += oracle.alpha_buffer_cost(p1, h, r0["alpha"][k + 1, 1:])
+            e += oracle.alpha_buffer_cost(p1, h, r0["alpha"][k, 1:])
         extra.append(r1["J"] - r0["J"])
         np.testing.assert_allclose(r1["J"] - r0["J"], e, rtol=1e-12, atol=1e-12)
     assert max(extra) > 0.0
