@@ -333,6 +333,104 @@ def measure_stress(dev, reps: int = 5):
                     "ALU-bound, so its HBM fraction is low by construction"}
 
 
+def _time_solve(solver, inst, stream, flush, reps):
+    import torch
+    ts = []
+    for r in range(reps + 3):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        solver.solve_device_ex(inst, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if r >= 3:
+            ts.append(e0.elapsed_time(e1))
+    return float(np.median(ts))
+
+
+def measure_variants(dev, reps: int = 20):
+    """The comparison of Table I on GB300: standard MPPI, MPPI + collision
+    cost and BR-MPPI on the same scene (8 obstacles), at the config-2 size
+    (S=4096, H=50) and at the paper's own sampling (S=5000, H=120); plus
+    BR-MPPI with the buffer cost, the crossing scene (parked e = 4
+    super-ellipses and moving pedestrians), and the hitch stabilizer (fused
+    into a solve, and as a batched kernel over 2^20 states)."""
+    import torch
+    import paper_2508_05773_gb300 as pkg
+    from paper_2508_05773_gb300 import scenarios as sc
+
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    t = lambda a, dt=torch.float32: torch.tensor(np.asarray(a), dtype=dt, device=dev)
+    out = {"table1_paper_ms": {"mppi": [3.20, 3.00], "mppi_collision": [13.0, 14.0],
+                               "br_mppi": [9.92, 9.75],
+                               "note": "forward / backward parking, S=5000, H=120, JAX, the "
+                                       "paper's GPU; context, not a target"}}
+    methods = (("br_mppi", 0), ("mppi", pkg.BRMPPI_FLAG_PROJ_NONE),
+               ("mppi_collision", pkg.BRMPPI_FLAG_PROJ_NONE | pkg.BRMPPI_FLAG_COLLISION_COST),
+               ("br_mppi_buffer", pkg.BRMPPI_FLAG_ALPHA_BUFFER))
+    for size, (S, H) in (("config2", (4096, 50)), ("paper_table1", (5000, 120))):
+        c = sc.config2(S=S, H=H)
+        row = {}
+        for name, flags in methods:
+            p = dict(c["params"], flags=flags)
+            solver = pkg.Solver(p, max_obstacles=16, max_path_pts=1024)
+            inst = dict(x0=t(c["x0"], torch.float64), U_nom=t(c["U_nom"]), obs=t(c["obs"]),
+                        path=t(c["path"]), ds=c["ds"], S=S, seed=c["seed"], counter=0,
+                        U_out=torch.empty((H, 3), device=dev), traj_out=torch.empty((H + 1, 7), device=dev))
+            solver.autotune(inst["x0"], inst["U_nom"], inst["obs"], inst["path"], c["ds"], reps=2,
+                            stream=stream)
+            ms = _time_solve(solver, inst, stream, flush, reps)
+            row[name] = {"ms_per_solve": ms, "rollout_steps_per_s": S * H / (ms * 1e-3),
+                         "launch": solver.launch(8)}
+            if name == "br_mppi":
+                inst_s = dict(inst, u_safe_out=torch.empty(4, device=dev))
+                row["br_mppi_with_stabilizer"] = {"ms_per_solve": _time_solve(solver, inst_s, stream, flush,
+                                                                               reps)}
+            solver.close()
+        out[size] = dict(row, S=S, H=H, n_obs=8)
+    # crossing scene: 6 parked e = 4 super-ellipses, 2 crossing pedestrians
+    c = sc.crossing()
+    S, H = int(c["params"]["S"]), int(c["params"]["H"])
+    solver = pkg.Solver(c["params"], max_obstacles=16, max_path_pts=1024)
+    inst = dict(x0=t(c["x0"], torch.float64), U_nom=t(c["U_nom"]), obs=t(c["obs"]), path=t(c["path"]),
+                ds=c["ds"], S=S, seed=c["seed"], counter=0, U_out=torch.empty((H, 3), device=dev))
+    solver.autotune(inst["x0"], inst["U_nom"], inst["obs"], inst["path"], c["ds"], reps=2, stream=stream)
+    ms = _time_solve(solver, inst, stream, flush, reps)
+    out["crossing"] = {"workload": "S=4096, H=50, 6 parked e=4 super-ellipses + 2 pedestrians crossing "
+                                   "at 1-1.5 m/s (8-float obstacle rows)",
+                       "ms_per_solve": ms, "rollout_steps_per_s": S * H / (ms * 1e-3),
+                       "launch": solver.launch(8)}
+    # batched stabilizer
+    n = 1 << 20
+    rng = np.random.default_rng(3)
+    th1 = rng.uniform(-3, 3, n)
+    X = np.stack([rng.uniform(-50, 50, n), rng.uniform(-50, 50, n), th1, th1 + rng.uniform(-1.0, 1.0, n),
+                  rng.uniform(-2, 2, n), rng.uniform(-0.5, 0.5, n), rng.uniform(0, 30, n)], 1)
+    Ur = np.stack([rng.uniform(-3, 3, n), rng.uniform(-1, 1, n), rng.uniform(0, 3, n)], 1)
+    xd, ud = t(X, torch.float64), t(Ur)
+    od = torch.empty((n, 4), device=dev)
+    ts = []
+    for r in range(reps + 3):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        solver.hitch_stabilize_device(xd, ud, od, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if r >= 3:
+            ts.append(e0.elapsed_time(e1))
+    ms = float(np.median(ts))
+    solver.close()
+    peaks = _measured_peaks()
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    nbytes = n * (7 * 8 + 3 * 4 + 4 * 4)
+    out["stabilizer_batched"] = {"states": n, "ms": ms, "states_per_s": n / (ms * 1e-3),
+                                 "bytes": nbytes, "hbm_gbs": nbytes / (ms * 1e-3) / 1e9,
+                                 "hbm_frac": nbytes / (ms * 1e-3) / 1e9 / hbm}
+    return out
+
+
 def measure_serving(rates=(2000, 10000, 50000), duration=2.0, warm=0.5, n_vehicles=512, seed=4):
     """Serving loop: Poisson arrivals from 512 vehicles (S=4096, H=50, 0-16
     ellipses per request, fresh state = the vehicle's start + N(0, 0.05)
@@ -599,6 +697,8 @@ def run_ours(args, world, rank, local):
             line["serving"] = measure_serving()
         if world == 1 and not args.no_stress:
             line["stress"] = measure_stress(dev)
+        if world == 1 and not args.no_variants:
+            line["variants"] = measure_variants(dev)
         if not args.no_cpu_baseline and world == 1:
             line["cpu_baseline"] = run_cpu_baseline()
         print(json.dumps(line), flush=True)
@@ -618,6 +718,7 @@ def main():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-stress", action="store_true")
+    ap.add_argument("--no-variants", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -25,6 +25,7 @@
  *   state      x0[7]        double  (px, py, theta1, theta2, v, delta, psi)
  *   inputs     U[H][3]      float   (a, omega, nu)
  *   obstacles  obs[n][6]    float   (cx, cy, mx, my, theta_o, e); e must be 2
+              obs[n][8]    float   with BRMPPI_FLAG_OBS8: + (vx, vy), e in {2, 4}
  *   path       path[n][3]   float   (x, y, heading unwrapped) at s = j*ds
  *   trajectory traj[H+1][7] float
  *   costs      J[S]         float
@@ -52,7 +53,7 @@
 extern "C" {
 #endif
 
-#define BRMPPI_ABI_VERSION 4u
+#define BRMPPI_ABI_VERSION 5u
 
 typedef enum {
   BRMPPI_OK = 0,
@@ -68,6 +69,21 @@ typedef enum {
 
 /* Flags */
 #define BRMPPI_FLAG_PROJ_NONE 0x1u /* standard MPPI: skip the projection (baseline) */
+/* MPPI + collision cost (the comparison method of Sec. V): every stage cost
+   adds q_coll * sum_o max(0, -h_o(x)) at the state after the step.  The
+   paper does not give the penalty's form; this is a penetration hinge. */
+#define BRMPPI_FLAG_COLLISION_COST 0x2u
+/* Obstacle rows of 8 floats (cx, cy, mx, my, theta_o, e, vx, vy): super-
+   ellipses with e in {2, 4} whose centre moves at (vx, vy) from the solve's
+   start (predicted pedestrians, Sec. IV-C); the rows of step tau use the
+   centre at tau*Ts and the relative velocity.  Without this flag rows are 6
+   floats and e must be 2. */
+#define BRMPPI_FLAG_OBS8 0x4u
+/* Barrier-rate buffer cost (Sec. IV-A): each obstacle row built at step tau
+   adds q_abuf * w(h) * max(0, alpha)^2 with its h and rate alpha, where
+   w(h) = clip(1 - h/h_buf, 0, 1): positive rates are charged near an
+   obstacle, pushing the samples toward hdot >= 0 there. */
+#define BRMPPI_FLAG_ALPHA_BUFFER 0x8u
 
 /* Every constant of the solve; POD. Fields the paper leaves open take the
    documented readings (alpha init, noise and bounds of u^alpha, W, rho, the
@@ -99,6 +115,10 @@ typedef struct brmppi_params {
   float ua_lo, ua_hi;            /* bounds of u^alpha */
   float w_u[3], w_alpha;         /* diagonal of W */
   float rho, h_floor;            /* soft-bound penalty; floor on |h| in A */
+  float q_coll;                  /* BRMPPI_FLAG_COLLISION_COST weight (>= 0) */
+  float alpha_stab;              /* hitch stabilizer: discrete CBF rate, (0, 1] */
+  float q_stab[2];               /* hitch stabilizer: Q_h = diag(q_stab) on (a, omega), > 0 */
+  float q_abuf, h_buf;           /* BRMPPI_FLAG_ALPHA_BUFFER weight (>= 0), zone width (> 0) */
 } brmppi_params;
 
 typedef struct brmppi_ctx brmppi_ctx; /* opaque: device buffers, stream */
@@ -117,6 +137,9 @@ typedef struct brmppi_instance {
   int32_t *status;                          /* may be NULL */
   float *states_out; /* may be NULL: stored-trajectory variant, every sample's
                         states S x (H+1) x 7 (world frame, x0 first) */
+  float *u_safe_out; /* may be NULL: U*[0] after the hitch stabilizer (see
+                        brmppi_hitch_stabilize_device), 4 floats, written by
+                        a small launch that follows the solve on its stream */
 } brmppi_instance;
 
 typedef struct brmppi_graph brmppi_graph; /* a captured batch launch */
@@ -162,6 +185,23 @@ brmppi_status brmppi_solve_device(brmppi_ctx *ctx, const double *x0_dev, const f
    optional stored-trajectory output.  Allocates nothing, does not
    synchronise. */
 brmppi_status brmppi_solve_device_ex(brmppi_ctx *ctx, const brmppi_instance *inst, void *stream);
+
+/* Hitch-angle stabilizer (Sec. IV-D, Eq. hitch_angle_qp) for n states at
+   once, one GPU thread each.  For state x_i (x_dev[i][7], double) and the
+   reference u_ref_dev[i][3] = (a, omega, nu) from BR-MPPI, u_out_dev[i][4]
+   receives (a, omega, nu, slack): (a, omega) minimises
+   (u - u_ref)^T diag(q_stab) (u - u_ref) over the input box z_lo..z_hi
+   subject to the discrete CBF condition of Eq. barrier_constraint_prelim on
+   the hitch barrier,  Ts hdot + Ts^2/2 hddot >= -alpha_stab h_h(x)  (the
+   increment of the rollout's hitch row; sign as in Eq. cbf_equality); nu
+   passes through.  slack = increment + alpha_stab h_h at the result: >= 0
+   (up to rounding) when the condition is met; < 0 means no input in the box
+   meets it and (a, omega) is the box corner that maximises the increment.
+   Solved in closed form (KKT of a one-row QP with a diagonal weight and a
+   box).  Enqueued on `stream`; allocates nothing.  n = 0 is a no-op. */
+brmppi_status brmppi_hitch_stabilize_device(brmppi_ctx *ctx, const double *x_dev,
+                                            const float *u_ref_dev, int32_t n, float *u_out_dev,
+                                            void *stream);
 
 /* A batch of independent solves (uneven S, H, obstacle count, path) in ONE
    launch of a persistent kernel: work items (instance, sample tile) are

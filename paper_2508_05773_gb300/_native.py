@@ -12,7 +12,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libbrmppi.so")
 
-BRMPPI_ABI_VERSION = 4
+BRMPPI_ABI_VERSION = 5
 BRMPPI_OK = 0
 BRMPPI_EINVAL = -1
 BRMPPI_ENOMEM = -2
@@ -22,6 +22,9 @@ BRMPPI_ENONFINITE = -5
 BRMPPI_ECUDA = -6
 BRMPPI_EBUSY = -7
 BRMPPI_FLAG_PROJ_NONE = 0x1
+BRMPPI_FLAG_COLLISION_COST = 0x2
+BRMPPI_FLAG_OBS8 = 0x4
+BRMPPI_FLAG_ALPHA_BUFFER = 0x8
 
 STATUS_NAMES = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "EAGAIN", -4: "ETIMEDOUT",
                 -5: "ENONFINITE", -6: "ECUDA", -7: "EBUSY"}
@@ -33,7 +36,7 @@ EXPORTS = (
     "brmppi_graph_launch", "brmppi_graph_destroy", "brmppi_autotune", "brmppi_autotune_batch",
     "brmppi_get_launch", "brmppi_transfer_bytes", "brmppi_vehicle_register", "brmppi_submit",
     "brmppi_poll", "brmppi_vehicle_export", "brmppi_vehicle_import", "brmppi_server_stats_get",
-    "brmppi_solve_device_noalloc",
+    "brmppi_solve_device_noalloc", "brmppi_hitch_stabilize_device",
 )
 
 
@@ -57,6 +60,8 @@ class brmppi_params(ctypes.Structure):
         ("ua_lo", ctypes.c_float), ("ua_hi", ctypes.c_float),
         ("w_u", ctypes.c_float * 3), ("w_alpha", ctypes.c_float),
         ("rho", ctypes.c_float), ("h_floor", ctypes.c_float),
+        ("q_coll", ctypes.c_float), ("alpha_stab", ctypes.c_float),
+        ("q_stab", ctypes.c_float * 2), ("q_abuf", ctypes.c_float), ("h_buf", ctypes.c_float),
     ]
 
 
@@ -68,7 +73,7 @@ class brmppi_instance(ctypes.Structure):
         ("seed", ctypes.c_uint64), ("counter", ctypes.c_uint64),
         ("U_out", ctypes.c_void_p), ("traj_out", ctypes.c_void_p), ("J_out", ctypes.c_void_p),
         ("U_next", ctypes.c_void_p), ("status", ctypes.c_void_p),
-        ("states_out", ctypes.c_void_p),
+        ("states_out", ctypes.c_void_p), ("u_safe_out", ctypes.c_void_p),
     ]
 
 
@@ -145,6 +150,8 @@ def load() -> ctypes.CDLL:
                                                            ctypes.c_int32, ctypes.c_float,
                                                            ctypes.c_uint64, ctypes.c_uint64, _VP,
                                                            _VP, _VP, _VP, _VP, _VP]),
+            "brmppi_hitch_stabilize_device": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int32, _VP,
+                                                             _VP]),
             "brmppi_transfer_bytes": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.c_int32,
                                                      ctypes.POINTER(ctypes.c_uint64),
                                                      ctypes.POINTER(ctypes.c_uint64)]),
@@ -222,6 +229,17 @@ def brmppi_last_error(ctx) -> str:
     return load().brmppi_last_error(ctx).decode()
 
 
+def _rows(obs) -> int:
+    """Obstacle count of an obstacle array: its first dimension when 2-D
+    (rows of 6, or of 8 under BRMPPI_FLAG_OBS8), else its size / 6."""
+    if obs is None:
+        return 0
+    shape = tuple(obs.shape)
+    if len(shape) == 2:
+        return int(shape[0])
+    return int(np.prod(shape)) // 6
+
+
 def _f32(a, n=None):
     arr = np.ascontiguousarray(a, dtype=np.float32)
     if n is not None and arr.size != n:
@@ -237,8 +255,8 @@ def brmppi_solve(ctx, x0, U_nom, obs, path, ds, seed, counter, H, S=None, want_t
     if x0.size != 7:
         raise ValueError("x0 must have 7 entries")
     U_nom = _f32(U_nom, 3 * H)
-    obs = _f32(obs).reshape(-1)
-    n_obs = obs.size // 6
+    n_obs = _rows(None if obs is None else np.asarray(obs))
+    obs = _f32(obs).reshape(-1) if obs is not None else np.zeros(0, np.float32)
     path = _f32(path).reshape(-1)
     n_pts = path.size // 3
     U = np.zeros((H, 3), dtype=np.float32)
@@ -264,7 +282,7 @@ def brmppi_solve_device(ctx, x0, U_nom, obs, path, ds, seed, counter, U_out, tra
     status int32[1]).  Enqueued on ``stream`` (torch stream or raw handle;
     default: torch's current stream); does not synchronise."""
     lib = load()
-    n_obs = 0 if obs is None else obs.numel() // 6
+    n_obs = _rows(obs)
     n_pts = path.numel() // 3
     if stream is None:
         import torch
@@ -297,7 +315,7 @@ def make_instances(insts) -> "ctypes.Array":
         q.x0 = d["x0"].data_ptr()
         q.U_nom = d["U_nom"].data_ptr()
         obs = d.get("obs")
-        q.n_obs = 0 if obs is None else obs.numel() // 6
+        q.n_obs = _rows(obs)
         q.obs = obs.data_ptr() if q.n_obs else None
         q.path = d["path"].data_ptr()
         q.n_pts = d["path"].numel() // 3
@@ -307,7 +325,7 @@ def make_instances(insts) -> "ctypes.Array":
         q.seed = int(d["seed"]) & (2**64 - 1)
         q.counter = int(d.get("counter", 0)) & (2**64 - 1)
         q.U_out = d["U_out"].data_ptr()
-        for key in ("traj_out", "J_out", "U_next", "status", "states_out"):
+        for key in ("traj_out", "J_out", "U_next", "status", "states_out", "u_safe_out"):
             t = d.get(key)
             setattr(q, key, None if t is None else t.data_ptr())
     return arr
@@ -344,7 +362,7 @@ def brmppi_graph_destroy(graph) -> None:
 
 
 def brmppi_autotune(ctx, x0, U_nom, obs, path, ds, reps=5, stream=None) -> int:
-    n_obs = 0 if obs is None else obs.numel() // 6
+    n_obs = _rows(obs)
     return load().brmppi_autotune(ctx, _dptr(x0), _dptr(U_nom), _dptr(obs) if n_obs else None,
                                   n_obs, _dptr(path), path.numel() // 3, float(ds), int(reps),
                                   ctypes.c_void_p(_stream_handle(stream)))
@@ -361,12 +379,20 @@ def brmppi_solve_device_noalloc(params, x0, U_nom, obs, path, ds, seed, counter,
                                 stream=None) -> int:
     """Allocation-free solve (no context) on torch CUDA tensors; see
     include/brmppi.h for its limits.  ``params``: brmppi_params."""
-    n_obs = 0 if obs is None else obs.numel() // 6
+    n_obs = _rows(obs)
     return load().brmppi_solve_device_noalloc(
         ctypes.byref(params), _dptr(x0), _dptr(U_nom), _dptr(obs) if n_obs else None, n_obs,
         _dptr(path), path.numel() // 3, float(ds), int(seed) & (2**64 - 1),
         int(counter) & (2**64 - 1), _dptr(U_out), _dptr(traj_out), _dptr(J_out), _dptr(U_next),
         _dptr(status), ctypes.c_void_p(_stream_handle(stream)))
+
+
+def brmppi_hitch_stabilize_device(ctx, x, u_ref, u_out, stream=None) -> int:
+    """Hitch stabilizer for n states: x float64[n,7], u_ref float32[n,3],
+    u_out float32[n,4] (a, omega, nu, slack), torch CUDA tensors."""
+    n = x.numel() // 7
+    return load().brmppi_hitch_stabilize_device(ctx, _dptr(x), _dptr(u_ref), n, _dptr(u_out),
+                                                ctypes.c_void_p(_stream_handle(stream)))
 
 
 def brmppi_get_launch(ctx, n_obs: int):
@@ -445,6 +471,12 @@ class Solver:
             raise BrmppiError(st, brmppi_last_error(self.ctx))
         return st
 
+    def hitch_stabilize_device(self, x, u_ref, u_out, stream=None, check=True) -> int:
+        st = brmppi_hitch_stabilize_device(self.ctx, x, u_ref, u_out, stream)
+        if check and st != BRMPPI_OK:
+            raise BrmppiError(st, brmppi_last_error(self.ctx))
+        return st
+
     def capture_batch(self, insts):
         return brmppi_batch_capture(self.ctx, insts)
 
@@ -468,9 +500,10 @@ class Solver:
         """Queue one solve; returns (status, ticket)."""
         x0 = np.ascontiguousarray(x0, dtype=np.float64)
         ob = np.zeros(0, np.float32) if obs is None else _f32(obs).reshape(-1)
+        row = 8 if int(self.params.get("flags", 0)) & BRMPPI_FLAG_OBS8 else 6
         t = ctypes.c_uint64()
         st = load().brmppi_submit(self.ctx, int(vehicle_id), x0.ctypes.data_as(_D),
-                                  ob.ctypes.data_as(_F) if ob.size else None, ob.size // 6,
+                                  ob.ctypes.data_as(_F) if ob.size else None, ob.size // row,
                                   ctypes.byref(t))
         return st, t.value
 

@@ -19,6 +19,10 @@
 
 using namespace brmppi_host;
 
+// The layouts the Python binding mirrors.
+static_assert(sizeof(brmppi_params) == 4 * 15 + 4 * 41, "brmppi_params layout");
+static_assert(sizeof(brmppi_instance) == 8 * 4 + 4 * 5 + 4 + 8 * 2 + 8 * 7, "brmppi_instance layout");
+
 namespace brmppi_host {
 
 namespace {
@@ -61,7 +65,9 @@ std::string check_params(const brmppi_params* p) {
   if (p->H < 1 || p->H > kMaxH) return "H must be in [1, 1024]";
   if (p->max_obstacles < 0 || p->max_obstacles > kMaxObstacles) return "max_obstacles must be in [0, 124]";
   if (p->max_path_pts < 2 || p->max_path_pts > kMaxPathPts) return "max_path_pts must be in [2, 12000]";
-  if (p->flags & ~static_cast<int32_t>(BRMPPI_FLAG_PROJ_NONE)) return "unknown flag";
+  if (p->flags & ~static_cast<int32_t>(BRMPPI_FLAG_PROJ_NONE | BRMPPI_FLAG_COLLISION_COST | BRMPPI_FLAG_OBS8 |
+                                        BRMPPI_FLAG_ALPHA_BUFFER))
+    return "unknown flag";
   if (p->threads_per_sample != 0 && !is_pow2_tps(p->threads_per_sample))
     return "threads_per_sample must be 0, 1, 2, 4, 8, 16 or 32";
   if (p->batch_threads_per_sample != 0 && !is_pow2_tps(p->batch_threads_per_sample))
@@ -91,12 +97,21 @@ std::string check_params(const brmppi_params* p) {
   if (!(p->sigma_alpha >= 0.f)) return "sigma_alpha must be >= 0";
   if (!(p->w_alpha + p->rho > 0.f) || !(p->w_alpha >= 0.f) || !(p->rho >= 0.f))
     return "w_alpha >= 0, rho >= 0 and w_alpha + rho > 0 required";
+  if (!(p->q_coll >= 0.f) || !std::isfinite(p->q_coll)) return "q_coll must be >= 0 and finite";
+  if (!(p->alpha_stab > 0.f && p->alpha_stab <= 1.f)) return "alpha_stab must be in (0, 1]";
+  if (!(p->q_stab[0] > 0.f) || !(p->q_stab[1] > 0.f) || !std::isfinite(p->q_stab[0]) || !std::isfinite(p->q_stab[1]))
+    return "q_stab must be positive and finite";
+  if (!(p->q_abuf >= 0.f) || !std::isfinite(p->q_abuf)) return "q_abuf must be >= 0 and finite";
+  if (!(p->h_buf > 0.f) || !std::isfinite(p->h_buf)) return "h_buf must be positive and finite";
   return "";
 }
 
 brmppi::KConst make_kconst(const brmppi_params& q) {
   brmppi::KConst k{};
   k.proj = (q.flags & BRMPPI_FLAG_PROJ_NONE) ? 0 : 1;
+  k.coll = (q.flags & BRMPPI_FLAG_COLLISION_COST) ? 1 : 0;
+  k.obs8 = (q.flags & BRMPPI_FLAG_OBS8) ? 1 : 0;
+  k.abuf = (q.flags & BRMPPI_FLAG_ALPHA_BUFFER) ? 1 : 0;
   k.Ts = q.Ts;
   k.hTs2 = 0.5f * q.Ts * q.Ts;
   k.inv_lambda = 1.0f / q.lambda;
@@ -143,6 +158,12 @@ brmppi::KConst make_kconst(const brmppi_params& q) {
   k.m_a = q.w_alpha + q.rho;
   k.inv_m_a = 1.0f / (q.w_alpha + q.rho);
   k.h_floor = q.h_floor;
+  k.q_coll = q.q_coll;
+  k.q_abuf = q.q_abuf;
+  k.inv_hbuf = 1.0f / q.h_buf;
+  k.alpha_stab = q.alpha_stab;
+  k.inv_qs0 = 1.0f / q.q_stab[0];
+  k.inv_qs1 = 1.0f / q.q_stab[1];
   return k;
 }
 
@@ -263,12 +284,13 @@ brmppi_status enqueue_plain_sized(brmppi_ctx* c, const Shape& sh, int S, int H, 
                                   const float* U_nom, const float* obs, int32_t n_obs, const float* path,
                                   int32_t n_pts, float ds, uint64_t seed, uint64_t counter, float* U_out,
                                   float* traj_out, float* J_out, float* U_next, int32_t* status, float* states_out,
-                                  cudaStream_t stream) {
+                                  float* u_safe, cudaStream_t stream) {
   const int spb = sh.threads / sh.tps;
   brmppi::LaunchDesc L{};
   L.single = make_inst(x0, U_nom, obs, n_obs, path, n_pts, ds, S, H, seed, counter, U_out, traj_out, J_out,
                        U_next, status, c->d_part, c->d_sync, spb);
   L.single.states_out = states_out;
+  L.single.u_safe = u_safe;
   L.caps = make_caps(n_obs, n_pts, H, sh.tps);
   L.uh = c->d_uh;
   L.uh_stride = 3 * H * spb;
@@ -278,8 +300,14 @@ brmppi_status enqueue_plain_sized(brmppi_ctx* c, const Shape& sh, int S, int H, 
   if (static_cast<size_t>(tiles) > c->part_tiles ||
       static_cast<size_t>(tiles) * static_cast<size_t>(L.uh_stride) > c->uh_floats)
     return fail(c, BRMPPI_EINVAL, "launch shape exceeds the context's scratch");
-  cudaError_t e = brmppi::launch_solve(sh.tps, sh.bpt, tiles, sh.threads, smem, stream, make_kconst(c->prm), L);
+  const brmppi::KConst k = make_kconst(c->prm);
+  cudaError_t e = brmppi::launch_solve(sh.tps, sh.bpt, tiles, sh.threads, smem, stream, k, L);
   if (e != cudaSuccess) return cuda_fail(c, e, "kernel launch");
+  if (u_safe) {
+    // the stabilizer on (x0, U*[0]): one thread, after the solve
+    e = brmppi::launch_stabilize(k, x0, U_out, 1, u_safe, stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "stabilizer launch");
+  }
   return BRMPPI_OK;
 }
 
@@ -288,7 +316,7 @@ brmppi_status enqueue_plain(brmppi_ctx* c, const Shape& sh, const double* x0, co
                             uint64_t seed, uint64_t counter, float* U_out, float* traj_out, float* J_out,
                             float* U_next, int32_t* status, cudaStream_t stream) {
   return enqueue_plain_sized(c, sh, c->prm.S, c->prm.H, x0, U_nom, obs, n_obs, path, n_pts, ds, seed, counter,
-                             U_out, traj_out, J_out, U_next, status, nullptr, stream);
+                             U_out, traj_out, J_out, U_next, status, nullptr, nullptr, stream);
 }
 
 // ------------------------------------------------------------- batches
@@ -361,9 +389,12 @@ brmppi_status launch_batch(brmppi_ctx* c, Lane& L, const BatchPlan& plan, cudaSt
   D.uh = L.d_buh;
   D.uh_stride = 3 * plan.Hmax * (plan.shape.threads / plan.shape.tps);
   D.caps = plan.caps;
+  const brmppi::KConst k = make_kconst(c->prm);
   cudaError_t e = brmppi::launch_solve(plan.shape.tps, plan.shape.bpt, plan.grid, plan.shape.threads, plan.smem,
-                                       stream, make_kconst(c->prm), D);
+                                       stream, k, D);
   if (e != cudaSuccess) return cuda_fail(c, e, "batch kernel launch");
+  if (plan.any_u_safe && (e = brmppi::launch_stabilize_table(k, L.d_inst, plan.n_inst, stream)) != cudaSuccess)
+    return cuda_fail(c, e, "stabilizer launch");
   return BRMPPI_OK;
 }
 
@@ -413,6 +444,8 @@ brmppi_status plan_batch(brmppi_ctx* c, Lane& L, const brmppi_instance* inst, in
     brmppi::Inst in = make_inst(q.x0, q.U_nom, q.obs, q.n_obs, q.path, q.n_pts, q.ds, q.S, H, q.seed, q.counter,
                                 q.U_out, q.traj_out, q.J_out, q.U_next, q.status, nullptr, L.d_bsync + 2 * i, spb);
     in.states_out = q.states_out;
+    in.u_safe = q.u_safe_out;
+    if (q.u_safe_out) plan->any_u_safe = true;
     in.part = L.d_bpart + pool;
     pool += static_cast<size_t>(in.tiles) * static_cast<size_t>(in.part_stride);
     if (pool > L.bpart_floats) return fail(c, BRMPPI_EINVAL, "batch partials exceed the context's pool");
@@ -426,7 +459,7 @@ brmppi_status plan_batch(brmppi_ctx* c, Lane& L, const brmppi_instance* inst, in
                      return a.first > b.first;
                    });
   for (size_t j = 0; j < items.size(); ++j) h_work[j] = items[j].second;
-  const int occ = brmppi::variant_occupancy(sh.tps, sh.bpt, sh.threads, smem);
+  const int occ = brmppi::variant_occupancy(sh.tps, sh.bpt, sh.threads, smem, brmppi::needs_ext(make_kconst(c->prm)));
   if (occ < 1) return fail(c, BRMPPI_EINVAL, "batch launch shape cannot be resident");
   int grid = occ * c->num_sms;
   if (grid > static_cast<int>(items.size())) grid = static_cast<int>(items.size());
@@ -500,6 +533,12 @@ void brmppi_default_params(brmppi_params* p) {
   p->w_alpha = 1.f;
   p->rho = 0.01f;
   p->h_floor = 1e-6f;
+  p->q_coll = 100.0f;
+  p->alpha_stab = 0.5f;
+  p->q_stab[0] = 1.0f;
+  p->q_stab[1] = 1.0f;
+  p->q_abuf = 10.0f;
+  p->h_buf = 0.5f;
 }
 
 brmppi_status brmppi_create(const brmppi_params* p, int device, brmppi_ctx** out) {
@@ -535,7 +574,7 @@ brmppi_status brmppi_create(const brmppi_params* p, int device, brmppi_ctx** out
   const size_t H = static_cast<size_t>(p->H), S = static_cast<size_t>(p->S);
   c->off_unom = 64;
   c->off_obs = align_up(c->off_unom + sizeof(float) * 3 * H, 16);
-  c->off_path = align_up(c->off_obs + sizeof(float) * 6 * static_cast<size_t>(p->max_obstacles), 16);
+  c->off_path = align_up(c->off_obs + sizeof(float) * obs_floats(*p) * static_cast<size_t>(p->max_obstacles), 16);
   c->in_bytes = align_up(c->off_path + sizeof(float) * 3 * static_cast<size_t>(p->max_path_pts), 16);
   c->out_floats = 3 * H + 7 * (H + 1) + 1;
   c->part_stride = static_cast<size_t>(part_stride_for(p->H));
@@ -606,8 +645,9 @@ brmppi_status brmppi_solve(brmppi_ctx* c, const double x0[7], const float* U_nom
   if (st != BRMPPI_OK) return st;
   for (int j = 0; j < 7; ++j)
     if (!std::isfinite(x0[j])) return fail(c, BRMPPI_ENONFINITE, "x0 is not finite");
+  const int of = obs_floats(c->prm);
   for (int o = 0; o < n_obs; ++o)
-    if (obs[6 * o + 5] != 2.0f) return fail(c, BRMPPI_EINVAL, "obstacle exponent must be 2");
+    if (!exponent_ok(c->prm, obs[of * o + 5])) return fail(c, BRMPPI_EINVAL, "unsupported obstacle exponent");
   Shape sh;
   if (!plain_shape(c, n_obs, n_pts, &sh)) return fail(c, BRMPPI_EINVAL, "no launch shape for this size");
   const int H = c->prm.H;
@@ -616,7 +656,7 @@ brmppi_status brmppi_solve(brmppi_ctx* c, const double x0[7], const float* U_nom
   // stage: x0 | U_nom | obs | path  (one pinned buffer, one copy)
   std::memcpy(c->h_in, x0, 7 * sizeof(double));
   std::memcpy(c->h_in + c->off_unom, U_nom, sizeof(float) * 3 * H);
-  if (n_obs > 0) std::memcpy(c->h_in + c->off_obs, obs, sizeof(float) * 6 * n_obs);
+  if (n_obs > 0) std::memcpy(c->h_in + c->off_obs, obs, sizeof(float) * of * n_obs);
   std::memcpy(c->h_in + c->off_path, path, sizeof(float) * 3 * n_pts);
   const size_t in_used = c->off_path + sizeof(float) * 3 * n_pts;
   if ((e = cudaMemcpyAsync(c->d_in, c->h_in, in_used, cudaMemcpyHostToDevice, c->stream)) != cudaSuccess)
@@ -677,7 +717,7 @@ brmppi_status brmppi_solve_device_ex(brmppi_ctx* c, const brmppi_instance* q, vo
   if (!plain_shape(c, q->n_obs, q->n_pts, &sh)) return fail(c, BRMPPI_EINVAL, "no launch shape for this size");
   return enqueue_plain_sized(c, sh, q->S, q->H, q->x0, q->U_nom, q->obs, q->n_obs, q->path, q->n_pts, q->ds,
                              q->seed, q->counter, q->U_out, q->traj_out, q->J_out, q->U_next, q->status,
-                             q->states_out, static_cast<cudaStream_t>(stream));
+                             q->states_out, q->u_safe_out, static_cast<cudaStream_t>(stream));
 }
 
 brmppi_status brmppi_solve_batch(brmppi_ctx* c, const brmppi_instance* inst, int32_t n, void* stream) {
@@ -888,6 +928,20 @@ brmppi_status brmppi_get_launch(brmppi_ctx* c, int32_t n_obs, int32_t* tps, int3
   if (tps) *tps = sh.tps;
   if (threads) *threads = sh.threads;
   if (blocks) *blocks = (c->prm.S + spb - 1) / spb;
+  return BRMPPI_OK;
+}
+
+brmppi_status brmppi_hitch_stabilize_device(brmppi_ctx* c, const double* x_dev, const float* u_ref_dev, int32_t n,
+                                            float* u_out_dev, void* stream) {
+  if (!c) return BRMPPI_EINVAL;
+  c->err.clear();
+  if (n < 0) return fail(c, BRMPPI_EINVAL, "n must be >= 0");
+  if (n == 0) return BRMPPI_OK;
+  if (!x_dev || !u_ref_dev || !u_out_dev) return fail(c, BRMPPI_EINVAL, "NULL buffer");
+  cudaError_t e = cudaSetDevice(c->device);
+  if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
+  e = brmppi::launch_stabilize(make_kconst(c->prm), x_dev, u_ref_dev, n, u_out_dev, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(c, e, "stabilizer launch");
   return BRMPPI_OK;
 }
 

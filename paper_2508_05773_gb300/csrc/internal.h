@@ -19,6 +19,12 @@ constexpr int kMaxThreads = 512;
 constexpr int kMinBatchSpb = 16;  // smallest tile of a batch launch
 constexpr int kMaxResidentThreads = 2048;
 
+// Floats per obstacle row, and the exponents a row may carry.
+inline int obs_floats(const brmppi_params& p) { return (p.flags & BRMPPI_FLAG_OBS8) ? 8 : 6; }
+inline bool exponent_ok(const brmppi_params& p, float e) {
+  return e == 2.0f || ((p.flags & BRMPPI_FLAG_OBS8) && e == 4.0f);
+}
+
 struct Shape {
   int tps = 0, bpt = 0, threads = 0;
 };
@@ -46,6 +52,7 @@ struct Lane {
 struct BatchPlan {
   Shape shape;
   int n_inst = 0, n_work = 0, grid = 0, Hmax = 0;
+  bool any_u_safe = false;  // some instance asks for the stabilized input
   brmppi::SmemCaps caps{};
   size_t smem = 0;
 };

@@ -12,19 +12,66 @@ void for_each_variant(F f) {
   for (int i = 0; i < n; ++i) f(a[i]);
   const Variant* b = variants_wide(&n);
   for (int i = 0; i < n; ++i) f(b[i]);
+  const Variant* c = variants_narrow_ext(&n);
+  for (int i = 0; i < n; ++i) f(c[i]);
+  const Variant* d = variants_wide_ext(&n);
+  for (int i = 0; i < n; ++i) f(d[i]);
 }
 
-const Variant* find(int tps, int bpt) {
+const Variant* find(int tps, int bpt, bool ext) {
   const Variant* hit = nullptr;
   for_each_variant([&](const Variant& v) {
-    if (v.tps == tps && v.bpt == bpt) hit = &v;
+    if (v.tps == tps && v.bpt == bpt && v.ext == ext) hit = &v;
   });
   return hit;
 }
 
+// One state per thread: the hitch stabilizer on (x_i, u_ref_i).
+__global__ void __launch_bounds__(256) stabilize_kernel(const KConst k, const double* x, const float* u_ref, int n,
+                                                        float* out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double* xi = x + 7 * static_cast<size_t>(i);
+  const float* ur = u_ref + 3 * static_cast<size_t>(i);
+  float o[4];
+  hitch_stabilize(k, static_cast<float>(xi[3] - xi[2]), static_cast<float>(xi[4]), static_cast<float>(xi[5]), ur[0],
+                  ur[1], ur[2], o);
+  float* dst = out + 4 * static_cast<size_t>(i);
+  dst[0] = o[0];
+  dst[1] = o[1];
+  dst[2] = o[2];
+  dst[3] = o[3];
+}
+
+// One instance per thread: the hitch stabilizer on (x0, U*[0]) of every
+// instance of a table that asks for it.  Runs after the solve on the same
+// stream (kept out of the solve kernel: the unused code cost the solve time).
+__global__ void __launch_bounds__(128) stabilize_table_kernel(const KConst k, const Inst* table, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const Inst in = table[i];
+  if (!in.u_safe) return;
+  hitch_stabilize(k, static_cast<float>(in.x0[3] - in.x0[2]), static_cast<float>(in.x0[4]),
+                  static_cast<float>(in.x0[5]), in.U_out[0], in.U_out[1], in.U_out[2], in.u_safe);
+}
+
 }  // namespace
 
-bool variant_exists(int tps, int bpt) { return find(tps, bpt) != nullptr; }
+cudaError_t launch_stabilize_table(const KConst& k, const Inst* d_table, int n, cudaStream_t stream) {
+  if (n <= 0) return cudaSuccess;
+  stabilize_table_kernel<<<(n + 127) / 128, 128, 0, stream>>>(k, d_table, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_stabilize(const KConst& k, const double* x, const float* u_ref, int n, float* out,
+                             cudaStream_t stream) {
+  if (n <= 0) return cudaSuccess;
+  const int threads = 256;
+  stabilize_kernel<<<(n + threads - 1) / threads, threads, 0, stream>>>(k, x, u_ref, n, out);
+  return cudaGetLastError();
+}
+
+bool variant_exists(int tps, int bpt) { return find(tps, bpt, false) != nullptr && find(tps, bpt, true) != nullptr; }
 
 cudaError_t set_smem_limit(size_t bytes) {
   cudaError_t err = cudaSuccess;
@@ -36,8 +83,8 @@ cudaError_t set_smem_limit(size_t bytes) {
   return err;
 }
 
-int variant_occupancy(int tps, int bpt, int threads, size_t smem) {
-  const Variant* v = find(tps, bpt);
+int variant_occupancy(int tps, int bpt, int threads, size_t smem, bool ext) {
+  const Variant* v = find(tps, bpt, ext);
   if (!v) return 0;
   int n = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, v->fn, threads, smem) != cudaSuccess) return 0;
@@ -46,7 +93,7 @@ int variant_occupancy(int tps, int bpt, int threads, size_t smem) {
 
 cudaError_t launch_solve(int tps, int bpt, int blocks, int threads, size_t smem, cudaStream_t stream,
                          const KConst& k, const LaunchDesc& L) {
-  const Variant* v = find(tps, bpt);
+  const Variant* v = find(tps, bpt, needs_ext(k));
   if (!v) return cudaErrorInvalidValue;
   v->fn<<<blocks, threads, smem, stream>>>(k, L);
   return cudaGetLastError();

@@ -11,13 +11,20 @@ using KernelFn = void (*)(const KConst, const LaunchDesc);
 
 struct Variant {
   int tps, bpt;
+  bool ext;  // carries the optional terms (BRMPPI_FLAG_COLLISION_COST, _OBS8, _ALPHA_BUFFER)
   KernelFn fn;
 };
 
-// Instantiations, one translation unit per group of team widths (compiled
-// in parallel); each returns its table and its length.
-const Variant* variants_narrow(int* n);  // 1 and 2 lanes per sample
-const Variant* variants_wide(int* n);    // 4 .. 32 lanes per sample
+// Instantiations, one translation unit per group of team widths and family
+// (compiled in parallel); each returns its table and its length.  Both
+// families hold the same (tps, bpt) pairs.
+const Variant* variants_narrow(int* n);      // 1 and 2 lanes per sample
+const Variant* variants_wide(int* n);        // 4 .. 32 lanes per sample
+const Variant* variants_narrow_ext(int* n);  // the same, with the optional terms
+const Variant* variants_wide_ext(int* n);
+
+// Whether a launch with these constants needs the family with the optional terms.
+inline bool needs_ext(const KConst& k) { return k.coll || k.obs8 || k.abuf; }
 
 // Supported (threads per sample, Philox blocks per lane) pairs.
 bool variant_exists(int tps, int bpt);
@@ -26,7 +33,15 @@ bool variant_exists(int tps, int bpt);
 cudaError_t set_smem_limit(size_t bytes);
 
 // CTAs of a variant resident per SM for a launch shape (0 if it cannot run).
-int variant_occupancy(int tps, int bpt, int threads, size_t smem);
+int variant_occupancy(int tps, int bpt, int threads, size_t smem, bool ext = false);
+
+// Enqueue the hitch stabilizer for n states (out: n x 4 floats).
+cudaError_t launch_stabilize(const KConst& k, const double* x, const float* u_ref, int n, float* out,
+                             cudaStream_t stream);
+
+// Enqueue the hitch stabilizer for the instances of a device table whose
+// u_safe is set (after their solve, on the same stream).
+cudaError_t launch_stabilize_table(const KConst& k, const Inst* d_table, int n, cudaStream_t stream);
 
 // Enqueue one launch of the solve kernel.
 cudaError_t launch_solve(int tps, int bpt, int blocks, int threads, size_t smem, cudaStream_t stream,

@@ -57,6 +57,7 @@ namespace brmppi {
 // Method constants shared by every instance of a launch.
 struct KConst {
   int proj;
+  int coll, obs8, abuf;  // collision cost, moving / e = 4 obstacle rows, buffer cost
   float Ts, hTs2, inv_lambda;
   float inv_l1, inv_l2, k_hitch, dtheta_max, kappa, r_inflate;
   float Qc, Ql, Qth, R0, R1, R2, mu, nu_bar;
@@ -66,6 +67,8 @@ struct KConst {
   float m_u0, m_u1, inv_m_u0, inv_m_u1, inv_m_u2;
   float w_a, pc_a, m_a, inv_m_a;
   float h_floor;
+  float q_coll, q_abuf, inv_hbuf;
+  float alpha_stab, inv_qs0, inv_qs1;  // hitch stabilizer: CBF rate, Q_h^-1
 };
 
 // One solve of a launch (all pointers device memory).
@@ -80,6 +83,8 @@ struct Inst {
   float* U_next;     // may be null
   int32_t* status;   // may be null
   float* states_out;  // may be null: every sample's states, S x (H+1) x 7
+  float* u_safe;      // may be null: stabilized U*[0] (a, omega, nu, slack), written
+                      // by the stabilizer launch that follows the solve
   float* part;       // tiles * part_stride floats
   unsigned int* sync;  // [0] finished tiles, [1] error bits
   int S, H, n_obs, n_pts, tiles, part_stride;
@@ -182,6 +187,98 @@ __device__ __forceinline__ void acc2(float& h, float& l, float inc) {
   h = sum;
 }
 
+// Barrier-rate row of the hitch barrier h = dtheta_max - kappa v - |Delta|,
+// Delta = theta2 - theta1 (Eq. hitch_angle_barrier), through the
+// second-order expansion of Eq. barrier_function_approx: the increment
+// Ts hdot + Ts^2/2 hddot along the field with the input held is
+// Aa a + Aw omega + c0 (progress never enters).  sp, cp = sin, cos of
+// phi = -Delta; tn = tan(delta).
+struct HitchRow {
+  float h, Aa, Aw, c0;
+};
+__device__ __forceinline__ HitchRow hitch_row(const KConst& k, float Delta, float sp, float cp, float tn,
+                                              float vv, float th1dot) {
+  const float sg = Delta >= 0.f ? 1.f : -1.f;
+  const float G = sp - k.k_hitch * cp * tn;
+  const float th2dot = vv * G * k.inv_l2;
+  const float phidot = th1dot - th2dot;
+  const float sec2 = 1.f + tn * tn;
+  HitchRow r;
+  r.h = k.dtheta_max - k.kappa * vv - sg * Delta;
+  r.Aa = -k.Ts * k.kappa - k.hTs2 * sg * (G * k.inv_l2 - tn * k.inv_l1);
+  r.Aw = k.hTs2 * sg * vv * sec2 * (k.k_hitch * cp * k.inv_l2 + k.inv_l1);
+  r.c0 = -k.Ts * sg * (th2dot - th1dot) - k.hTs2 * sg * vv * k.inv_l2 * (cp + k.k_hitch * tn * sp) * phidot;
+  return r;
+}
+
+// Hitch-angle stabilizer (Sec. IV-D, Eq. hitch_angle_qp): the (a, omega)
+// nearest the reference in the diag(q_stab) norm, inside the input box,
+// whose hitch increment g.u + c0 meets the discrete CBF condition
+// (Eq. barrier_constraint_prelim, sign of Eq. cbf_equality)
+//   g.u >= rhs = -alpha_stab h - c0.
+// KKT with a diagonal weight and a box: the box projection of the reference
+// if it meets the condition; else u(mu) = clip(u_ref + mu Q^-1 g) at the
+// mu > 0 where g.u(mu) = rhs.  g.u(mu) is piecewise linear and
+// non-decreasing with breaks where a coordinate meets a bound, so the root is
+// found exactly on the segment that crosses rhs.  No crossing: the box
+// corner that maximises the increment.  out = (a, omega, nu, slack).
+__device__ __forceinline__ void hitch_stabilize(const KConst& k, float Delta, float vv, float dl, float ua, float uw,
+                                                float un, float* out) {
+  float sp, cp;
+  sincosf(-Delta, &sp, &cp);
+  const float tn = tanf(dl);
+  const HitchRow r = hitch_row(k, Delta, sp, cp, tn, vv, vv * tn * k.inv_l1);
+  const float g0 = r.Aa, g1 = r.Aw;
+  const float rhs = -k.alpha_stab * r.h - r.c0;
+  float a = clampf(ua, k.zlo0, k.zhi0), w = clampf(uw, k.zlo1, k.zhi1);
+  const float f0 = g0 * a + g1 * w;
+  if (f0 < rhs) {
+    const float d0 = g0 * k.inv_qs0, d1 = g1 * k.inv_qs1;
+    // breakpoints: the mu > 0 where a coordinate meets a bound (+inf: none)
+    auto brk = [](float ref, float d, float bound) {
+      const float m = (bound - ref) / d;
+      return (d != 0.f && m > 0.f) ? m : CUDART_INF_F;
+    };
+    float b0 = brk(ua, d0, k.zlo0), b1 = brk(ua, d0, k.zhi0);
+    float b2 = brk(uw, d1, k.zlo1), b3 = brk(uw, d1, k.zhi1);
+    auto cswap = [](float& x, float& y) {
+      const float lo = fminf(x, y), hi = fmaxf(x, y);
+      x = lo;
+      y = hi;
+    };
+    cswap(b0, b1);  // sorting network for four keys
+    cswap(b2, b3);
+    cswap(b0, b2);
+    cswap(b1, b3);
+    cswap(b1, b2);
+    float m_prev = 0.f, f_prev = f0;
+    bool crossed = false;
+    const float bs[4] = {b0, b1, b2, b3};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const float m = bs[i];
+      if (crossed || !(m < CUDART_INF_F)) continue;
+      const float f = g0 * clampf(ua + m * d0, k.zlo0, k.zhi0) + g1 * clampf(uw + m * d1, k.zlo1, k.zhi1);
+      if (f >= rhs) {
+        const float mu = m_prev + (rhs - f_prev) * (m - m_prev) / (f - f_prev);
+        a = clampf(ua + mu * d0, k.zlo0, k.zhi0);
+        w = clampf(uw + mu * d1, k.zlo1, k.zhi1);
+        crossed = true;
+      }
+      m_prev = m;
+      f_prev = f;
+    }
+    if (!crossed) {
+      if (d0 != 0.f) a = d0 > 0.f ? k.zhi0 : k.zlo0;
+      if (d1 != 0.f) w = d1 > 0.f ? k.zhi1 : k.zlo1;
+    }
+  }
+  out[0] = a;
+  out[1] = w;
+  out[2] = un;
+  out[3] = (g0 * a + g1 * w) - rhs;
+}
+
 // Frame of one solve (relative coordinates).  Doubles of x0 enter as
 // unevaluated float pairs (hi + lo), so the staging needs no FP64 trig.
 struct Frame {
@@ -218,7 +315,9 @@ __device__ __forceinline__ void make_frame(const double* x0, float ds, unsigned 
 
 // Shared memory of a CTA (offsets into the dynamic buffer, floats).
 struct Smem {
-  float* obs;    // 8 per obstacle: cx, cy, cos, sin, 1/Ax^2, 1/Ay^2, -, -
+  float* obs;    // 8 per obstacle: cx, cy, cos, sin, kx, ky, vx', vy' with
+                 // k = 1/A^2 (e = 2) or 1/A^4 (e = 4, kx stored negated) and
+                 // the velocity in the obstacle frame (zero unless moving)
   float* path;   // 3 per row: x, y, heading (relative frame)
   float* unom;   // 3H
   float* ustar;  // 3H + 1 (merge)
@@ -250,7 +349,7 @@ struct Shared {
 };
 
 // ----------------------------------------------------------- one sample tile
-template <int TPS, int BPT>
+template <int TPS, int BPT, bool EXT>
 __device__ void run_tile(const KConst& k, const Inst& in, int tile, float* uh, const Smem& S,
                          Shared& sh) {
   const int spb = blockDim.x / TPS;
@@ -264,16 +363,23 @@ __device__ void run_tile(const KConst& k, const Inst& in, int tile, float* uh, c
   if (threadIdx.x == 0) make_frame(in.x0, in.ds, in.sync + 1, sh.fr);
   __syncthreads();
   const Frame& fr = sh.fr;
+  const bool obs8 = EXT && k.obs8;
+  const int ostride = obs8 ? 8 : 6;
   for (int o = threadIdx.x; o < in.n_obs; o += blockDim.x) {
-    const float* ob = in.obs + 6 * o;
+    const float* ob = in.obs + ostride * o;
     float* d = S.obs + 8 * o;
-    if (ob[5] != 2.0f) atomicOr(in.sync + 1, ERR_EXPONENT);
+    const bool e4 = obs8 && ob[5] == 4.0f;
+    if (ob[5] != 2.0f && !e4) atomicOr(in.sync + 1, ERR_EXPONENT);
     const float Ax = ob[2] + k.r_inflate, Ay = ob[3] + k.r_inflate;
     d[0] = (ob[0] - fr.ox_h) - fr.ox_l;
     d[1] = (ob[1] - fr.oy_h) - fr.oy_l;
     sincosf(ob[4], &d[3], &d[2]);
-    d[4] = 1.0f / (Ax * Ax);
-    d[5] = 1.0f / (Ay * Ay);
+    const float ix = 1.0f / (Ax * Ax), iy = 1.0f / (Ay * Ay);
+    d[4] = e4 ? -(ix * ix) : ix;
+    d[5] = e4 ? iy * iy : iy;
+    const float vx = obs8 ? ob[6] : 0.f, vy = obs8 ? ob[7] : 0.f;
+    d[6] = d[2] * vx + d[3] * vy;
+    d[7] = d[2] * vy - d[3] * vx;
   }
   for (int j = threadIdx.x; j < in.n_pts; j += blockDim.x) {
     const float* r = in.path + 3 * j;
@@ -320,8 +426,22 @@ __device__ void run_tile(const KConst& k, const Inst& in, int tile, float* uh, c
     }
   };
 
-  // stage cost of the current state reached with input (ua, uw, un)
-  auto stage_cost = [&]() {
+  // barrier of obstacle j at the current state and time t (Eq.
+  // barrier_function; moving centres at c + t v)
+  auto obstacle_h = [&](int j, float t) -> float {
+    const float4 o0 = *reinterpret_cast<const float4*>(S.obs + 8 * j);
+    const float4 o1 = *reinterpret_cast<const float4*>(S.obs + 8 * j + 4);
+    const float dx = (px - o0.x) + pxl, dy = (py - o0.y) + pyl;
+    const float xp = o0.z * dx + o0.w * dy - t * o1.z;
+    const float yp = o0.z * dy - o0.w * dx - t * o1.w;
+    const bool e4 = o1.x < 0.f;
+    const float kx = fabsf(o1.x), ky = o1.y;
+    const float X = e4 ? xp * xp * kx : kx, Y = e4 ? yp * yp * ky : ky;
+    return xp * xp * X + yp * yp * Y - 1.f;
+  };
+
+  // stage cost of the current state (time t) reached with input (ua, uw, un)
+  auto stage_cost = [&](float t) {
     const float qf = qf0 + (ps * in.inv_ds + psl * in.inv_ds);
     const float fl = floorf(qf);
     int ii = i0 + static_cast<int>(fl);
@@ -346,8 +466,15 @@ __device__ void run_tile(const KConst& k, const Inst& in, int tile, float* uh, c
     const float el = -cth * dxr - sth * dyr;
     const float e1 = wrap_pi(t1 - thr), e2 = wrap_pi(t2 - thr);
     const float dn = k.nu_bar - un;
-    const float rc = k.Qc * ec * ec + k.Ql * el * el + k.Qth * (e1 * e1 + e2 * e2) + k.R0 * ua * ua +
-                     k.R1 * uw * uw + k.R2 * un * un + k.mu * dn * dn;
+    float rc = k.Qc * ec * ec + k.Ql * el * el + k.Qth * (e1 * e1 + e2 * e2) + k.R0 * ua * ua +
+               k.R1 * uw * uw + k.R2 * un * un + k.mu * dn * dn;
+    if (EXT && k.coll) {
+      // the comparison method's collision penalty: depth of every
+      // obstacle the state is inside (obstacles spread over the team)
+      float c = 0.f;
+      for (int j = lt; j < in.n_obs; j += TPS) c += fmaxf(-obstacle_h(j, t), 0.f);
+      rc += k.q_coll * team_sum<TPS>(c);
+    }
     acc2(Jh, Jl, rc);
   };
 
@@ -374,8 +501,9 @@ __device__ void run_tile(const KConst& k, const Inst& in, int tile, float* uh, c
   // per-team double buffer in shared memory, and constraint i is built by
   // lane i % TPS, so rows spread evenly over the team.
   float* nz = S.noise + team * S.noise_per_team;  // [2][P][4] (wide teams)
+  const int P_drawn = k.proj ? in.P : 1;  // standard MPPI needs the input normals only
   auto stage_step = [&](int tau_d, float* buf) {
-    for (int b = lt; b < in.P; b += TPS) {
+    for (int b = lt; b < P_drawn; b += TPS) {
       float t4[4];
       draw_block(b, tau_d, t4);
       *reinterpret_cast<float4*>(buf + 4 * b) = make_float4(t4[0], t4[1], t4[2], t4[3]);
@@ -411,7 +539,7 @@ __device__ void run_tile(const KConst& k, const Inst& in, int tile, float* uh, c
     const float th1dot = vv * tn * k.inv_l1;
 
     // cost of the previous step, at this state (independent of the rows)
-    if (tau > 0) stage_cost();
+    if (tau > 0) stage_cost(static_cast<float>(tau) * k.Ts);
 
     float na, nw, nn;
     if constexpr (TPS == 1) {
@@ -438,56 +566,75 @@ __device__ void run_tile(const KConst& k, const Inst& in, int tile, float* uh, c
       float Saa, Saw, Sww, ga, gw, ca_h, cw_h, cc_h;
       {
         const float n_h = (TPS == 1) ? nrm[3] : cur[3];
-        const float Delta = t2 - t1;
-        const float sg = Delta >= 0.f ? 1.f : -1.f;
-        const float G = sp - k.k_hitch * cp * tn;
-        const float th2dot = vv * G * k.inv_l2;
-        const float phidot = th1dot - th2dot;
-        const float sec2 = 1.f + tn * tn;
-        const float h = k.dtheta_max - k.kappa * vv - sg * Delta;
-        const float Aa = -k.Ts * k.kappa - k.hTs2 * sg * (G * k.inv_l2 - tn * k.inv_l1);
-        const float Aw = k.hTs2 * sg * vv * sec2 * (k.k_hitch * cp * k.inv_l2 + k.inv_l1);
-        const float c0h = -k.Ts * sg * (th2dot - th1dot) -
-                          k.hTs2 * sg * vv * k.inv_l2 * (cp + k.k_hitch * tn * sp) * phidot;
-        const float hm = fmaxf(fabsf(h), k.h_floor);
-        const float ht = h >= 0.f ? hm : -hm;
+        const HitchRow hr = hitch_row(k, t2 - t1, sp, cp, tn, vv, th1dot);
+        const float hm = fmaxf(fabsf(hr.h), k.h_floor);
+        const float ht = hr.h >= 0.f ? hm : -hm;
         const float zda = clampf(k.sigma_alpha * n_h, k.ua_lo, k.ua_hi);
         const float pa = k.w_a * zda + k.pc_a;
-        const float b = -alpha_h * h - c0h;
-        const float r = Aa * q0 + Aw * q1 + ht * pa * k.inv_m_a - b;
+        const float b = -alpha_h * hr.h - hr.c0;
+        const float r = hr.Aa * q0 + hr.Aw * q1 + ht * pa * k.inv_m_a - b;
         const float iht = 1.f / ht;
         const float own = (lt == 0) ? k.m_a * iht * iht : 0.f;  // 1/D on lane 0
-        Saa = Aa * Aa * own;
-        Saw = Aa * Aw * own;
-        Sww = Aw * Aw * own;
-        ga = Aa * r * own;
-        gw = Aw * r * own;
-        ca_h = Aa * iht;
-        cw_h = Aw * iht;
+        Saa = hr.Aa * hr.Aa * own;
+        Saw = hr.Aa * hr.Aw * own;
+        Sww = hr.Aw * hr.Aw * own;
+        ga = hr.Aa * r * own;
+        gw = hr.Aw * r * own;
+        ca_h = hr.Aa * iht;
+        cw_h = hr.Aw * iht;
         cc_h = pa * k.inv_m_a - r * iht;
       }
 
-      // ellipse rows (e = 2) in the obstacle frame; the steer rate does not
-      // enter at second order, and hdot shares dh/da's direction term.
+      // obstacle rows in the obstacle frame; the steer rate does not enter
+      // at second order.  Parked ellipses (e = 2): hdot shares dh/da's
+      // direction term.  Moving or e = 4 rows (uniform branch): barrier of
+      // the relative position at this step's time, relative velocity.
       // `live` = 0 turns a padding slot into a no-op without branching.
       float ca[OBS_SLOTS], cc[OBS_SLOTS];
 #pragma unroll
       for (int q = 0; q < OBS_SLOTS; ++q) ca[q] = cc[q] = 0.f;
+      const float tnow = static_cast<float>(tau) * k.Ts;
+      float cbuf = 0.f;  // buffer cost of this lane's rows
       auto obstacle_row = [&](int j, float n_alpha, int slot, float live) {
-        const float4 o0 = *reinterpret_cast<const float4*>(S.obs + 8 * j);
-        const float2 o1 = *reinterpret_cast<const float2*>(S.obs + 8 * j + 4);
-        const float dx = (px - o0.x) + pxl, dy = (py - o0.y) + pyl;
-        const float co = o0.z, so = o0.w, iax = o1.x, iay = o1.y;
-        const float xp = co * dx + so * dy;
-        const float yp = co * dy - so * dx;
-        const float h = xp * xp * iax + yp * yp * iay - 1.f;
-        const float hx = 2.f * xp * iax, hy = 2.f * yp * iay;
-        const float dirx = co * c1 + so * s1, diry = co * s1 - so * c1;
-        const float gda = hx * dirx + hy * diry;  // dh along the heading
-        const float hdd0 = vv * th1dot * (hy * dirx - hx * diry) +
-                           2.f * vv * vv * (iax * dirx * dirx + iay * diry * diry);
-        const float Aa = k.hTs2 * gda;
-        const float brest = -k.Ts * vv * gda - k.hTs2 * hdd0;
+        float h, Aa, brest;
+        if constexpr (!EXT) {
+          const float4 o0 = *reinterpret_cast<const float4*>(S.obs + 8 * j);
+          const float2 o1 = *reinterpret_cast<const float2*>(S.obs + 8 * j + 4);
+          const float dx = (px - o0.x) + pxl, dy = (py - o0.y) + pyl;
+          const float co = o0.z, so = o0.w, iax = o1.x, iay = o1.y;
+          const float xp = co * dx + so * dy;
+          const float yp = co * dy - so * dx;
+          h = xp * xp * iax + yp * yp * iay - 1.f;
+          const float hx = 2.f * xp * iax, hy = 2.f * yp * iay;
+          const float dirx = co * c1 + so * s1, diry = co * s1 - so * c1;
+          const float gda = hx * dirx + hy * diry;  // dh along the heading
+          const float hdd0 = vv * th1dot * (hy * dirx - hx * diry) +
+                             2.f * vv * vv * (iax * dirx * dirx + iay * diry * diry);
+          Aa = k.hTs2 * gda;
+          brest = -k.Ts * vv * gda - k.hTs2 * hdd0;
+        } else {
+          const float4 o0 = *reinterpret_cast<const float4*>(S.obs + 8 * j);
+          const float4 o1 = *reinterpret_cast<const float4*>(S.obs + 8 * j + 4);
+          const float dx = (px - o0.x) + pxl, dy = (py - o0.y) + pyl;
+          const float co = o0.z, so = o0.w;
+          const float dirx = co * c1 + so * s1, diry = co * s1 - so * c1;
+          // moving centre at tnow; e = 4 flagged by a negated kx;
+          // X = xp^(e-2) / Ax^e: h = xp^2 X + ..., h_x = e xp X, h_xx = e (e-1) X
+          const float xp = co * dx + so * dy - tnow * o1.z;
+          const float yp = co * dy - so * dx - tnow * o1.w;
+          const bool e4 = o1.x < 0.f;
+          const float kx = fabsf(o1.x), ky = o1.y;
+          const float X = e4 ? xp * xp * kx : kx, Y = e4 ? yp * yp * ky : ky;
+          const float ce = e4 ? 4.f : 2.f, cee = e4 ? 12.f : 2.f;
+          h = xp * xp * X + yp * yp * Y - 1.f;
+          const float hx = ce * xp * X, hy = ce * yp * Y;
+          const float velx = vv * dirx - o1.z, vely = vv * diry - o1.w;  // relative velocity
+          const float gda = hx * dirx + hy * diry;
+          const float hdot = hx * velx + hy * vely;
+          const float hdd0 = vv * th1dot * (hy * dirx - hx * diry) + cee * (X * velx * velx + Y * vely * vely);
+          Aa = k.hTs2 * gda;
+          brest = -k.Ts * hdot - k.hTs2 * hdd0;
+        }
         const float hm = fmaxf(fabsf(h), k.h_floor);
         const float ht = h >= 0.f ? hm : -hm;
         const float zda = clampf(k.sigma_alpha * n_alpha, k.ua_lo, k.ua_hi);
@@ -500,6 +647,12 @@ __device__ void run_tile(const KConst& k, const Inst& in, int tile, float* uh, c
         ga += Aa * r * invD;
         ca[slot] = live * (Aa * iht);
         cc[slot] = live * (pa * k.inv_m_a - r * iht);
+        if (EXT && k.abuf) {
+          // buffer zone: positive rates charged with weight clip(1 - h/h_buf)
+          const float wz = clampf(1.f - h * k.inv_hbuf, 0.f, 1.f);
+          const float ap = fmaxf(alpha[slot], 0.f);
+          cbuf += live * (k.q_abuf * wz * ap * ap);
+        }
       };
 
       if constexpr (TPS == 1) {
@@ -539,6 +692,7 @@ __device__ void run_tile(const KConst& k, const Inst& in, int tile, float* uh, c
           }
         }
       }
+      if (EXT && k.abuf) acc2(Jh, Jl, team_sum<TPS>(cbuf));
       Saa = team_sum<TPS>(Saa) + k.m_u0;
       Saw = team_sum<TPS>(Saw);
       Sww = team_sum<TPS>(Sww) + k.m_u1;
@@ -583,7 +737,7 @@ __device__ void run_tile(const KConst& k, const Inst& in, int tile, float* uh, c
       for (int q = 0; q < 4; ++q) nrm[q] = nxt[q];
     }
   }
-  stage_cost();  // cost of the last step
+  stage_cost(static_cast<float>(H) * k.Ts);  // cost of the last step
 
   // --- per-sample cost: normalise the pair
   {
@@ -764,7 +918,9 @@ static __device__ void merge_instance(const KConst& k, const Inst& in, const Sme
 }
 
 // -------------------------------------------------------------- the kernel
-template <int TPS, int BPT>
+// EXT: the instantiations that also carry the optional terms (moving and
+// e = 4 obstacles, collision cost, buffer cost); the others compile them out.
+template <int TPS, int BPT, bool EXT>
 __global__ void __launch_bounds__(512) solve_kernel(const KConst k, const LaunchDesc L) {
   extern __shared__ float dyn[];
   __shared__ Shared sh;
@@ -790,7 +946,7 @@ __global__ void __launch_bounds__(512) solve_kernel(const KConst k, const Launch
     Inst in;
     if (L.work) in = L.inst[inst_id];
     else in = L.single;
-    run_tile<TPS, BPT>(k, in, tile, uh, S, sh);
+    run_tile<TPS, BPT, EXT>(k, in, tile, uh, S, sh);
 
     // the CTA that completes an instance's last tile merges its partials
     __threadfence();

@@ -161,7 +161,7 @@ void Server::scheduler_loop() {
     Lane& L = lanes[lane];
     brmppi_status st = BRMPPI_OK;
     cudaError_t e = cudaSuccess;
-    const size_t in_bytes = 64 + sizeof(float) * 6 * static_cast<size_t>(max_obs);
+    const size_t in_bytes = 64 + sizeof(float) * obs_floats(shadow.prm) * static_cast<size_t>(max_obs);
     for (int s : pick) {
       if (e == cudaSuccess)
         e = cudaMemcpyAsync(d_in + static_cast<size_t>(s) * in_stride, h_in + static_cast<size_t>(s) * in_stride,
@@ -249,7 +249,7 @@ brmppi_status server_create(brmppi_ctx* c) {
   sv->shape.tps = 1;
   sv->shape.threads = 128;
   const int n_lanes = p.serve_lanes > 0 ? p.serve_lanes : 2;
-  sv->in_stride = align_up(64 + sizeof(float) * 6 * static_cast<size_t>(p.max_obstacles), 256);
+  sv->in_stride = align_up(64 + sizeof(float) * obs_floats(p) * static_cast<size_t>(p.max_obstacles), 256);
   sv->out_stride = align_up(3 * static_cast<size_t>(p.H) + 7 * static_cast<size_t>(p.H + 1) + 1, 64);
   c->server = sv;
   cudaError_t e;
@@ -362,7 +362,7 @@ brmppi_status brmppi_submit(brmppi_ctx* c, uint32_t vid, const double x0[7], con
   for (int j = 0; j < 7; ++j)
     if (!std::isfinite(x0[j])) return BRMPPI_ENONFINITE;
   for (int o = 0; o < n_obs; ++o)
-    if (obs[6 * o + 5] != 2.0f) return BRMPPI_EINVAL;
+    if (!exponent_ok(c->prm, obs[obs_floats(c->prm) * o + 5])) return BRMPPI_EINVAL;
   {
     std::lock_guard<std::mutex> lk(sv->mu);
     if (vid >= sv->veh.size() || !sv->veh[vid].registered) return BRMPPI_EINVAL;
@@ -371,7 +371,7 @@ brmppi_status brmppi_submit(brmppi_ctx* c, uint32_t vid, const double x0[7], con
     sv->free_slots.pop_back();
     unsigned char* h = sv->h_in + static_cast<size_t>(s) * sv->in_stride;
     std::memcpy(h, x0, 7 * sizeof(double));
-    if (n_obs > 0) std::memcpy(h + 64, obs, sizeof(float) * 6 * n_obs);
+    if (n_obs > 0) std::memcpy(h + 64, obs, sizeof(float) * obs_floats(c->prm) * n_obs);
     Slot& sl = sv->slots[s];
     sl.state = kQueued;
     sl.ticket = sv->next_ticket++;

@@ -133,7 +133,8 @@ def _far_from(c, pts, semi):
 
 def _scenario(p, x0, path, ds, obs, seed=0, counter=0, U_nom=None):
     H = int(p["H"])
-    obs = np.asarray(obs, dtype=np.float32).reshape(-1, 6)
+    width = 8 if int(p.get("flags", 0)) & FLAG_OBS8 else 6
+    obs = np.asarray(obs, dtype=np.float32).reshape(-1, width)
     if U_nom is None:
         U_nom = np.zeros((H, 3), dtype=np.float32)
     return dict(params=p, x0=np.asarray(x0, dtype=np.float64), U_nom=np.asarray(U_nom, np.float32),
@@ -274,3 +275,59 @@ def small_random(seed: int, S: int = 64, H: int = 12, n_obs: int = 3, reverse: b
     U_nom[:, 2] = np.abs(U_nom[:, 2]) * 3.0
     return _scenario(p, x0, path, 0.1, obs, seed=int(rng.integers(0, 2**63 - 1)),
                      counter=int(rng.integers(0, 2**32)), U_nom=U_nom)
+
+
+def with_moving(c: dict, seed: int, e4_frac: float = 0.5, speed=(0.3, 1.5)) -> dict:
+    """The scenario with 8-float obstacle rows (flag FLAG_OBS8): a share
+    e4_frac of its obstacles become e = 4 super-ellipses (parked vehicles,
+    Sec. IV-C), the others move at a speed U[speed] m/s in a random
+    direction (predicted pedestrians; constant-velocity prediction)."""
+    rng = np.random.default_rng(seed)
+    p = dict(c["params"], flags=int(c["params"].get("flags", 0)) | FLAG_OBS8)
+    rows = []
+    for o in np.asarray(c["obs"], np.float64).reshape(-1, 6):
+        if rng.random() < e4_frac:
+            rows.append((*o[:5], 4.0, 0.0, 0.0))
+        else:
+            sp = rng.uniform(*speed)
+            ang = rng.uniform(-math.pi, math.pi)
+            rows.append((*o[:5], 2.0, sp * math.cos(ang), sp * math.sin(ang)))
+    out = dict(c)
+    out["params"] = p
+    out["obs"] = np.asarray(rows, dtype=np.float32).reshape(-1, 8)
+    return out
+
+
+def crossing(seed: int = 6, S: int = 4096, H: int = 50, n_parked: int = 6, n_ped: int = 2) -> dict:
+    """Reverse parking with parked vehicles and crossing pedestrians (the
+    scene type of Sec. V): config-2's reverse-parking path, parked vehicles
+    as e = 4 super-ellipses with semi-axes (2.3, 0.95) m beside the path
+    (3.5-6 m lateral, either side), pedestrians as e = 2 circles of radius
+    0.5 m starting 3-5 m to one side of a path point and walking across the
+    path at 1.0-1.5 m/s.  Obstacle rows of 8 (flag FLAG_OBS8)."""
+    rng = np.random.default_rng(seed)
+    p = params(S=S, H=H, flags=FLAG_OBS8)
+    path = path_table(C2_SEGMENTS, 0.1, reverse=True)
+    L = _segments_length(C2_SEGMENTS)
+    x0 = (0.0, 0.0, math.pi, math.pi, -1.0, 0.0, 0.0)
+    end = path[-1].astype(np.float64)
+    keep_out = [(x0[0], x0[1]), (float(end[0]), float(end[1]))]
+    obs = []
+    while len(obs) < n_parked:
+        s = rng.uniform(0.0, L)
+        lat = float(rng.choice((-1.0, 1.0))) * rng.uniform(3.5, 6.0)
+        px, py, ph = _path_point(C2_SEGMENTS, s)
+        c = (px - lat * math.sin(ph), py + lat * math.cos(ph))
+        if _far_from(c, keep_out, (2.3, 0.95)):
+            obs.append((c[0], c[1], 2.3, 0.95, ph, 4.0, 0.0, 0.0))
+    while len(obs) < n_parked + n_ped:
+        s = rng.uniform(2.0, 12.0)
+        side = float(rng.choice((-1.0, 1.0)))
+        px, py, ph = _path_point(C2_SEGMENTS, s)
+        d = rng.uniform(3.0, 5.0)
+        c = (px - side * d * math.sin(ph), py + side * d * math.cos(ph))
+        sp = rng.uniform(1.0, 1.5)
+        vel = (side * sp * math.sin(ph), -side * sp * math.cos(ph))  # toward the path
+        obs.append((c[0], c[1], 0.5, 0.5, 0.0, 2.0, vel[0], vel[1]))
+    return _scenario(p, x0, path, 0.1, obs, seed=seed)
+

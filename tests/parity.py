@@ -93,3 +93,32 @@ def assert_solve_matches(out, ref, p, label="", check_J=True):
     assert ex <= TOL_STATE, f"{label} trajectory rel err {ex:.3e}"
     return dict(err_u=eu, err_traj=ex, err_J=ej, err_J_median=ejm, tol_frac=excess,
                 kappa_max=float(kappa.max()))
+
+
+# ---------------------------------------------------------------------------
+# Hitch stabilizer.  Its result moves with the constraint's right-hand side
+# rhs = -alpha_stab h - c0 by |Q^-1 g| / (g^T Q^-1 g) per unit of rhs, and g
+# (the hitch row, ~Ts kappa ~ 5e-3) is small, so the problem itself
+# amplifies the binary32 rounding of h = dtheta_max - kappa v - |Delta| (a
+# difference of O(1) terms): a few ulps of those terms, divided by |g|.
+def stab_tolerance(p, x, g, o):
+    """Per-component bound on |u_gpu - u_oracle| for one stabilized input:
+    TOL_U of the input scale plus the rhs rounding carried through the
+    active constraint by the coordinates that are free in the oracle's
+    solution (a coordinate at a bound does not move, so the others carry the
+    whole change: an omega alone moves by d rhs / g_omega)."""
+    g = np.asarray(g, np.float64)
+    q = np.asarray(p["q_stab"], np.float64)
+    lo = np.asarray(p["z_lo"][:2], np.float64)
+    hi = np.asarray(p["z_hi"][:2], np.float64)
+    u = np.asarray(o[:2], np.float64)
+    free = (u > lo + 1e-9) & (u < hi - 1e-9)
+    qig = np.where(free, g / q, 0.0)
+    den = float(g @ qig)
+    ulp = 2.0 ** -23
+    terms = abs(p["dtheta_max"]) + abs(p["kappa"] * x[4]) + abs(x[3] - x[2]) + 1.0
+    eps_rhs = 8.0 * ulp * terms
+    span = np.asarray(p["z_hi"][:2], np.float64) - np.asarray(p["z_lo"][:2], np.float64)
+    base = TOL_U * np.maximum(np.abs(np.asarray(o[:2], np.float64)), 0.01 * span)
+    carry = eps_rhs * np.abs(qig) / den if den > 0 else np.zeros(2)
+    return base + carry, eps_rhs

@@ -48,8 +48,11 @@ def test_params_struct_layout_matches(lib):
     assert list(p.sigma) == [0.5, pytest.approx(0.3), 0.5]
     # last fields: a shifted layout would scramble these
     assert abs(p.rho - 0.01) < 1e-9 and abs(p.h_floor - 1e-6) < 1e-12
-    assert ctypes.sizeof(pkg.brmppi_params) == 4 * 15 + 4 * 35
-    assert ctypes.sizeof(pkg.brmppi_instance) == 8 * 4 + 4 * 5 + 4 + 8 * 2 + 8 * 6
+    assert p.q_coll == 100.0 and p.alpha_stab == 0.5 and list(p.q_stab) == [1.0, 1.0]
+    assert p.q_abuf == 10.0 and p.h_buf == 0.5
+    # the library checks the same sizes at compile time
+    assert ctypes.sizeof(pkg.brmppi_params) == 4 * 15 + 4 * 41
+    assert ctypes.sizeof(pkg.brmppi_instance) == 8 * 4 + 4 * 5 + 4 + 8 * 2 + 8 * 7
 
 
 @pytest.mark.parametrize("field,value", [
@@ -58,6 +61,7 @@ def test_params_struct_layout_matches(lib):
     ("lambda_", -1.0), ("h_floor", 0.0), ("flags", 0x10), ("abi_version", 99),
     ("max_batch", -1), ("batch_threads_per_sample", 5), ("batch_block_threads", 1000),
     ("max_vehicles", -2), ("serve_lanes", 99), ("serve_max_batch", -1), ("serve_queue", -5),
+    ("q_coll", -1.0), ("alpha_stab", 0.0), ("alpha_stab", 1.5), ("q_abuf", -1.0), ("h_buf", 0.0),
 ])
 def test_create_rejects_bad_params_without_gpu(lib, field, value):
     import paper_2508_05773_gb300 as pkg
