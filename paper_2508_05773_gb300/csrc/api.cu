@@ -74,6 +74,9 @@ std::string check_params(const brmppi_params* p) {
     return "batch_threads_per_sample must be 0, 1, 2, 4, 8, 16 or 32";
   if (!valid_threads(p->block_threads) || !valid_threads(p->batch_block_threads))
     return "block_threads must be 0 or a multiple of 32 in [64, 512]";
+  if ((p->threads_per_sample != 1 && p->block_threads > kMaxThreads - 32) ||
+      (p->batch_threads_per_sample != 1 && p->batch_block_threads > kMaxThreads - 32))
+    return "block_threads above 480 needs threads_per_sample = 1 (wider teams add a noise warp)";
   if (p->max_batch < 0 || p->max_batch > 65536) return "max_batch must be in [0, 65536]";
   if (p->max_vehicles < 0 || p->max_vehicles > 65536) return "max_vehicles must be in [0, 65536]";
   if (p->serve_lanes < 0 || p->serve_lanes > 16) return "serve_lanes must be in [0, 16]";

@@ -83,19 +83,22 @@ cudaError_t set_smem_limit(size_t bytes) {
   return err;
 }
 
+int block_threads(int tps, int threads) { return threads + (tps > 1 ? 32 : 0); }
+
 int variant_occupancy(int tps, int bpt, int threads, size_t smem, bool ext) {
   const Variant* v = find(tps, bpt, ext);
-  if (!v) return 0;
+  if (!v || block_threads(tps, threads) > kMaxBlockThreads) return 0;
   int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, v->fn, threads, smem) != cudaSuccess) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, v->fn, block_threads(tps, threads), smem) != cudaSuccess)
+    return 0;
   return n;
 }
 
 cudaError_t launch_solve(int tps, int bpt, int blocks, int threads, size_t smem, cudaStream_t stream,
                          const KConst& k, const LaunchDesc& L) {
   const Variant* v = find(tps, bpt, needs_ext(k));
-  if (!v) return cudaErrorInvalidValue;
-  v->fn<<<blocks, threads, smem, stream>>>(k, L);
+  if (!v || block_threads(tps, threads) > kMaxBlockThreads) return cudaErrorInvalidValue;
+  v->fn<<<blocks, block_threads(tps, threads), smem, stream>>>(k, L);
   return cudaGetLastError();
 }
 

@@ -26,6 +26,12 @@ const Variant* variants_wide_ext(int* n);
 // Whether a launch with these constants needs the family with the optional terms.
 inline bool needs_ext(const KConst& k) { return k.coll || k.obs8 || k.abuf; }
 
+// Threads of a launch: `threads` roll out samples; teams wider than one lane
+// add one warp that produces the noise.  At most kMaxBlockThreads (the
+// kernels' launch bound).
+constexpr int kMaxBlockThreads = 512;
+int block_threads(int tps, int threads);
+
 // Supported (threads per sample, Philox blocks per lane) pairs.
 bool variant_exists(int tps, int bpt);
 

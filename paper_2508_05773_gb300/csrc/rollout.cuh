@@ -348,12 +348,28 @@ struct Shared {
   int last;
 };
 
+// Threads of a CTA that roll out samples: all of them with one lane per
+// sample; with wider teams the last warp produces the noise.
+template <int TPS>
+__device__ __forceinline__ int compute_threads() {
+  return TPS > 1 ? static_cast<int>(blockDim.x) - 32 : static_cast<int>(blockDim.x);
+}
+
+// The per-step hand-over between the noise warp and the compute warps
+// (named barrier 1, every thread of the CTA; whole warps take one role).
+__device__ __forceinline__ void step_barrier() { asm volatile("bar.sync 1, %0;" ::"r"(blockDim.x) : "memory"); }
+
 // ----------------------------------------------------------- one sample tile
 template <int TPS, int BPT, bool EXT>
 __device__ void run_tile(const KConst& k, const Inst& in, int tile, float* uh, const Smem& S,
                          Shared& sh) {
-  const int spb = blockDim.x / TPS;
-  const int team = threadIdx.x / TPS;
+  // Teams wider than one lane run with one extra warp (the last) that
+  // produces every team's normals a step ahead (warp specialisation: the
+  // noise leaves the compute warps' dependency chain).
+  const int nc = compute_threads<TPS>();
+  const int spb = nc / TPS;
+  const bool producer = TPS > 1 && static_cast<int>(threadIdx.x) >= nc;
+  const int team = producer ? 0 : static_cast<int>(threadIdx.x) / TPS;
   const int lt = threadIdx.x % TPS;
   const int s = tile * spb + team;
   const int H = in.H;
@@ -480,7 +496,7 @@ __device__ void run_tile(const KConst& k, const Inst& in, int tile, float* uh, c
 
   // stored-trajectory variant: the state of this sample after step tau, in
   // world coordinates (written by the team's first lane)
-  float* st_out = (in.states_out && lt == 0 && s < in.S)
+  float* st_out = (!producer && in.states_out && lt == 0 && s < in.S)
                       ? in.states_out + static_cast<size_t>(s) * static_cast<size_t>(H + 1) * 7
                       : nullptr;
   auto store_state = [&](int tau) {
@@ -496,34 +512,48 @@ __device__ void run_tile(const KConst& k, const Inst& in, int tile, float* uh, c
   if (st_out) store_state(0);
 
   // Noise.  One lane per sample: the lane draws Philox block 0 a step ahead
-  // and the further blocks where their rows are built.  Wider teams: each
-  // lane draws the blocks b = lt, lt + TPS, ... of the next step into a
-  // per-team double buffer in shared memory, and constraint i is built by
-  // lane i % TPS, so rows spread evenly over the team.
+  // and the further blocks where their rows are built.  Wider teams: the
+  // producer warp writes the P blocks of every team's step tau + 1 into a
+  // per-team double buffer in shared memory while the compute warps run step
+  // tau; one CTA barrier per step hands the buffers over (at barrier tau the
+  // producer has written step tau and the compute warps have finished step
+  // tau - 1, whose buffer it fills next).  Constraint i is built by lane
+  // i % TPS, so rows spread evenly over the team.
   float* nz = S.noise + team * S.noise_per_team;  // [2][P][4] (wide teams)
   const int P_drawn = k.proj ? in.P : 1;  // standard MPPI needs the input normals only
-  auto stage_step = [&](int tau_d, float* buf) {
-    for (int b = lt; b < P_drawn; b += TPS) {
-      float t4[4];
-      draw_block(b, tau_d, t4);
-      *reinterpret_cast<float4*>(buf + 4 * b) = make_float4(t4[0], t4[1], t4[2], t4[3]);
+  if constexpr (TPS > 1) {
+    if (producer) {
+      const int pl = static_cast<int>(threadIdx.x) - nc;
+      const int n_blocks = spb * P_drawn;
+      auto produce = [&](int tau_d) {
+        for (int i = pl; i < n_blocks; i += 32) {
+          const int tm = i / P_drawn, b = i - tm * P_drawn;
+          const uint4 w = philox4x32_10(make_uint4(static_cast<uint32_t>(b), static_cast<uint32_t>(tau_d),
+                                                   static_cast<uint32_t>(tile * spb + tm), in.ctr),
+                                        in.key0, in.key1);
+          float4 g;
+          box_muller(w.x, w.y, g.x, g.y);
+          box_muller(w.z, w.w, g.z, g.w);
+          *reinterpret_cast<float4*>(S.noise + tm * S.noise_per_team + (tau_d & 1) * 4 * in.P + 4 * b) = g;
+        }
+      };
+      produce(0);
+      for (int tau = 0; tau < H; ++tau) {
+        step_barrier();
+        if (tau + 1 < H) produce(tau + 1);
+      }
     }
-  };
-  float nrm[4];
-  if constexpr (TPS == 1) {
-    draw_first(0, nrm);
-  } else {
-    stage_step(0, nz);
   }
-  for (int tau = 0; tau < H; ++tau) {
+  float nrm[4];
+  if constexpr (TPS == 1) draw_first(0, nrm);
+  for (int tau = 0; tau < H && !producer; ++tau) {
     float nxt[4];
     float* cur = nz;
     if constexpr (TPS == 1) {
       draw_first(tau + 1 < H ? tau + 1 : tau, nxt);  // off the state's critical path
     } else {
-      __syncwarp();  // this step's normals are staged; last step's reads are done
+      step_barrier();  // this step's normals are staged
       cur = nz + (tau & 1) * 4 * in.P;
-      if (tau + 1 < H) stage_step(tau + 1, nz + ((tau + 1) & 1) * 4 * in.P);
     }
 
     // trigonometry of the current state
@@ -737,7 +767,7 @@ __device__ void run_tile(const KConst& k, const Inst& in, int tile, float* uh, c
       for (int q = 0; q < 4; ++q) nrm[q] = nxt[q];
     }
   }
-  stage_cost(static_cast<float>(H) * k.Ts);  // cost of the last step
+  if (!producer) stage_cost(static_cast<float>(H) * k.Ts);  // cost of the last step
 
   // --- per-sample cost: normalise the pair
   {
@@ -746,7 +776,7 @@ __device__ void run_tile(const KConst& k, const Inst& in, int tile, float* uh, c
     Jh = sum;
   }
   const bool valid = s < in.S;
-  if (lt == 0) {
+  if (!producer && lt == 0) {
     const bool fin = valid && isfinite(Jh) && isfinite(Jl);
     S.jh[team] = fin ? Jh : CUDART_INF_F;
     S.jl[team] = fin ? Jl : 0.f;
@@ -924,7 +954,7 @@ template <int TPS, int BPT, bool EXT>
 __global__ void __launch_bounds__(512) solve_kernel(const KConst k, const LaunchDesc L) {
   extern __shared__ float dyn[];
   __shared__ Shared sh;
-  const int spb = blockDim.x / TPS;
+  const int spb = compute_threads<TPS>() / TPS;
   const Smem S(dyn, L.caps, spb);
   float* uh = L.uh + static_cast<size_t>(blockIdx.x) * L.uh_stride;
 
