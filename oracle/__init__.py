@@ -65,7 +65,11 @@ class _Params(ctypes.Structure):
         ("q_coll", ctypes.c_double),
         ("alpha_stab", ctypes.c_double), ("q_stab", ctypes.c_double * 2),
         ("q_abuf", ctypes.c_double), ("h_buf", ctypes.c_double),
+        ("n_discs", ctypes.c_int32), ("disc_trailer_mask", ctypes.c_int32),
+        ("disc_off", ctypes.c_double * 8),
     ]
+
+_INT_FIELDS = ("S", "H", "flags", "n_discs", "disc_trailer_mask")
 
 PROJ_NONE = 1
 COLLISION_COST = 2
@@ -121,6 +125,11 @@ def _load():
                                                          ctypes.c_double, _DP]),
                 "orc_alpha_buffer_cost": (ctypes.c_double, [P, ctypes.c_int, _DP, _DP]),
                 "orc_hitch_stabilize": (ctypes.c_int, [P, _DP, _DP, _DP, _DP]),
+                "orc_disc_position": (None, [P, ctypes.c_int, _DP, _DP]),
+                "orc_disc_h": (ctypes.c_double, [P, _DP, ctypes.c_int, ctypes.c_double,
+                                                 ctypes.c_int, _DP]),
+                "orc_disc_row": (None, [P, _DP, ctypes.c_int, ctypes.c_double, ctypes.c_int, _DP,
+                                        _DP, _DP, _DP]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(lib, name)
@@ -151,7 +160,8 @@ class using_library:
                      "orc_obstacle_row", "orc_hitch_h", "orc_hitch_row", "orc_project",
                      "orc_path_lookup", "orc_stage_cost", "orc_softmin", "orc_rollout_sample",
                      "orc_solve", "orc_integrate", "orc_obstacle_h_at", "orc_obstacle_row_at",
-                     "orc_collision_cost", "orc_alpha_buffer_cost", "orc_hitch_stabilize"):
+                     "orc_collision_cost", "orc_alpha_buffer_cost", "orc_hitch_stabilize",
+                     "orc_disc_position", "orc_disc_h", "orc_disc_row"):
             src = getattr(self.saved, name)
             dst = getattr(lib, name)
             dst.restype = src.restype
@@ -199,7 +209,7 @@ def _params(p: dict, S: int | None = None, H: int | None = None) -> _Params:
         if isinstance(attr, ctypes.Array):
             for i, v in enumerate(val):
                 attr[i] = float(v)
-        elif name in ("S", "H", "flags"):
+        elif name in _INT_FIELDS:
             setattr(out, name, int(val))
         else:
             setattr(out, name, float(val))
@@ -308,6 +318,32 @@ def alpha_buffer_cost(p: dict, h, alpha) -> float:
                                      _ptr(_d(alpha, h.size)))
 
 
+def disc_position(p: dict, m: int, x):
+    lib = _load()
+    pos = np.zeros(2)
+    lib.orc_disc_position(ctypes.byref(_params(p)), int(m), _ptr(_d(x, 7)), _ptr(pos))
+    return pos
+
+
+def disc_h(p: dict, obs, m: int, x, t: float = 0.0) -> float:
+    lib = _load()
+    o = _d(obs)
+    return lib.orc_disc_h(ctypes.byref(_params(p)), _ptr(o), o.size, float(t), int(m),
+                          _ptr(_d(x, 7)))
+
+
+def disc_row(p: dict, obs, m: int, x, t: float = 0.0):
+    """Row of one obstacle (6 or 8 entries) seen from disc m: (A_u[3], h, b_rest)."""
+    lib = _load()
+    o = _d(obs)
+    Au = np.zeros(3)
+    h = ctypes.c_double()
+    br = ctypes.c_double()
+    lib.orc_disc_row(ctypes.byref(_params(p)), _ptr(o), o.size, float(t), int(m), _ptr(_d(x, 7)),
+                     _ptr(Au), ctypes.byref(h), ctypes.byref(br))
+    return Au, h.value, br.value
+
+
 def hitch_stabilize(p: dict, x, u_ref):
     """Returns (infeasible, u[3], slack)."""
     lib = _load()
@@ -382,7 +418,7 @@ def rollout_sample(p: dict, x0, U_nom, obs, path, ds, seed, counter, s):
     H = int(p["H"])
     obs = _d(obs).reshape(-1, obs_stride(p))
     n_obs = obs.shape[0]
-    Nc = 1 + n_obs
+    Nc = 1 + n_obs * int(p.get("n_discs", 1))
     d = 3 + Nc
     path = _d(path)
     out = dict(states=np.zeros((H + 1, 7)), u=np.zeros((H, 3)), alpha=np.zeros((H + 1, Nc)),

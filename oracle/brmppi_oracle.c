@@ -228,16 +228,123 @@ void orc_obstacle_row(const orc_params *P, const double obs[6], const double x[7
   orc_obstacle_row_at(P, obs, 6, 0.0, x, A_u, h, b_rest);
 }
 
+/* ------------------------------------------------------------------ */
+/* Footprint discs.  Heading accelerations along the field with the input
+   held (a, omega constant): with t = tan(delta), phi = th1 - th2,
+   k = lh / l1, G = sin(phi) - k cos(phi) t,
+     th1dot  = v t / l1,                 th1ddot = (a t + v (1 + t^2) omega) / l1,
+     th2dot  = v G / l2,
+     th2ddot = a G / l2 + v / l2 ((cos(phi) + k t sin(phi)) phidot
+                                  - k cos(phi) (1 + t^2) omega).
+   Tractor disc p_d = p + d e1:
+     pdot  = v e1 + d th1dot n1,
+     pddot = a e1 + v th1dot n1 + d th1ddot n1 - d th1dot^2 e1;
+   trailer disc p_d = p - lh e1 - L e2, L = l2 - d:
+     pdot  = v e1 - lh th1dot n1 - L th2dot n2,
+     pddot = a e1 + v th1dot n1 - lh th1ddot n1 + lh th1dot^2 e1
+             - L th2ddot n2 + L th2dot^2 e2,
+   with n1, n2 the headings turned by +90 degrees. */
+typedef struct {
+  double pos[2], vel[2];
+  double acc0[2], acc_a[2], acc_w[2]; /* pddot = acc0 + a acc_a + omega acc_w */
+} disc_motion;
+
+static void disc_kinematics(const orc_params *P, int m, const double x[7], disc_motion *dm) {
+  const double th1 = x[2], th2 = x[3], v = x[4], delta = x[5];
+  const double e1[2] = {cos(th1), sin(th1)}, n1[2] = {-sin(th1), cos(th1)};
+  const double e2[2] = {cos(th2), sin(th2)}, n2[2] = {-sin(th2), cos(th2)};
+  const double t = tan(delta), sec2 = 1.0 + t * t;
+  const double phi = th1 - th2, k = P->lh / P->l1;
+  const double G = sin(phi) - k * cos(phi) * t;
+  const double th1dot = v * t / P->l1, th2dot = v * G / P->l2;
+  const double phidot = th1dot - th2dot;
+  /* heading accelerations: constant part, coefficient of a, of omega */
+  const double a1_0 = 0.0, a1_a = t / P->l1, a1_w = v * sec2 / P->l1;
+  const double a2_0 = v / P->l2 * (cos(phi) + k * t * sin(phi)) * phidot;
+  const double a2_a = G / P->l2, a2_w = -v / P->l2 * k * cos(phi) * sec2;
+  const double d = P->disc_off[m];
+  const int on_trailer = (P->disc_trailer_mask >> m) & 1;
+  for (int j = 0; j < 2; ++j) {
+    if (!on_trailer) {
+      dm->pos[j] = x[j] + d * e1[j];
+      dm->vel[j] = v * e1[j] + d * th1dot * n1[j];
+      dm->acc0[j] = v * th1dot * n1[j] + d * a1_0 * n1[j] - d * th1dot * th1dot * e1[j];
+      dm->acc_a[j] = e1[j] + d * a1_a * n1[j];
+      dm->acc_w[j] = d * a1_w * n1[j];
+    } else {
+      const double L = P->l2 - d;
+      dm->pos[j] = x[j] - P->lh * e1[j] - L * e2[j];
+      dm->vel[j] = v * e1[j] - P->lh * th1dot * n1[j] - L * th2dot * n2[j];
+      dm->acc0[j] = v * th1dot * n1[j] - P->lh * a1_0 * n1[j] + P->lh * th1dot * th1dot * e1[j] -
+                    L * a2_0 * n2[j] + L * th2dot * th2dot * e2[j];
+      dm->acc_a[j] = e1[j] - P->lh * a1_a * n1[j] - L * a2_a * n2[j];
+      dm->acc_w[j] = -P->lh * a1_w * n1[j] - L * a2_w * n2[j];
+    }
+  }
+}
+
+void orc_disc_position(const orc_params *P, int m, const double x[7], double pos[2]) {
+  disc_motion dm;
+  disc_kinematics(P, m, x, &dm);
+  pos[0] = dm.pos[0];
+  pos[1] = dm.pos[1];
+}
+
+double orc_disc_h(const orc_params *P, const double *obs, int stride, double t, int m,
+                  const double x[7]) {
+  double xd[7];
+  memcpy(xd, x, sizeof(xd));
+  orc_disc_position(P, m, x, xd);
+  return orc_obstacle_h_at(P, obs, stride, t, xd);
+}
+
+/* Row of obstacle `obs` seen from disc m: the super-ellipse of the relative
+   position p_d - c(t), hdot = grad h . (pdot - c_dot)',
+   hddot = grad h . pddot' + (pdot - c_dot)'^T Hess h (pdot - c_dot)',
+   affine in (a, omega). */
+void orc_disc_row(const orc_params *P, const double *obs, int stride, double t, int m,
+                  const double x[7], double A_u[3], double *h, double *b_rest) {
+  const int e = obstacle_exponent(obs);
+  double vx, vy;
+  obstacle_velocity(obs, stride, &vx, &vy);
+  disc_motion dm;
+  disc_kinematics(P, m, x, &dm);
+  const double cx = obs[0] + t * vx, cy = obs[1] + t * vy;
+  const double Ax = obs[2] + P->r_inflate, Ay = obs[3] + P->r_inflate;
+  const double co = cos(obs[4]), so = sin(obs[4]);
+#define DROT_X(wx, wy) (co * (wx) + so * (wy))
+#define DROT_Y(wx, wy) (-so * (wx) + co * (wy))
+  const double xp = DROT_X(dm.pos[0] - cx, dm.pos[1] - cy);
+  const double yp = DROT_Y(dm.pos[0] - cx, dm.pos[1] - cy);
+  const double Axe = ipow(Ax, e), Aye = ipow(Ay, e);
+  const double hx = e * ipow(xp, e - 1) / Axe, hy = e * ipow(yp, e - 1) / Aye;
+  const double hxx = e * (e - 1) * ipow(xp, e - 2) / Axe, hyy = e * (e - 1) * ipow(yp, e - 2) / Aye;
+  const double wx = DROT_X(dm.vel[0] - vx, dm.vel[1] - vy), wy = DROT_Y(dm.vel[0] - vx, dm.vel[1] - vy);
+  const double c0x = DROT_X(dm.acc0[0], dm.acc0[1]), c0y = DROT_Y(dm.acc0[0], dm.acc0[1]);
+  const double cax = DROT_X(dm.acc_a[0], dm.acc_a[1]), cay = DROT_Y(dm.acc_a[0], dm.acc_a[1]);
+  const double cwx = DROT_X(dm.acc_w[0], dm.acc_w[1]), cwy = DROT_Y(dm.acc_w[0], dm.acc_w[1]);
+#undef DROT_X
+#undef DROT_Y
+  const double hdot = hx * wx + hy * wy;
+  const double hddot_0 = hx * c0x + hy * c0y + hxx * wx * wx + hyy * wy * wy;
+  A_u[0] = 0.5 * P->Ts * P->Ts * (hx * cax + hy * cay);
+  A_u[1] = 0.5 * P->Ts * P->Ts * (hx * cwx + hy * cwy);
+  A_u[2] = 0.0;
+  *h = ipow(xp / Ax, e) + ipow(yp / Ay, e) - 1.0;
+  *b_rest = -P->Ts * hdot - 0.5 * P->Ts * P->Ts * hddot_0;
+}
+
 /* Standard MPPI with a collision cost (the comparison method of Sec. V):
    each obstacle the state penetrates adds q_coll times its depth -h_o (a
    hinge, zero outside). */
 double orc_collision_cost(const orc_params *P, const double *obs, int stride, int n_obs, double t,
                           const double x[7]) {
   double c = 0.0;
-  for (int o = 0; o < n_obs; ++o) {
-    const double h = orc_obstacle_h_at(P, obs + (size_t)stride * (size_t)o, stride, t, x);
-    if (h < 0.0) c += -h;
-  }
+  for (int o = 0; o < n_obs; ++o)
+    for (int m = 0; m < P->n_discs; ++m) {
+      const double h = orc_disc_h(P, obs + (size_t)stride * (size_t)o, stride, t, m, x);
+      if (h < 0.0) c += -h;
+    }
   return P->q_coll * c;
 }
 
@@ -550,13 +657,14 @@ int orc_rollout_sample(const orc_params *P, const double x0[7], const double *U_
                        uint64_t seed, uint64_t counter, uint32_t s, double *states, double *u_out,
                        double *alpha_out, double *z_des_out, double *z_star_out, double *J_out) {
   const int H = P->H;
-  const int Nc = 1 + n_obs;
+  const int nd = P->n_discs;
+  const int Nc = 1 + n_obs * nd;
   const int d = 3 + Nc;
   const int proj = !(P->flags & ORC_PROJ_NONE);
   const int stride = (P->flags & ORC_OBS8) ? 8 : 6;
   for (int o = 0; o < n_obs; ++o)
     if (obstacle_exponent(obs + (size_t)stride * (size_t)o) < 0) return ORC_EINVAL;
-  if (n_pts < 2 || !(ds > 0.0)) return ORC_EINVAL;
+  if (n_pts < 2 || !(ds > 0.0) || nd < 1 || nd > 8) return ORC_EINVAL;
 
   double *n = (double *)malloc(sizeof(double) * (size_t)d);
   double *alpha = (double *)malloc(sizeof(double) * (size_t)Nc);
@@ -602,8 +710,8 @@ int orc_rollout_sample(const orc_params *P, const double x0[7], const double *U_
         if (i == 0)
           orc_hitch_row(P, x, Au, &h, &b_rest);
         else
-          orc_obstacle_row_at(P, obs + (size_t)stride * (size_t)(i - 1), stride, tau * P->Ts, x,
-                              Au, &h, &b_rest);
+          orc_disc_row(P, obs + (size_t)stride * (size_t)((i - 1) / nd), stride, tau * P->Ts,
+                       (i - 1) % nd, x, Au, &h, &b_rest);
         hrow[i] = h;
         const double hmag = fabs(h) > P->h_floor ? fabs(h) : P->h_floor;
         const double h_tilde = (h >= 0.0) ? hmag : -hmag;
@@ -628,7 +736,7 @@ int orc_rollout_sample(const orc_params *P, const double x0[7], const double *U_
     /* buffer cost of the obstacle rows just built: their h at this state
        and the rates alpha_tau they were built with */
     if (proj && (P->flags & ORC_ALPHA_BUFFER))
-      J += orc_alpha_buffer_cost(P, n_obs, hrow + 1, alpha + 1);
+      J += orc_alpha_buffer_cost(P, n_obs * nd, hrow + 1, alpha + 1);
 
     /* 4. applied input (clipped) and barrier-rate update */
     for (int j = 0; j < 3; ++j) u[j] = clip(zs[j], P->z_lo[j], P->z_hi[j]);

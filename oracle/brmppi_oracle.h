@@ -54,6 +54,10 @@ typedef struct {
   double q_coll;                      /* collision-cost weight (ORC_COLLISION_COST) */
   double alpha_stab, q_stab[2];       /* hitch stabilizer: CBF rate, Q_h on (a, omega) */
   double q_abuf, h_buf;               /* buffer cost weight and zone width (ORC_ALPHA_BUFFER) */
+  int32_t n_discs;                    /* footprint discs (>= 1) */
+  int32_t disc_trailer_mask;          /* bit m: disc m sits on the trailer */
+  double disc_off[8];                 /* disc m: offset along its body's heading from the
+                                         tractor rear axle / the trailer axle */
 } orc_params;
 
 /* Philox4x32 with 10 rounds (Salmon, Moraes, Dror, Shaw, SC'11). */
@@ -84,7 +88,23 @@ double orc_obstacle_h_at(const orc_params *P, const double *obs, int stride, dou
 void orc_obstacle_row_at(const orc_params *P, const double *obs, int stride, double t,
                          const double x[7], double A_u[3], double *h, double *b_rest);
 
-/* MPPI + collision cost baseline: q_coll * sum_o max(0, -h_o(x, t)). */
+/* Footprint discs (Sec. IV-C: the body covered by discs of radius r, the
+   obstacles inflated by r).  Disc m of the tractor sits at p + d e1, of the
+   trailer at p - lh e1 - (l2 - d) e2, with e1, e2 the unit headings and d =
+   disc_off[m].  Constraint 1 + o * n_discs + m is obstacle o seen from disc
+   m.  Centre of disc m at state x: */
+void orc_disc_position(const orc_params *P, int m, const double x[7], double pos[2]);
+/* h of obstacle row `obs` (stride 6 or 8) seen from disc m at time t, and
+   its barrier-rate row (second-order expansion along the field with the
+   input held; the steer rate enters through the heading accelerations of
+   offset discs). */
+double orc_disc_h(const orc_params *P, const double *obs, int stride, double t, int m,
+                  const double x[7]);
+void orc_disc_row(const orc_params *P, const double *obs, int stride, double t, int m,
+                  const double x[7], double A_u[3], double *h, double *b_rest);
+
+/* MPPI + collision cost baseline: q_coll * sum_o max(0, -h_o(x, t)) over
+   every obstacle and footprint disc. */
 double orc_collision_cost(const orc_params *P, const double *obs, int stride, int n_obs, double t,
                           const double x[7]);
 

@@ -36,7 +36,13 @@ DEFAULT_PARAMS = dict(
     alpha0=0.5, sigma_alpha=0.1, ua_lo=-0.5, ua_hi=0.5,
     w_u=(1.0, 1.0, 1.0), w_alpha=1.0, rho=0.01, h_floor=1e-6,
     q_coll=100.0, alpha_stab=0.5, q_stab=(1.0, 1.0), q_abuf=10.0, h_buf=0.5,
+    n_discs=1, disc_trailer_mask=0, disc_off=(0.0,) * 8,
 )
+
+#: A tractor-trailer footprint of five discs: three along the tractor (rear
+#: axle, mid, front) and two along the trailer (axle, front).
+FIVE_DISCS = dict(n_discs=5, disc_trailer_mask=0b11000,
+                  disc_off=(0.0, 2.0, 4.0, 0.0, 4.0, 0.0, 0.0, 0.0))
 
 FLAG_PROJ_NONE = 1
 FLAG_COLLISION_COST = 2
@@ -55,7 +61,7 @@ def as_float32(p: dict) -> dict:
     receives), so a second consumer sees identical numbers."""
     out = {}
     for k, v in p.items():
-        if k in ("S", "H", "flags"):
+        if k in ("S", "H", "flags", "n_discs", "disc_trailer_mask"):
             out[k] = int(v)
         elif isinstance(v, (tuple, list, np.ndarray)):
             out[k] = tuple(float(np.float32(x)) for x in v)

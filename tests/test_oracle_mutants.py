@@ -17,6 +17,7 @@ from tests import test_oracle_dynamics as td
 from tests import test_oracle_philox as tp
 from tests import test_oracle_projection as tj
 from tests import test_oracle_solve as ts
+from tests import test_oracle_discs as tdd
 from tests import test_oracle_obstacle_variants as tv
 from tests import test_oracle_stabilizer as tz
 
@@ -37,12 +38,20 @@ MUTANTS = [
     ("ellipse inflation dropped", "const double Ax = obs[2] + P->r_inflate, Ay = obs[3] + P->r_inflate;\n  const double th_o = obs[4];\n  const double xp", "const double Ax = obs[2], Ay = obs[3];\n  const double th_o = obs[4];\n  const double xp"),
     ("moving centre sign", "const double cx = obs[0] + t * vx, cy = obs[1] + t * vy;\n  const double Ax = obs[2] + P->r_inflate, Ay = obs[3] + P->r_inflate;\n  const double th_o = obs[4];\n  const double xp", "const double cx = obs[0] - t * vx, cy = obs[1] + t * vy;\n  const double Ax = obs[2] + P->r_inflate, Ay = obs[3] + P->r_inflate;\n  const double th_o = obs[4];\n  const double xp"),
     ("moving row ignores obstacle velocity", "const double vel_x = ROT_X(v * c1 - vx, v * s1 - vy)", "const double vel_x = ROT_X(v * c1, v * s1 - vy)"),
-    ("moving rows at time zero", "stride, tau * P->Ts, x,", "stride, 0.0, x,"),
+    ("moving rows at time zero", "stride, tau * P->Ts,\n                       (i - 1) % nd", "stride, 0.0,\n                       (i - 1) % nd"),
     ("collision penalty sign", "if (h < 0.0) c += -h;", "if (h < 0.0) c += h;"),
     ("collision cost at the step's start time", "(tau + 1) * P->Ts, x);", "tau * P->Ts, x);"),
     ("buffer ramp reversed", "double w = 1.0 - h[i] / P->h_buf;", "double w = h[i] / P->h_buf;"),
-    ("buffer charged with updated rates", "    if (proj && (P->flags & ORC_ALPHA_BUFFER))\n      J += orc_alpha_buffer_cost(P, n_obs, hrow + 1, alpha + 1);\n\n    /* 4. applied input (clipped) and barrier-rate update */\n    for (int j = 0; j < 3; ++j) u[j] = clip(zs[j], P->z_lo[j], P->z_hi[j]);\n    if (proj)\n      for (int i = 0; i < Nc; ++i) alpha[i] += zs[3 + i];\n", "    for (int j = 0; j < 3; ++j) u[j] = clip(zs[j], P->z_lo[j], P->z_hi[j]);\n    if (proj)\n      for (int i = 0; i < Nc; ++i) alpha[i] += zs[3 + i];\n    if (proj && (P->flags & ORC_ALPHA_BUFFER))\n      J += orc_alpha_buffer_cost(P, n_obs, hrow + 1, alpha + 1);\n"),
+    ("buffer charged with updated rates", "    if (proj && (P->flags & ORC_ALPHA_BUFFER))\n      J += orc_alpha_buffer_cost(P, n_obs * nd, hrow + 1, alpha + 1);\n\n    /* 4. applied input (clipped) and barrier-rate update */\n    for (int j = 0; j < 3; ++j) u[j] = clip(zs[j], P->z_lo[j], P->z_hi[j]);\n    if (proj)\n      for (int i = 0; i < Nc; ++i) alpha[i] += zs[3 + i];\n", "    for (int j = 0; j < 3; ++j) u[j] = clip(zs[j], P->z_lo[j], P->z_hi[j]);\n    if (proj)\n      for (int i = 0; i < Nc; ++i) alpha[i] += zs[3 + i];\n    if (proj && (P->flags & ORC_ALPHA_BUFFER))\n      J += orc_alpha_buffer_cost(P, n_obs * nd, hrow + 1, alpha + 1);\n"),
     ("buffer charges negative rates", "const double ap = alpha[i] > 0.0 ? alpha[i] : 0.0;", "const double ap = alpha[i];"),
+    ("disc rotation sign", "#define DROT_Y(wx, wy) (-so * (wx) + co * (wy))", "#define DROT_Y(wx, wy) (so * (wx) + co * (wy))"),
+    ("trailer disc lever sign", "const double L = P->l2 - d;", "const double L = P->l2 + d;"),
+    ("trailer steer coupling dropped", "a2_w = -v / P->l2 * k * cos(phi) * sec2;", "a2_w = 0.0;"),
+    ("tractor disc centripetal dropped", " - d * th1dot * th1dot * e1[j];", ";"),
+    ("trailer disc centripetal dropped", " + L * th2dot * th2dot * e2[j];", ";"),
+    ("tractor disc steer term dropped", "a1_w = v * sec2 / P->l1;", "a1_w = 0.0;"),
+    ("every row seen from disc 0", "(i - 1) % nd, x, Au, &h, &b_rest);", "0, x, Au, &h, &b_rest);"),
+    ("collision cost skips discs", "for (int m = 0; m < P->n_discs; ++m) {", "for (int m = 0; m < 1; ++m) {"),
     ("stabilizer CBF sign", "const double rhs = -P->alpha_stab * h - c0;", "const double rhs = P->alpha_stab * h - c0;"),
     ("stabilizer ignores Q_h", "(out)[j] = clip(u_ref[j] + (mu) * g[j] / P->q_stab[j], P->z_lo[j], P->z_hi[j]);", "(out)[j] = clip(u_ref[j] + (mu) * g[j], P->z_lo[j], P->z_hi[j]);"),
     ("stabilizer infeasible corner swapped", "u[j] = g[j] > 0.0 ? P->z_hi[j] : (g[j] < 0.0 ? P->z_lo[j]", "u[j] = g[j] > 0.0 ? P->z_lo[j] : (g[j] < 0.0 ? P->z_hi[j]"),
@@ -127,6 +136,15 @@ def _battery():
         ("coll-wiring", tv.test_collision_cost_enters_after_each_step),
         ("buffer-values", tv.test_alpha_buffer_cost_values),
         ("buffer-wiring", tv.test_alpha_buffer_cost_enters_with_updated_rates),
+        ("disc-slip", lambda: tdd.test_axles_do_not_slip((0.0, 0.0, 0.3, 0.1, 1.2, 0.2, 0.0))),
+        ("disc-hitch-point", tdd.test_hitch_point_seen_from_both_bodies),
+        ("disc-taylor-tractor", lambda: tdd.test_disc_row_is_second_order_taylor(2, tdd.OBS[1], tb.STATES[0])),
+        ("disc-taylor-trailer", lambda: tdd.test_disc_row_is_second_order_taylor(3, tdd.OBS[0], tdd.FAST_FOLD)),
+        ("disc-taylor-trailer-front", lambda: tdd.test_disc_row_is_second_order_taylor(4, tdd.OBS[1], tb.STATES[0])),
+        ("disc-point", tdd.test_single_rear_axle_disc_is_the_point_row),
+        ("disc-steer", tdd.test_steer_rate_enters_offset_discs_only),
+        ("disc-rollout", tdd.test_rollout_rows_cover_every_obstacle_and_disc),
+        ("disc-collision", tdd.test_collision_cost_counts_every_disc),
         ("stab-admissible", tz.test_admissible_reference_is_unchanged),
         ("stab-closed-form", lambda: tz.test_closed_form_without_active_bounds(0)),
         ("stab-brute", lambda: tz.test_brute_force_grid(0)),
