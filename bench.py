@@ -401,6 +401,15 @@ def measure_variants(dev, reps: int = 20):
                                    "at 1-1.5 m/s (8-float obstacle rows)",
                        "ms_per_solve": ms, "rollout_steps_per_s": S * H / (ms * 1e-3),
                        "launch": solver.launch(8)}
+    solver.close()
+    # the same scene seen from a five-disc tractor-trailer footprint (40 rows)
+    solver = pkg.Solver(dict(c["params"], **sc.FIVE_DISCS), max_obstacles=16, max_path_pts=1024)
+    solver.autotune(inst["x0"], inst["U_nom"], inst["obs"], inst["path"], c["ds"], reps=2, stream=stream)
+    ms = _time_solve(solver, inst, stream, flush, reps)
+    out["crossing_five_discs"] = {"workload": "the crossing scene, footprint of 3 tractor + 2 trailer discs "
+                                              "(8 obstacles x 5 discs = 40 barrier rows)",
+                                  "ms_per_solve": ms, "rollout_steps_per_s": S * H / (ms * 1e-3),
+                                  "launch": solver.launch(8)}
     # batched stabilizer
     n = 1 << 20
     rng = np.random.default_rng(3)

@@ -53,7 +53,7 @@
 extern "C" {
 #endif
 
-#define BRMPPI_ABI_VERSION 5u
+#define BRMPPI_ABI_VERSION 6u
 
 typedef enum {
   BRMPPI_OK = 0,
@@ -119,6 +119,16 @@ typedef struct brmppi_params {
   float alpha_stab;              /* hitch stabilizer: discrete CBF rate, (0, 1] */
   float q_stab[2];               /* hitch stabilizer: Q_h = diag(q_stab) on (a, omega), > 0 */
   float q_abuf, h_buf;           /* BRMPPI_FLAG_ALPHA_BUFFER weight (>= 0), zone width (> 0) */
+  /* Footprint discs (Sec. IV-C: the body covered by discs whose radius,
+     r_inflate, inflates the obstacles).  Disc m sits on the tractor at
+     p + disc_off[m] e1, or (bit m of disc_trailer_mask) on the trailer at
+     p - lh e1 - (l2 - disc_off[m]) e2, e1 / e2 the unit headings; obstacle o
+     seen from disc m is constraint 1 + o * n_discs + m (so
+     max_obstacles * n_discs <= 124).  Default: one disc at the tractor's
+     rear axle. */
+  int32_t n_discs;               /* 1..8 */
+  int32_t disc_trailer_mask;     /* bits below n_discs */
+  float disc_off[8];             /* [m] */
 } brmppi_params;
 
 typedef struct brmppi_ctx brmppi_ctx; /* opaque: device buffers, stream */

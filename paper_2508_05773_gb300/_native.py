@@ -12,7 +12,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libbrmppi.so")
 
-BRMPPI_ABI_VERSION = 5
+BRMPPI_ABI_VERSION = 6
 BRMPPI_OK = 0
 BRMPPI_EINVAL = -1
 BRMPPI_ENOMEM = -2
@@ -62,6 +62,8 @@ class brmppi_params(ctypes.Structure):
         ("rho", ctypes.c_float), ("h_floor", ctypes.c_float),
         ("q_coll", ctypes.c_float), ("alpha_stab", ctypes.c_float),
         ("q_stab", ctypes.c_float * 2), ("q_abuf", ctypes.c_float), ("h_buf", ctypes.c_float),
+        ("n_discs", ctypes.c_int32), ("disc_trailer_mask", ctypes.c_int32),
+        ("disc_off", ctypes.c_float * 8),
     ]
 
 

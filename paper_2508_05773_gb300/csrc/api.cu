@@ -20,7 +20,7 @@
 using namespace brmppi_host;
 
 // The layouts the Python binding mirrors.
-static_assert(sizeof(brmppi_params) == 4 * 15 + 4 * 41, "brmppi_params layout");
+static_assert(sizeof(brmppi_params) == 4 * 15 + 4 * 41 + 4 * 10, "brmppi_params layout");
 static_assert(sizeof(brmppi_instance) == 8 * 4 + 4 * 5 + 4 + 8 * 2 + 8 * 7, "brmppi_instance layout");
 
 namespace brmppi_host {
@@ -48,7 +48,9 @@ brmppi_status cuda_fail(brmppi_ctx* c, cudaError_t e, const char* what) {
   return fail(c, e == cudaErrorMemoryAllocation ? BRMPPI_ENOMEM : BRMPPI_ECUDA, m);
 }
 
-int philox_blocks(int n_obs) { return (4 + n_obs + 3) / 4; }  // d = 3 + (1 + n_obs)
+int philox_blocks(int n_rows) { return (4 + n_rows + 3) / 4; }  // d = 3 + (1 + n_rows), rows = obstacles x discs
+
+int ext_team_width(int P) { return P <= 4 ? 2 : (P <= 8 ? 4 : (P <= 16 ? 8 : 16)); }
 
 namespace {
 
@@ -106,6 +108,11 @@ std::string check_params(const brmppi_params* p) {
     return "q_stab must be positive and finite";
   if (!(p->q_abuf >= 0.f) || !std::isfinite(p->q_abuf)) return "q_abuf must be >= 0 and finite";
   if (!(p->h_buf > 0.f) || !std::isfinite(p->h_buf)) return "h_buf must be positive and finite";
+  if (p->n_discs < 1 || p->n_discs > 8) return "n_discs must be in [1, 8]";
+  if (p->disc_trailer_mask & ~((1 << p->n_discs) - 1)) return "disc_trailer_mask has bits at or above n_discs";
+  for (int m = 0; m < 8; ++m)
+    if (!std::isfinite(p->disc_off[m])) return "disc_off must be finite";
+  if (p->max_obstacles * p->n_discs > kMaxObstacles) return "max_obstacles * n_discs must be <= 124";
   return "";
 }
 
@@ -167,16 +174,25 @@ brmppi::KConst make_kconst(const brmppi_params& q) {
   k.alpha_stab = q.alpha_stab;
   k.inv_qs0 = 1.0f / q.q_stab[0];
   k.inv_qs1 = 1.0f / q.q_stab[1];
+  k.nd = q.n_discs;
+  k.inv_nd = 1.0f / static_cast<float>(q.n_discs);
+  k.discs = (q.n_discs != 1 || q.disc_trailer_mask != 0 || q.disc_off[0] != 0.f) ? 1 : 0;
+  for (int m = 0; m < 8; ++m) {
+    // lever arms along e1 and e2 (tractor: d, 0; trailer: -lh, -(l2 - d))
+    const bool tr = (q.disc_trailer_mask >> m) & 1;
+    k.disc_e1[m] = (m < q.n_discs) ? (tr ? -q.lh : q.disc_off[m]) : 0.f;
+    k.disc_e2[m] = (m < q.n_discs && tr) ? -(q.l2 - q.disc_off[m]) : 0.f;
+  }
   return k;
 }
 
-brmppi::SmemCaps make_caps(int n_obs, int n_pts, int H, int tps) {
+brmppi::SmemCaps make_caps(int n_obs, int n_rows, int n_pts, int H, int tps) {
   brmppi::SmemCaps c{};
   c.obs = 8 * n_obs;
   c.path = brmppi::SmemCaps::pad4(3 * n_pts);
   c.unom = brmppi::SmemCaps::pad4(3 * H);
   c.ustar = brmppi::SmemCaps::pad4(3 * H + 1);
-  c.noise_per_team = tps > 1 ? 8 * philox_blocks(n_obs) : 0;
+  c.noise_per_team = tps > 1 ? 8 * philox_blocks(n_rows) : 0;
   return c;
 }
 
@@ -198,7 +214,7 @@ int part_stride_for(int H) { return static_cast<int>(align_up(3 + 3 * static_cas
 // SM, else 64.  Narrower blocks (then wider teams) while the shared-memory
 // tables do not fit.
 bool heuristic_plain(const brmppi_ctx* c, int n_obs, int n_pts, Shape* out) {
-  const int P = philox_blocks(n_obs);
+  const int P = philox_blocks(rows_of(c->prm, n_obs));
   const bool fixed_tps = c->prm.threads_per_sample != 0;
   int tps = c->prm.threads_per_sample;
   if (!fixed_tps) {
@@ -215,7 +231,7 @@ bool heuristic_plain(const brmppi_ctx* c, int n_obs, int n_pts, Shape* out) {
     if ((c->prm.S + spb - 1) / spb < 2 * c->num_sms) threads = 64;
   }
   if (threads < tps) return false;
-  while (smem_bytes(make_caps(n_obs, n_pts, c->prm.H, tps), threads / tps) > c->smem_limit) {
+  while (smem_bytes(make_caps(n_obs, rows_of(c->prm, n_obs), n_pts, c->prm.H, tps), threads / tps) > c->smem_limit) {
     if (!fixed_threads && threads > kMinThreads) {
       threads -= 32;
     } else if (!fixed_tps && tps < 32) {
@@ -235,7 +251,7 @@ bool plain_shape(const brmppi_ctx* c, int n_obs, int n_pts, Shape* out) {
   if (c->prm.threads_per_sample == 0 && c->prm.block_threads == 0) {
     auto it = c->tuned.find(n_obs);
     if (it != c->tuned.end()) {
-      const brmppi::SmemCaps caps = make_caps(n_obs, n_pts, c->prm.H, it->second.tps);
+      const brmppi::SmemCaps caps = make_caps(n_obs, rows_of(c->prm, n_obs), n_pts, c->prm.H, it->second.tps);
       if (smem_bytes(caps, it->second.threads / it->second.tps) <= c->smem_limit) {
         *out = it->second;
         return true;
@@ -248,7 +264,7 @@ bool plain_shape(const brmppi_ctx* c, int n_obs, int n_pts, Shape* out) {
 brmppi::Inst make_inst(const double* x0, const float* U_nom, const float* obs, int n_obs, const float* path,
                        int n_pts, float ds, int S, int H, uint64_t seed, uint64_t counter, float* U_out,
                        float* traj_out, float* J_out, float* U_next, int32_t* status, float* part,
-                       unsigned int* sync, int spb) {
+                       unsigned int* sync, int spb, int n_discs) {
   brmppi::Inst in{};
   in.x0 = x0;
   in.U_nom = U_nom;
@@ -272,7 +288,7 @@ brmppi::Inst make_inst(const double* x0, const float* U_nom, const float* obs, i
   in.key0 = static_cast<uint32_t>(seed);
   in.key1 = static_cast<uint32_t>(seed >> 32);
   in.ctr = static_cast<uint32_t>(counter);
-  in.P = philox_blocks(n_obs);
+  in.P = philox_blocks(n_obs * n_discs);
   return in;
 }
 
@@ -291,10 +307,10 @@ brmppi_status enqueue_plain_sized(brmppi_ctx* c, const Shape& sh, int S, int H, 
   const int spb = sh.threads / sh.tps;
   brmppi::LaunchDesc L{};
   L.single = make_inst(x0, U_nom, obs, n_obs, path, n_pts, ds, S, H, seed, counter, U_out, traj_out, J_out,
-                       U_next, status, c->d_part, c->d_sync, spb);
+                       U_next, status, c->d_part, c->d_sync, spb, c->prm.n_discs);
   L.single.states_out = states_out;
   L.single.u_safe = u_safe;
-  L.caps = make_caps(n_obs, n_pts, H, sh.tps);
+  L.caps = make_caps(n_obs, rows_of(c->prm, n_obs), n_pts, H, sh.tps);
   L.uh = c->d_uh;
   L.uh_stride = 3 * H * spb;
   const size_t smem = smem_bytes(L.caps, spb);
@@ -371,8 +387,11 @@ bool batch_shape_default(const brmppi_ctx* c, int max_P, Shape* out) {
   if (s.tps == 0 && s.threads == 0 && c->batch_tuned) {
     s = c->batch_shape;
   } else {
-    if (s.tps == 0) s.tps = 1;
-    if (s.threads == 0) s.threads = 128;
+    // the optional terms' rows carry a steer-rate column: teams wide enough
+    // for at most two Philox blocks per lane keep them out of local memory
+    const bool ext = brmppi::needs_ext(make_kconst(c->prm));
+    if (s.tps == 0) s.tps = ext ? ext_team_width(max_P) : 1;
+    if (s.threads == 0) s.threads = std::max(128, kMinBatchSpb * s.tps);
   }
   while (!pick_bpt(s.tps, max_P, &s.bpt)) {
     if (s.tps >= 32) return false;
@@ -418,7 +437,7 @@ brmppi_status plan_batch(brmppi_ctx* c, Lane& L, const brmppi_instance* inst, in
       return fail(c, BRMPPI_EINVAL, "instance " + std::to_string(i) + ": S or H beyond the capacity");
     brmppi_status st = check_sizes(c, q.n_obs, q.n_pts, q.ds);
     if (st != BRMPPI_OK) return fail(c, st, "instance " + std::to_string(i) + ": " + c->err);
-    max_P = std::max(max_P, philox_blocks(q.n_obs));
+    max_P = std::max(max_P, philox_blocks(rows_of(c->prm, q.n_obs)));
     Hmax = std::max(Hmax, static_cast<int>(q.H));
     nobs_max = std::max(nobs_max, static_cast<int>(q.n_obs));
     npts_max = std::max(npts_max, static_cast<int>(q.n_pts));
@@ -426,7 +445,7 @@ brmppi_status plan_batch(brmppi_ctx* c, Lane& L, const brmppi_instance* inst, in
   // The kernel variant follows the context's obstacle capacity, not this
   // batch's content: every batch on a context runs the same instantiation,
   // so a solve gives the same bits alone and in any mix.
-  const int P_cap = std::max(max_P, philox_blocks(c->prm.max_obstacles));
+  const int P_cap = std::max(max_P, philox_blocks(rows_of(c->prm, c->prm.max_obstacles)));
   Shape sh;
   if (forced) {
     sh = *forced;
@@ -435,7 +454,7 @@ brmppi_status plan_batch(brmppi_ctx* c, Lane& L, const brmppi_instance* inst, in
     return fail(c, BRMPPI_EINVAL, "no batch launch shape for these instances");
   }
   const int spb = sh.threads / sh.tps;
-  const brmppi::SmemCaps caps = make_caps(nobs_max, npts_max, Hmax, sh.tps);
+  const brmppi::SmemCaps caps = make_caps(nobs_max, rows_of(c->prm, nobs_max), npts_max, Hmax, sh.tps);
   const size_t smem = smem_bytes(caps, spb);
   if (smem > c->smem_limit) return fail(c, BRMPPI_EINVAL, "batch tables exceed shared memory");
   size_t pool = 0;
@@ -445,7 +464,8 @@ brmppi_status plan_batch(brmppi_ctx* c, Lane& L, const brmppi_instance* inst, in
     const brmppi_instance& q = inst[i];
     const int H = q.H;
     brmppi::Inst in = make_inst(q.x0, q.U_nom, q.obs, q.n_obs, q.path, q.n_pts, q.ds, q.S, H, q.seed, q.counter,
-                                q.U_out, q.traj_out, q.J_out, q.U_next, q.status, nullptr, L.d_bsync + 2 * i, spb);
+                                q.U_out, q.traj_out, q.J_out, q.U_next, q.status, nullptr, L.d_bsync + 2 * i, spb,
+                                c->prm.n_discs);
     in.states_out = q.states_out;
     in.u_safe = q.u_safe_out;
     if (q.u_safe_out) plan->any_u_safe = true;
@@ -542,6 +562,9 @@ void brmppi_default_params(brmppi_params* p) {
   p->q_stab[1] = 1.0f;
   p->q_abuf = 10.0f;
   p->h_buf = 0.5f;
+  p->n_discs = 1;
+  p->disc_trailer_mask = 0;
+  for (int m = 0; m < 8; ++m) p->disc_off[m] = 0.f;
 }
 
 brmppi_status brmppi_create(const brmppi_params* p, int device, brmppi_ctx** out) {
@@ -818,14 +841,14 @@ brmppi_status brmppi_autotune(brmppi_ctx* c, const double* x0, const float* U_no
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  const int P = philox_blocks(n_obs);
+  const int P = philox_blocks(rows_of(c->prm, n_obs));
   const int H = c->prm.H;
   float* dU = c->d_out;
   float* dT = dU + 3 * H;
   Shape best;
   float best_ms = 1e30f;
   for (int tps : {1, 2, 4, 8, 16, 32}) {
-    const brmppi::SmemCaps caps = make_caps(n_obs, n_pts, H, tps);
+    const brmppi::SmemCaps caps = make_caps(n_obs, rows_of(c->prm, n_obs), n_pts, H, tps);
     int bpt;
     if (!pick_bpt(tps, P, &bpt)) continue;
     for (int threads : {64, 128, 256}) {
@@ -873,8 +896,8 @@ brmppi_status brmppi_autotune_batch(brmppi_ctx* c, const brmppi_instance* inst, 
   Lane& L = c->batch;
   if (L.pending && (e = cudaEventSynchronize(L.batch_done)) != cudaSuccess) return cuda_fail(c, e, "sync");
   L.pending = false;
-  int max_P = philox_blocks(c->prm.max_obstacles);
-  for (int i = 0; inst && i < n; ++i) max_P = std::max(max_P, philox_blocks(inst[i].n_obs));
+  int max_P = philox_blocks(rows_of(c->prm, c->prm.max_obstacles));
+  for (int i = 0; inst && i < n; ++i) max_P = std::max(max_P, philox_blocks(rows_of(c->prm, inst[i].n_obs)));
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);

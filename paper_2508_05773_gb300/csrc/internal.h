@@ -19,6 +19,9 @@ constexpr int kMaxThreads = 512;
 constexpr int kMinBatchSpb = 16;  // smallest tile of a batch launch
 constexpr int kMaxResidentThreads = 2048;
 
+// Constraint rows of obstacles: each obstacle seen from every footprint disc.
+inline int rows_of(const brmppi_params& p, int n_obs) { return n_obs * p.n_discs; }
+
 // Floats per obstacle row, and the exponents a row may carry.
 inline int obs_floats(const brmppi_params& p) { return (p.flags & BRMPPI_FLAG_OBS8) ? 8 : 6; }
 inline bool exponent_ok(const brmppi_params& p, float e) {
@@ -101,9 +104,12 @@ namespace brmppi_host {
 size_t align_up(size_t v, size_t a);
 brmppi_status fail(brmppi_ctx* c, brmppi_status st, const std::string& msg);
 brmppi_status cuda_fail(brmppi_ctx* c, cudaError_t e, const char* what);
-int philox_blocks(int n_obs);
+int philox_blocks(int n_rows);  // per step, for n_rows obstacle rows
 bool pick_bpt(int tps, int P, int* bpt);
 int part_stride_for(int H);
+// Team width of batches and serving when the optional terms are on: at most
+// two Philox blocks per lane.
+int ext_team_width(int P);
 brmppi_status check_sizes(brmppi_ctx* c, int32_t n_obs, int32_t n_pts, float ds);
 
 // Allocate / free the buffers of a lane for max_batch instances of at most

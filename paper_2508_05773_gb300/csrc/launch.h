@@ -11,7 +11,8 @@ using KernelFn = void (*)(const KConst, const LaunchDesc);
 
 struct Variant {
   int tps, bpt;
-  bool ext;  // carries the optional terms (BRMPPI_FLAG_COLLISION_COST, _OBS8, _ALPHA_BUFFER)
+  bool ext;  // carries the optional terms (BRMPPI_FLAG_COLLISION_COST, _OBS8, _ALPHA_BUFFER,
+             // footprint discs other than the rear-axle point)
   KernelFn fn;
 };
 
@@ -24,7 +25,7 @@ const Variant* variants_narrow_ext(int* n);  // the same, with the optional term
 const Variant* variants_wide_ext(int* n);
 
 // Whether a launch with these constants needs the family with the optional terms.
-inline bool needs_ext(const KConst& k) { return k.coll || k.obs8 || k.abuf; }
+inline bool needs_ext(const KConst& k) { return k.coll || k.obs8 || k.abuf || k.discs; }
 
 // Threads of a launch: `threads` roll out samples; teams wider than one lane
 // add one warp that produces the noise.  At most kMaxBlockThreads (the

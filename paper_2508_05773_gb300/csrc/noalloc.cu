@@ -25,12 +25,12 @@ namespace brmppi_host {
 // defined in api.cu
 std::string check_params(const brmppi_params* p);
 brmppi::KConst make_kconst(const brmppi_params& q);
-brmppi::SmemCaps make_caps(int n_obs, int n_pts, int H, int tps);
+brmppi::SmemCaps make_caps(int n_obs, int n_rows, int n_pts, int H, int tps);
 size_t smem_bytes(const brmppi::SmemCaps& c, int spb);
 brmppi::Inst make_inst(const double* x0, const float* U_nom, const float* obs, int n_obs, const float* path,
                        int n_pts, float ds, int S, int H, uint64_t seed, uint64_t counter, float* U_out,
                        float* traj_out, float* J_out, float* U_next, int32_t* status, float* part,
-                       unsigned int* sync, int spb);
+                       unsigned int* sync, int spb, int n_discs);
 }  // namespace brmppi_host
 
 namespace {
@@ -111,13 +111,14 @@ extern "C" brmppi_status brmppi_solve_device_noalloc(const brmppi_params* p, con
   brmppi_status st = scratch_for_current_device(&scratch);
   if (st != BRMPPI_OK) return st;
   int bpt = 0;
-  if (!pick_bpt(kNaTps, philox_blocks(n_obs), &bpt)) return fail(nullptr, BRMPPI_EINVAL, "no-alloc solve: no variant");
+  const int n_rows = rows_of(*p, n_obs);
+  if (!pick_bpt(kNaTps, philox_blocks(n_rows), &bpt)) return fail(nullptr, BRMPPI_EINVAL, "no-alloc solve: no variant");
   brmppi::LaunchDesc L{};
   unsigned int* sync = reinterpret_cast<unsigned int*>(scratch);
   float* part = scratch + kNaSyncFloats;
   L.single = make_inst(x0_dev, U_nom_dev, obs_dev, n_obs, path_dev, n_pts, ds, p->S, p->H, seed, counter, U_out_dev,
-                       traj_out_dev, J_out_dev, U_next_dev, status_dev, part, sync, kNaSpb);
-  L.caps = make_caps(n_obs, n_pts, p->H, kNaTps);
+                       traj_out_dev, J_out_dev, U_next_dev, status_dev, part, sync, kNaSpb, p->n_discs);
+  L.caps = make_caps(n_obs, n_rows, n_pts, p->H, kNaTps);
   L.uh = part + kNaPartFloats;
   L.uh_stride = 3 * p->H * kNaSpb;
   const size_t smem = smem_bytes(L.caps, kNaSpb);

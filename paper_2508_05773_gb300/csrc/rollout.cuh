@@ -69,6 +69,9 @@ struct KConst {
   float h_floor;
   float q_coll, q_abuf, inv_hbuf;
   float alpha_stab, inv_qs0, inv_qs1;  // hitch stabilizer: CBF rate, Q_h^-1
+  int nd, discs;                       // footprint discs; non-default footprint
+  float inv_nd;
+  float disc_e1[8], disc_e2[8];        // disc m at p + disc_e1[m] e1 + disc_e2[m] e2
 };
 
 // One solve of a launch (all pointers device memory).
@@ -101,7 +104,7 @@ struct SmemCaps {
   int noise_per_team;  // teams wider than one lane: staged normals, 2 steps x P blocks x 4
   __host__ __device__ static int pad4(int n) { return (n + 3) & ~3; }
   __host__ __device__ int total(int spb) const {
-    return obs + path + unom + ustar + pad4(3 * spb) + 256 + noise_per_team * spb;
+    return obs + path + unom + ustar + pad4(3 * spb) + 256 + 16 + noise_per_team * spb;
   }
 };
 
@@ -325,6 +328,7 @@ struct Smem {
   float* jl;     // spb
   float* w;      // spb
   float* chunk;  // 256
+  float* disc;   // 16: lever arms (along e1, along e2) of the footprint discs
   float* noise;  // spb x noise_per_team
   int noise_per_team;
   __device__ Smem(float* base, const SmemCaps& c, int spb) {
@@ -336,7 +340,8 @@ struct Smem {
     jl = jh + spb;
     w = jl + spb;
     chunk = jh + SmemCaps::pad4(3 * spb);
-    noise = chunk + 256;
+    disc = chunk + 256;
+    noise = disc + 16;
     noise_per_team = c.noise_per_team;
   }
 };
@@ -373,7 +378,7 @@ __device__ void run_tile(const KConst& k, const Inst& in, int tile, float* uh, c
   const int lt = threadIdx.x % TPS;
   const int s = tile * spb + team;
   const int H = in.H;
-  const int Nc = 1 + in.n_obs;
+  const int n_rows = EXT ? in.n_obs * k.nd : in.n_obs;  // obstacle rows (obstacle x disc)
 
   // --- frame and staging (tables in shared memory, relative coordinates)
   if (threadIdx.x == 0) make_frame(in.x0, in.ds, in.sync + 1, sh.fr);
@@ -405,6 +410,14 @@ __device__ void run_tile(const KConst& k, const Inst& in, int tile, float* uh, c
     d[2] = (r[2] - fr.oth_h) - fr.oth_l;
   }
   for (int j = threadIdx.x; j < 3 * H; j += blockDim.x) S.unom[j] = in.U_nom[j];
+  if constexpr (EXT) {
+#pragma unroll
+    for (int m = 0; m < 8; ++m)
+      if (static_cast<int>(threadIdx.x) == m) {
+        S.disc[2 * m] = k.disc_e1[m];
+        S.disc[2 * m + 1] = k.disc_e2[m];
+      }
+  }
   __syncthreads();
 
   // --- per-sample state (relative frame)
@@ -442,12 +455,17 @@ __device__ void run_tile(const KConst& k, const Inst& in, int tile, float* uh, c
     }
   };
 
-  // barrier of obstacle j at the current state and time t (Eq.
-  // barrier_function; moving centres at c + t v)
-  auto obstacle_h = [&](int j, float t) -> float {
-    const float4 o0 = *reinterpret_cast<const float4*>(S.obs + 8 * j);
-    const float4 o1 = *reinterpret_cast<const float4*>(S.obs + 8 * j + 4);
-    const float dx = (px - o0.x) + pxl, dy = (py - o0.y) + pyl;
+  // barrier of constraint row j (obstacle o seen from footprint disc m) at
+  // the current state and time t (Eq. barrier_function; moving centres at
+  // c + t v); (ce1, se1) and (ce2, se2) the unit headings of the state
+  auto row_h = [&](int j, float t, float ce1, float se1, float ce2, float se2) -> float {
+    const int o = (k.nd == 1) ? j : __float2int_rz((static_cast<float>(j) + 0.5f) * k.inv_nd);
+    const int m = j - o * k.nd;
+    const float4 o0 = *reinterpret_cast<const float4*>(S.obs + 8 * o);
+    const float4 o1 = *reinterpret_cast<const float4*>(S.obs + 8 * o + 4);
+    const float2 lv = *reinterpret_cast<const float2*>(S.disc + 2 * m);
+    const float dx = (px - o0.x) + pxl + lv.x * ce1 + lv.y * ce2;
+    const float dy = (py - o0.y) + pyl + lv.x * se1 + lv.y * se2;
     const float xp = o0.z * dx + o0.w * dy - t * o1.z;
     const float yp = o0.z * dy - o0.w * dx - t * o1.w;
     const bool e4 = o1.x < 0.f;
@@ -457,7 +475,7 @@ __device__ void run_tile(const KConst& k, const Inst& in, int tile, float* uh, c
   };
 
   // stage cost of the current state (time t) reached with input (ua, uw, un)
-  auto stage_cost = [&](float t) {
+  auto stage_cost = [&](float t, float ce1, float se1, float ce2, float se2) {
     const float qf = qf0 + (ps * in.inv_ds + psl * in.inv_ds);
     const float fl = floorf(qf);
     int ii = i0 + static_cast<int>(fl);
@@ -488,7 +506,7 @@ __device__ void run_tile(const KConst& k, const Inst& in, int tile, float* uh, c
       // the comparison method's collision penalty: depth of every
       // obstacle the state is inside (obstacles spread over the team)
       float c = 0.f;
-      for (int j = lt; j < in.n_obs; j += TPS) c += fmaxf(-obstacle_h(j, t), 0.f);
+      for (int j = lt; j < n_rows; j += TPS) c += fmaxf(-row_h(j, t, ce1, se1, ce2, se2), 0.f);
       rc += k.q_coll * team_sum<TPS>(c);
     }
     acc2(Jh, Jl, rc);
@@ -569,7 +587,7 @@ __device__ void run_tile(const KConst& k, const Inst& in, int tile, float* uh, c
     const float th1dot = vv * tn * k.inv_l1;
 
     // cost of the previous step, at this state (independent of the rows)
-    if (tau > 0) stage_cost(static_cast<float>(tau) * k.Ts);
+    if (tau > 0) stage_cost(static_cast<float>(tau) * k.Ts, c1, s1, c1 * cp + s1 * sp, s1 * cp - c1 * sp);
 
     float na, nw, nn;
     if constexpr (TPS == 1) {
@@ -621,12 +639,33 @@ __device__ void run_tile(const KConst& k, const Inst& in, int tile, float* uh, c
       // the relative position at this step's time, relative velocity.
       // `live` = 0 turns a padding slot into a no-op without branching.
       float ca[OBS_SLOTS], cc[OBS_SLOTS];
+      float cw[EXT ? OBS_SLOTS : 1];  // steer-rate column (footprint discs off the rear axle)
 #pragma unroll
       for (int q = 0; q < OBS_SLOTS; ++q) ca[q] = cc[q] = 0.f;
+      if constexpr (EXT) {
+#pragma unroll
+        for (int q = 0; q < OBS_SLOTS; ++q) cw[q] = 0.f;
+      }
       const float tnow = static_cast<float>(tau) * k.Ts;
       float cbuf = 0.f;  // buffer cost of this lane's rows
+      // heading rates and accelerations of the bodies (footprint discs):
+      // th2 = th1 - phi; heading accelerations with the input held,
+      // th1ddot = a1a a + a1w omega, th2ddot = a20 + a2a a + a2w omega
+      float c2 = 0.f, s2 = 0.f, th2dot = 0.f, a1a = 0.f, a1w = 0.f, a20 = 0.f, a2a = 0.f, a2w = 0.f;
+      if (EXT && k.discs) {
+        c2 = c1 * cp + s1 * sp;
+        s2 = s1 * cp - c1 * sp;
+        const float G = sp - k.k_hitch * cp * tn;
+        const float sec2 = 1.f + tn * tn;
+        th2dot = vv * G * k.inv_l2;
+        a1a = tn * k.inv_l1;
+        a1w = vv * sec2 * k.inv_l1;
+        a2a = G * k.inv_l2;
+        a2w = -vv * k.k_hitch * cp * sec2 * k.inv_l2;
+        a20 = vv * k.inv_l2 * (cp + k.k_hitch * tn * sp) * (th1dot - th2dot);
+      }
       auto obstacle_row = [&](int j, float n_alpha, int slot, float live) {
-        float h, Aa, brest;
+        float h, Aa, Aw = 0.f, brest;
         if constexpr (!EXT) {
           const float4 o0 = *reinterpret_cast<const float4*>(S.obs + 8 * j);
           const float2 o1 = *reinterpret_cast<const float2*>(S.obs + 8 * j + 4);
@@ -643,26 +682,44 @@ __device__ void run_tile(const KConst& k, const Inst& in, int tile, float* uh, c
           Aa = k.hTs2 * gda;
           brest = -k.Ts * vv * gda - k.hTs2 * hdd0;
         } else {
-          const float4 o0 = *reinterpret_cast<const float4*>(S.obs + 8 * j);
-          const float4 o1 = *reinterpret_cast<const float4*>(S.obs + 8 * j + 4);
-          const float dx = (px - o0.x) + pxl, dy = (py - o0.y) + pyl;
+          // row j: obstacle o seen from footprint disc m (obstacle-major)
+          const int o = (k.nd == 1) ? j : __float2int_rz((static_cast<float>(j) + 0.5f) * k.inv_nd);
+          const int m = j - o * k.nd;
+          const float4 o0 = *reinterpret_cast<const float4*>(S.obs + 8 * o);
+          const float4 o1 = *reinterpret_cast<const float4*>(S.obs + 8 * o + 4);
+          const float2 lv = *reinterpret_cast<const float2*>(S.disc + 2 * m);  // lever arms on e1, e2
           const float co = o0.z, so = o0.w;
+          // unit headings in the obstacle frame: e1' = (dirx, diry),
+          // n1' = (-diry, dirx), e2' = (d2x, d2y), n2' = (-d2y, d2x)
           const float dirx = co * c1 + so * s1, diry = co * s1 - so * c1;
-          // moving centre at tnow; e = 4 flagged by a negated kx;
-          // X = xp^(e-2) / Ax^e: h = xp^2 X + ..., h_x = e xp X, h_xx = e (e-1) X
-          const float xp = co * dx + so * dy - tnow * o1.z;
-          const float yp = co * dy - so * dx - tnow * o1.w;
+          const float d2x = co * c2 + so * s2, d2y = co * s2 - so * c2;
+          const float dx = (px - o0.x) + pxl, dy = (py - o0.y) + pyl;
+          // disc centre relative to the (moving) obstacle centre at tnow;
+          // e = 4 flagged by a negated kx; X = xp^(e-2) / Ax^e:
+          // h = xp^2 X + ..., h_x = e xp X, h_xx = e (e-1) X
+          const float xp = co * dx + so * dy + lv.x * dirx + lv.y * d2x - tnow * o1.z;
+          const float yp = co * dy - so * dx + lv.x * diry + lv.y * d2y - tnow * o1.w;
           const bool e4 = o1.x < 0.f;
           const float kx = fabsf(o1.x), ky = o1.y;
           const float X = e4 ? xp * xp * kx : kx, Y = e4 ? yp * yp * ky : ky;
           const float ce = e4 ? 4.f : 2.f, cee = e4 ? 12.f : 2.f;
           h = xp * xp * X + yp * yp * Y - 1.f;
           const float hx = ce * xp * X, hy = ce * yp * Y;
-          const float velx = vv * dirx - o1.z, vely = vv * diry - o1.w;  // relative velocity
-          const float gda = hx * dirx + hy * diry;
+          // disc velocity relative to the obstacle
+          const float velx = vv * dirx - lv.x * th1dot * diry - lv.y * th2dot * d2y - o1.z;
+          const float vely = vv * diry + lv.x * th1dot * dirx + lv.y * th2dot * d2x - o1.w;
+          // disc acceleration = acc0 + a acc_a + omega acc_w
+          const float aax = dirx - lv.x * a1a * diry - lv.y * a2a * d2y;
+          const float aay = diry + lv.x * a1a * dirx + lv.y * a2a * d2x;
+          const float awx = -lv.x * a1w * diry - lv.y * a2w * d2y;
+          const float awy = lv.x * a1w * dirx + lv.y * a2w * d2x;
+          const float t1q = th1dot * th1dot, t2q = th2dot * th2dot;
+          const float a0x = -vv * th1dot * diry - lv.x * t1q * dirx - lv.y * (a20 * d2y + t2q * d2x);
+          const float a0y = vv * th1dot * dirx - lv.x * t1q * diry + lv.y * (a20 * d2x - t2q * d2y);
           const float hdot = hx * velx + hy * vely;
-          const float hdd0 = vv * th1dot * (hy * dirx - hx * diry) + cee * (X * velx * velx + Y * vely * vely);
-          Aa = k.hTs2 * gda;
+          const float hdd0 = hx * a0x + hy * a0y + cee * (X * velx * velx + Y * vely * vely);
+          Aa = k.hTs2 * (hx * aax + hy * aay);
+          Aw = k.hTs2 * (hx * awx + hy * awy);
           brest = -k.Ts * hdot - k.hTs2 * hdd0;
         }
         const float hm = fmaxf(fabsf(h), k.h_floor);
@@ -670,13 +727,19 @@ __device__ void run_tile(const KConst& k, const Inst& in, int tile, float* uh, c
         const float zda = clampf(k.sigma_alpha * n_alpha, k.ua_lo, k.ua_hi);
         const float pa = k.w_a * zda + k.pc_a;
         const float b = -alpha[slot] * h + brest;
-        const float r = Aa * q0 + ht * pa * k.inv_m_a - b;
+        const float r = Aa * q0 + Aw * q1 + ht * pa * k.inv_m_a - b;
         const float iht = 1.f / ht;
         const float invD = live * k.m_a * iht * iht;
         Saa += Aa * Aa * invD;
         ga += Aa * r * invD;
         ca[slot] = live * (Aa * iht);
         cc[slot] = live * (pa * k.inv_m_a - r * iht);
+        if constexpr (EXT) {
+          Saw += Aa * Aw * invD;
+          Sww += Aw * Aw * invD;
+          gw += Aw * r * invD;
+          cw[slot] = live * (Aw * iht);
+        }
         if (EXT && k.abuf) {
           // buffer zone: positive rates charged with weight clip(1 - h/h_buf)
           const float wz = clampf(1.f - h * k.inv_hbuf, 0.f, 1.f);
@@ -686,7 +749,7 @@ __device__ void run_tile(const KConst& k, const Inst& in, int tile, float* uh, c
       };
 
       if constexpr (TPS == 1) {
-        // obstacle j uses normal 4 + j: block 1 + j/4, drawn here
+        // row j uses normal 4 + j: block 1 + j/4, drawn here
 #pragma unroll
         for (int b8 = 1; b8 < BPT; ++b8) {
           if (b8 < in.P) {
@@ -697,26 +760,29 @@ __device__ void run_tile(const KConst& k, const Inst& in, int tile, float* uh, c
               const int j = 4 * (b8 - 1) + m;
               ca[j] = 0.f;
               cc[j] = 0.f;
-              if (j < in.n_obs) obstacle_row(j, nb[m], j, 1.f);
+              if constexpr (EXT) cw[j] = 0.f;
+              if (j < n_rows) obstacle_row(j, nb[m], j, 1.f);
             }
           } else {
 #pragma unroll
             for (int m = 0; m < 4; ++m) {
               ca[4 * (b8 - 1) + m] = 0.f;
               cc[4 * (b8 - 1) + m] = 0.f;
+              if constexpr (EXT) cw[4 * (b8 - 1) + m] = 0.f;
             }
           }
         }
       } else {
-        // obstacle j on lane j % TPS; every lane runs the team's slot count
-        const int per_lane = (in.n_obs + TPS - 1) / TPS;
+        // row j on lane j % TPS; every lane runs the team's slot count
+        const int per_lane = (n_rows + TPS - 1) / TPS;
 #pragma unroll
         for (int slot = 0; slot < OBS_SLOTS; ++slot) {
           ca[slot] = 0.f;
           cc[slot] = 0.f;
+          if constexpr (EXT) cw[slot] = 0.f;
           if (slot < per_lane) {
             const int j = lt + TPS * slot;
-            const bool live = j < in.n_obs;
+            const bool live = j < n_rows;
             const int jj = live ? j : 0;
             obstacle_row(jj, cur[4 + jj], slot, live ? 1.f : 0.f);
           }
@@ -736,7 +802,13 @@ __device__ void run_tile(const KConst& k, const Inst& in, int tile, float* uh, c
       zn = pu2 * k.inv_m_u2;
       alpha_h += cc_h + ca_h * ya + cw_h * yw;
 #pragma unroll
-      for (int slot = 0; slot < OBS_SLOTS; ++slot) alpha[slot] += cc[slot] + ca[slot] * ya;
+      for (int slot = 0; slot < OBS_SLOTS; ++slot) {
+        if constexpr (EXT) {
+          alpha[slot] += cc[slot] + ca[slot] * ya + cw[slot] * yw;
+        } else {
+          alpha[slot] += cc[slot] + ca[slot] * ya;
+        }
+      }
     } else {
       za = zd0;
       zw = zd1;
@@ -767,7 +839,19 @@ __device__ void run_tile(const KConst& k, const Inst& in, int tile, float* uh, c
       for (int q = 0; q < 4; ++q) nrm[q] = nxt[q];
     }
   }
-  if (!producer) stage_cost(static_cast<float>(H) * k.Ts);  // cost of the last step
+  if (!producer) {  // cost of the last step
+    float ce1 = 0.f, se1 = 0.f, ce2 = 0.f, se2 = 0.f;
+    if (EXT && k.coll && k.discs) {
+      float sr, cr, sq, cq;
+      sincosf(t1, &sr, &cr);
+      sincosf(t1 - t2, &sq, &cq);
+      ce1 = c0 * cr - s0 * sr;
+      se1 = s0 * cr + c0 * sr;
+      ce2 = ce1 * cq + se1 * sq;
+      se2 = se1 * cq - ce1 * sq;
+    }
+    stage_cost(static_cast<float>(H) * k.Ts, ce1, se1, ce2, se2);
+  }
 
   // --- per-sample cost: normalise the pair
   {

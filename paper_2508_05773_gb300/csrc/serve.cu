@@ -29,6 +29,8 @@
 
 namespace brmppi_host {
 
+brmppi::KConst make_kconst(const brmppi_params& q);  // api.cu
+
 namespace {
 
 double now_s() {
@@ -246,8 +248,14 @@ brmppi_status server_create(brmppi_ctx* c) {
   sv->S = p.S;
   sv->max_obs = p.max_obstacles;
   sv->max_batch = p.serve_max_batch > 0 ? p.serve_max_batch : 64;
-  sv->shape.tps = 1;
-  sv->shape.threads = 128;
+  if (brmppi::needs_ext(make_kconst(p))) {
+    // rows with a steer-rate column: at most two Philox blocks per lane
+    sv->shape.tps = ext_team_width(philox_blocks(rows_of(p, p.max_obstacles)));
+    sv->shape.threads = std::max(128, kMinBatchSpb * sv->shape.tps);
+  } else {
+    sv->shape.tps = 1;
+    sv->shape.threads = 128;
+  }
   const int n_lanes = p.serve_lanes > 0 ? p.serve_lanes : 2;
   sv->in_stride = align_up(64 + sizeof(float) * obs_floats(p) * static_cast<size_t>(p.max_obstacles), 256);
   sv->out_stride = align_up(3 * static_cast<size_t>(p.H) + 7 * static_cast<size_t>(p.H + 1) + 1, 64);

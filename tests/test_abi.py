@@ -51,7 +51,8 @@ def test_params_struct_layout_matches(lib):
     assert p.q_coll == 100.0 and p.alpha_stab == 0.5 and list(p.q_stab) == [1.0, 1.0]
     assert p.q_abuf == 10.0 and p.h_buf == 0.5
     # the library checks the same sizes at compile time
-    assert ctypes.sizeof(pkg.brmppi_params) == 4 * 15 + 4 * 41
+    assert p.n_discs == 1 and p.disc_trailer_mask == 0 and list(p.disc_off) == [0.0] * 8
+    assert ctypes.sizeof(pkg.brmppi_params) == 4 * 15 + 4 * 41 + 4 * 10
     assert ctypes.sizeof(pkg.brmppi_instance) == 8 * 4 + 4 * 5 + 4 + 8 * 2 + 8 * 7
 
 
@@ -62,6 +63,7 @@ def test_params_struct_layout_matches(lib):
     ("max_batch", -1), ("batch_threads_per_sample", 5), ("batch_block_threads", 1000),
     ("max_vehicles", -2), ("serve_lanes", 99), ("serve_max_batch", -1), ("serve_queue", -5),
     ("q_coll", -1.0), ("alpha_stab", 0.0), ("alpha_stab", 1.5), ("q_abuf", -1.0), ("h_buf", 0.0),
+    ("n_discs", 0), ("n_discs", 9), ("disc_trailer_mask", 2),
 ])
 def test_create_rejects_bad_params_without_gpu(lib, field, value):
     import paper_2508_05773_gb300 as pkg

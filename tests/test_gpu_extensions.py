@@ -9,7 +9,7 @@ import pytest
 import oracle
 from paper_2508_05773_gb300 import scenarios as sc
 from tests import test_oracle_stabilizer as tz
-from tests.parity import assert_solve_matches, stab_tolerance
+from tests.parity import assert_solve_matches, buffer_conditioning, stab_tolerance
 
 pytestmark = pytest.mark.gpu
 
@@ -277,5 +277,92 @@ def test_served_moving_obstacles(pkg):
         ref = oracle.solve(p, c["x0"], c["U_nom"], c["obs"], c["path"], c["ds"], c["seed"], 0,
                            want_uhist=True)
         assert_solve_matches(dict(U=U, traj=traj, J=None), ref, p, "served moving", check_J=False)
+    finally:
+        s.close()
+
+
+# ------------------------------------------------------------ footprint discs
+def _discs(c, **kw):
+    out = dict(c)
+    out["params"] = dict(c["params"], **sc.FIVE_DISCS, **kw)
+    return out
+
+
+@pytest.mark.parametrize("tps", [0, 1, 2, 4, 8])
+def test_footprint_discs(pkg, tps):
+    c = _discs(sc.small_random(81, S=300, H=20, n_obs=4), r_inflate=0.3)
+    p, ref = _oracle(c)
+    out = _gpu(pkg, c, tps=tps)
+    assert_solve_matches(out, ref, p, f"discs tps={tps}")
+
+
+@pytest.mark.parametrize("flags", [sc.FLAG_OBS8, sc.FLAG_ALPHA_BUFFER, sc.FLAG_COLLISION_COST])
+def test_discs_with_one_optional_term(pkg, flags):
+    c = _discs(sc.with_moving(sc.small_random(83, S=257, H=18, n_obs=5), 4), flags=flags, q_abuf=3.0,
+               h_buf=1.0)
+    if not flags & sc.FLAG_OBS8:  # rows of 6: parked ellipses
+        c["obs"] = np.ascontiguousarray(
+            np.hstack([c["obs"][:, :5], np.full((len(c["obs"]), 1), 2.0, np.float32)]))
+    p, ref = _oracle(c)
+    out = _gpu(pkg, c)
+    extra = buffer_conditioning(p, c) if flags & sc.FLAG_ALPHA_BUFFER else None
+    assert_solve_matches(out, ref, p, f"discs + flags {flags}", j_extra=extra)
+
+
+def test_discs_with_every_optional_term(pkg):
+    c = _discs(sc.with_moving(sc.small_random(83, S=257, H=18, n_obs=5), 4),
+               flags=sc.FLAG_OBS8 | sc.FLAG_ALPHA_BUFFER | sc.FLAG_COLLISION_COST, q_abuf=3.0, h_buf=1.0)
+    p, ref = _oracle(c)
+    out = _gpu(pkg, c)
+    assert_solve_matches(out, ref, p, "discs + all terms", j_extra=buffer_conditioning(p, c))
+
+
+def test_mppi_collision_cost_with_discs(pkg):
+    c = _discs(_on_path(sc.small_random(85, S=300, H=20, n_obs=3), 3),
+               flags=sc.FLAG_PROJ_NONE | sc.FLAG_COLLISION_COST)
+    p, ref = _oracle(c)
+    out = _gpu(pkg, c)
+    assert_solve_matches(out, ref, p, "collision + discs")
+
+
+def test_batch_and_serving_with_discs(pkg, torch):
+    rng = np.random.default_rng(86)
+    cases = [_discs(sc.small_random(int(rng.integers(1 << 30)), S=int(rng.integers(50, 300)), H=16,
+                                    n_obs=int(rng.integers(0, 6)))) for _ in range(8)]
+    pd = dict(sc.params(S=300, H=16), **sc.FIVE_DISCS)
+    s = pkg.Solver(pd, max_obstacles=6, max_path_pts=512, max_batch=8, max_vehicles=2)
+    try:
+        t = lambda a, dt=torch.float32: torch.as_tensor(np.asarray(a), dtype=dt, device="cuda")
+        insts = [dict(x0=t(c["x0"], torch.float64), U_nom=t(c["U_nom"]),
+                      obs=t(c["obs"]) if len(c["obs"]) else None, path=t(c["path"]), ds=c["ds"],
+                      S=c["params"]["S"], seed=c["seed"], counter=c["counter"],
+                      U_out=torch.zeros((16, 3), device="cuda"),
+                      traj_out=torch.zeros((17, 7), device="cuda"),
+                      J_out=torch.zeros(c["params"]["S"], device="cuda")) for c in cases]
+        s.solve_batch(insts)
+        torch.cuda.synchronize()
+        for k, (c, q) in enumerate(zip(cases, insts)):
+            p, ref = _oracle(c)
+            out = dict(U=q["U_out"].cpu().numpy(), traj=q["traj_out"].cpu().numpy(),
+                       J=q["J_out"].cpu().numpy())
+            assert_solve_matches(out, ref, p, f"disc batch {k}")
+        # serving: one vehicle, one request
+        c = _discs(sc.small_random(87, S=300, H=16, n_obs=4))
+        s.register(0, c["path"], c["ds"], c["U_nom"], c["seed"])
+        st, tk = s.submit(0, c["x0"], c["obs"])
+        assert st == 0
+        import time
+        t0 = time.time()
+        while True:
+            st, U, traj, lat = s.poll(tk, True)
+            if st != pkg.BRMPPI_EAGAIN:
+                break
+            assert time.time() - t0 < 30
+            time.sleep(1e-4)
+        assert st == 0
+        p = sc.as_float32(c["params"])
+        ref = oracle.solve(p, c["x0"], c["U_nom"], c["obs"], c["path"], c["ds"], c["seed"], 0,
+                           want_uhist=True)
+        assert_solve_matches(dict(U=U, traj=traj, J=None), ref, p, "served discs", check_J=False)
     finally:
         s.close()
