@@ -75,6 +75,7 @@ PROJ_NONE = 1
 COLLISION_COST = 2
 OBS8 = 4
 ALPHA_BUFFER = 8
+THIRD_ORDER = 16
 
 
 def obs_stride(p: dict) -> int:
@@ -125,6 +126,8 @@ def _load():
                                                          ctypes.c_double, _DP]),
                 "orc_alpha_buffer_cost": (ctypes.c_double, [P, ctypes.c_int, _DP, _DP]),
                 "orc_hitch_stabilize": (ctypes.c_int, [P, _DP, _DP, _DP, _DP]),
+                "orc_obstacle_row3": (None, [P, _DP, ctypes.c_int, ctypes.c_double, _DP, _DP, _DP,
+                                             _DP]),
                 "orc_disc_position": (None, [P, ctypes.c_int, _DP, _DP]),
                 "orc_disc_h": (ctypes.c_double, [P, _DP, ctypes.c_int, ctypes.c_double,
                                                  ctypes.c_int, _DP]),
@@ -161,7 +164,7 @@ class using_library:
                      "orc_path_lookup", "orc_stage_cost", "orc_softmin", "orc_rollout_sample",
                      "orc_solve", "orc_integrate", "orc_obstacle_h_at", "orc_obstacle_row_at",
                      "orc_collision_cost", "orc_alpha_buffer_cost", "orc_hitch_stabilize",
-                     "orc_disc_position", "orc_disc_h", "orc_disc_row"):
+                     "orc_disc_position", "orc_disc_h", "orc_disc_row", "orc_obstacle_row3"):
             src = getattr(self.saved, name)
             dst = getattr(lib, name)
             dst.restype = src.restype
@@ -316,6 +319,18 @@ def alpha_buffer_cost(p: dict, h, alpha) -> float:
     h = _d(h)
     return lib.orc_alpha_buffer_cost(ctypes.byref(_params(p)), h.size, _ptr(h),
                                      _ptr(_d(alpha, h.size)))
+
+
+def obstacle_row3(p: dict, obs, x, t: float = 0.0):
+    """Third-order row of one obstacle (6 or 8 entries): (A_u[3], h, b_rest)."""
+    lib = _load()
+    o = _d(obs)
+    Au = np.zeros(3)
+    h = ctypes.c_double()
+    br = ctypes.c_double()
+    lib.orc_obstacle_row3(ctypes.byref(_params(p)), _ptr(o), o.size, float(t), _ptr(_d(x, 7)),
+                          _ptr(Au), ctypes.byref(h), ctypes.byref(br))
+    return Au, h.value, br.value
 
 
 def disc_position(p: dict, m: int, x):

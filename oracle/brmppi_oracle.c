@@ -228,6 +228,63 @@ void orc_obstacle_row(const orc_params *P, const double obs[6], const double x[7
   orc_obstacle_row_at(P, obs, 6, 0.0, x, A_u, h, b_rest);
 }
 
+/* Third-order row (the expansion of Eq. barrier_function_approx carried one
+   order further, which brings the steer rate into obstacle rows).  With the
+   input held, for the rear-axle point and w = pdot - c_dot:
+     pddot  = a e1 + v th1dot n1,
+     pdddot = 2 a th1dot n1 + v th1ddot n1 - v th1dot^2 e1,
+     th1ddot = (a t + v (1 + t^2) omega) / l1,
+     hdddot = grad h . pdddot + 3 w^T Hess h pddot + D3 h [w, w, w],
+   D3 h [w, w, w] = h_xxx w_x^3 + h_yyy w_y^3 in the obstacle frame.  All
+   three are affine in (a, omega); the coefficients are read off by
+   evaluating the increment at unit inputs, as for the hitch row. */
+static double point_increment3(const orc_params *P, const double *obs, int stride, double t,
+                               const double x[7], double a, double omega) {
+  const int e = obstacle_exponent(obs);
+  double vx, vy;
+  obstacle_velocity(obs, stride, &vx, &vy);
+  const double cx = obs[0] + t * vx, cy = obs[1] + t * vy;
+  const double Ax = obs[2] + P->r_inflate, Ay = obs[3] + P->r_inflate;
+  const double co = cos(obs[4]), so = sin(obs[4]);
+  const double th1 = x[2], v = x[4], tn = tan(x[5]);
+  const double th1dot = v * tn / P->l1;
+  const double th1ddot = (a * tn + v * (1.0 + tn * tn) * omega) / P->l1;
+  const double e1[2] = {cos(th1), sin(th1)}, n1[2] = {-sin(th1), cos(th1)};
+  double w[2], acc[2], jerk[2];
+  for (int j = 0; j < 2; ++j) {
+    w[j] = v * e1[j] - (j == 0 ? vx : vy);
+    acc[j] = a * e1[j] + v * th1dot * n1[j];
+    jerk[j] = 2.0 * a * th1dot * n1[j] + v * th1ddot * n1[j] - v * th1dot * th1dot * e1[j];
+  }
+  /* into the obstacle frame */
+  const double rx = x[0] - cx, ry = x[1] - cy;
+  const double xp = co * rx + so * ry, yp = -so * rx + co * ry;
+  const double wx = co * w[0] + so * w[1], wy = -so * w[0] + co * w[1];
+  const double ax_ = co * acc[0] + so * acc[1], ay_ = -so * acc[0] + co * acc[1];
+  const double jx = co * jerk[0] + so * jerk[1], jy = -so * jerk[0] + co * jerk[1];
+  const double Axe = ipow(Ax, e), Aye = ipow(Ay, e);
+  const double hx = e * ipow(xp, e - 1) / Axe, hy = e * ipow(yp, e - 1) / Aye;
+  const double hxx = e * (e - 1) * ipow(xp, e - 2) / Axe, hyy = e * (e - 1) * ipow(yp, e - 2) / Aye;
+  const double hxxx = e * (e - 1) * (e - 2) * (e >= 3 ? ipow(xp, e - 3) : 0.0) / Axe;
+  const double hyyy = e * (e - 1) * (e - 2) * (e >= 3 ? ipow(yp, e - 3) : 0.0) / Aye;
+  const double hdot = hx * wx + hy * wy;
+  const double hddot = hx * ax_ + hy * ay_ + hxx * wx * wx + hyy * wy * wy;
+  const double hdddot = hx * jx + hy * jy + 3.0 * (hxx * wx * ax_ + hyy * wy * ay_) +
+                        hxxx * wx * wx * wx + hyyy * wy * wy * wy;
+  const double Ts = P->Ts;
+  return Ts * hdot + 0.5 * Ts * Ts * hddot + Ts * Ts * Ts / 6.0 * hdddot;
+}
+
+void orc_obstacle_row3(const orc_params *P, const double *obs, int stride, double t,
+                       const double x[7], double A_u[3], double *h, double *b_rest) {
+  const double c0 = point_increment3(P, obs, stride, t, x, 0.0, 0.0);
+  A_u[0] = point_increment3(P, obs, stride, t, x, 1.0, 0.0) - c0;
+  A_u[1] = point_increment3(P, obs, stride, t, x, 0.0, 1.0) - c0;
+  A_u[2] = 0.0;
+  *h = orc_obstacle_h_at(P, obs, stride, t, x);
+  *b_rest = -c0;
+}
+
 /* ------------------------------------------------------------------ */
 /* Footprint discs.  Heading accelerations along the field with the input
    held (a, omega constant): with t = tan(delta), phi = th1 - th2,
@@ -665,6 +722,9 @@ int orc_rollout_sample(const orc_params *P, const double x0[7], const double *U_
   for (int o = 0; o < n_obs; ++o)
     if (obstacle_exponent(obs + (size_t)stride * (size_t)o) < 0) return ORC_EINVAL;
   if (n_pts < 2 || !(ds > 0.0) || nd < 1 || nd > 8) return ORC_EINVAL;
+  if ((P->flags & ORC_THIRD_ORDER) &&
+      (nd != 1 || P->disc_trailer_mask != 0 || P->disc_off[0] != 0.0))
+    return ORC_EINVAL; /* offset discs: the third-order term is not affine in the input */
 
   double *n = (double *)malloc(sizeof(double) * (size_t)d);
   double *alpha = (double *)malloc(sizeof(double) * (size_t)Nc);
@@ -709,6 +769,9 @@ int orc_rollout_sample(const orc_params *P, const double x0[7], const double *U_
         double Au[3], h, b_rest;
         if (i == 0)
           orc_hitch_row(P, x, Au, &h, &b_rest);
+        else if (P->flags & ORC_THIRD_ORDER)
+          orc_obstacle_row3(P, obs + (size_t)stride * (size_t)(i - 1), stride, tau * P->Ts, x, Au, &h,
+                            &b_rest);
         else
           orc_disc_row(P, obs + (size_t)stride * (size_t)((i - 1) / nd), stride, tau * P->Ts,
                        (i - 1) % nd, x, Au, &h, &b_rest);

@@ -40,6 +40,7 @@ extern "C" {
 #define ORC_OBS8 4           /* obstacle rows of 8: (cx, cy, mx, my, theta_o, e, vx, vy),
                                 the centre moving at (vx, vy) from t = 0 */
 #define ORC_ALPHA_BUFFER 8   /* barrier-rate buffer cost on the obstacle rows */
+#define ORC_THIRD_ORDER 16   /* obstacle rows to third order (one rear-axle disc only) */
 
 typedef struct {
   int32_t S, H, flags;
@@ -102,6 +103,12 @@ double orc_disc_h(const orc_params *P, const double *obs, int stride, double t, 
                   const double x[7]);
 void orc_disc_row(const orc_params *P, const double *obs, int stride, double t, int m,
                   const double x[7], double A_u[3], double *h, double *b_rest);
+
+/* Third-order barrier-rate row of obstacle `obs` at the rear axle:
+   Ts hdot + Ts^2/2 hddot + Ts^3/6 hdddot along the field with the input held
+   (affine in (a, omega): the steer rate enters through th1ddot). */
+void orc_obstacle_row3(const orc_params *P, const double *obs, int stride, double t,
+                       const double x[7], double A_u[3], double *h, double *b_rest);
 
 /* MPPI + collision cost baseline: q_coll * sum_o max(0, -h_o(x, t)) over
    every obstacle and footprint disc. */

@@ -48,6 +48,7 @@ FLAG_PROJ_NONE = 1
 FLAG_COLLISION_COST = 2
 FLAG_OBS8 = 4
 FLAG_ALPHA_BUFFER = 8
+FLAG_THIRD_ORDER = 16
 
 
 def params(**overrides) -> dict:

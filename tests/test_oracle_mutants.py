@@ -20,6 +20,7 @@ from tests import test_oracle_solve as ts
 from tests import test_oracle_discs as tdd
 from tests import test_oracle_obstacle_variants as tv
 from tests import test_oracle_stabilizer as tz
+from tests import test_oracle_third_order as t3
 
 MUTANTS = [
     ("philox multiplier swapped", "(uint64_t)PHILOX_M0 * (uint64_t)c0", "(uint64_t)PHILOX_M1 * (uint64_t)c0"),
@@ -52,6 +53,12 @@ MUTANTS = [
     ("tractor disc steer term dropped", "a1_w = v * sec2 / P->l1;", "a1_w = 0.0;"),
     ("every row seen from disc 0", "(i - 1) % nd, x, Au, &h, &b_rest);", "0, x, Au, &h, &b_rest);"),
     ("collision cost skips discs", "for (int m = 0; m < P->n_discs; ++m) {", "for (int m = 0; m < 1; ++m) {"),
+    ("third-order weight", "return Ts * hdot + 0.5 * Ts * Ts * hddot + Ts * Ts * Ts / 6.0 * hdddot;", "return Ts * hdot + 0.5 * Ts * Ts * hddot + Ts * Ts * Ts / 2.0 * hdddot;"),
+    ("third-order jerk factor", "jerk[j] = 2.0 * a * th1dot * n1[j]", "jerk[j] = a * th1dot * n1[j]"),
+    ("third-order Hessian-acceleration factor", "3.0 * (hxx * wx * ax_ + hyy * wy * ay_)", "2.0 * (hxx * wx * ax_ + hyy * wy * ay_)"),
+    ("third-order D3 term dropped", "hxxx * wx * wx * wx + hyyy * wy * wy * wy;", "0.0;"),
+    ("third-order steer term dropped", "const double th1ddot = (a * tn + v * (1.0 + tn * tn) * omega) / P->l1;", "const double th1ddot = (a * tn) / P->l1;"),
+    ("rollout ignores the third-order flag", "else if (P->flags & ORC_THIRD_ORDER)", "else if (0)"),
     ("stabilizer CBF sign", "const double rhs = -P->alpha_stab * h - c0;", "const double rhs = P->alpha_stab * h - c0;"),
     ("stabilizer ignores Q_h", "(out)[j] = clip(u_ref[j] + (mu) * g[j] / P->q_stab[j], P->z_lo[j], P->z_hi[j]);", "(out)[j] = clip(u_ref[j] + (mu) * g[j], P->z_lo[j], P->z_hi[j]);"),
     ("stabilizer infeasible corner swapped", "u[j] = g[j] > 0.0 ? P->z_hi[j] : (g[j] < 0.0 ? P->z_lo[j]", "u[j] = g[j] > 0.0 ? P->z_lo[j] : (g[j] < 0.0 ? P->z_hi[j]"),
@@ -145,6 +152,11 @@ def _battery():
         ("disc-steer", tdd.test_steer_rate_enters_offset_discs_only),
         ("disc-rollout", tdd.test_rollout_rows_cover_every_obstacle_and_disc),
         ("disc-collision", tdd.test_collision_cost_counts_every_disc),
+        ("third-taylor-e2", lambda: t3.test_third_order_row_misses_by_ts4(t3.OBS[0], t3.STATES[2])),
+        ("third-taylor-e4-moving", lambda: t3.test_third_order_row_misses_by_ts4(t3.OBS[2], t3.STATES[2])),
+        ("third-extends", lambda: t3.test_third_order_extends_the_second_order_row(t3.OBS[1])),
+        ("third-steer", t3.test_steer_rate_enters_at_third_order),
+        ("third-rollout", t3.test_rollout_uses_third_order_rows),
         ("stab-admissible", tz.test_admissible_reference_is_unchanged),
         ("stab-closed-form", lambda: tz.test_closed_form_without_active_bounds(0)),
         ("stab-brute", lambda: tz.test_brute_force_grid(0)),
