@@ -352,7 +352,8 @@ def measure_variants(dev, reps: int = 20):
     """The comparison of Table I on GB300: standard MPPI, MPPI + collision
     cost and BR-MPPI on the same scene (8 obstacles), at the config-2 size
     (S=4096, H=50) and at the paper's own sampling (S=5000, H=120); plus
-    BR-MPPI with the buffer cost, the crossing scene (parked e = 4
+    BR-MPPI with the buffer cost and with third-order obstacle rows, the
+    crossing scene (parked e = 4
     super-ellipses and moving pedestrians), and the hitch stabilizer (fused
     into a solve, and as a batched kernel over 2^20 states)."""
     import torch
@@ -368,7 +369,8 @@ def measure_variants(dev, reps: int = 20):
                                        "paper's GPU; context, not a target"}}
     methods = (("br_mppi", 0), ("mppi", pkg.BRMPPI_FLAG_PROJ_NONE),
                ("mppi_collision", pkg.BRMPPI_FLAG_PROJ_NONE | pkg.BRMPPI_FLAG_COLLISION_COST),
-               ("br_mppi_buffer", pkg.BRMPPI_FLAG_ALPHA_BUFFER))
+               ("br_mppi_buffer", pkg.BRMPPI_FLAG_ALPHA_BUFFER),
+               ("br_mppi_third_order", pkg.BRMPPI_FLAG_THIRD_ORDER))
     for size, (S, H) in (("config2", (4096, 50)), ("paper_table1", (5000, 120))):
         c = sc.config2(S=S, H=H)
         row = {}

@@ -84,6 +84,11 @@ typedef enum {
    w(h) = clip(1 - h/h_buf, 0, 1): positive rates are charged near an
    obstacle, pushing the samples toward hdot >= 0 there. */
 #define BRMPPI_FLAG_ALPHA_BUFFER 0x8u
+/* Obstacle rows to third order: Ts hdot + Ts^2/2 hddot + Ts^3/6 hdddot with
+   the input held, which brings the steer rate into obstacle rows (through
+   the tractor's yaw acceleration).  Needs the single rear-axle disc (offset
+   discs make the third-order term quadratic in the input). */
+#define BRMPPI_FLAG_THIRD_ORDER 0x10u
 
 /* Every constant of the solve; POD. Fields the paper leaves open take the
    documented readings (alpha init, noise and bounds of u^alpha, W, rho, the

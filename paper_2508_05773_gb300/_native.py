@@ -25,6 +25,7 @@ BRMPPI_FLAG_PROJ_NONE = 0x1
 BRMPPI_FLAG_COLLISION_COST = 0x2
 BRMPPI_FLAG_OBS8 = 0x4
 BRMPPI_FLAG_ALPHA_BUFFER = 0x8
+BRMPPI_FLAG_THIRD_ORDER = 0x10
 
 STATUS_NAMES = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "EAGAIN", -4: "ETIMEDOUT",
                 -5: "ENONFINITE", -6: "ECUDA", -7: "EBUSY"}

@@ -68,7 +68,7 @@ std::string check_params(const brmppi_params* p) {
   if (p->max_obstacles < 0 || p->max_obstacles > kMaxObstacles) return "max_obstacles must be in [0, 124]";
   if (p->max_path_pts < 2 || p->max_path_pts > kMaxPathPts) return "max_path_pts must be in [2, 12000]";
   if (p->flags & ~static_cast<int32_t>(BRMPPI_FLAG_PROJ_NONE | BRMPPI_FLAG_COLLISION_COST | BRMPPI_FLAG_OBS8 |
-                                        BRMPPI_FLAG_ALPHA_BUFFER))
+                                        BRMPPI_FLAG_ALPHA_BUFFER | BRMPPI_FLAG_THIRD_ORDER))
     return "unknown flag";
   if (p->threads_per_sample != 0 && !is_pow2_tps(p->threads_per_sample))
     return "threads_per_sample must be 0, 1, 2, 4, 8, 16 or 32";
@@ -113,6 +113,8 @@ std::string check_params(const brmppi_params* p) {
   for (int m = 0; m < 8; ++m)
     if (!std::isfinite(p->disc_off[m])) return "disc_off must be finite";
   if (p->max_obstacles * p->n_discs > kMaxObstacles) return "max_obstacles * n_discs must be <= 124";
+  if ((p->flags & BRMPPI_FLAG_THIRD_ORDER) && (p->n_discs != 1 || p->disc_trailer_mask != 0 || p->disc_off[0] != 0.f))
+    return "third-order rows need the single rear-axle disc";
   return "";
 }
 
@@ -174,6 +176,8 @@ brmppi::KConst make_kconst(const brmppi_params& q) {
   k.alpha_stab = q.alpha_stab;
   k.inv_qs0 = 1.0f / q.q_stab[0];
   k.inv_qs1 = 1.0f / q.q_stab[1];
+  k.third = (q.flags & BRMPPI_FLAG_THIRD_ORDER) ? 1 : 0;
+  k.Ts3_6 = q.Ts * q.Ts * q.Ts / 6.0f;
   k.nd = q.n_discs;
   k.inv_nd = 1.0f / static_cast<float>(q.n_discs);
   k.discs = (q.n_discs != 1 || q.disc_trailer_mask != 0 || q.disc_off[0] != 0.f) ? 1 : 0;

@@ -25,7 +25,7 @@ const Variant* variants_narrow_ext(int* n);  // the same, with the optional term
 const Variant* variants_wide_ext(int* n);
 
 // Whether a launch with these constants needs the family with the optional terms.
-inline bool needs_ext(const KConst& k) { return k.coll || k.obs8 || k.abuf || k.discs; }
+inline bool needs_ext(const KConst& k) { return k.coll || k.obs8 || k.abuf || k.discs || k.third; }
 
 // Threads of a launch: `threads` roll out samples; teams wider than one lane
 // add one warp that produces the noise.  At most kMaxBlockThreads (the

@@ -70,6 +70,8 @@ struct KConst {
   float q_coll, q_abuf, inv_hbuf;
   float alpha_stab, inv_qs0, inv_qs1;  // hitch stabilizer: CBF rate, Q_h^-1
   int nd, discs;                       // footprint discs; non-default footprint
+  int third;                           // obstacle rows to third order (rear-axle point only)
+  float Ts3_6;                         // Ts^3 / 6
   float inv_nd;
   float disc_e1[8], disc_e2[8];        // disc m at p + disc_e1[m] e1 + disc_e2[m] e2
 };
@@ -352,6 +354,9 @@ struct Shared {
   int item;
   int last;
 };
+
+// grad h . e1' in the obstacle frame.
+__device__ __forceinline__ float gda3(float hx, float hy, float dirx, float diry) { return hx * dirx + hy * diry; }
 
 // Threads of a CTA that roll out samples: all of them with one lane per
 // sample; with wider teams the last warp produces the noise.
@@ -721,6 +726,22 @@ __device__ void run_tile(const KConst& k, const Inst& in, int tile, float* uh, c
           Aa = k.hTs2 * (hx * aax + hy * aay);
           Aw = k.hTs2 * (hx * awx + hy * awy);
           brest = -k.Ts * hdot - k.hTs2 * hdd0;
+          if (k.third) {
+            // Ts^3/6 hdddot at the rear axle (lever arms zero), affine in
+            // (a, omega): pdddot = 2 a th1dot n1 + v th1ddot n1 - v th1dot^2 e1,
+            // hdddot = grad h . pdddot + 3 w^T Hess h pddot + D3 h [w, w, w]
+            const float gn = hy * dirx - hx * diry;  // grad h . n1'
+            const float hxxx = e4 ? 24.f * xp * kx : 0.f, hyyy = e4 ? 24.f * yp * ky : 0.f;
+            const float wHx = cee * X * velx, wHy = cee * Y * vely;  // Hess h w
+            const float ca3 = (2.f * th1dot + vv * tn * k.inv_l1) * gn + 3.f * (wHx * dirx + wHy * diry);
+            const float cw3 = vv * vv * (1.f + tn * tn) * k.inv_l1 * gn;
+            const float c03 = -vv * th1dot * th1dot * gda3(hx, hy, dirx, diry) +
+                              3.f * vv * th1dot * (wHy * dirx - wHx * diry) +
+                              hxxx * velx * velx * velx + hyyy * vely * vely * vely;
+            Aa += k.Ts3_6 * ca3;
+            Aw += k.Ts3_6 * cw3;
+            brest -= k.Ts3_6 * c03;
+          }
         }
         const float hm = fmaxf(fabsf(h), k.h_floor);
         const float ht = h >= 0.f ? hm : -hm;

@@ -366,3 +366,20 @@ def test_batch_and_serving_with_discs(pkg, torch):
         assert_solve_matches(dict(U=U, traj=traj, J=None), ref, p, "served discs", check_J=False)
     finally:
         s.close()
+
+
+# ------------------------------------------------------------ third-order rows
+@pytest.mark.parametrize("tps", [0, 1, 4, 8])
+def test_third_order_rows(pkg, tps):
+    c = sc.small_random(91, S=300, H=20, n_obs=5)
+    p, ref = _oracle(c, flags=sc.FLAG_THIRD_ORDER)
+    out = _gpu(pkg, c, tps=tps, flags=sc.FLAG_THIRD_ORDER)
+    assert_solve_matches(out, ref, p, f"third order tps={tps}")
+
+
+def test_third_order_with_moving_superellipses(pkg):
+    c = sc.with_moving(sc.small_random(93, S=300, H=20, n_obs=6), 5)
+    flags = sc.FLAG_OBS8 | sc.FLAG_THIRD_ORDER
+    p, ref = _oracle(c, flags=flags)
+    out = _gpu(pkg, c, flags=flags)
+    assert_solve_matches(out, ref, p, "third order + moving")
