@@ -324,7 +324,7 @@ brmppi_status enqueue_plain_sized(brmppi_ctx* c, const Shape& sh, int S, int H, 
       static_cast<size_t>(tiles) * static_cast<size_t>(L.uh_stride) > c->uh_floats)
     return fail(c, BRMPPI_EINVAL, "launch shape exceeds the context's scratch");
   const brmppi::KConst k = make_kconst(c->prm);
-  cudaError_t e = brmppi::launch_solve(sh.tps, sh.bpt, tiles, sh.threads, smem, stream, k, L);
+  cudaError_t e = brmppi::launch_solve(sh.tps, sh.bpt, tiles, sh.threads, smem, stream, k, L, L.single.P);
   if (e != cudaSuccess) return cuda_fail(c, e, "kernel launch");
   if (u_safe) {
     // the stabilizer on (x0, U*[0]): one thread, after the solve
@@ -417,7 +417,7 @@ brmppi_status launch_batch(brmppi_ctx* c, Lane& L, const BatchPlan& plan, cudaSt
   D.caps = plan.caps;
   const brmppi::KConst k = make_kconst(c->prm);
   cudaError_t e = brmppi::launch_solve(plan.shape.tps, plan.shape.bpt, plan.grid, plan.shape.threads, plan.smem,
-                                       stream, k, D);
+                                       stream, k, D, plan.P);
   if (e != cudaSuccess) return cuda_fail(c, e, "batch kernel launch");
   if (plan.any_u_safe && (e = brmppi::launch_stabilize_table(k, L.d_inst, plan.n_inst, stream)) != cudaSuccess)
     return cuda_fail(c, e, "stabilizer launch");
@@ -486,13 +486,15 @@ brmppi_status plan_batch(brmppi_ctx* c, Lane& L, const brmppi_instance* inst, in
                      return a.first > b.first;
                    });
   for (size_t j = 0; j < items.size(); ++j) h_work[j] = items[j].second;
-  const int occ = brmppi::variant_occupancy(sh.tps, sh.bpt, sh.threads, smem, brmppi::needs_ext(make_kconst(c->prm)));
+  const int occ =
+      brmppi::variant_occupancy(sh.tps, sh.bpt, sh.threads, smem, brmppi::needs_ext(make_kconst(c->prm)), P_cap);
   if (occ < 1) return fail(c, BRMPPI_EINVAL, "batch launch shape cannot be resident");
   int grid = occ * c->num_sms;
   if (grid > static_cast<int>(items.size())) grid = static_cast<int>(items.size());
   if (static_cast<size_t>(grid) * 3 * Hmax * spb > L.buh_floats)
     return fail(c, BRMPPI_EINVAL, "batch history scratch too small");
   plan->shape = sh;
+  plan->P = P_cap;
   plan->n_inst = n;
   plan->n_work = static_cast<int>(items.size());
   plan->grid = grid;

@@ -56,6 +56,7 @@ struct BatchPlan {
   Shape shape;
   int n_inst = 0, n_work = 0, grid = 0, Hmax = 0;
   bool any_u_safe = false;  // some instance asks for the stabilized input
+  int P = 1;                // Philox blocks per step the launch is shaped for
   brmppi::SmemCaps caps{};
   size_t smem = 0;
 };

@@ -83,22 +83,35 @@ cudaError_t set_smem_limit(size_t bytes) {
   return err;
 }
 
-int block_threads(int tps, int threads) { return threads + (tps > 1 ? 32 : 0); }
+int noise_warps(int tps, int bpt, int threads, int P) {
+  if (tps <= 1 || bpt > 2) return 0;  // the team's lanes draw (or stage) the blocks themselves
+  const int blocks_per_step = P * (threads / tps);
+  int w = (blocks_per_step + 63) / 64;  // at most two Philox blocks per producer lane and step
+  const int room = (kMaxBlockThreads - threads) / 32;
+  w = w > 4 ? 4 : w;
+  w = w > room ? room : w;
+  return w < 1 ? 1 : w;
+}
 
-int variant_occupancy(int tps, int bpt, int threads, size_t smem, bool ext) {
+int block_threads(int tps, int bpt, int threads, int P) { return threads + 32 * noise_warps(tps, bpt, threads, P); }
+
+int variant_occupancy(int tps, int bpt, int threads, size_t smem, bool ext, int P) {
   const Variant* v = find(tps, bpt, ext);
-  if (!v || block_threads(tps, threads) > kMaxBlockThreads) return 0;
+  if (!v || block_threads(tps, bpt, threads, P) > kMaxBlockThreads) return 0;
   int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, v->fn, block_threads(tps, threads), smem) != cudaSuccess)
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, v->fn, block_threads(tps, bpt, threads, P), smem) !=
+      cudaSuccess)
     return 0;
   return n;
 }
 
 cudaError_t launch_solve(int tps, int bpt, int blocks, int threads, size_t smem, cudaStream_t stream,
-                         const KConst& k, const LaunchDesc& L) {
+                         const KConst& k, const LaunchDesc& L, int P) {
   const Variant* v = find(tps, bpt, needs_ext(k));
-  if (!v || block_threads(tps, threads) > kMaxBlockThreads) return cudaErrorInvalidValue;
-  v->fn<<<blocks, block_threads(tps, threads), smem, stream>>>(k, L);
+  if (!v || block_threads(tps, bpt, threads, P) > kMaxBlockThreads) return cudaErrorInvalidValue;
+  LaunchDesc D = L;
+  D.noise_warps = noise_warps(tps, bpt, threads, P);
+  v->fn<<<blocks, block_threads(tps, bpt, threads, P), smem, stream>>>(k, D);
   return cudaGetLastError();
 }
 

@@ -28,10 +28,14 @@ const Variant* variants_wide_ext(int* n);
 inline bool needs_ext(const KConst& k) { return k.coll || k.obs8 || k.abuf || k.discs || k.third; }
 
 // Threads of a launch: `threads` roll out samples; teams wider than one lane
-// add one warp that produces the noise.  At most kMaxBlockThreads (the
-// kernels' launch bound).
+// with at most two Philox blocks per lane add warps that produce the noise,
+// enough for two blocks per producer lane and step where the CTA has room
+// (up to four; P blocks per sample).  Other variants draw on their own
+// lanes (0 noise warps).  At most kMaxBlockThreads (the kernels' launch
+// bound).
 constexpr int kMaxBlockThreads = 512;
-int block_threads(int tps, int threads);
+int noise_warps(int tps, int bpt, int threads, int P);
+int block_threads(int tps, int bpt, int threads, int P);
 
 // Supported (threads per sample, Philox blocks per lane) pairs.
 bool variant_exists(int tps, int bpt);
@@ -40,7 +44,7 @@ bool variant_exists(int tps, int bpt);
 cudaError_t set_smem_limit(size_t bytes);
 
 // CTAs of a variant resident per SM for a launch shape (0 if it cannot run).
-int variant_occupancy(int tps, int bpt, int threads, size_t smem, bool ext = false);
+int variant_occupancy(int tps, int bpt, int threads, size_t smem, bool ext, int P);
 
 // Enqueue the hitch stabilizer for n states (out: n x 4 floats).
 cudaError_t launch_stabilize(const KConst& k, const double* x, const float* u_ref, int n, float* out,
@@ -52,6 +56,6 @@ cudaError_t launch_stabilize_table(const KConst& k, const Inst* d_table, int n, 
 
 // Enqueue one launch of the solve kernel.
 cudaError_t launch_solve(int tps, int bpt, int blocks, int threads, size_t smem, cudaStream_t stream,
-                         const KConst& k, const LaunchDesc& L);
+                         const KConst& k, const LaunchDesc& L, int P);
 
 }  // namespace brmppi

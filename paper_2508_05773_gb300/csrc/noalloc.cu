@@ -125,7 +125,7 @@ extern "C" brmppi_status brmppi_solve_device_noalloc(const brmppi_params* p, con
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   cudaError_t e = cudaMemsetAsync(sync, 0, sizeof(float) * kNaSyncFloats, s);
   if (e != cudaSuccess) return cuda_fail(nullptr, e, "no-alloc solve: clearing counters");
-  e = brmppi::launch_solve(kNaTps, bpt, L.single.tiles, kNaThreads, smem, s, make_kconst(*p), L);
+  e = brmppi::launch_solve(kNaTps, bpt, L.single.tiles, kNaThreads, smem, s, make_kconst(*p), L, L.single.P);
   if (e != cudaSuccess) return cuda_fail(nullptr, e, "no-alloc solve: kernel launch");
   return BRMPPI_OK;
 }

@@ -118,6 +118,7 @@ struct LaunchDesc {
   unsigned int* work_ctr;  // [0] next item, [1] CTAs that ran out of work
   float* uh;            // per-CTA applied-input history: gridDim.x * uh_stride floats
   int uh_stride;        // 3 * H_max * samples per CTA
+  int noise_warps;      // teams wider than one lane: warps that produce the noise
   SmemCaps caps;
 };
 
@@ -359,11 +360,16 @@ struct Shared {
 __device__ __forceinline__ float gda3(float hx, float hy, float dirx, float diry) { return hx * dirx + hy * diry; }
 
 // Threads of a CTA that roll out samples: all of them with one lane per
-// sample; with wider teams the last warp produces the noise.
+// sample; with wider teams the last noise_warps warps produce the noise.
 template <int TPS>
-__device__ __forceinline__ int compute_threads() {
-  return TPS > 1 ? static_cast<int>(blockDim.x) - 32 : static_cast<int>(blockDim.x);
+__device__ __forceinline__ int compute_threads(int noise_warps) {
+  return static_cast<int>(blockDim.x) - 32 * noise_warps;
 }
+
+// Variants whose noise comes from producer warps: wider teams with at most
+// two Philox blocks per lane.
+template <int TPS, int BPT>
+constexpr bool kNoiseWarps = TPS > 1 && BPT <= 2;
 
 // The per-step hand-over between the noise warp and the compute warps
 // (named barrier 1, every thread of the CTA; whole warps take one role).
@@ -372,13 +378,13 @@ __device__ __forceinline__ void step_barrier() { asm volatile("bar.sync 1, %0;" 
 // ----------------------------------------------------------- one sample tile
 template <int TPS, int BPT, bool EXT>
 __device__ void run_tile(const KConst& k, const Inst& in, int tile, float* uh, const Smem& S,
-                         Shared& sh) {
-  // Teams wider than one lane run with one extra warp (the last) that
-  // produces every team's normals a step ahead (warp specialisation: the
+                         Shared& sh, int noise_warps) {
+  // Teams wider than one lane run with extra warps (the last ones) that
+  // produce every team's normals a step ahead (warp specialisation: the
   // noise leaves the compute warps' dependency chain).
-  const int nc = compute_threads<TPS>();
+  const int nc = compute_threads<TPS>(noise_warps);
   const int spb = nc / TPS;
-  const bool producer = TPS > 1 && static_cast<int>(threadIdx.x) >= nc;
+  const bool producer = kNoiseWarps<TPS, BPT> && static_cast<int>(threadIdx.x) >= nc;
   const int team = producer ? 0 : static_cast<int>(threadIdx.x) / TPS;
   const int lt = threadIdx.x % TPS;
   const int s = tile * spb + team;
@@ -544,12 +550,24 @@ __device__ void run_tile(const KConst& k, const Inst& in, int tile, float* uh, c
   // i % TPS, so rows spread evenly over the team.
   float* nz = S.noise + team * S.noise_per_team;  // [2][P][4] (wide teams)
   const int P_drawn = k.proj ? in.P : 1;  // standard MPPI needs the input normals only
-  if constexpr (TPS > 1) {
+  // Variants with more than two blocks per lane (many constraints) stage
+  // them on the team's own lanes instead (blocks b = lt, lt + TPS, ...): a
+  // producer would need more warps than the CTA can hold.
+  constexpr bool lane_staged = TPS > 1 && !kNoiseWarps<TPS, BPT>;
+  auto stage_step = [&](int tau_d, float* buf) {
+    for (int b = lt; b < P_drawn; b += TPS) {
+      float t4[4];
+      draw_block(b, tau_d, t4);
+      *reinterpret_cast<float4*>(buf + 4 * b) = make_float4(t4[0], t4[1], t4[2], t4[3]);
+    }
+  };
+  if constexpr (lane_staged) stage_step(0, nz);
+  if constexpr (kNoiseWarps<TPS, BPT>) {
     if (producer) {
       const int pl = static_cast<int>(threadIdx.x) - nc;
       const int n_blocks = spb * P_drawn;
       auto produce = [&](int tau_d) {
-        for (int i = pl; i < n_blocks; i += 32) {
+        for (int i = pl; i < n_blocks; i += 32 * noise_warps) {
           const int tm = i / P_drawn, b = i - tm * P_drawn;
           const uint4 w = philox4x32_10(make_uint4(static_cast<uint32_t>(b), static_cast<uint32_t>(tau_d),
                                                    static_cast<uint32_t>(tile * spb + tm), in.ctr),
@@ -574,6 +592,10 @@ __device__ void run_tile(const KConst& k, const Inst& in, int tile, float* uh, c
     float* cur = nz;
     if constexpr (TPS == 1) {
       draw_first(tau + 1 < H ? tau + 1 : tau, nxt);  // off the state's critical path
+    } else if constexpr (lane_staged) {
+      __syncwarp();  // this step's normals are staged; last step's reads are done
+      cur = nz + (tau & 1) * 4 * in.P;
+      if (tau + 1 < H) stage_step(tau + 1, nz + ((tau + 1) & 1) * 4 * in.P);
     } else {
       step_barrier();  // this step's normals are staged
       cur = nz + (tau & 1) * 4 * in.P;
@@ -1059,7 +1081,7 @@ template <int TPS, int BPT, bool EXT>
 __global__ void __launch_bounds__(512) solve_kernel(const KConst k, const LaunchDesc L) {
   extern __shared__ float dyn[];
   __shared__ Shared sh;
-  const int spb = compute_threads<TPS>() / TPS;
+  const int spb = compute_threads<TPS>(L.noise_warps) / TPS;
   const Smem S(dyn, L.caps, spb);
   float* uh = L.uh + static_cast<size_t>(blockIdx.x) * L.uh_stride;
 
@@ -1081,7 +1103,7 @@ __global__ void __launch_bounds__(512) solve_kernel(const KConst k, const Launch
     Inst in;
     if (L.work) in = L.inst[inst_id];
     else in = L.single;
-    run_tile<TPS, BPT, EXT>(k, in, tile, uh, S, sh);
+    run_tile<TPS, BPT, EXT>(k, in, tile, uh, S, sh, L.noise_warps);
 
     // the CTA that completes an instance's last tile merges its partials
     __threadfence();
