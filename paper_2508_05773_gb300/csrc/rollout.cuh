@@ -648,7 +648,7 @@ __device__ void run_tile(const KConst& k, const Inst& in, int tile, float* uh, c
         const float pa = k.w_a * zda + k.pc_a;
         const float b = -alpha_h * hr.h - hr.c0;
         const float r = hr.Aa * q0 + hr.Aw * q1 + ht * pa * k.inv_m_a - b;
-        const float iht = 1.f / ht;
+        const float iht = __fdividef(1.f, ht);  // MUFU reciprocal (~1 ulp)
         const float own = (lt == 0) ? k.m_a * iht * iht : 0.f;  // 1/D on lane 0
         Saa = hr.Aa * hr.Aa * own;
         Saw = hr.Aa * hr.Aw * own;
@@ -771,7 +771,7 @@ __device__ void run_tile(const KConst& k, const Inst& in, int tile, float* uh, c
         const float pa = k.w_a * zda + k.pc_a;
         const float b = -alpha[slot] * h + brest;
         const float r = Aa * q0 + Aw * q1 + ht * pa * k.inv_m_a - b;
-        const float iht = 1.f / ht;
+        const float iht = __fdividef(1.f, ht);  // MUFU reciprocal (~1 ulp)
         const float invD = live * k.m_a * iht * iht;
         Saa += Aa * Aa * invD;
         ga += Aa * r * invD;
@@ -837,7 +837,7 @@ __device__ void run_tile(const KConst& k, const Inst& in, int tile, float* uh, c
       Sww = team_sum<TPS>(Sww) + k.m_u1;
       ga = team_sum<TPS>(ga);
       gw = team_sum<TPS>(gw);
-      const float idet = 1.f / (Saa * Sww - Saw * Saw);
+      const float idet = __fdividef(1.f, Saa * Sww - Saw * Saw);  // SPD: det > 0
       const float ya = (Sww * ga - Saw * gw) * idet;
       const float yw = (Saa * gw - Saw * ga) * idet;
       za = q0 - ya;
