@@ -961,6 +961,127 @@ __device__ void run_tile(const KConst& k, const Inst& in, int tile, float* uh, c
 // Run by the CTA that finished the instance's last tile: global minimum
 // pair, rescaled sums in tile order, U*, warm start, status and the optimal
 // trajectory (x0 integrated with U*).
+// Optimal trajectory: x0 integrated with U* in the relative frame (explicit
+// Euler, as the rollouts).  Speed, steer angle and progress are prefix sums
+// of U*, the tractor heading an FMA chain; only the trailer angle is a
+// nonlinear recurrence.  So the CTA computes the per-step terms in parallel
+// around short serial chains (thread 0: headings; warp 1's first lane:
+// positions), in `scratch` (8 (H+1) floats: the instance's tile partials,
+// consumed by then).
+// The elementary functions are the SFU approximations (absolute error
+// ~2^-21 per call, far inside the trajectory tolerance).
+static __device__ void optimal_trajectory(const KConst& k, const Inst& in, const Smem& S, Shared& sh, float* scratch) {
+  const int H = in.H, n = H + 1;
+  const Frame& fr = sh.fr;
+  float* V = scratch;          // speed
+  float* D = scratch + n;      // steer angle
+  float* Q = scratch + 2 * n;  // progress
+  float* T = scratch + 3 * n;  // tan(steer angle)
+  float* A = scratch + 4 * n;  // tractor heading
+  float* B = scratch + 5 * n;  // trailer heading
+  float* X = scratch + 6 * n;  // x
+  float* Y = scratch + 7 * n;  // y
+  const float* ustar = S.ustar;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float qv = fr.v_h + fr.v_l, qd = fr.dl, qp = 0.f;
+    for (int tau = 0; tau <= H; ++tau) {
+      V[tau] = qv;
+      D[tau] = qd;
+      Q[tau] = qp;
+      if (tau < H) {
+        qv += k.Ts * ustar[3 * tau + 0];
+        qd += k.Ts * ustar[3 * tau + 1];
+        qp += k.Ts * ustar[3 * tau + 2];
+      }
+    }
+  }
+  __syncthreads();
+  for (int tau = threadIdx.x; tau < H; tau += blockDim.x) {
+    float ad, bd;
+    __sincosf(D[tau], &ad, &bd);
+    T[tau] = __fdividef(ad, bd);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float q1 = 0.f;
+    for (int tau = 0; tau <= H; ++tau) {
+      A[tau] = q1;
+      if (tau < H) q1 += (k.Ts * V[tau]) * T[tau] * k.inv_l1;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {  // trailer angle
+    float q2 = fr.t2;
+    for (int tau = 0; tau <= H; ++tau) {
+      B[tau] = q2;
+      if (tau < H) {
+        float a2, b2;
+        __sincosf(A[tau] - q2, &a2, &b2);
+        q2 += (k.Ts * V[tau]) * k.inv_l2 * (a2 - k.k_hitch * b2 * T[tau]);
+      }
+    }
+  } else if (threadIdx.x == 32) {  // position
+    const float c0 = fr.c0, s0 = fr.s0;
+    float qx = 0.f, qy = 0.f;
+    for (int tau = 0; tau <= H; ++tau) {
+      X[tau] = qx;
+      Y[tau] = qy;
+      if (tau < H) {
+        float a1, b1;
+        __sincosf(A[tau], &a1, &b1);
+        const float Tv = k.Ts * V[tau];
+        qx += Tv * (c0 * b1 - s0 * a1);
+        qy += Tv * (s0 * b1 + c0 * a1);
+      }
+    }
+  }
+  __syncthreads();
+  float* tr = in.traj_out;
+  for (int tau = threadIdx.x; tau <= H; tau += blockDim.x) {
+    tr[7 * tau + 0] = (fr.ox_h + X[tau]) + fr.ox_l;
+    tr[7 * tau + 1] = (fr.oy_h + Y[tau]) + fr.oy_l;
+    tr[7 * tau + 2] = (fr.oth_h + A[tau]) + fr.oth_l;
+    tr[7 * tau + 3] = (fr.oth_h + B[tau]) + fr.oth_l;
+    tr[7 * tau + 4] = V[tau];
+    tr[7 * tau + 5] = D[tau];
+    tr[7 * tau + 6] = (fr.psi_h + Q[tau]) + fr.psi_l;
+  }
+}
+
+// The same, one thread, no scratch (solves of one or two tiles).
+static __device__ void serial_trajectory(const KConst& k, const Inst& in, const Smem& S, Shared& sh) {
+  const Frame& fr = sh.fr;
+  const float c0 = fr.c0, s0 = fr.s0;
+  const float* ustar = S.ustar;
+  const int H = in.H;
+  float qx = 0.f, qy = 0.f, q1 = 0.f, q2 = fr.t2, qv = fr.v_h + fr.v_l, qd = fr.dl, qp = 0.f;
+  float* tr = in.traj_out;
+  for (int tau = 0; tau <= H; ++tau) {
+    tr[7 * tau + 0] = (fr.ox_h + qx) + fr.ox_l;
+    tr[7 * tau + 1] = (fr.oy_h + qy) + fr.oy_l;
+    tr[7 * tau + 2] = (fr.oth_h + q1) + fr.oth_l;
+    tr[7 * tau + 3] = (fr.oth_h + q2) + fr.oth_l;
+    tr[7 * tau + 4] = qv;
+    tr[7 * tau + 5] = qd;
+    tr[7 * tau + 6] = (fr.psi_h + qp) + fr.psi_l;
+    if (tau == H) break;
+    float a1, b1, a2, b2, ad, bd;
+    __sincosf(q1, &a1, &b1);
+    __sincosf(q1 - q2, &a2, &b2);
+    __sincosf(qd, &ad, &bd);
+    const float tq = __fdividef(ad, bd);
+    const float Tv = k.Ts * qv;
+    qx += Tv * (c0 * b1 - s0 * a1);
+    qy += Tv * (s0 * b1 + c0 * a1);
+    q2 += Tv * k.inv_l2 * (a2 - k.k_hitch * b2 * tq);
+    q1 += Tv * tq * k.inv_l1;
+    qv += k.Ts * ustar[3 * tau + 0];
+    qd += k.Ts * ustar[3 * tau + 1];
+    qp += k.Ts * ustar[3 * tau + 2];
+  }
+}
+
 static __device__ void merge_instance(const KConst& k, const Inst& in, const Smem& S, Shared& sh) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nb = in.tiles;
@@ -997,10 +1118,23 @@ static __device__ void merge_instance(const KConst& k, const Inst& in, const Sme
     __syncthreads();
     const int bend = min(256, nb - b0);
     for (int q = threadIdx.x; q < nrows; q += blockDim.x) {
-      // four independent chains (tiles t mod 4), combined in a fixed order
+      // four independent chains (tiles t mod 4), combined in a fixed order;
+      // sixteen L2 loads in flight per pass
       float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
       const float* col = in.part + static_cast<size_t>(b0) * stride + 3 + q;
       int t = 0;
+      for (; t + 16 <= bend; t += 16) {
+        float v[16];
+#pragma unroll
+        for (int m = 0; m < 16; ++m) v[m] = __ldcg(col + static_cast<size_t>(t + m) * stride);
+#pragma unroll
+        for (int m = 0; m < 16; m += 4) {
+          a0 += S.chunk[t + m + 0] * v[m + 0];
+          a1 += S.chunk[t + m + 1] * v[m + 1];
+          a2 += S.chunk[t + m + 2] * v[m + 2];
+          a3 += S.chunk[t + m + 3] * v[m + 3];
+        }
+      }
       for (; t + 4 <= bend; t += 4) {
         a0 += S.chunk[t + 0] * __ldcg(col + static_cast<size_t>(t + 0) * stride);
         a1 += S.chunk[t + 1] * __ldcg(col + static_cast<size_t>(t + 1) * stride);
@@ -1033,43 +1167,15 @@ static __device__ void merge_instance(const KConst& k, const Inst& in, const Sme
       else if ((err & ERR_NONFINITE_X0) || !ok) st = -5;
       *in.status = st;
     }
-    // optimal trajectory: x0 integrated with U* in the relative frame; the
-    // elementary functions are the SFU approximations (absolute error
-    // ~2^-21 per call, far inside the trajectory tolerance) to keep this
-    // serial tail short
-    if (in.traj_out) {
-      const Frame& fr = sh.fr;
-      const float c0 = fr.c0, s0 = fr.s0;
-      float qx = 0.f, qy = 0.f, q1 = 0.f, q2 = fr.t2, qv = fr.v_h + fr.v_l, qd = fr.dl, qp = 0.f;
-      float* tr = in.traj_out;
-      for (int tau = 0; tau <= H; ++tau) {
-        tr[7 * tau + 0] = (fr.ox_h + qx) + fr.ox_l;
-        tr[7 * tau + 1] = (fr.oy_h + qy) + fr.oy_l;
-        tr[7 * tau + 2] = (fr.oth_h + q1) + fr.oth_l;
-        tr[7 * tau + 3] = (fr.oth_h + q2) + fr.oth_l;
-        tr[7 * tau + 4] = qv;
-        tr[7 * tau + 5] = qd;
-        tr[7 * tau + 6] = (fr.psi_h + qp) + fr.psi_l;
-        if (tau == H) break;
-        float a1, b1, a2, b2, ad, bd;
-        __sincosf(q1, &a1, &b1);
-        __sincosf(q1 - q2, &a2, &b2);
-        __sincosf(qd, &ad, &bd);
-        const float tq = __fdividef(ad, bd);
-        const float cc1 = c0 * b1 - s0 * a1, ss1 = s0 * b1 + c0 * a1;
-        const float Tv = k.Ts * qv;
-        qx += Tv * cc1;
-        qy += Tv * ss1;
-        const float d1 = Tv * tq * k.inv_l1;
-        q2 += Tv * k.inv_l2 * (a2 - k.k_hitch * b2 * tq);
-        q1 += d1;
-        qv += k.Ts * ustar[3 * tau + 0];
-        qd += k.Ts * ustar[3 * tau + 1];
-        qp += k.Ts * ustar[3 * tau + 2];
-      }
-    }
     in.sync[1] = 0u;
     in.sync[0] = 0u;
+  }
+  if (in.traj_out) {
+    if (static_cast<long long>(in.tiles) * in.part_stride >= 8LL * (H + 1)) {
+      optimal_trajectory(k, in, S, sh, in.part);  // the partials are consumed
+    } else if (threadIdx.x == 0) {
+      serial_trajectory(k, in, S, sh);
+    }
   }
   __syncthreads();
 }
