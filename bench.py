@@ -204,18 +204,7 @@ def measure_batched(dev, reps: int = 10):
     import paper_2508_05773_gb300 as pkg
     from paper_2508_05773_gb300 import scenarios as sc
 
-    cases = sc.config3()
-    t = lambda a, dt=torch.float32: torch.tensor(np.asarray(a), dtype=dt, device=dev)
-    insts = []
-    for c in cases:
-        H, S = int(c["params"]["H"]), int(c["params"]["S"])
-        insts.append(dict(x0=t(c["x0"], torch.float64), U_nom=t(c["U_nom"]),
-                          obs=t(c["obs"]) if c["obs"].shape[0] else None, path=t(c["path"]),
-                          ds=c["ds"], S=S, seed=c["seed"], counter=0,
-                          U_out=torch.empty((H, 3), device=dev),
-                          traj_out=torch.empty((H + 1, 7), device=dev),
-                          U_next=torch.empty((H, 3), device=dev),
-                          status=torch.zeros(1, dtype=torch.int32, device=dev)))
+    cases, insts = _config3_instances(dev)
     work = sum(int(c["params"]["S"]) * int(c["params"]["H"]) for c in cases)
     Smax = max(int(c["params"]["S"]) for c in cases)
     Hmax = max(int(c["params"]["H"]) for c in cases)
@@ -440,6 +429,64 @@ def measure_variants(dev, reps: int = 20):
                                  "bytes": nbytes, "hbm_gbs": nbytes / (ms * 1e-3) / 1e9,
                                  "hbm_frac": nbytes / (ms * 1e-3) / 1e9 / hbm}
     return out
+
+
+def _config3_instances(dev):
+    import torch
+    from paper_2508_05773_gb300 import scenarios as sc
+    cases = sc.config3()
+    t = lambda a, dt=torch.float32: torch.tensor(np.asarray(a), dtype=dt, device=dev)
+    insts = []
+    for c in cases:
+        H, S = int(c["params"]["H"]), int(c["params"]["S"])
+        insts.append(dict(x0=t(c["x0"], torch.float64), U_nom=t(c["U_nom"]),
+                          obs=t(c["obs"]) if c["obs"].shape[0] else None, path=t(c["path"]),
+                          ds=c["ds"], S=S, seed=c["seed"], counter=0,
+                          U_out=torch.empty((H, 3), device=dev),
+                          traj_out=torch.empty((H + 1, 7), device=dev),
+                          U_next=torch.empty((H, 3), device=dev),
+                          status=torch.zeros(1, dtype=torch.int32, device=dev)))
+    return cases, insts
+
+
+def run_profile(args):
+    """A few launches of one workload for ncu (no timing): `solve` = the
+    config-2 solve (S=4096, H=50, 8 ellipses), `batch` = the config-3 batch
+    (256 uneven instances, one persistent launch), each with a fixed launch
+    shape (--tps / --threads; defaults: the shapes the autotuners pick on
+    GB300).  Four launches with an L2 flush before each; capture the last."""
+    import torch
+    import paper_2508_05773_gb300 as pkg
+    from paper_2508_05773_gb300 import scenarios as sc
+    dev = torch.device("cuda", 0)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    t = lambda a, dt=torch.float32: torch.tensor(np.asarray(a), dtype=dt, device=dev)
+    if args.profile == "solve":
+        c = sc.config2()
+        H = int(c["params"]["H"])
+        solver = pkg.Solver(c["params"], max_obstacles=16, max_path_pts=1024,
+                            threads_per_sample=args.tps or 4, block_threads=args.threads or 128)
+        x0, U, obs, path = t(c["x0"], torch.float64), t(c["U_nom"]), t(c["obs"]), t(c["path"])
+        Uo, tr = torch.empty((H, 3), device=dev), torch.empty((H + 1, 7), device=dev)
+        for r in range(4):
+            flush.zero_()
+            if solver.solve_device(x0, U, obs, path, c["ds"], c["seed"], r, Uo, tr) != 0:
+                raise RuntimeError(pkg.brmppi_last_error(solver.ctx))
+    else:
+        cases, insts = _config3_instances(dev)
+        Smax = max(int(c["params"]["S"]) for c in cases)
+        Hmax = max(int(c["params"]["H"]) for c in cases)
+        npts = max(c["path"].shape[0] for c in cases)
+        solver = pkg.Solver(dict(cases[0]["params"], S=Smax, H=Hmax), max_obstacles=16, max_path_pts=npts,
+                            max_batch=len(cases), batch_threads_per_sample=args.tps or 1,
+                            batch_block_threads=args.threads or 256)
+        for r in range(4):
+            flush.zero_()
+            solver.solve_batch(insts)
+    torch.cuda.synchronize()
+    solver.close()
+    print(json.dumps({"profile": args.profile, "launches": 4}), flush=True)
+    return 0
 
 
 def measure_serving(rates=(2000, 10000, 50000), duration=2.0, warm=0.5, n_vehicles=512, seed=4):
@@ -730,10 +777,16 @@ def main():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-stress", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--profile", choices=("solve", "batch"), default=None,
+                    help="a few launches of one workload for ncu, no timing")
+    ap.add_argument("--tps", type=int, default=0, help="--profile: threads per sample")
+    ap.add_argument("--threads", type=int, default=0, help="--profile: threads per block")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     world, rank, local = _dist_env()
+    if args.profile:
+        return run_profile(args)
     if args.impl == "reference":
         return run_reference(args, world, rank)
     return run_ours(args, world, rank, local)
