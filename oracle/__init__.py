@@ -76,6 +76,12 @@ COLLISION_COST = 2
 OBS8 = 4
 ALPHA_BUFFER = 8
 THIRD_ORDER = 16
+JERK = 32
+
+
+def state_dim(p: dict) -> int:
+    """Entries of a state under the flags of p (8 for the jerk model)."""
+    return 8 if int(p["flags"]) & JERK else 7
 
 
 def obs_stride(p: dict) -> int:
@@ -128,6 +134,11 @@ def _load():
                 "orc_hitch_stabilize": (ctypes.c_int, [P, _DP, _DP, _DP, _DP]),
                 "orc_obstacle_row3": (None, [P, _DP, ctypes.c_int, ctypes.c_double, _DP, _DP, _DP,
                                              _DP]),
+                "orc_jerk_step": (None, [P, _DP, _DP, _DP]),
+                "orc_jerk_integrate": (None, [P, _DP, _DP, ctypes.c_int, _DP]),
+                "orc_jerk_hitch_row": (None, [P, _DP, _DP, _DP, _DP]),
+                "orc_jerk_obstacle_row": (None, [P, _DP, ctypes.c_int, ctypes.c_double, _DP, _DP,
+                                                 _DP, _DP]),
                 "orc_disc_position": (None, [P, ctypes.c_int, _DP, _DP]),
                 "orc_disc_h": (ctypes.c_double, [P, _DP, ctypes.c_int, ctypes.c_double,
                                                  ctypes.c_int, _DP]),
@@ -164,7 +175,9 @@ class using_library:
                      "orc_path_lookup", "orc_stage_cost", "orc_softmin", "orc_rollout_sample",
                      "orc_solve", "orc_integrate", "orc_obstacle_h_at", "orc_obstacle_row_at",
                      "orc_collision_cost", "orc_alpha_buffer_cost", "orc_hitch_stabilize",
-                     "orc_disc_position", "orc_disc_h", "orc_disc_row", "orc_obstacle_row3"):
+                     "orc_disc_position", "orc_disc_h", "orc_disc_row", "orc_obstacle_row3",
+                     "orc_jerk_step", "orc_jerk_integrate", "orc_jerk_hitch_row",
+                     "orc_jerk_obstacle_row"):
             src = getattr(self.saved, name)
             dst = getattr(lib, name)
             dst.restype = src.restype
@@ -321,6 +334,43 @@ def alpha_buffer_cost(p: dict, h, alpha) -> float:
                                      _ptr(_d(alpha, h.size)))
 
 
+def jerk_step(p: dict, x, u) -> np.ndarray:
+    lib = _load()
+    xn = np.zeros(8)
+    lib.orc_jerk_step(ctypes.byref(_params(p)), _ptr(_d(x, 8)), _ptr(_d(u, 3)), _ptr(xn))
+    return xn
+
+
+def jerk_integrate(p: dict, x0, U) -> np.ndarray:
+    lib = _load()
+    U = _d(U)
+    H = U.size // 3
+    traj = np.zeros((H + 1, 8))
+    lib.orc_jerk_integrate(ctypes.byref(_params(p)), _ptr(_d(x0, 8)), _ptr(U), H, _ptr(traj))
+    return traj
+
+
+def jerk_hitch_row(p: dict, x):
+    lib = _load()
+    Au = np.zeros(3)
+    h = ctypes.c_double()
+    br = ctypes.c_double()
+    lib.orc_jerk_hitch_row(ctypes.byref(_params(p)), _ptr(_d(x, 8)), _ptr(Au), ctypes.byref(h),
+                           ctypes.byref(br))
+    return Au, h.value, br.value
+
+
+def jerk_obstacle_row(p: dict, obs, x, t: float = 0.0):
+    lib = _load()
+    o = _d(obs)
+    Au = np.zeros(3)
+    h = ctypes.c_double()
+    br = ctypes.c_double()
+    lib.orc_jerk_obstacle_row(ctypes.byref(_params(p)), _ptr(o), o.size, float(t), _ptr(_d(x, 8)),
+                              _ptr(Au), ctypes.byref(h), ctypes.byref(br))
+    return Au, h.value, br.value
+
+
 def obstacle_row3(p: dict, obs, x, t: float = 0.0):
     """Third-order row of one obstacle (6 or 8 entries): (A_u[3], h, b_rest)."""
     lib = _load()
@@ -436,11 +486,12 @@ def rollout_sample(p: dict, x0, U_nom, obs, path, ds, seed, counter, s):
     Nc = 1 + n_obs * int(p.get("n_discs", 1))
     d = 3 + Nc
     path = _d(path)
-    out = dict(states=np.zeros((H + 1, 7)), u=np.zeros((H, 3)), alpha=np.zeros((H + 1, Nc)),
+    nx = state_dim(p)
+    out = dict(states=np.zeros((H + 1, nx)), u=np.zeros((H, 3)), alpha=np.zeros((H + 1, Nc)),
                z_des=np.zeros((H, d)), z_star=np.zeros((H, d)))
     J = ctypes.c_double()
     P = _params(p)
-    st = lib.orc_rollout_sample(ctypes.byref(P), _ptr(_d(x0, 7)), _ptr(_d(U_nom, 3 * H)),
+    st = lib.orc_rollout_sample(ctypes.byref(P), _ptr(_d(x0, nx)), _ptr(_d(U_nom, 3 * H)),
                                 _ptr(obs) if n_obs else None, n_obs, _ptr(path), path.size // 3,
                                 float(ds), int(seed), int(counter), int(s),
                                 _ptr(out["states"]), _ptr(out["u"]), _ptr(out["alpha"]),
@@ -459,13 +510,14 @@ def solve(p: dict, x0, U_nom, obs, path, ds, seed, counter, *, want_J=True, want
     obs = _d(obs).reshape(-1, obs_stride(p))
     n_obs = obs.shape[0]
     path = _d(path)
+    nx = state_dim(p)
     U = np.zeros((H, 3))
-    traj = np.zeros((H + 1, 7))
+    traj = np.zeros((H + 1, nx))
     J = np.zeros(S) if want_J else None
     uh = np.zeros((S, H, 3)) if want_uhist else None
-    xs = np.zeros((S, H + 1, 7)) if want_states else None
+    xs = np.zeros((S, H + 1, nx)) if want_states else None
     P = _params(p, S=S)
-    st = lib.orc_solve(ctypes.byref(P), _ptr(_d(x0, 7)), _ptr(_d(U_nom, 3 * H)),
+    st = lib.orc_solve(ctypes.byref(P), _ptr(_d(x0, nx)), _ptr(_d(U_nom, 3 * H)),
                        _ptr(obs) if n_obs else None, n_obs, _ptr(path), path.size // 3,
                        float(ds), int(seed), int(counter), _ptr(U), _ptr(traj), _ptr(J),
                        _ptr(uh), _ptr(xs))

@@ -286,6 +286,114 @@ void orc_obstacle_row3(const orc_params *P, const double *obs, int stride, doubl
 }
 
 /* ------------------------------------------------------------------ */
+/* Jerk-input model: the paper's own form of the kinematics, where the
+   longitudinal acceleration a is a state integrated from the jerk.  Explicit
+   Euler with every right-hand side at step k, as for the acceleration model;
+   the extra state is x[7] = a. */
+void orc_jerk_step(const orc_params *P, const double x[8], const double u[3], double xn[8]) {
+  const double ua[3] = {x[7], u[1], u[2]}; /* the acceleration drives the speed */
+  orc_dynamics_step(P, x, ua, xn);
+  xn[7] = x[7] + P->Ts * u[0];
+}
+
+void orc_jerk_integrate(const orc_params *P, const double x0[8], const double *U, int H,
+                        double *traj) {
+  memcpy(traj, x0, 8 * sizeof(double));
+  for (int k = 0; k < H; ++k) orc_jerk_step(P, traj + 8 * k, U + 3 * k, traj + 8 * (k + 1));
+}
+
+/* Hitch barrier along the jerk model with the input held: a is a state,
+     hdot  = -kappa a - sigma (th2dot - th1dot),
+     hddot = -kappa jerk - sigma (th2ddot - th1ddot),
+   th1ddot, th2ddot as for the acceleration model with a the state value.
+   Affine in (jerk, omega); read off at unit inputs. */
+static double jerk_hitch_increment(const orc_params *P, const double x[8], double jerk, double omega) {
+  const double th1 = x[2], th2 = x[3], v = x[4], delta = x[5], a = x[7];
+  const double Delta = th2 - th1;
+  const double sigma = (Delta >= 0.0) ? 1.0 : -1.0;
+  const double phi = th1 - th2;
+  const double t = tan(delta);
+  const double k = P->lh / P->l1;
+  const double G = sin(phi) - k * cos(phi) * t;
+  const double th1dot = v * t / P->l1;
+  const double th2dot = v * G / P->l2;
+  const double phidot = th1dot - th2dot;
+  const double th1ddot = (a * t + v * (1.0 + t * t) * omega) / P->l1;
+  const double th2ddot =
+      a * G / P->l2 +
+      v / P->l2 * ((cos(phi) + k * t * sin(phi)) * phidot - k * cos(phi) * (1.0 + t * t) * omega);
+  const double hdot = -P->kappa * a - sigma * (th2dot - th1dot);
+  const double hddot = -P->kappa * jerk - sigma * (th2ddot - th1ddot);
+  return P->Ts * hdot + 0.5 * P->Ts * P->Ts * hddot;
+}
+
+void orc_jerk_hitch_row(const orc_params *P, const double x[8], double A_u[3], double *h,
+                        double *b_rest) {
+  const double c0 = jerk_hitch_increment(P, x, 0.0, 0.0);
+  A_u[0] = jerk_hitch_increment(P, x, 1.0, 0.0) - c0;
+  A_u[1] = jerk_hitch_increment(P, x, 0.0, 1.0) - c0;
+  A_u[2] = 0.0;
+  *h = orc_hitch_h(P, x);
+  *b_rest = -c0;
+}
+
+/* Obstacle at the rear axle along the jerk model, input held:
+     pddot  = a e1 + v th1dot n1                           (no input),
+     pdddot = jerk e1 + 2 a th1dot n1 + v th1ddot n1 - v th1dot^2 e1,
+     th1ddot = (a t + v (1 + t^2) omega) / l1;
+   second order carries no input (relative degree 3), third order brings
+   the jerk and the steer rate in. */
+static double jerk_point_increment(const orc_params *P, const double *obs, int stride, double t,
+                                   const double x[8], double jerk, double omega) {
+  const int e = obstacle_exponent(obs);
+  double vx, vy;
+  obstacle_velocity(obs, stride, &vx, &vy);
+  const double cx = obs[0] + t * vx, cy = obs[1] + t * vy;
+  const double Ax = obs[2] + P->r_inflate, Ay = obs[3] + P->r_inflate;
+  const double co = cos(obs[4]), so = sin(obs[4]);
+  const double th1 = x[2], v = x[4], tn = tan(x[5]), a = x[7];
+  const double th1dot = v * tn / P->l1;
+  const double th1ddot = (a * tn + v * (1.0 + tn * tn) * omega) / P->l1;
+  const double e1[2] = {cos(th1), sin(th1)}, n1[2] = {-sin(th1), cos(th1)};
+  double w[2], acc[2], jk[2];
+  for (int j = 0; j < 2; ++j) {
+    w[j] = v * e1[j] - (j == 0 ? vx : vy);
+    acc[j] = a * e1[j] + v * th1dot * n1[j];
+    jk[j] = jerk * e1[j] + 2.0 * a * th1dot * n1[j] + v * th1ddot * n1[j] - v * th1dot * th1dot * e1[j];
+  }
+  const double rx = x[0] - cx, ry = x[1] - cy;
+  const double xp = co * rx + so * ry, yp = -so * rx + co * ry;
+  const double wx = co * w[0] + so * w[1], wy = -so * w[0] + co * w[1];
+  const double ax_ = co * acc[0] + so * acc[1], ay_ = -so * acc[0] + co * acc[1];
+  const double jx = co * jk[0] + so * jk[1], jy = -so * jk[0] + co * jk[1];
+  const double Axe = ipow(Ax, e), Aye = ipow(Ay, e);
+  const double hx = e * ipow(xp, e - 1) / Axe, hy = e * ipow(yp, e - 1) / Aye;
+  const double hxx = e * (e - 1) * ipow(xp, e - 2) / Axe, hyy = e * (e - 1) * ipow(yp, e - 2) / Aye;
+  const double hxxx = e * (e - 1) * (e - 2) * (e >= 3 ? ipow(xp, e - 3) : 0.0) / Axe;
+  const double hyyy = e * (e - 1) * (e - 2) * (e >= 3 ? ipow(yp, e - 3) : 0.0) / Aye;
+  const double hdot = hx * wx + hy * wy;
+  const double hddot = hx * ax_ + hy * ay_ + hxx * wx * wx + hyy * wy * wy;
+  const double Ts = P->Ts;
+  double inc = Ts * hdot + 0.5 * Ts * Ts * hddot;
+  if (P->flags & ORC_THIRD_ORDER) {
+    const double hdddot = hx * jx + hy * jy + 3.0 * (hxx * wx * ax_ + hyy * wy * ay_) +
+                          hxxx * wx * wx * wx + hyyy * wy * wy * wy;
+    inc += Ts * Ts * Ts / 6.0 * hdddot;
+  }
+  return inc;
+}
+
+void orc_jerk_obstacle_row(const orc_params *P, const double *obs, int stride, double t,
+                           const double x[8], double A_u[3], double *h, double *b_rest) {
+  const double c0 = jerk_point_increment(P, obs, stride, t, x, 0.0, 0.0);
+  A_u[0] = jerk_point_increment(P, obs, stride, t, x, 1.0, 0.0) - c0;
+  A_u[1] = jerk_point_increment(P, obs, stride, t, x, 0.0, 1.0) - c0;
+  A_u[2] = 0.0;
+  *h = orc_obstacle_h_at(P, obs, stride, t, x);
+  *b_rest = -c0;
+}
+
+/* ------------------------------------------------------------------ */
 /* Footprint discs.  Heading accelerations along the field with the input
    held (a, omega constant): with t = tan(delta), phi = th1 - th2,
    k = lh / l1, G = sin(phi) - k cos(phi) t,
@@ -709,7 +817,7 @@ int orc_softmin(int S, const double *J, double lambda, double *gamma_bar) {
    barrier-rate rows at the current state, project, apply the clipped input,
    update the barrier rates alpha_{tau+1} = alpha_tau + u^alpha, step the
    kinematics and accumulate the stage cost. */
-int orc_rollout_sample(const orc_params *P, const double x0[7], const double *U_nom,
+int orc_rollout_sample(const orc_params *P, const double *x0, const double *U_nom,
                        const double *obs, int n_obs, const double *path, int n_pts, double ds,
                        uint64_t seed, uint64_t counter, uint32_t s, double *states, double *u_out,
                        double *alpha_out, double *z_des_out, double *z_star_out, double *J_out) {
@@ -722,9 +830,11 @@ int orc_rollout_sample(const orc_params *P, const double x0[7], const double *U_
   for (int o = 0; o < n_obs; ++o)
     if (obstacle_exponent(obs + (size_t)stride * (size_t)o) < 0) return ORC_EINVAL;
   if (n_pts < 2 || !(ds > 0.0) || nd < 1 || nd > 8) return ORC_EINVAL;
-  if ((P->flags & ORC_THIRD_ORDER) &&
+  const int jerk = (P->flags & ORC_JERK) != 0;
+  const int nx = jerk ? 8 : 7;
+  if ((P->flags & (ORC_THIRD_ORDER | ORC_JERK)) &&
       (nd != 1 || P->disc_trailer_mask != 0 || P->disc_off[0] != 0.0))
-    return ORC_EINVAL; /* offset discs: the third-order term is not affine in the input */
+    return ORC_EINVAL; /* offset discs: the rows are not affine in the input */
 
   double *n = (double *)malloc(sizeof(double) * (size_t)d);
   double *alpha = (double *)malloc(sizeof(double) * (size_t)Nc);
@@ -747,9 +857,9 @@ int orc_rollout_sample(const orc_params *P, const double x0[7], const double *U_
     zhi[3 + i] = P->ua_hi;
     alpha[i] = P->alpha0;
   }
-  double x[7], xn[7], u[3];
-  memcpy(x, x0, sizeof(x));
-  if (states) memcpy(states, x0, sizeof(x));
+  double x[8] = {0}, xn[8] = {0}, u[3];
+  memcpy(x, x0, sizeof(double) * (size_t)nx);
+  if (states) memcpy(states, x0, sizeof(double) * (size_t)nx);
   if (alpha_out)
     for (int i = 0; i < Nc; ++i) alpha_out[i] = alpha[i];
   double J = 0.0;
@@ -767,8 +877,13 @@ int orc_rollout_sample(const orc_params *P, const double x0[7], const double *U_
       /* 2. barrier-rate equality rows A z = b at the current state */
       for (int i = 0; i < Nc; ++i) {
         double Au[3], h, b_rest;
-        if (i == 0)
+        if (i == 0 && jerk)
+          orc_jerk_hitch_row(P, x, Au, &h, &b_rest);
+        else if (i == 0)
           orc_hitch_row(P, x, Au, &h, &b_rest);
+        else if (jerk)
+          orc_jerk_obstacle_row(P, obs + (size_t)stride * (size_t)(i - 1), stride, tau * P->Ts, x, Au,
+                                &h, &b_rest);
         else if (P->flags & ORC_THIRD_ORDER)
           orc_obstacle_row3(P, obs + (size_t)stride * (size_t)(i - 1), stride, tau * P->Ts, x, Au, &h,
                             &b_rest);
@@ -808,13 +923,16 @@ int orc_rollout_sample(const orc_params *P, const double x0[7], const double *U_
 
     /* 5. kinematics and stage cost at the new state, and the comparison
        method's collision cost there */
-    orc_dynamics_step(P, x, u, xn);
+    if (jerk)
+      orc_jerk_step(P, x, u, xn);
+    else
+      orc_dynamics_step(P, x, u, xn);
     memcpy(x, xn, sizeof(x));
     J += orc_stage_cost(P, x, u, path, n_pts, ds);
     if (P->flags & ORC_COLLISION_COST)
       J += orc_collision_cost(P, obs, stride, n_obs, (tau + 1) * P->Ts, x);
 
-    if (states) memcpy(states + 7 * (tau + 1), x, sizeof(x));
+    if (states) memcpy(states + (size_t)nx * (size_t)(tau + 1), x, sizeof(double) * (size_t)nx);
     if (u_out) memcpy(u_out + 3 * tau, u, sizeof(u));
     if (alpha_out)
       for (int i = 0; i < Nc; ++i) alpha_out[(size_t)Nc * (tau + 1) + i] = alpha[i];
@@ -837,11 +955,12 @@ int orc_rollout_sample(const orc_params *P, const double x0[7], const double *U_
 /* The solve: S rollouts, softmin weights, and the update of
    Eq. MPPI_update_rule over the applied inputs; then the optimal
    trajectory, x0 integrated with U*. */
-int orc_solve(const orc_params *P, const double x0[7], const double *U_nom, const double *obs,
+int orc_solve(const orc_params *P, const double *x0, const double *U_nom, const double *obs,
               int n_obs, const double *path, int n_pts, double ds, uint64_t seed,
               uint64_t counter, double *U_out, double *traj_out, double *J_out, double *u_hist,
               double *states_out) {
   const int S = P->S, H = P->H;
+  const int nx = (P->flags & ORC_JERK) ? 8 : 7;
   if (S <= 0 || H <= 0 || n_obs < 0 || n_pts < 2) return ORC_EINVAL;
   double *J = (double *)malloc(sizeof(double) * (size_t)S);
   double *uh = u_hist ? u_hist : (double *)malloc(sizeof(double) * (size_t)S * (size_t)H * 3);
@@ -850,7 +969,8 @@ int orc_solve(const orc_params *P, const double x0[7], const double *U_nom, cons
   for (int s = 0; s < S && status == ORC_OK; ++s) {
     status = orc_rollout_sample(P, x0, U_nom, obs, n_obs, path, n_pts, ds, seed, counter,
                                 (uint32_t)s,
-                                states_out ? states_out + (size_t)s * (size_t)(H + 1) * 7 : NULL,
+                                states_out ? states_out + (size_t)s * (size_t)(H + 1) * (size_t)nx
+                                           : NULL,
                                 uh + (size_t)s * (size_t)H * 3, NULL, NULL, NULL, &J[s]);
   }
   if (status == ORC_OK) {
@@ -864,7 +984,12 @@ int orc_solve(const orc_params *P, const double x0[7], const double *U_nom, cons
     } else {
       for (int k = 0; k < 3 * H; ++k) U_out[k] = U_nom[k];
     }
-    if (traj_out) orc_integrate(P, x0, U_out, H, traj_out);
+    if (traj_out) {
+      if (P->flags & ORC_JERK)
+        orc_jerk_integrate(P, x0, U_out, H, traj_out);
+      else
+        orc_integrate(P, x0, U_out, H, traj_out);
+    }
     if (J_out) memcpy(J_out, J, sizeof(double) * (size_t)S);
   }
   free(J);

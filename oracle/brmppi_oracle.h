@@ -41,6 +41,8 @@ extern "C" {
                                 the centre moving at (vx, vy) from t = 0 */
 #define ORC_ALPHA_BUFFER 8   /* barrier-rate buffer cost on the obstacle rows */
 #define ORC_THIRD_ORDER 16   /* obstacle rows to third order (one rear-axle disc only) */
+#define ORC_JERK 32          /* jerk-input model: state (px, py, th1, th2, v, delta, psi, a),
+                                input (jerk, omega, nu); one rear-axle disc only */
 
 typedef struct {
   int32_t S, H, flags;
@@ -104,6 +106,20 @@ double orc_disc_h(const orc_params *P, const double *obs, int stride, double t, 
 void orc_disc_row(const orc_params *P, const double *obs, int stride, double t, int m,
                   const double x[7], double A_u[3], double *h, double *b_rest);
 
+/* Jerk-input model (Sec. III-A, Eq. tt_discrete_kinematics as the paper
+   writes it: acceleration a is a state driven by the jerk).  State x[8] =
+   (px, py, th1, th2, v, delta, psi, a), input u = (jerk, omega, nu). */
+void orc_jerk_step(const orc_params *P, const double x[8], const double u[3], double xn[8]);
+void orc_jerk_integrate(const orc_params *P, const double x0[8], const double *U, int H,
+                        double *traj);
+/* Barrier-rate rows of the jerk model (same expansion orders as the
+   acceleration model: hitch second order, obstacles second or -- with
+   ORC_THIRD_ORDER -- third). */
+void orc_jerk_hitch_row(const orc_params *P, const double x[8], double A_u[3], double *h,
+                        double *b_rest);
+void orc_jerk_obstacle_row(const orc_params *P, const double *obs, int stride, double t,
+                           const double x[8], double A_u[3], double *h, double *b_rest);
+
 /* Third-order barrier-rate row of obstacle `obs` at the rear axle:
    Ts hdot + Ts^2/2 hddot + Ts^3/6 hdddot along the field with the input held
    (affine in (a, omega): the steer rate enters through th1ddot). */
@@ -151,17 +167,18 @@ double orc_stage_cost(const orc_params *P, const double x[7], const double u[3],
 int orc_softmin(int S, const double *J, double lambda, double *gamma_bar);
 
 /* One rollout of sample s.  Any output pointer may be NULL:
-   states (H+1)*7, u (H)*3 applied inputs, alpha (H+1)*Nc, z_des H*d,
-   z_star H*d, J scalar. Returns ORC_OK or ORC_EINVAL. */
-int orc_rollout_sample(const orc_params *P, const double x0[7], const double *U_nom,
+   states (H+1)*NX, u (H)*3 applied inputs, alpha (H+1)*Nc, z_des H*d,
+   z_star H*d, J scalar; NX = 8 under ORC_JERK (x0 then has 8 entries),
+   else 7.  Returns ORC_OK or ORC_EINVAL. */
+int orc_rollout_sample(const orc_params *P, const double *x0, const double *U_nom,
                        const double *obs, int n_obs, const double *path, int n_pts, double ds,
                        uint64_t seed, uint64_t counter, uint32_t s, double *states, double *u,
                        double *alpha, double *z_des, double *z_star, double *J);
 
-/* The full solve.  U_out H*3 (required); traj_out (H+1)*7, J_out S,
-   u_hist S*H*3, states_out S*(H+1)*7 optional.  On ORC_ENONFINITE U_out is
-   the nominal sequence. */
-int orc_solve(const orc_params *P, const double x0[7], const double *U_nom, const double *obs,
+/* The full solve.  U_out H*3 (required); traj_out (H+1)*NX, J_out S,
+   u_hist S*H*3, states_out S*(H+1)*NX optional (NX as for rollouts).  On
+   ORC_ENONFINITE U_out is the nominal sequence. */
+int orc_solve(const orc_params *P, const double *x0, const double *U_nom, const double *obs,
               int n_obs, const double *path, int n_pts, double ds, uint64_t seed,
               uint64_t counter, double *U_out, double *traj_out, double *J_out, double *u_hist,
               double *states_out);

@@ -49,6 +49,7 @@ FLAG_COLLISION_COST = 2
 FLAG_OBS8 = 4
 FLAG_ALPHA_BUFFER = 8
 FLAG_THIRD_ORDER = 16
+FLAG_JERK = 32
 
 
 def params(**overrides) -> dict:
@@ -337,4 +338,21 @@ def crossing(seed: int = 6, S: int = 4096, H: int = 50, n_parked: int = 6, n_ped
         vel = (side * sp * math.sin(ph), -side * sp * math.cos(ph))  # toward the path
         obs.append((c[0], c[1], 0.5, 0.5, 0.0, 2.0, vel[0], vel[1]))
     return _scenario(p, x0, path, 0.1, obs, seed=seed)
+
+
+def jerk_model(c: dict, a0: float = 0.0, seed: int = 0) -> dict:
+    """The scenario under the paper's jerk-input model (flag FLAG_JERK): the
+    state gains the acceleration a (x0[7] = a0) and the inputs become
+    (jerk, steer rate, progress rate), jerk bounded by +-2 m/s^3 (Sec. V);
+    the nominal jerk is drawn small."""
+    rng = np.random.default_rng(seed)
+    p = dict(c["params"], flags=int(c["params"].get("flags", 0)) | FLAG_JERK,
+             z_lo=(-2.0,) + tuple(c["params"]["z_lo"][1:]), z_hi=(2.0,) + tuple(c["params"]["z_hi"][1:]))
+    out = dict(c)
+    out["params"] = p
+    out["x0"] = np.concatenate([np.asarray(c["x0"], np.float64)[:7], [a0]])
+    U = np.array(c["U_nom"], np.float32)
+    U[:, 0] = rng.uniform(-0.3, 0.3, size=U.shape[0]).astype(np.float32)
+    out["U_nom"] = U
+    return out
 

@@ -21,6 +21,7 @@ from tests import test_oracle_discs as tdd
 from tests import test_oracle_obstacle_variants as tv
 from tests import test_oracle_stabilizer as tz
 from tests import test_oracle_third_order as t3
+from tests import test_oracle_jerk as tjk
 
 MUTANTS = [
     ("philox multiplier swapped", "(uint64_t)PHILOX_M0 * (uint64_t)c0", "(uint64_t)PHILOX_M1 * (uint64_t)c0"),
@@ -55,17 +56,23 @@ MUTANTS = [
     ("collision cost skips discs", "for (int m = 0; m < P->n_discs; ++m) {", "for (int m = 0; m < 1; ++m) {"),
     ("third-order weight", "return Ts * hdot + 0.5 * Ts * Ts * hddot + Ts * Ts * Ts / 6.0 * hdddot;", "return Ts * hdot + 0.5 * Ts * Ts * hddot + Ts * Ts * Ts / 2.0 * hdddot;"),
     ("third-order jerk factor", "jerk[j] = 2.0 * a * th1dot * n1[j]", "jerk[j] = a * th1dot * n1[j]"),
-    ("third-order Hessian-acceleration factor", "3.0 * (hxx * wx * ax_ + hyy * wy * ay_)", "2.0 * (hxx * wx * ax_ + hyy * wy * ay_)"),
-    ("third-order D3 term dropped", "hxxx * wx * wx * wx + hyyy * wy * wy * wy;", "0.0;"),
-    ("third-order steer term dropped", "const double th1ddot = (a * tn + v * (1.0 + tn * tn) * omega) / P->l1;", "const double th1ddot = (a * tn) / P->l1;"),
+    ("third-order Hessian-acceleration factor", "\n  const double hdddot = hx * jx + hy * jy + 3.0 * (hxx * wx * ax_ + hyy * wy * ay_) +", "\n  const double hdddot = hx * jx + hy * jy + 2.0 * (hxx * wx * ax_ + hyy * wy * ay_) +"),
+    ("third-order D3 term dropped", "                        hxxx * wx * wx * wx + hyyy * wy * wy * wy;\n  const double Ts = P->Ts;\n  return", "                        0.0;\n  const double Ts = P->Ts;\n  return"),
+    ("third-order steer term dropped", "tn = tan(x[5]);\n  const double th1dot = v * tn / P->l1;\n  const double th1ddot = (a * tn + v * (1.0 + tn * tn) * omega) / P->l1;", "tn = tan(x[5]);\n  const double th1dot = v * tn / P->l1;\n  const double th1ddot = (a * tn) / P->l1;"),
     ("rollout ignores the third-order flag", "else if (P->flags & ORC_THIRD_ORDER)", "else if (0)"),
+    ("jerk model: speed driven by the input", "const double ua[3] = {x[7], u[1], u[2]};", "const double ua[3] = {u[0], u[1], u[2]};"),
+    ("jerk not integrated", "xn[7] = x[7] + P->Ts * u[0];", "xn[7] = x[7];"),
+    ("jerk hitch: jerk term dropped", "const double hddot = -P->kappa * jerk - sigma * (th2ddot - th1ddot);", "const double hddot = -sigma * (th2ddot - th1ddot);"),
+    ("jerk obstacle: acceleration state dropped", "    acc[j] = a * e1[j] + v * th1dot * n1[j];\n    jk[j] = jerk * e1[j]", "    acc[j] = v * th1dot * n1[j];\n    jk[j] = jerk * e1[j]"),
+    ("jerk obstacle: jerk column dropped", "jk[j] = jerk * e1[j] + 2.0 * a", "jk[j] = 0.0 * e1[j] + 2.0 * a"),
+    ("rollout ignores the jerk hitch row", "if (i == 0 && jerk)", "if (i == 0 && 0)"),
     ("stabilizer CBF sign", "const double rhs = -P->alpha_stab * h - c0;", "const double rhs = P->alpha_stab * h - c0;"),
     ("stabilizer ignores Q_h", "(out)[j] = clip(u_ref[j] + (mu) * g[j] / P->q_stab[j], P->z_lo[j], P->z_hi[j]);", "(out)[j] = clip(u_ref[j] + (mu) * g[j], P->z_lo[j], P->z_hi[j]);"),
     ("stabilizer infeasible corner swapped", "u[j] = g[j] > 0.0 ? P->z_hi[j] : (g[j] < 0.0 ? P->z_lo[j]", "u[j] = g[j] > 0.0 ? P->z_lo[j] : (g[j] < 0.0 ? P->z_hi[j]"),
-    ("hitch sign of Delta", "const double sigma = (Delta >= 0.0) ? 1.0 : -1.0;", "const double sigma = (Delta >= 0.0) ? -1.0 : 1.0;"),
-    ("hitch steer-rate term dropped", " - k * cos(phi) * (1.0 + t * t) * omega);", ");"),
+    ("hitch sign of Delta", "double a, double omega) {\n  const double th1 = x[2], th2 = x[3], v = x[4], delta = x[5];\n  const double Delta = th2 - th1;\n  const double sigma = (Delta >= 0.0) ? 1.0 : -1.0;", "double a, double omega) {\n  const double th1 = x[2], th2 = x[3], v = x[4], delta = x[5];\n  const double Delta = th2 - th1;\n  const double sigma = (Delta >= 0.0) ? -1.0 : 1.0;"),
+    ("hitch steer-rate term dropped", " - k * cos(phi) * (1.0 + t * t) * omega);\n  const double hdot = -P->kappa * a - sigma * (th2dot - th1dot);\n  const double hddot = -sigma * (th2ddot - th1ddot);", ");\n  const double hdot = -P->kappa * a - sigma * (th2dot - th1dot);\n  const double hddot = -sigma * (th2ddot - th1ddot);"),
     ("hitch speed threshold", "return P->dtheta_max - P->kappa * x[4] - fabs(x[3] - x[2]);", "return P->dtheta_max + P->kappa * x[4] - fabs(x[3] - x[2]);"),
-    ("hitch kappa in hdot", "const double hdot = -P->kappa * a - sigma * (th2dot - th1dot);", "const double hdot = -sigma * (th2dot - th1dot);"),
+    ("hitch kappa in hdot", "const double hdot = -P->kappa * a - sigma * (th2dot - th1dot);\n  const double hddot = -sigma * (th2ddot - th1ddot);", "const double hdot = -sigma * (th2dot - th1dot);\n  const double hddot = -sigma * (th2ddot - th1ddot);"),
     ("projection residual sign", "lam[i] = t - b[i]; /* A M^-1 p - b */", "lam[i] = t + b[i];"),
     ("projection box centre", "p[j] = w[j] * z_des[j] + 0.5 * rho * (z_hi[j] + z_lo[j]);", "p[j] = w[j] * z_des[j] + 0.5 * rho * (z_hi[j] - z_lo[j]);"),
     ("projection M^-1 dropped", "z_star[j] = Minv[j] * t;", "z_star[j] = t;"),
@@ -157,6 +164,12 @@ def _battery():
         ("third-extends", lambda: t3.test_third_order_extends_the_second_order_row(t3.OBS[1])),
         ("third-steer", t3.test_steer_rate_enters_at_third_order),
         ("third-rollout", t3.test_rollout_uses_third_order_rows),
+        ("jerk-closed-form", tjk.test_constant_jerk_closed_form),
+        ("jerk-step", lambda: tjk.test_step_is_the_acceleration_model_driven_by_the_state(tjk.STATES[0])),
+        ("jerk-hitch-taylor", lambda: tjk.test_hitch_row_is_second_order_taylor(tjk.STATES[0])),
+        ("jerk-obs-taylor3", lambda: tjk.test_obstacle_row_taylor_order(tjk.STATES[2], tjk.OBS[0], True)),
+        ("jerk-rows", lambda: tjk.test_rows_match_the_acceleration_model(tjk.STATES[2])),
+        ("jerk-rollout", tjk.test_rollout_rows_and_zero_noise_integration),
         ("stab-admissible", tz.test_admissible_reference_is_unchanged),
         ("stab-closed-form", lambda: tz.test_closed_form_without_active_bounds(0)),
         ("stab-brute", lambda: tz.test_brute_force_grid(0)),
