@@ -379,6 +379,19 @@ def measure_variants(dev, reps: int = 20):
                 row["br_mppi_with_stabilizer"] = {"ms_per_solve": _time_solve(solver, inst_s, stream, flush,
                                                                                reps)}
             solver.close()
+        # the paper's jerk-input model (third-order obstacle rows bring the
+        # inputs in; x0 gains the acceleration)
+        cj = sc.jerk_model(c)
+        pj = dict(cj["params"], flags=int(cj["params"]["flags"]) | pkg.BRMPPI_FLAG_THIRD_ORDER)
+        solver = pkg.Solver(pj, max_obstacles=16, max_path_pts=1024)
+        inst = dict(x0=t(cj["x0"], torch.float64), U_nom=t(cj["U_nom"]), obs=t(cj["obs"]), path=t(cj["path"]),
+                    ds=cj["ds"], S=S, seed=cj["seed"], counter=0, U_out=torch.empty((H, 3), device=dev),
+                    traj_out=torch.empty((H + 1, 7), device=dev))
+        solver.autotune(inst["x0"], inst["U_nom"], inst["obs"], inst["path"], cj["ds"], reps=2, stream=stream)
+        ms = _time_solve(solver, inst, stream, flush, reps)
+        row["br_mppi_jerk_model_third_order"] = {"ms_per_solve": ms, "rollout_steps_per_s": S * H / (ms * 1e-3),
+                                                 "launch": solver.launch(8)}
+        solver.close()
         out[size] = dict(row, S=S, H=H, n_obs=8)
     # crossing scene: 6 parked e = 4 super-ellipses, 2 crossing pedestrians
     c = sc.crossing()

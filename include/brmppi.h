@@ -89,6 +89,13 @@ typedef enum {
    the tractor's yaw acceleration).  Needs the single rear-axle disc (offset
    discs make the third-order term quadratic in the input). */
 #define BRMPPI_FLAG_THIRD_ORDER 0x10u
+/* The paper's jerk-input model (Sec. III-A): the longitudinal acceleration
+   a is a state and input 0 is the jerk (bounds z_lo[0], z_hi[0] and noise
+   sigma[0] apply to the jerk).  x0 then holds 8 doubles, (px, py, theta1,
+   theta2, v, delta, psi, a); outputs keep 7 columns.  The hitch row sees the
+   jerk at second order, obstacle rows only with BRMPPI_FLAG_THIRD_ORDER
+   (relative degree 3).  Needs the single rear-axle disc. */
+#define BRMPPI_FLAG_JERK_MODEL 0x20u
 
 /* Every constant of the solve; POD. Fields the paper leaves open take the
    documented readings (alpha init, noise and bounds of u^alpha, W, rho, the
@@ -213,7 +220,9 @@ brmppi_status brmppi_solve_device_ex(brmppi_ctx *ctx, const brmppi_instance *ins
    (up to rounding) when the condition is met; < 0 means no input in the box
    meets it and (a, omega) is the box corner that maximises the increment.
    Solved in closed form (KKT of a one-row QP with a diagonal weight and a
-   box).  Enqueued on `stream`; allocates nothing.  n = 0 is a no-op. */
+   box).  Under BRMPPI_FLAG_JERK_MODEL x_dev is n x 8 (a last) and the QP is
+   over (jerk, omega).  Enqueued on `stream`; allocates nothing.  n = 0 is a
+   no-op. */
 brmppi_status brmppi_hitch_stabilize_device(brmppi_ctx *ctx, const double *x_dev,
                                             const float *u_ref_dev, int32_t n, float *u_out_dev,
                                             void *stream);

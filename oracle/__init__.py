@@ -414,7 +414,7 @@ def hitch_stabilize(p: dict, x, u_ref):
     lib = _load()
     u = np.zeros(3)
     sl = ctypes.c_double()
-    st = lib.orc_hitch_stabilize(ctypes.byref(_params(p)), _ptr(_d(x, 7)), _ptr(_d(u_ref, 3)),
+    st = lib.orc_hitch_stabilize(ctypes.byref(_params(p)), _ptr(_d(x, state_dim(p))), _ptr(_d(u_ref, 3)),
                                  _ptr(u), ctypes.byref(sl))
     return st, u, sl.value
 

@@ -589,10 +589,13 @@ void orc_hitch_row(const orc_params *P, const double x[7], double A_u[3], double
    u(mu) = clip(u_ref + mu Q_h^-1 g) with the smallest mu >= 0 that meets it.
    g . u(mu) is continuous and non-decreasing in mu, so mu is found by
    bisection. */
-int orc_hitch_stabilize(const orc_params *P, const double x[7], const double u_ref[3],
+int orc_hitch_stabilize(const orc_params *P, const double *x, const double u_ref[3],
                         double u_out[3], double *slack) {
   double A_u[3], h, b_rest;
-  orc_hitch_row(P, x, A_u, &h, &b_rest);
+  if (P->flags & ORC_JERK) /* the paper's inputs: (jerk, omega); x holds the acceleration */
+    orc_jerk_hitch_row(P, x, A_u, &h, &b_rest);
+  else
+    orc_hitch_row(P, x, A_u, &h, &b_rest);
   const double g[2] = {A_u[0], A_u[1]};
   const double c0 = -b_rest;
   const double rhs = -P->alpha_stab * h - c0; /* need g . u >= rhs */

@@ -144,8 +144,8 @@ void orc_hitch_row(const orc_params *P, const double x[7], double A_u[3], double
    hitch increment meets the discrete CBF condition, nu passed through;
    *slack = increment + alpha_stab h (>= 0 when met).  Returns 0, or 1 when
    no input in the box meets it (u_out then maximises the increment). */
-int orc_hitch_stabilize(const orc_params *P, const double x[7], const double u_ref[3],
-                        double u_out[3], double *slack);
+int orc_hitch_stabilize(const orc_params *P, const double *x, const double u_ref[3],
+                        double u_out[3], double *slack); /* x: 8 entries under ORC_JERK */
 
 /* Soft-bound equality projection, closed form (Sec. IV-A), dense.
    A is nc x d row-major, w the diagonal of W (d entries).  Returns ORC_OK or

@@ -8,7 +8,7 @@ library; the first call does, and fails loudly if it has not been built.
 """
 from ._native import (  # noqa: F401
     BRMPPI_ABI_VERSION, BRMPPI_EAGAIN, BRMPPI_EBUSY, BRMPPI_ECUDA, BRMPPI_EINVAL, BRMPPI_ENOMEM,
-    BRMPPI_ENONFINITE, BRMPPI_ETIMEDOUT, BRMPPI_FLAG_ALPHA_BUFFER, BRMPPI_FLAG_COLLISION_COST,
+    BRMPPI_ENONFINITE, BRMPPI_ETIMEDOUT, BRMPPI_FLAG_ALPHA_BUFFER, BRMPPI_FLAG_COLLISION_COST, BRMPPI_FLAG_JERK_MODEL,
     BRMPPI_FLAG_OBS8, BRMPPI_FLAG_PROJ_NONE, BRMPPI_FLAG_THIRD_ORDER, BRMPPI_OK, EXPORTS, BrmppiError,
     NativeLibraryMissing, Solver, brmppi_autotune, brmppi_autotune_batch, brmppi_batch_capture,
     brmppi_create, brmppi_default_params, brmppi_destroy, brmppi_get_launch, brmppi_graph_destroy,

@@ -26,6 +26,7 @@ BRMPPI_FLAG_COLLISION_COST = 0x2
 BRMPPI_FLAG_OBS8 = 0x4
 BRMPPI_FLAG_ALPHA_BUFFER = 0x8
 BRMPPI_FLAG_THIRD_ORDER = 0x10
+BRMPPI_FLAG_JERK_MODEL = 0x20
 
 STATUS_NAMES = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "EAGAIN", -4: "ETIMEDOUT",
                 -5: "ENONFINITE", -6: "ECUDA", -7: "EBUSY"}
@@ -255,8 +256,8 @@ def brmppi_solve(ctx, x0, U_nom, obs, path, ds, seed, counter, H, S=None, want_t
     """Host-buffer solve. Returns (status, U[H,3], traj[H+1,7] or None, J[S] or None)."""
     lib = load()
     x0 = np.ascontiguousarray(x0, dtype=np.float64)
-    if x0.size != 7:
-        raise ValueError("x0 must have 7 entries")
+    if x0.size not in (7, 8):
+        raise ValueError("x0 must have 7 entries (8 under the jerk-input model)")
     U_nom = _f32(U_nom, 3 * H)
     n_obs = _rows(None if obs is None else np.asarray(obs))
     obs = _f32(obs).reshape(-1) if obs is not None else np.zeros(0, np.float32)
@@ -391,9 +392,10 @@ def brmppi_solve_device_noalloc(params, x0, U_nom, obs, path, ds, seed, counter,
 
 
 def brmppi_hitch_stabilize_device(ctx, x, u_ref, u_out, stream=None) -> int:
-    """Hitch stabilizer for n states: x float64[n,7], u_ref float32[n,3],
-    u_out float32[n,4] (a, omega, nu, slack), torch CUDA tensors."""
-    n = x.numel() // 7
+    """Hitch stabilizer for n states: x float64[n,7] (n x 8 under the
+    jerk-input model), u_ref float32[n,3], u_out float32[n,4]
+    (a or jerk, omega, nu, slack), torch CUDA tensors."""
+    n = u_ref.numel() // 3
     return load().brmppi_hitch_stabilize_device(ctx, _dptr(x), _dptr(u_ref), n, _dptr(u_out),
                                                 ctypes.c_void_p(_stream_handle(stream)))
 

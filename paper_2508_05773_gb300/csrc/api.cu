@@ -68,7 +68,7 @@ std::string check_params(const brmppi_params* p) {
   if (p->max_obstacles < 0 || p->max_obstacles > kMaxObstacles) return "max_obstacles must be in [0, 124]";
   if (p->max_path_pts < 2 || p->max_path_pts > kMaxPathPts) return "max_path_pts must be in [2, 12000]";
   if (p->flags & ~static_cast<int32_t>(BRMPPI_FLAG_PROJ_NONE | BRMPPI_FLAG_COLLISION_COST | BRMPPI_FLAG_OBS8 |
-                                        BRMPPI_FLAG_ALPHA_BUFFER | BRMPPI_FLAG_THIRD_ORDER))
+                                        BRMPPI_FLAG_ALPHA_BUFFER | BRMPPI_FLAG_THIRD_ORDER | BRMPPI_FLAG_JERK_MODEL))
     return "unknown flag";
   if (p->threads_per_sample != 0 && !is_pow2_tps(p->threads_per_sample))
     return "threads_per_sample must be 0, 1, 2, 4, 8, 16 or 32";
@@ -115,6 +115,8 @@ std::string check_params(const brmppi_params* p) {
   if (p->max_obstacles * p->n_discs > kMaxObstacles) return "max_obstacles * n_discs must be <= 124";
   if ((p->flags & BRMPPI_FLAG_THIRD_ORDER) && (p->n_discs != 1 || p->disc_trailer_mask != 0 || p->disc_off[0] != 0.f))
     return "third-order rows need the single rear-axle disc";
+  if ((p->flags & BRMPPI_FLAG_JERK_MODEL) && (p->n_discs != 1 || p->disc_trailer_mask != 0 || p->disc_off[0] != 0.f))
+    return "the jerk-input model needs the single rear-axle disc";
   return "";
 }
 
@@ -177,6 +179,7 @@ brmppi::KConst make_kconst(const brmppi_params& q) {
   k.inv_qs0 = 1.0f / q.q_stab[0];
   k.inv_qs1 = 1.0f / q.q_stab[1];
   k.third = (q.flags & BRMPPI_FLAG_THIRD_ORDER) ? 1 : 0;
+  k.jerk = (q.flags & BRMPPI_FLAG_JERK_MODEL) ? 1 : 0;
   k.Ts3_6 = q.Ts * q.Ts * q.Ts / 6.0f;
   k.nd = q.n_discs;
   k.inv_nd = 1.0f / static_cast<float>(q.n_discs);
@@ -675,7 +678,8 @@ brmppi_status brmppi_solve(brmppi_ctx* c, const double x0[7], const float* U_nom
   if (!x0 || !U_nom || !path || !U_out || (n_obs > 0 && !obs)) return fail(c, BRMPPI_EINVAL, "NULL buffer");
   brmppi_status st = check_sizes(c, n_obs, n_pts, ds);
   if (st != BRMPPI_OK) return st;
-  for (int j = 0; j < 7; ++j)
+  const int nx = state_dim(c->prm);
+  for (int j = 0; j < nx; ++j)
     if (!std::isfinite(x0[j])) return fail(c, BRMPPI_ENONFINITE, "x0 is not finite");
   const int of = obs_floats(c->prm);
   for (int o = 0; o < n_obs; ++o)
@@ -686,7 +690,7 @@ brmppi_status brmppi_solve(brmppi_ctx* c, const double x0[7], const float* U_nom
   cudaError_t e = cudaSetDevice(c->device);
   if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
   // stage: x0 | U_nom | obs | path  (one pinned buffer, one copy)
-  std::memcpy(c->h_in, x0, 7 * sizeof(double));
+  std::memcpy(c->h_in, x0, nx * sizeof(double));
   std::memcpy(c->h_in + c->off_unom, U_nom, sizeof(float) * 3 * H);
   if (n_obs > 0) std::memcpy(c->h_in + c->off_obs, obs, sizeof(float) * of * n_obs);
   std::memcpy(c->h_in + c->off_path, path, sizeof(float) * 3 * n_pts);

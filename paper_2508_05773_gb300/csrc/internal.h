@@ -19,6 +19,9 @@ constexpr int kMaxThreads = 512;
 constexpr int kMinBatchSpb = 16;  // smallest tile of a batch launch
 constexpr int kMaxResidentThreads = 2048;
 
+// Doubles of a state (the jerk-input model adds the acceleration).
+inline int state_dim(const brmppi_params& p) { return (p.flags & BRMPPI_FLAG_JERK_MODEL) ? 8 : 7; }
+
 // Constraint rows of obstacles: each obstacle seen from every footprint disc.
 inline int rows_of(const brmppi_params& p, int n_obs) { return n_obs * p.n_discs; }
 

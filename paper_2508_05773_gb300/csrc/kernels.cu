@@ -31,11 +31,12 @@ __global__ void __launch_bounds__(256) stabilize_kernel(const KConst k, const do
                                                         float* out) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  const double* xi = x + 7 * static_cast<size_t>(i);
+  const int nx = k.jerk ? 8 : 7;
+  const double* xi = x + nx * static_cast<size_t>(i);
   const float* ur = u_ref + 3 * static_cast<size_t>(i);
   float o[4];
-  hitch_stabilize(k, static_cast<float>(xi[3] - xi[2]), static_cast<float>(xi[4]), static_cast<float>(xi[5]), ur[0],
-                  ur[1], ur[2], o);
+  hitch_stabilize(k, static_cast<float>(xi[3] - xi[2]), static_cast<float>(xi[4]), static_cast<float>(xi[5]),
+                  k.jerk ? static_cast<float>(xi[7]) : 0.f, ur[0], ur[1], ur[2], o);
   float* dst = out + 4 * static_cast<size_t>(i);
   dst[0] = o[0];
   dst[1] = o[1];
@@ -52,7 +53,8 @@ __global__ void __launch_bounds__(128) stabilize_table_kernel(const KConst k, co
   const Inst in = table[i];
   if (!in.u_safe) return;
   hitch_stabilize(k, static_cast<float>(in.x0[3] - in.x0[2]), static_cast<float>(in.x0[4]),
-                  static_cast<float>(in.x0[5]), in.U_out[0], in.U_out[1], in.U_out[2], in.u_safe);
+                  static_cast<float>(in.x0[5]), k.jerk ? static_cast<float>(in.x0[7]) : 0.f, in.U_out[0],
+                  in.U_out[1], in.U_out[2], in.u_safe);
 }
 
 }  // namespace

@@ -25,7 +25,7 @@ const Variant* variants_narrow_ext(int* n);  // the same, with the optional term
 const Variant* variants_wide_ext(int* n);
 
 // Whether a launch with these constants needs the family with the optional terms.
-inline bool needs_ext(const KConst& k) { return k.coll || k.obs8 || k.abuf || k.discs || k.third; }
+inline bool needs_ext(const KConst& k) { return k.coll || k.obs8 || k.abuf || k.discs || k.third || k.jerk; }
 
 // Threads of a launch: `threads` roll out samples; teams wider than one lane
 // with at most two Philox blocks per lane add warps that produce the noise,

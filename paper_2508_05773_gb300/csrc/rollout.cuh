@@ -71,6 +71,7 @@ struct KConst {
   float alpha_stab, inv_qs0, inv_qs1;  // hitch stabilizer: CBF rate, Q_h^-1
   int nd, discs;                       // footprint discs; non-default footprint
   int third;                           // obstacle rows to third order (rear-axle point only)
+  int jerk;                            // jerk-input model: a is a state (x0[7]), input 0 the jerk
   float Ts3_6;                         // Ts^3 / 6
   float inv_nd;
   float disc_e1[8], disc_e2[8];        // disc m at p + disc_e1[m] e1 + disc_e2[m] e2
@@ -218,7 +219,7 @@ __device__ __forceinline__ HitchRow hitch_row(const KConst& k, float Delta, floa
 }
 
 // Hitch-angle stabilizer (Sec. IV-D, Eq. hitch_angle_qp): the (a, omega)
-// nearest the reference in the diag(q_stab) norm, inside the input box,
+// (jerk-input model: (jerk, omega)) nearest the reference in the diag(q_stab) norm, inside the input box,
 // whose hitch increment g.u + c0 meets the discrete CBF condition
 // (Eq. barrier_constraint_prelim, sign of Eq. cbf_equality)
 //   g.u >= rhs = -alpha_stab h - c0.
@@ -228,12 +229,16 @@ __device__ __forceinline__ HitchRow hitch_row(const KConst& k, float Delta, floa
 // non-decreasing with breaks where a coordinate meets a bound, so the root is
 // found exactly on the segment that crosses rhs.  No crossing: the box
 // corner that maximises the increment.  out = (a, omega, nu, slack).
-__device__ __forceinline__ void hitch_stabilize(const KConst& k, float Delta, float vv, float dl, float ua, float uw,
-                                                float un, float* out) {
+__device__ __forceinline__ void hitch_stabilize(const KConst& k, float Delta, float vv, float dl, float acc, float ua,
+                                                float uw, float un, float* out) {
   float sp, cp;
   sincosf(-Delta, &sp, &cp);
   const float tn = tanf(dl);
-  const HitchRow r = hitch_row(k, Delta, sp, cp, tn, vv, vv * tn * k.inv_l1);
+  HitchRow r = hitch_row(k, Delta, sp, cp, tn, vv, vv * tn * k.inv_l1);
+  if (k.jerk) {  // jerk-input model: (jerk, omega), the acceleration acc a state
+    r.c0 += acc * r.Aa;
+    r.Aa = -k.hTs2 * k.kappa;
+  }
   const float g0 = r.Aa, g1 = r.Aw;
   const float rhs = -k.alpha_stab * r.h - r.c0;
   float a = clampf(ua, k.zlo0, k.zhi0), w = clampf(uw, k.zlo1, k.zhi1);
@@ -291,15 +296,18 @@ struct Frame {
   float ox_h, ox_l, oy_h, oy_l, oth_h, oth_l;  // origin (px0, py0, theta1_0)
   float c0, s0;                                // cos / sin of theta1_0
   float t2, v_h, v_l, dl;                      // theta2 - theta1_0, speed, steer angle
+  float a0;                                    // acceleration (jerk-input model)
   float qf0;                                   // fractional path cell of psi0
   int i0;                                      // integer path cell of psi0
   float psi_h, psi_l;                          // psi0
   double psi0;
 };
 
-__device__ __forceinline__ void make_frame(const double* x0, float ds, unsigned int* err, Frame& fr) {
+__device__ __forceinline__ void make_frame(const double* x0, float ds, unsigned int* err, Frame& fr,
+                                           bool jerk = false) {
   bool finite = true;
-  for (int j = 0; j < 7; ++j) finite = finite && isfinite(x0[j]);
+  for (int j = 0; j < (jerk ? 8 : 7); ++j) finite = finite && isfinite(x0[j]);
+  fr.a0 = jerk ? static_cast<float>(x0[7]) : 0.f;
   if (!finite) atomicOr(err, ERR_NONFINITE_X0);
   split_double(x0[0], fr.ox_h, fr.ox_l);
   split_double(x0[1], fr.oy_h, fr.oy_l);
@@ -392,7 +400,7 @@ __device__ void run_tile(const KConst& k, const Inst& in, int tile, float* uh, c
   const int n_rows = EXT ? in.n_obs * k.nd : in.n_obs;  // obstacle rows (obstacle x disc)
 
   // --- frame and staging (tables in shared memory, relative coordinates)
-  if (threadIdx.x == 0) make_frame(in.x0, in.ds, in.sync + 1, sh.fr);
+  if (threadIdx.x == 0) make_frame(in.x0, in.ds, in.sync + 1, sh.fr, EXT && k.jerk);
   __syncthreads();
   const Frame& fr = sh.fr;
   const bool obs8 = EXT && k.obs8;
@@ -433,6 +441,7 @@ __device__ void run_tile(const KConst& k, const Inst& in, int tile, float* uh, c
 
   // --- per-sample state (relative frame)
   const float c0 = fr.c0, s0 = fr.s0;
+  float acc = fr.a0;  // acceleration state of the jerk-input model
   float px = 0.f, pxl = 0.f, py = 0.f, pyl = 0.f, t1 = 0.f, t2 = fr.t2, v = fr.v_h, vl = fr.v_l,
         dl = fr.dl, ps = 0.f, psl = 0.f;
   // obstacle slots per lane: one lane per sample holds every obstacle of
@@ -641,7 +650,11 @@ __device__ void run_tile(const KConst& k, const Inst& in, int tile, float* uh, c
       float Saa, Saw, Sww, ga, gw, ca_h, cw_h, cc_h;
       {
         const float n_h = (TPS == 1) ? nrm[3] : cur[3];
-        const HitchRow hr = hitch_row(k, t2 - t1, sp, cp, tn, vv, th1dot);
+        HitchRow hr = hitch_row(k, t2 - t1, sp, cp, tn, vv, th1dot);
+        if (EXT && k.jerk) {  // a is a state: its terms join the constant; the jerk enters via -kappa
+          hr.c0 += acc * hr.Aa;
+          hr.Aa = -k.hTs2 * k.kappa;
+        }
         const float hm = fmaxf(fabsf(hr.h), k.h_floor);
         const float ht = hr.h >= 0.f ? hm : -hm;
         const float zda = clampf(k.sigma_alpha * n_h, k.ua_lo, k.ua_hi);
@@ -764,6 +777,12 @@ __device__ void run_tile(const KConst& k, const Inst& in, int tile, float* uh, c
             Aw += k.Ts3_6 * cw3;
             brest -= k.Ts3_6 * c03;
           }
+          if (k.jerk) {
+            // a is a state (rear-axle point): its terms join the constant;
+            // the jerk enters only at third order, through grad h . e1'
+            brest -= acc * Aa;
+            Aa = k.third ? k.Ts3_6 * gda3(hx, hy, dirx, diry) : 0.f;
+          }
         }
         const float hm = fmaxf(fabsf(h), k.h_floor);
         const float ht = h >= 0.f ? hm : -hm;
@@ -867,7 +886,12 @@ __device__ void run_tile(const KConst& k, const Inst& in, int tile, float* uh, c
     acc2(py, pyl, Tv * s1);
     t1 += k.Ts * th1dot;
     t2 += Tv * k.inv_l2 * (sp - k.k_hitch * cp * tn);
-    acc2(v, vl, k.Ts * ua);
+    if (EXT && k.jerk) {  // input 0 is the jerk; the acceleration state drives the speed
+      acc2(v, vl, k.Ts * acc);
+      acc += k.Ts * ua;
+    } else {
+      acc2(v, vl, k.Ts * ua);
+    }
     dl += k.Ts * uw;
     acc2(ps, psl, k.Ts * un);
 
@@ -984,13 +1008,18 @@ static __device__ void optimal_trajectory(const KConst& k, const Inst& in, const
   const float* ustar = S.ustar;
   __syncthreads();
   if (threadIdx.x == 0) {
-    float qv = fr.v_h + fr.v_l, qd = fr.dl, qp = 0.f;
+    float qv = fr.v_h + fr.v_l, qd = fr.dl, qp = 0.f, qa = fr.a0;
     for (int tau = 0; tau <= H; ++tau) {
       V[tau] = qv;
       D[tau] = qd;
       Q[tau] = qp;
       if (tau < H) {
-        qv += k.Ts * ustar[3 * tau + 0];
+        if (k.jerk) {
+          qv += k.Ts * qa;
+          qa += k.Ts * ustar[3 * tau + 0];
+        } else {
+          qv += k.Ts * ustar[3 * tau + 0];
+        }
         qd += k.Ts * ustar[3 * tau + 1];
         qp += k.Ts * ustar[3 * tau + 2];
       }
@@ -1055,7 +1084,7 @@ static __device__ void serial_trajectory(const KConst& k, const Inst& in, const 
   const float c0 = fr.c0, s0 = fr.s0;
   const float* ustar = S.ustar;
   const int H = in.H;
-  float qx = 0.f, qy = 0.f, q1 = 0.f, q2 = fr.t2, qv = fr.v_h + fr.v_l, qd = fr.dl, qp = 0.f;
+  float qx = 0.f, qy = 0.f, q1 = 0.f, q2 = fr.t2, qv = fr.v_h + fr.v_l, qd = fr.dl, qp = 0.f, qa = fr.a0;
   float* tr = in.traj_out;
   for (int tau = 0; tau <= H; ++tau) {
     tr[7 * tau + 0] = (fr.ox_h + qx) + fr.ox_l;
@@ -1076,7 +1105,12 @@ static __device__ void serial_trajectory(const KConst& k, const Inst& in, const 
     qy += Tv * (s0 * b1 + c0 * a1);
     q2 += Tv * k.inv_l2 * (a2 - k.k_hitch * b2 * tq);
     q1 += Tv * tq * k.inv_l1;
-    qv += k.Ts * ustar[3 * tau + 0];
+    if (k.jerk) {
+      qv += k.Ts * qa;
+      qa += k.Ts * ustar[3 * tau + 0];
+    } else {
+      qv += k.Ts * ustar[3 * tau + 0];
+    }
     qd += k.Ts * ustar[3 * tau + 1];
     qp += k.Ts * ustar[3 * tau + 2];
   }

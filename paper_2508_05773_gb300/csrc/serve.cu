@@ -367,7 +367,7 @@ brmppi_status brmppi_submit(brmppi_ctx* c, uint32_t vid, const double x0[7], con
   Server* sv = c->server;
   if (!sv) return BRMPPI_EINVAL;
   if (!x0 || (n_obs > 0 && !obs) || n_obs < 0 || n_obs > sv->max_obs) return BRMPPI_EINVAL;
-  for (int j = 0; j < 7; ++j)
+  for (int j = 0; j < state_dim(c->prm); ++j)
     if (!std::isfinite(x0[j])) return BRMPPI_ENONFINITE;
   for (int o = 0; o < n_obs; ++o)
     if (!exponent_ok(c->prm, obs[obs_floats(c->prm) * o + 5])) return BRMPPI_EINVAL;
@@ -378,7 +378,7 @@ brmppi_status brmppi_submit(brmppi_ctx* c, uint32_t vid, const double x0[7], con
     const int s = sv->free_slots.back();
     sv->free_slots.pop_back();
     unsigned char* h = sv->h_in + static_cast<size_t>(s) * sv->in_stride;
-    std::memcpy(h, x0, 7 * sizeof(double));
+    std::memcpy(h, x0, state_dim(c->prm) * sizeof(double));  // 64 bytes reserved
     if (n_obs > 0) std::memcpy(h + 64, obs, sizeof(float) * obs_floats(c->prm) * n_obs);
     Slot& sl = sv->slots[s];
     sl.state = kQueued;

@@ -59,7 +59,7 @@ def test_params_struct_layout_matches(lib):
 @pytest.mark.parametrize("field,value", [
     ("S", 0), ("H", 0), ("H", 5000), ("max_obstacles", -1), ("max_obstacles", 125),
     ("max_path_pts", 1), ("threads_per_sample", 3), ("block_threads", 48), ("Ts", 0.0),
-    ("lambda_", -1.0), ("h_floor", 0.0), ("flags", 0x20), ("abi_version", 99),
+    ("lambda_", -1.0), ("h_floor", 0.0), ("flags", 0x40), ("abi_version", 99),
     ("max_batch", -1), ("batch_threads_per_sample", 5), ("batch_block_threads", 1000),
     ("max_vehicles", -2), ("serve_lanes", 99), ("serve_max_batch", -1), ("serve_queue", -5),
     ("q_coll", -1.0), ("alpha_stab", 0.0), ("alpha_stab", 1.5), ("q_abuf", -1.0), ("h_buf", 0.0),
@@ -111,4 +111,15 @@ def test_third_order_needs_the_rear_axle_disc(lib):
         pkg.brmppi_create(p, 0)
     assert ei.value.status == pkg.BRMPPI_EINVAL
     assert "third-order" in pkg.brmppi_last_error(None)
+
+
+def test_jerk_model_needs_the_rear_axle_disc(lib):
+    import paper_2508_05773_gb300 as pkg
+    p = pkg.brmppi_default_params()
+    p.flags = pkg.BRMPPI_FLAG_JERK_MODEL
+    p.n_discs = 3
+    with pytest.raises(pkg.BrmppiError) as ei:
+        pkg.brmppi_create(p, 0)
+    assert ei.value.status == pkg.BRMPPI_EINVAL
+    assert "jerk" in pkg.brmppi_last_error(None)
 

@@ -383,3 +383,76 @@ def test_third_order_with_moving_superellipses(pkg):
     p, ref = _oracle(c, flags=flags)
     out = _gpu(pkg, c, flags=flags)
     assert_solve_matches(out, ref, p, "third order + moving")
+
+
+# ------------------------------------------------------------ jerk-input model
+def _ref7(ref):
+    out = dict(ref)
+    out["traj"] = ref["traj"][:, :7]  # the GPU outputs keep 7 state columns
+    return out
+
+
+@pytest.mark.parametrize("tps", [0, 1, 4, 8])
+def test_jerk_model(pkg, tps):
+    c = sc.jerk_model(sc.small_random(101, S=300, H=20, n_obs=5), a0=0.3, seed=1)
+    p, ref = _oracle(c)
+    out = _gpu(pkg, c, tps=tps)
+    assert_solve_matches(out, _ref7(ref), p, f"jerk tps={tps}")
+
+
+def test_jerk_model_third_order_and_moving(pkg):
+    c = sc.jerk_model(sc.with_moving(sc.small_random(103, S=300, H=20, n_obs=5), 2), a0=-0.4, seed=2)
+    flags = c["params"]["flags"] | sc.FLAG_THIRD_ORDER
+    p, ref = _oracle(c, flags=flags)
+    out = _gpu(pkg, c, flags=flags)
+    assert_solve_matches(out, _ref7(ref), p, "jerk third order + moving")
+
+
+def test_jerk_model_stabilizer(pkg, torch):
+    pd = sc.params(flags=sc.FLAG_JERK, alpha_stab=0.6)
+    p = sc.as_float32(pd)
+    rng = np.random.default_rng(7)
+    X, U = _stab_cases(sc.as_float32(sc.params(alpha_stab=0.6)), rng, 600)
+    X = np.hstack([X, rng.uniform(-1.0, 1.0, (len(X), 1))])  # acceleration state
+    s = pkg.Solver(pd)
+    try:
+        out = torch.zeros((len(X), 4), dtype=torch.float32, device="cuda")
+        s.hitch_stabilize_device(torch.from_numpy(X).cuda(), torch.from_numpy(U).cuda(), out)
+        torch.cuda.synchronize()
+        G = out.cpu().numpy().astype(np.float64)
+    finally:
+        s.close()
+    for i in range(len(X)):
+        st, o, slack = oracle.hitch_stabilize(p, X[i], U[i].astype(np.float64))
+        Au, h, br = oracle.jerk_hitch_row(p, X[i])
+        tol, eps_rhs = stab_tolerance(p, X[i], Au[:2], o)
+        eps_rhs += 8 * 2.0 ** -23 * abs(X[i][7] * 0.05)  # the folded a-term
+        assert abs(G[i, 3] - slack) <= 4 * eps_rhs + float(np.abs(Au[:2]) @ tol) + 1e-6, (i, G[i], slack)
+        if st == 1 and slack < -4 * eps_rhs - 1e-6:
+            np.testing.assert_array_equal(G[i, :2], o[:2].astype(np.float32), err_msg=str(i))
+            continue
+        assert np.all(np.abs(G[i, :2] - o[:2]) <= tol + 1e-5), (i, G[i], o, tol)
+
+
+def test_jerk_model_batch(pkg, torch):
+    rng = np.random.default_rng(104)
+    cases = [sc.jerk_model(sc.small_random(int(rng.integers(1 << 30)), S=int(rng.integers(50, 300)), H=16,
+                                           n_obs=int(rng.integers(0, 6))), a0=float(rng.uniform(-1, 1)),
+                           seed=k) for k in range(6)]
+    pd = cases[0]["params"] | dict(S=300, H=16)
+    s = pkg.Solver(pd, max_obstacles=6, max_path_pts=512, max_batch=8)
+    try:
+        t = lambda a, dt=torch.float32: torch.as_tensor(np.asarray(a), dtype=dt, device="cuda")
+        insts = [dict(x0=t(c["x0"], torch.float64), U_nom=t(c["U_nom"]),
+                      obs=t(c["obs"]) if len(c["obs"]) else None, path=t(c["path"]), ds=c["ds"],
+                      S=c["params"]["S"], seed=c["seed"], counter=c["counter"],
+                      U_out=torch.zeros((16, 3), device="cuda"), traj_out=torch.zeros((17, 7), device="cuda"),
+                      J_out=torch.zeros(c["params"]["S"], device="cuda")) for c in cases]
+        s.solve_batch(insts)
+        torch.cuda.synchronize()
+        for k, (c, q) in enumerate(zip(cases, insts)):
+            p, ref = _oracle(c)
+            out = dict(U=q["U_out"].cpu().numpy(), traj=q["traj_out"].cpu().numpy(), J=q["J_out"].cpu().numpy())
+            assert_solve_matches(out, _ref7(ref), p, f"jerk batch {k}")
+    finally:
+        s.close()
