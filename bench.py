@@ -213,6 +213,7 @@ def measure_batched(dev, reps: int = 10):
     solver = pkg.Solver(base, max_obstacles=16, max_path_pts=npts, max_batch=len(cases))
     stream = torch.cuda.current_stream(dev)
     solver.autotune_batch(insts, reps=2, stream=stream)
+    batch_launch = solver.batch_launch()
     graph = solver.capture_batch(insts)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     times = []
@@ -260,7 +261,7 @@ def measure_batched(dev, reps: int = 10):
             "rollout_steps": work, "value": work / (batched_ms * 1e-3), "unit": UNIT,
             "ms_per_batch": batched_ms, "plain_value": work / (plain_ms * 1e-3),
             "plain_ms_per_batch": plain_ms, "speedup_vs_plain": plain_ms / batched_ms,
-            "launches_per_batch": 1, "plain_launches_per_batch": len(cases),
+            "launches_per_batch": 1, "plain_launches_per_batch": len(cases), "launch": batch_launch,
             "how": "CUDA-graph replay of one persistent launch vs brmppi_solve_device per "
                    "instance on one stream; L2 flushed between batches; median"}
 

@@ -331,6 +331,11 @@ brmppi_status brmppi_server_stats_get(brmppi_ctx *ctx, brmppi_server_stats *out)
 brmppi_status brmppi_get_launch(brmppi_ctx *ctx, int32_t n_obs, int32_t *threads_per_sample,
                                 int32_t *block_threads, int32_t *blocks);
 
+/* Launch configuration batches (and serving batches) of this context use:
+   the autotuned shape after brmppi_autotune_batch, else the default for the
+   context's obstacle capacity.  Threads per block exclude noise warps. */
+brmppi_status brmppi_get_batch_launch(brmppi_ctx *ctx, int32_t *threads_per_sample, int32_t *block_threads);
+
 /* Bytes the host entry point brmppi_solve copies per call for a solve with
    n_obs obstacles and n_pts path rows: *h2d (inputs, one copy) and *d2h
    (U*, trajectory and status, one copy; plus 4*S when costs are asked

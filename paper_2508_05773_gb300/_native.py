@@ -38,7 +38,7 @@ EXPORTS = (
     "brmppi_graph_launch", "brmppi_graph_destroy", "brmppi_autotune", "brmppi_autotune_batch",
     "brmppi_get_launch", "brmppi_transfer_bytes", "brmppi_vehicle_register", "brmppi_submit",
     "brmppi_poll", "brmppi_vehicle_export", "brmppi_vehicle_import", "brmppi_server_stats_get",
-    "brmppi_solve_device_noalloc", "brmppi_hitch_stabilize_device",
+    "brmppi_solve_device_noalloc", "brmppi_hitch_stabilize_device", "brmppi_get_batch_launch",
 )
 
 
@@ -138,6 +138,7 @@ def load() -> ctypes.CDLL:
             "brmppi_autotune_batch": (ctypes.c_int, [_VP, ctypes.POINTER(brmppi_instance),
                                                      ctypes.c_int32, ctypes.c_int32, _VP]),
             "brmppi_get_launch": (ctypes.c_int, [_VP, ctypes.c_int32, _I32, _I32, _I32]),
+            "brmppi_get_batch_launch": (ctypes.c_int, [_VP, _I32, _I32]),
             "brmppi_vehicle_register": (ctypes.c_int, [_VP, ctypes.c_uint32, _F, ctypes.c_int32,
                                                        ctypes.c_float, _F, ctypes.c_uint64]),
             "brmppi_submit": (ctypes.c_int, [_VP, ctypes.c_uint32, _D, _F, ctypes.c_int32,
@@ -460,6 +461,13 @@ class Solver:
 
     def launch(self, n_obs: int) -> dict:
         return brmppi_get_launch(self.ctx, n_obs)
+
+    def batch_launch(self) -> dict:
+        tps, thr = ctypes.c_int32(), ctypes.c_int32()
+        st = load().brmppi_get_batch_launch(self.ctx, ctypes.byref(tps), ctypes.byref(thr))
+        if st != BRMPPI_OK:
+            raise BrmppiError(st, brmppi_last_error(self.ctx))
+        return dict(threads_per_sample=tps.value, block_threads=thr.value)
 
     def transfer_bytes(self, n_obs: int, n_pts: int):
         return brmppi_transfer_bytes(self.ctx, n_obs, n_pts)

@@ -955,6 +955,16 @@ brmppi_status brmppi_autotune_batch(brmppi_ctx* c, const brmppi_instance* inst, 
   return BRMPPI_OK;
 }
 
+brmppi_status brmppi_get_batch_launch(brmppi_ctx* c, int32_t* tps, int32_t* threads) {
+  if (!c) return BRMPPI_EINVAL;
+  Shape sh;
+  if (!batch_shape_default(c, philox_blocks(rows_of(c->prm, c->prm.max_obstacles)), &sh))
+    return fail(c, BRMPPI_EINVAL, "no batch launch shape");
+  if (tps) *tps = sh.tps;
+  if (threads) *threads = sh.threads;
+  return BRMPPI_OK;
+}
+
 brmppi_status brmppi_get_launch(brmppi_ctx* c, int32_t n_obs, int32_t* tps, int32_t* threads, int32_t* blocks) {
   if (!c) return BRMPPI_EINVAL;
   if (n_obs < 0 || n_obs > c->prm.max_obstacles) return fail(c, BRMPPI_EINVAL, "n_obs out of range");

@@ -5,12 +5,16 @@
 // with the BR-MPPI rollout of Sec. IV-A):
 //
 //   for each sample s, step tau:
-//     noise        Philox4x32-10 + Box-Muller, recomputed in registers
+//     noise        Philox4x32-10 + Box-Muller, recomputed (never stored in
+//                  HBM): in registers a step ahead (one lane per sample) or
+//                  by noise warps into shared memory (wider teams)
 //     sample       z_des = clip(U_nom + sigma n), u^alpha_des = clip(sigma_a n)
 //     rows         barrier-rate equality per constraint (Eq. cbf_equality):
-//                  hitch (Eq. hitch_angle_barrier) and ellipses
+//                  hitch (Eq. hitch_angle_barrier) and obstacles
 //                  (Eq. barrier_function) through the second-order expansion
-//                  of Eq. barrier_function_approx
+//                  of Eq. barrier_function_approx (optionally third order for
+//                  obstacles; moving and e = 4 obstacles, footprint discs, the
+//                  jerk-input model: the extended instantiations)
 //     projection   Eq. closed-form_projection in Woodbury form (below)
 //     apply        u = clip(z*_u), alpha += z*_alpha
 //     dynamics     explicit Euler (Eq. tt_discrete_kinematics)
@@ -26,11 +30,11 @@
 // so a solve gives the same bits alone or inside any batch with the same
 // launch shape.
 //
-// Team decomposition: TPS consecutive lanes own one sample.  Lane j owns
-// Philox blocks b = j, j + TPS, ... (< ceil(d/4)), i.e. the normals
-// q = 4b..4b+3 and with them the constraints i = q - 3; block 0 (lane 0)
-// carries the three input normals and the hitch row.  The rank-2 structure
-// of the projection makes the cross-lane exchange five floats per step.
+// Team decomposition: TPS consecutive lanes own one sample.  Every lane of
+// a team computes the hitch row (its terms enter the team sums once); the
+// obstacle rows are spread round-robin over the team (row j on lane
+// j % TPS), each with its noise normal 4 + j.  The rank-2 structure of the
+// projection makes the cross-lane exchange five floats per step.
 //
 // Projection in Woodbury form.  A = [A_u | diag(h~)] where only the a and
 // omega columns of A_u are non-zero, M = diag(m_u, m_alpha):
