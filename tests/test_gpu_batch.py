@@ -189,3 +189,44 @@ def test_autotune_keeps_results_within_tolerance(pkg):
         assert_solve_matches(out, ref, p, f"autotuned {launch}")
     finally:
         s.close()
+
+
+@pytest.mark.slow
+def test_config3_full_batch_sampled(pkg):
+    """The full 256-instance config-3 batch in one persistent launch with
+    the shape the bench times (one lane per sample, 256 threads, capacity
+    16 obstacles): four instances (the largest S and H among them) against
+    the full oracle solve, and sampled rollouts of eight more compared one
+    by one (cost and applied inputs are per sample, so the oracle computes
+    them alone)."""
+    import torch
+    dev = torch.device("cuda:0")
+    cases = sc.config3()
+    Smax = max(int(c["params"]["S"]) for c in cases)
+    Hmax = max(int(c["params"]["H"]) for c in cases)
+    npts = max(c["path"].shape[0] for c in cases)
+    s = pkg.Solver(dict(cases[0]["params"], S=Smax, H=Hmax), max_obstacles=16, max_path_pts=npts,
+                   max_batch=len(cases), batch_threads_per_sample=1, batch_block_threads=256)
+    try:
+        insts = [_device_inst(c, dev) for c in cases]
+        s.solve_batch(insts)
+        torch.cuda.synchronize()
+        assert all(int(d["status"].item()) == 0 for d in insts)
+        order = sorted(range(len(cases)), key=lambda i: -int(cases[i]["params"]["S"]) * int(cases[i]["params"]["H"]))
+        for i in [order[0], order[1], order[len(order) // 2], order[-1]]:
+            c = cases[i]
+            p = sc.as_float32(c["params"])
+            ref = oracle.solve(p, c["x0"], c["U_nom"], c["obs"], c["path"], c["ds"], c["seed"], c["counter"],
+                               want_uhist=True)
+            assert_solve_matches(_out(insts[i]), ref, p, f"config-3 instance {i}")
+        rng = np.random.default_rng(0)
+        for i in rng.choice(len(cases), 8, replace=False):
+            c = cases[int(i)]
+            p = sc.as_float32(c["params"])
+            J = insts[int(i)]["J_out"].cpu().numpy()
+            for smp in rng.choice(int(c["params"]["S"]), 3, replace=False):
+                one = oracle.rollout_sample(p, c["x0"], c["U_nom"], c["obs"], c["path"], c["ds"], c["seed"],
+                                            c["counter"], int(smp))
+                assert abs(J[smp] - one["J"]) <= 2.0 ** -18 * abs(one["J"]), (int(i), int(smp))
+    finally:
+        s.close()

@@ -153,3 +153,26 @@ def test_backpressure_and_errors(pkg):
         assert srv.submit(0, x, c["obs"])[0] == pkg.BRMPPI_ENONFINITE
     finally:
         srv.close()
+
+
+def test_config4_full_size_request(pkg):
+    """A served request of the config-4 size (S=4096, H=50, obstacles as in
+    config 3) through the serving loop's own launch shape, against the
+    oracle on the state and warm start it was solved from."""
+    rng = np.random.default_rng(4)
+    c = sc.random_instance(rng, S_choices=(4096,), H_range=(50, 50), obs_range=(12, 12))
+    pd = sc.params(S=4096, H=50)
+    srv = pkg.Solver(pd, max_obstacles=16, max_path_pts=1024, max_vehicles=4, serve_lanes=2,
+                     serve_max_batch=16)
+    try:
+        srv.register(0, c["path"], c["ds"], c["U_nom"], c["seed"])
+        U0, seed, ctr = srv.vehicle_export(0)
+        st, t = srv.submit(0, c["x0"], c["obs"])
+        assert st == 0
+        st, U, traj, lat = _wait(srv, t)
+        assert st == 0
+        p = sc.as_float32(pd)
+        ref = oracle.solve(p, c["x0"], U0, c["obs"], c["path"], c["ds"], seed, ctr, want_uhist=True)
+        assert_solve_matches(dict(U=U, traj=traj, J=None), ref, p, "config-4 request", check_J=False)
+    finally:
+        srv.close()
