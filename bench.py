@@ -588,55 +588,93 @@ def measure_serving(rates=(2000, 10000, 50000), duration=2.0, warm=0.5, n_vehicl
             "rates": results}
 
 
-def run_cpu_baseline(budget_s: float = 12.0):
-    """The FP64 oracle on host cores (single thread) on full config-2 solves,
-    as many ticks as fit the budget (at least one)."""
+_WORKER_CASE = None
+
+
+def _oracle_worker(task):
+    """One worker process of the CPU baseline: FP64 oracle solves of the
+    config-2 workload (S_run rollouts each, counters from `first` on) until
+    `budget_s` has passed (at least `min_solves`).  Returns (solves, seconds)."""
+    S_run, first, budget_s, min_solves = task
     import oracle
-    from paper_2508_05773_gb300 import scenarios as sc
-    c = sc.config2()
-    p = sc.as_float32(c["params"])
-    S, H = int(p["S"]), int(p["H"])
+    global _WORKER_CASE
+    if _WORKER_CASE is None:
+        from paper_2508_05773_gb300 import scenarios as sc
+        c = sc.config2()
+        _WORKER_CASE = c, sc.as_float32(c["params"])
+    c, p = _WORKER_CASE
     t0 = time.perf_counter()
     n = 0
-    while True:
-        oracle.solve(p, c["x0"], c["U_nom"], c["obs"], c["path"], c["ds"], c["seed"], n,
+    while n < min_solves or time.perf_counter() - t0 < budget_s:
+        oracle.solve(p, c["x0"], c["U_nom"], c["obs"], c["path"], c["ds"], c["seed"], first + n, S=S_run,
                      want_J=False)
         n += 1
-        if time.perf_counter() - t0 > budget_s:
-            break
-    el = time.perf_counter() - t0
-    return {"value": n * S * H / el, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{n} full solves (S={S}, H={H}, 8 obstacles) of the same workload, "
-                      f"FP64, single thread, {el:.1f} s"}
+    return n, time.perf_counter() - t0
+
+
+def _oracle_pool():
+    """Worker processes on every host core (spawned: a forked child of a
+    CUDA process can hang), imports done before any timing."""
+    import multiprocessing as mp
+    cores = os.cpu_count() or 1
+    pool = mp.get_context("spawn").Pool(cores)
+    pool.map(_oracle_worker, [(1, 10 ** 6 + i, 0.0, 1) for i in range(cores)])
+    return pool, cores
+
+
+def run_cpu_baseline(budget_s: float = 12.0):
+    """The FP64 oracle on every host core (one process per core, independent
+    full config-2 solves, different noise counters), about budget_s of
+    work: rollout-steps of all cores per wall second."""
+    from paper_2508_05773_gb300 import scenarios as sc
+    p = sc.config2()["params"]
+    S, H = int(p["S"]), int(p["H"])
+    pool, cores = _oracle_pool()
+    try:
+        t0 = time.perf_counter()
+        res = pool.map(_oracle_worker, [(S, 1000 * w, budget_s, 1) for w in range(cores)])
+        el = time.perf_counter() - t0
+    finally:
+        pool.close()
+        pool.join()
+    n = sum(r[0] for r in res)
+    return {"value": n * S * H / el, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{n} full solves (S={S}, H={H}, 8 obstacles) of the same workload on {cores} "
+                      f"processes (one per core), FP64, {el:.1f} s"}
 
 
 def run_reference(args, world, rank):
-    """Reference arm: the oracle as it stands, on bounded samples of the
-    workload (512 of the 4096 rollouts of each solve)."""
+    """Reference arm: the oracle as it stands, on every host core; each
+    step is a bounded sample of the workload (512 of the 4096 rollouts of a
+    solve per core, one process per core, different noise counters)."""
     if rank != 0:
         return 0
-    import oracle
     from paper_2508_05773_gb300 import scenarios as sc
     c = sc.config2()
-    p = sc.as_float32(c["params"])
+    p = c["params"]
     S_sample, H = 512, int(p["H"])
-    for i in range(args.warmup):
-        oracle.solve(p, c["x0"], c["U_nom"], c["obs"], c["path"], c["ds"], c["seed"], i,
-                     S=S_sample, want_J=False)
-    t0 = time.perf_counter()
-    for i in range(args.steps):
-        oracle.solve(p, c["x0"], c["U_nom"], c["obs"], c["path"], c["ds"], c["seed"], i,
-                     S=S_sample, want_J=False)
-    el = time.perf_counter() - t0
-    value = args.steps * S_sample * H / el
+    pool, cores = _oracle_pool()
+    try:
+        for i in range(args.warmup):
+            pool.map(_oracle_worker, [(S_sample, 10 ** 5 * i + w, 0.0, 1) for w in range(cores)])
+        t0 = time.perf_counter()
+        for i in range(args.steps):
+            pool.map(_oracle_worker, [(S_sample, 10 ** 7 + 10 ** 5 * i + w, 0.0, 1) for w in range(cores)])
+        el = time.perf_counter() - t0
+    finally:
+        pool.close()
+        pool.join()
+    value = args.steps * cores * S_sample * H / el
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": _config_block(c, {"rollouts_per_step": S_sample}),
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"{S_sample} of the {int(p['S'])} rollouts of each solve, "
-                                   "FP64 oracle, single thread"},
+        "data": "synthetic", "config": _config_block(c, {"rollouts_per_step": cores * S_sample,
+                                                       "l2": "not applicable (host cores)",
+                                                       "timing": "host wall clock over the timed steps"}),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{S_sample} of the {int(p['S'])} rollouts of a solve on each of {cores} "
+                                   "processes (one per core) per step, FP64 oracle"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         "gpu_launches": 0,
     }
