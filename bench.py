@@ -256,12 +256,19 @@ def measure_batched(dev, reps: int = 10):
     for s in ctxs.values():
         s.close()
     plain_ms = float(np.median(plain_times))
+    ops = sum(int(c["params"]["S"]) * int(c["params"]["H"]) * ops_per_rollout_step(int(c["obs"].shape[0]))
+              for c in cases)
+    peak_ops = N_SM * FP32_LANES_PER_SM * float(_measured_peaks().get("sm_max_mhz", 2070.0)) * 1e6
+    achieved = ops / (batched_ms * 1e-3)
     return {"workload": "256 uneven solves: S in {1024,2048,4096,8192}, H in [30,80], "
                         "0-16 ellipses, random straight+arc paths (seed 1)",
             "rollout_steps": work, "value": work / (batched_ms * 1e-3), "unit": UNIT,
             "ms_per_batch": batched_ms, "plain_value": work / (plain_ms * 1e-3),
             "plain_ms_per_batch": plain_ms, "speedup_vs_plain": plain_ms / batched_ms,
             "launches_per_batch": 1, "plain_launches_per_batch": len(cases), "launch": batch_launch,
+            "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
+                         "unit": "Tops/s (FP32 lane ops)", "frac": achieved / peak_ops,
+                         "ops_per_launch": ops, "kernel": "solve_kernel (persistent batch launch)"},
             "how": "CUDA-graph replay of one persistent launch vs brmppi_solve_device per "
                    "instance on one stream; L2 flushed between batches; median"}
 
@@ -468,7 +475,9 @@ def run_profile(args):
     config-2 solve (S=4096, H=50, 8 ellipses), `batch` = the config-3 batch
     (256 uneven instances, one persistent launch), each with a fixed launch
     shape (--tps / --threads; defaults: the shapes the autotuners pick on
-    GB300).  Four launches with an L2 flush before each; capture the last."""
+    GB300), `stress` / `stress_stored` = the config-5 solve (S=65536, H=100,
+    64 ellipses) without / with every sample's states stored (185 MB).
+    Four launches with an L2 flush before each; capture the last."""
     import torch
     import paper_2508_05773_gb300 as pkg
     from paper_2508_05773_gb300 import scenarios as sc
@@ -486,6 +495,25 @@ def run_profile(args):
             flush.zero_()
             if solver.solve_device(x0, U, obs, path, c["ds"], c["seed"], r, Uo, tr) != 0:
                 raise RuntimeError(pkg.brmppi_last_error(solver.ctx))
+    elif args.profile in ("stress", "stress_stored"):
+        c = sc.config5()
+        S, H = int(c["params"]["S"]), int(c["params"]["H"])
+        n_obs = int(c["obs"].shape[0])
+        solver = pkg.Solver(c["params"], max_obstacles=n_obs, max_path_pts=c["path"].shape[0],
+                            threads_per_sample=args.tps or 8, block_threads=args.threads or 256)
+        inst = dict(x0=t(c["x0"], torch.float64), U_nom=t(c["U_nom"]), obs=t(c["obs"]), path=t(c["path"]),
+                    ds=c["ds"], S=S, seed=c["seed"], counter=0,
+                    U_out=torch.empty((H, 3), device=dev), traj_out=torch.empty((H + 1, 7), device=dev),
+                    status=torch.zeros(1, dtype=torch.int32, device=dev))
+        if args.profile == "stress_stored":
+            inst["states_out"] = torch.empty((S, H + 1, 7), device=dev)
+        stream = torch.cuda.current_stream(dev)
+        for r in range(4):
+            flush.zero_()
+            solver.solve_device_ex(dict(inst, counter=r), stream)
+        torch.cuda.synchronize()
+        if int(inst["status"].item()) != 0:
+            raise RuntimeError("config-5 solve failed")
     else:
         cases, insts = _config3_instances(dev)
         Smax = max(int(c["params"]["S"]) for c in cases)
@@ -622,25 +650,43 @@ def _oracle_pool():
     return pool, cores
 
 
+def _cpu_model():
+    """The host CPU's model name (x86: `model name`; Arm: implementer/part)."""
+    import platform
+    try:
+        info = open("/proc/cpuinfo").read().splitlines()
+    except OSError:
+        return platform.machine()
+    for key in ("model name", "Model"):
+        for ln in info:
+            if ln.startswith(key) and ":" in ln:
+                return ln.split(":", 1)[1].strip()
+    part = [ln.split(":", 1)[1].strip() for ln in info if ln.startswith(("CPU implementer", "CPU part"))]
+    return f"{platform.machine()} (implementer/part {'/'.join(part[:2])})" if part else platform.machine()
+
+
 def run_cpu_baseline(budget_s: float = 12.0):
-    """The FP64 oracle on every host core (one process per core, independent
-    full config-2 solves, different noise counters), about budget_s of
-    work: rollout-steps of all cores per wall second."""
+    """The FP64 oracle on the host cores, full config-2 solves: first one
+    process alone (about a third of budget_s), then one process per core
+    (independent solves, different noise counters) for the rest;
+    rollout-steps per wall second of all cores, the single core beside it."""
     from paper_2508_05773_gb300 import scenarios as sc
     p = sc.config2()["params"]
     S, H = int(p["S"]), int(p["H"])
     pool, cores = _oracle_pool()
     try:
+        n1, el1 = pool.apply(_oracle_worker, ((S, 5 * 10 ** 6, budget_s / 3.0, 1),))
         t0 = time.perf_counter()
-        res = pool.map(_oracle_worker, [(S, 1000 * w, budget_s, 1) for w in range(cores)])
+        res = pool.map(_oracle_worker, [(S, 1000 * w, 2.0 * budget_s / 3.0, 1) for w in range(cores)])
         el = time.perf_counter() - t0
     finally:
         pool.close()
         pool.join()
     n = sum(r[0] for r in res)
     return {"value": n * S * H / el, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "single_core_value": n1 * S * H / el1, "cpu": _cpu_model(),
             "sample": f"{n} full solves (S={S}, H={H}, 8 obstacles) of the same workload on {cores} "
-                      f"processes (one per core), FP64, {el:.1f} s"}
+                      f"processes (one per core), FP64, {el:.1f} s; single core: {n1} solves in {el1:.1f} s"}
 
 
 def run_reference(args, world, rank):
@@ -829,7 +875,7 @@ def main():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-stress", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
-    ap.add_argument("--profile", choices=("solve", "batch"), default=None,
+    ap.add_argument("--profile", choices=("solve", "batch", "stress", "stress_stored"), default=None,
                     help="a few launches of one workload for ncu, no timing")
     ap.add_argument("--tps", type=int, default=0, help="--profile: threads per sample")
     ap.add_argument("--threads", type=int, default=0, help="--profile: threads per block")
