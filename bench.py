@@ -76,16 +76,24 @@ def _dist_env():
     return world, rank, local
 
 
+def kernel_source_hash() -> str:
+    """First 16 hex digits of the SHA-256 of the solve kernel's device code
+    and launch logic (rollout.cuh, then kernels.cu)."""
+    import hashlib
+    h = hashlib.sha256()
+    for name in ("rollout.cuh", "kernels.cu"):
+        with open(os.path.join(ROOT, "paper_2508_05773_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
 def _traffic_for_current_kernel():
     """DRAM bytes per launch of the config-2 solve from the committed ncu
     capture, or None when the kernel source changed since that capture."""
-    import hashlib
     try:
         with open(os.path.join(ROOT, "profiles", "traffic_config2.json")) as f:
             rec = json.load(f)
-        src = os.path.join(ROOT, "paper_2508_05773_gb300", "csrc", "rollout.cuh")
-        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-        if h != rec["rollout_cuh_sha256_16"]:
+        if kernel_source_hash() != rec["kernel_source_sha256_16"]:
             return None
         return int(rec["dram_read_bytes"]) + int(rec["dram_write_bytes"])
     except Exception:

@@ -89,6 +89,11 @@ int noise_warps(int tps, int bpt, int threads, int P) {
   if (tps <= 1 || bpt > 2) return 0;  // the team's lanes draw (or stage) the blocks themselves
   const int blocks_per_step = P * (threads / tps);
   int w = (blocks_per_step + 63) / 64;  // at most two Philox blocks per producer lane and step
+  // and at least one producer per compute warp: warps go to the four
+  // schedulers round-robin, so each compute warp then shares its scheduler
+  // with the same producer load (two producers for four compute warps left
+  // two schedulers slower, and the step barrier waits for the slowest)
+  if (w < threads / 32) w = threads / 32;
   const int room = (kMaxBlockThreads - threads) / 32;
   w = w > 4 ? 4 : w;
   w = w > room ? room : w;
