@@ -985,20 +985,39 @@ __device__ void run_tile(const KConst& k, const Inst& in, int tile, float* uh, c
   }
 }
 
+// Exclusive prefix sum over the 32 lanes of a warp (lane order), offset by
+// `carry`; `carry` advances by the warp's total (chunked scans).
+static __device__ __forceinline__ float warp_exclusive_scan(float x, float& carry) {
+  const int lane = threadIdx.x & 31;
+  float s = x;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const float y = __shfl_up_sync(0xffffffffu, s, o);
+    if (lane >= o) s += y;
+  }
+  const float total = __shfl_sync(0xffffffffu, s, 31);
+  float e = __shfl_up_sync(0xffffffffu, s, 1);
+  if (lane == 0) e = 0.f;
+  const float r = carry + e;
+  carry += total;
+  return r;
+}
+
 // --------------------------------------- merge of an instance's partials
 // Run by the CTA that finished the instance's last tile: global minimum
 // pair, rescaled sums in tile order, U*, warm start, status and the optimal
 // trajectory (x0 integrated with U*).
 // Optimal trajectory: x0 integrated with U* in the relative frame (explicit
-// Euler, as the rollouts).  Speed, steer angle and progress are prefix sums
-// of U*, the tractor heading an FMA chain; only the trailer angle is a
-// nonlinear recurrence.  So the CTA computes the per-step terms in parallel
-// around short serial chains (thread 0: headings; warp 1's first lane:
-// positions), in `scratch` (8 (H+1) floats: the instance's tile partials,
-// consumed by then).
-// The elementary functions are the SFU approximations (absolute error
-// ~2^-21 per call, far inside the trajectory tolerance).
-static __device__ void optimal_trajectory(const KConst& k, const Inst& in, const Smem& S, Shared& sh, float* scratch) {
+// Euler, as the rollouts).  Speed, steer angle, progress, the acceleration
+// of the jerk-input model and the tractor heading are prefix sums, scanned
+// by warp 0 32 steps at a time; the trailer angle is the one nonlinear
+// recurrence (thread 0, serial) while warp 1 scans the positions.  Per-step
+// values go to `scratch` (8 (H+1) floats: the CTA's table regions when they
+// can hold them, else the instance's consumed tile partials).  The
+// elementary functions are the SFU approximations (absolute error ~2^-21
+// per call, far inside the trajectory tolerance).
+static __device__ void optimal_trajectory(const KConst& k, const Inst& in, const Smem& S, Shared& sh,
+                                          float* __restrict__ scratch) {
   const int H = in.H, n = H + 1;
   const Frame& fr = sh.fr;
   float* V = scratch;          // speed
@@ -1009,67 +1028,78 @@ static __device__ void optimal_trajectory(const KConst& k, const Inst& in, const
   float* B = scratch + 5 * n;  // trailer heading
   float* X = scratch + 6 * n;  // x
   float* Y = scratch + 7 * n;  // y
-  const float* ustar = S.ustar;
+  const float* __restrict__ ustar = S.ustar;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const float Ts = k.Ts;
   __syncthreads();
-  if (threadIdx.x == 0) {
-    float qv = fr.v_h + fr.v_l, qd = fr.dl, qp = 0.f, qa = fr.a0;
-    for (int tau = 0; tau <= H; ++tau) {
-      V[tau] = qv;
-      D[tau] = qd;
-      Q[tau] = qp;
-      if (tau < H) {
-        if (k.jerk) {
-          qv += k.Ts * qa;
-          qa += k.Ts * ustar[3 * tau + 0];
-        } else {
-          qv += k.Ts * ustar[3 * tau + 0];
-        }
-        qd += k.Ts * ustar[3 * tau + 1];
-        qp += k.Ts * ustar[3 * tau + 2];
+  if (warp == 0) {
+    float cv = fr.v_h + fr.v_l, cd = fr.dl, cq = 0.f, ca = fr.a0, c1 = 0.f;
+    for (int base = 0; base < n; base += 32) {
+      const int tau = base + lane;
+      const bool step = tau < H;  // an input acts at tau < H; states run to H
+      const float u0 = step ? ustar[3 * tau + 0] : 0.f;
+      const float u1 = step ? ustar[3 * tau + 1] : 0.f;
+      const float u2 = step ? ustar[3 * tau + 2] : 0.f;
+      float iv = Ts * u0;
+      if (k.jerk) {  // the speed integrates the acceleration state
+        const float acc = warp_exclusive_scan(Ts * u0, ca);
+        iv = step ? Ts * acc : 0.f;
+      }
+      const float v = warp_exclusive_scan(iv, cv);
+      const float d = warp_exclusive_scan(Ts * u1, cd);
+      const float q = warp_exclusive_scan(Ts * u2, cq);
+      float sd, cs;
+      __sincosf(d, &sd, &cs);
+      const float t = __fdividef(sd, cs);
+      const float a = warp_exclusive_scan(step ? (Ts * v) * t * k.inv_l1 : 0.f, c1);
+      if (tau < n) {
+        V[tau] = v;
+        D[tau] = d;
+        Q[tau] = q;
+        T[tau] = t;
+        A[tau] = a;
       }
     }
   }
   __syncthreads();
-  for (int tau = threadIdx.x; tau < H; tau += blockDim.x) {
-    float ad, bd;
-    __sincosf(D[tau], &ad, &bd);
-    T[tau] = __fdividef(ad, bd);
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    float q1 = 0.f;
-    for (int tau = 0; tau <= H; ++tau) {
-      A[tau] = q1;
-      if (tau < H) q1 += (k.Ts * V[tau]) * T[tau] * k.inv_l1;
-    }
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {  // trailer angle
-    float q2 = fr.t2;
-    for (int tau = 0; tau <= H; ++tau) {
-      B[tau] = q2;
-      if (tau < H) {
-        float a2, b2;
-        __sincosf(A[tau] - q2, &a2, &b2);
-        q2 += (k.Ts * V[tau]) * k.inv_l2 * (a2 - k.k_hitch * b2 * T[tau]);
-      }
-    }
-  } else if (threadIdx.x == 32) {  // position
-    const float c0 = fr.c0, s0 = fr.s0;
-    float qx = 0.f, qy = 0.f;
-    for (int tau = 0; tau <= H; ++tau) {
-      X[tau] = qx;
-      Y[tau] = qy;
+  const float c0 = fr.c0, s0 = fr.s0;
+  auto positions = [&]() {  // one warp
+    float cx = 0.f, cy = 0.f;
+    for (int base = 0; base < n; base += 32) {
+      const int tau = base + lane;
+      float ix = 0.f, iy = 0.f;
       if (tau < H) {
         float a1, b1;
         __sincosf(A[tau], &a1, &b1);
-        const float Tv = k.Ts * V[tau];
-        qx += Tv * (c0 * b1 - s0 * a1);
-        qy += Tv * (s0 * b1 + c0 * a1);
+        const float Tv = Ts * V[tau];
+        ix = Tv * (c0 * b1 - s0 * a1);
+        iy = Tv * (s0 * b1 + c0 * a1);
+      }
+      const float x = warp_exclusive_scan(ix, cx);
+      const float y = warp_exclusive_scan(iy, cy);
+      if (tau < n) {
+        X[tau] = x;
+        Y[tau] = y;
       }
     }
+  };
+  if (threadIdx.x == 0) {  // trailer angle
+    float q2 = fr.t2;
+#pragma unroll 4
+    for (int tau = 0; tau < H; ++tau) {
+      B[tau] = q2;
+      float a2, b2;
+      __sincosf(A[tau] - q2, &a2, &b2);
+      q2 += (Ts * V[tau]) * k.inv_l2 * (a2 - k.k_hitch * b2 * T[tau]);
+    }
+    B[H] = q2;
   }
+  if (warp == 1) positions();
   __syncthreads();
+  if (blockDim.x < 64 && warp == 0) {  // no second warp: positions after the headings
+    positions();
+    __syncwarp();
+  }
   float* tr = in.traj_out;
   for (int tau = threadIdx.x; tau <= H; tau += blockDim.x) {
     tr[7 * tau + 0] = (fr.ox_h + X[tau]) + fr.ox_l;
@@ -1082,7 +1112,8 @@ static __device__ void optimal_trajectory(const KConst& k, const Inst& in, const
   }
 }
 
-// The same, one thread, no scratch (solves of one or two tiles).
+// The same, one thread, no scratch (when neither scratch region can hold
+// 8 (H+1) floats).
 static __device__ void serial_trajectory(const KConst& k, const Inst& in, const Smem& S, Shared& sh) {
   const Frame& fr = sh.fr;
   const float c0 = fr.c0, s0 = fr.s0;
@@ -1209,8 +1240,12 @@ static __device__ void merge_instance(const KConst& k, const Inst& in, const Sme
     in.sync[0] = 0u;
   }
   if (in.traj_out) {
-    if (static_cast<long long>(in.tiles) * in.part_stride >= 8LL * (H + 1)) {
-      optimal_trajectory(k, in, S, sh, in.part);  // the partials are consumed
+    // scratch: the obstacle, path and nominal-input tables (contiguous, no
+    // longer read by this CTA's merge), else the consumed partials
+    if (static_cast<long long>(S.ustar - S.obs) >= 8LL * (H + 1)) {
+      optimal_trajectory(k, in, S, sh, S.obs);
+    } else if (static_cast<long long>(in.tiles) * in.part_stride >= 8LL * (H + 1)) {
+      optimal_trajectory(k, in, S, sh, in.part);
     } else if (threadIdx.x == 0) {
       serial_trajectory(k, in, S, sh);
     }
