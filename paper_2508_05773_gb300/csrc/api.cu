@@ -292,6 +292,7 @@ brmppi::Inst make_inst(const double* x0, const float* U_nom, const float* obs, i
   in.part_stride = part_stride_for(H);
   in.ds = ds;
   in.inv_ds = 1.0f / ds;
+  in.inv_ds_d = 1.0 / static_cast<double>(ds);
   in.key0 = static_cast<uint32_t>(seed);
   in.key1 = static_cast<uint32_t>(seed >> 32);
   in.ctr = static_cast<uint32_t>(counter);

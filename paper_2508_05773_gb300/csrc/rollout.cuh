@@ -99,6 +99,7 @@ struct Inst {
   unsigned int* sync;  // [0] finished tiles, [1] error bits
   int S, H, n_obs, n_pts, tiles, part_stride;
   float ds, inv_ds;
+  double inv_ds_d;   // 1 / ds in FP64 (path cell of psi0)
   uint32_t key0, key1, ctr;
   int P;             // Philox blocks per step, ceil((4 + n_obs) / 4)
 };
@@ -307,28 +308,47 @@ struct Frame {
   double psi0;
 };
 
-__device__ __forceinline__ void make_frame(const double* x0, float ds, unsigned int* err, Frame& fr,
-                                           bool jerk = false) {
-  bool finite = true;
-  for (int j = 0; j < (jerk ? 8 : 7); ++j) finite = finite && isfinite(x0[j]);
-  fr.a0 = jerk ? static_cast<float>(x0[7]) : 0.f;
-  if (!finite) atomicOr(err, ERR_NONFINITE_X0);
-  split_double(x0[0], fr.ox_h, fr.ox_l);
-  split_double(x0[1], fr.oy_h, fr.oy_l);
-  split_double(x0[2], fr.oth_h, fr.oth_l);
-  float sn, cs;
-  sincosf(fr.oth_h, &sn, &cs);
-  fr.c0 = cs - sn * fr.oth_l;  // cos(hi + lo), lo below one ulp of hi
-  fr.s0 = sn + cs * fr.oth_l;
-  fr.t2 = static_cast<float>(x0[3] - x0[2]);
-  split_double(x0[4], fr.v_h, fr.v_l);
-  fr.dl = static_cast<float>(x0[5]);
-  fr.psi0 = x0[6];
-  split_double(x0[6], fr.psi_h, fr.psi_l);
-  const double q0 = x0[6] / static_cast<double>(ds);
-  const double fq = fmin(fmax(floor(q0), -1.0e9), 1.0e9);
-  fr.i0 = static_cast<int>(fq);
-  fr.qf0 = static_cast<float>(q0 - fq);
+// The frame of x0, built by warp 0: lane j takes state component j, so the
+// FP64 work runs side by side; the path cell of psi0 uses the host's FP64
+// reciprocal of ds (no device division).
+__device__ __forceinline__ void make_frame_warp(const double* x0, double inv_ds, unsigned int* err, Frame& fr,
+                                                bool jerk) {
+  const int lane = threadIdx.x & 31;
+  if (lane >= (jerk ? 8 : 7)) {
+    if (lane == 7) fr.a0 = 0.f;
+    return;
+  }
+  const double x = x0[lane];
+  if (!isfinite(x)) atomicOr(err, ERR_NONFINITE_X0);
+  float hi, lo;
+  split_double(x, hi, lo);
+  switch (lane) {
+    case 0: fr.ox_h = hi; fr.ox_l = lo; break;
+    case 1: fr.oy_h = hi; fr.oy_l = lo; break;
+    case 2: {
+      fr.oth_h = hi;
+      fr.oth_l = lo;
+      float sn, cs;
+      sincosf(hi, &sn, &cs);
+      fr.c0 = cs - sn * lo;  // cos(hi + lo), lo below one ulp of hi
+      fr.s0 = sn + cs * lo;
+      break;
+    }
+    case 3: fr.t2 = static_cast<float>(x - x0[2]); break;
+    case 4: fr.v_h = hi; fr.v_l = lo; break;
+    case 5: fr.dl = static_cast<float>(x); break;
+    case 6: {
+      fr.psi0 = x;
+      fr.psi_h = hi;
+      fr.psi_l = lo;
+      const double q0 = x * inv_ds;
+      const double fq = fmin(fmax(floor(q0), -1.0e9), 1.0e9);
+      fr.i0 = static_cast<int>(fq);
+      fr.qf0 = static_cast<float>(q0 - fq);
+      break;
+    }
+    default: fr.a0 = static_cast<float>(x); break;  // lane 7: acceleration (jerk-input model)
+  }
 }
 
 // Shared memory of a CTA (offsets into the dynamic buffer, floats).
@@ -403,36 +423,49 @@ __device__ void run_tile(const KConst& k, const Inst& in, int tile, float* uh, c
   const int H = in.H;
   const int n_rows = EXT ? in.n_obs * k.nd : in.n_obs;  // obstacle rows (obstacle x disc)
 
-  // --- frame and staging (tables in shared memory, relative coordinates)
-  if (threadIdx.x == 0) make_frame(in.x0, in.ds, in.sync + 1, sh.fr, EXT && k.jerk);
-  __syncthreads();
-  const Frame& fr = sh.fr;
+  // --- frame and staging (tables in shared memory, relative coordinates).
+  // The raw path, the nominal inputs and each thread's first obstacle are
+  // loaded first, so that their global loads overlap warp 0's frame; the
+  // shift into the frame follows the barrier.
   const bool obs8 = EXT && k.obs8;
   const int ostride = obs8 ? 8 : 6;
-  for (int o = threadIdx.x; o < in.n_obs; o += blockDim.x) {
-    const float* ob = in.obs + ostride * o;
+  for (int j = threadIdx.x; j < 3 * in.n_pts; j += blockDim.x) S.path[j] = in.path[j];
+  for (int j = threadIdx.x; j < 3 * H; j += blockDim.x) S.unom[j] = in.U_nom[j];
+  float ob0[8];
+  const bool has_ob0 = static_cast<int>(threadIdx.x) < in.n_obs;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) ob0[q] = (has_ob0 && q < ostride) ? in.obs[ostride * threadIdx.x + q] : 0.f;
+  if (threadIdx.x < 32) make_frame_warp(in.x0, in.inv_ds_d, in.sync + 1, sh.fr, EXT && k.jerk);
+  __syncthreads();
+  const Frame& fr = sh.fr;
+  auto stage_obstacle = [&](int o, float cx, float cy, float ax, float ay, float th, float e, float vx, float vy) {
     float* d = S.obs + 8 * o;
-    const bool e4 = obs8 && ob[5] == 4.0f;
-    if (ob[5] != 2.0f && !e4) atomicOr(in.sync + 1, ERR_EXPONENT);
-    const float Ax = ob[2] + k.r_inflate, Ay = ob[3] + k.r_inflate;
-    d[0] = (ob[0] - fr.ox_h) - fr.ox_l;
-    d[1] = (ob[1] - fr.oy_h) - fr.oy_l;
-    sincosf(ob[4], &d[3], &d[2]);
+    const bool e4 = obs8 && e == 4.0f;
+    if (e != 2.0f && !e4) atomicOr(in.sync + 1, ERR_EXPONENT);
+    const float Ax = ax + k.r_inflate, Ay = ay + k.r_inflate;
+    d[0] = (cx - fr.ox_h) - fr.ox_l;
+    d[1] = (cy - fr.oy_h) - fr.oy_l;
+    float so, co;
+    sincosf(th, &so, &co);
+    d[2] = co;
+    d[3] = so;
     const float ix = 1.0f / (Ax * Ax), iy = 1.0f / (Ay * Ay);
     d[4] = e4 ? -(ix * ix) : ix;
     d[5] = e4 ? iy * iy : iy;
-    const float vx = obs8 ? ob[6] : 0.f, vy = obs8 ? ob[7] : 0.f;
-    d[6] = d[2] * vx + d[3] * vy;
-    d[7] = d[2] * vy - d[3] * vx;
+    d[6] = co * vx + so * vy;
+    d[7] = co * vy - so * vx;
+  };
+  if (has_ob0) stage_obstacle(threadIdx.x, ob0[0], ob0[1], ob0[2], ob0[3], ob0[4], ob0[5], ob0[6], ob0[7]);
+  for (int o = threadIdx.x + blockDim.x; o < in.n_obs; o += blockDim.x) {
+    const float* ob = in.obs + ostride * o;
+    stage_obstacle(o, ob[0], ob[1], ob[2], ob[3], ob[4], ob[5], obs8 ? ob[6] : 0.f, obs8 ? ob[7] : 0.f);
   }
   for (int j = threadIdx.x; j < in.n_pts; j += blockDim.x) {
-    const float* r = in.path + 3 * j;
     float* d = S.path + 3 * j;
-    d[0] = (r[0] - fr.ox_h) - fr.ox_l;
-    d[1] = (r[1] - fr.oy_h) - fr.oy_l;
-    d[2] = (r[2] - fr.oth_h) - fr.oth_l;
+    d[0] = (d[0] - fr.ox_h) - fr.ox_l;
+    d[1] = (d[1] - fr.oy_h) - fr.oy_l;
+    d[2] = (d[2] - fr.oth_h) - fr.oth_l;
   }
-  for (int j = threadIdx.x; j < 3 * H; j += blockDim.x) S.unom[j] = in.U_nom[j];
   if constexpr (EXT) {
 #pragma unroll
     for (int m = 0; m < 8; ++m)
@@ -940,7 +973,7 @@ __device__ void run_tile(const KConst& k, const Inst& in, int tile, float* uh, c
   __syncthreads();
 
   // --- tile softmin partial: min pair, weights, weight sum, weighted inputs
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (warp == 0) {
     float mh = CUDART_INF_F, ml = 0.f;
     for (int t = lane; t < spb; t += 32) {
@@ -967,16 +1000,28 @@ __device__ void run_tile(const KConst& k, const Inst& in, int tile, float* uh, c
   __syncthreads();
   float* part = in.part + static_cast<size_t>(tile) * in.part_stride;
   const int nrows = 3 * H + 1;  // row 3H: the weight sum
-  for (int row = warp; row < nrows; row += nwarps) {
-    float acc = 0.f;
-    if (row < 3 * H) {
-      for (int t = lane; t < spb; t += 32) acc += S.w[t] * uh[row * spb + t];
-    } else {
-      for (int t = lane; t < spb; t += 32) acc += S.w[t];
+  // one thread per row: its spb weighted inputs in sample order, four
+  // chains (samples t mod 4) combined in a fixed order; the row's loads are
+  // issued together (one L2 round trip per row instead of one per warp pass)
+  const bool vec = (spb & 3) == 0 && (reinterpret_cast<uintptr_t>(uh) & 15) == 0;
+  for (int row = threadIdx.x; row < nrows; row += blockDim.x) {
+    float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+    const float* src = uh + static_cast<size_t>(row) * spb;
+    const bool wsum = row == 3 * H;
+    int t = 0;
+    if (vec) {
+#pragma unroll 8
+      for (; t < spb; t += 4) {
+        const float4 w4 = *reinterpret_cast<const float4*>(S.w + t);
+        const float4 v4 = wsum ? make_float4(1.f, 1.f, 1.f, 1.f) : *reinterpret_cast<const float4*>(src + t);
+        a0 += w4.x * v4.x;
+        a1 += w4.y * v4.y;
+        a2 += w4.z * v4.z;
+        a3 += w4.w * v4.w;
+      }
     }
-#pragma unroll
-    for (int m = 16; m > 0; m >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, m);
-    if (lane == 0) part[3 + row] = acc;
+    for (; t < spb; ++t) a0 += S.w[t] * (wsum ? 1.f : src[t]);
+    part[3 + row] = (a0 + a1) + (a2 + a3);
   }
   if (threadIdx.x == 0) {
     part[0] = bmh;
@@ -1188,16 +1233,16 @@ static __device__ void merge_instance(const KConst& k, const Inst& in, const Sme
     const int bend = min(256, nb - b0);
     for (int q = threadIdx.x; q < nrows; q += blockDim.x) {
       // four independent chains (tiles t mod 4), combined in a fixed order;
-      // sixteen L2 loads in flight per pass
+      // thirty-two L2 loads in flight per pass
       float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
       const float* col = in.part + static_cast<size_t>(b0) * stride + 3 + q;
       int t = 0;
-      for (; t + 16 <= bend; t += 16) {
-        float v[16];
+      for (; t + 32 <= bend; t += 32) {
+        float v[32];
 #pragma unroll
-        for (int m = 0; m < 16; ++m) v[m] = __ldcg(col + static_cast<size_t>(t + m) * stride);
+        for (int m = 0; m < 32; ++m) v[m] = __ldcg(col + static_cast<size_t>(t + m) * stride);
 #pragma unroll
-        for (int m = 0; m < 16; m += 4) {
+        for (int m = 0; m < 32; m += 4) {
           a0 += S.chunk[t + m + 0] * v[m + 0];
           a1 += S.chunk[t + m + 1] * v[m + 1];
           a2 += S.chunk[t + m + 2] * v[m + 2];
