@@ -384,9 +384,18 @@ struct Smem {
 struct Shared {
   Frame fr;
   float red_h[2], red_l[2];
+  float wred_h[16], wred_l[16];  // per-warp pair minima (merge)
   int item;
   int last;
 };
+
+// Asynchronous 4-byte copy global -> shared (cp.async): the copies of a
+// loop stay in flight together instead of one load-store round trip each.
+__device__ __forceinline__ void cp_async4(float* smem_dst, const float* gmem_src) {
+  const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(smem_dst));
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 // grad h . e1' in the obstacle frame.
 __device__ __forceinline__ float gda3(float hx, float hy, float dirx, float diry) { return hx * dirx + hy * diry; }
@@ -429,13 +438,14 @@ __device__ void run_tile(const KConst& k, const Inst& in, int tile, float* uh, c
   // shift into the frame follows the barrier.
   const bool obs8 = EXT && k.obs8;
   const int ostride = obs8 ? 8 : 6;
-  for (int j = threadIdx.x; j < 3 * in.n_pts; j += blockDim.x) S.path[j] = in.path[j];
-  for (int j = threadIdx.x; j < 3 * H; j += blockDim.x) S.unom[j] = in.U_nom[j];
+  for (int j = threadIdx.x; j < 3 * in.n_pts; j += blockDim.x) cp_async4(S.path + j, in.path + j);
+  for (int j = threadIdx.x; j < 3 * H; j += blockDim.x) cp_async4(S.unom + j, in.U_nom + j);
   float ob0[8];
   const bool has_ob0 = static_cast<int>(threadIdx.x) < in.n_obs;
 #pragma unroll
   for (int q = 0; q < 8; ++q) ob0[q] = (has_ob0 && q < ostride) ? in.obs[ostride * threadIdx.x + q] : 0.f;
   if (threadIdx.x < 32) make_frame_warp(in.x0, in.inv_ds_d, in.sync + 1, sh.fr, EXT && k.jerk);
+  cp_async_wait_all();
   __syncthreads();
   const Frame& fr = sh.fr;
   auto stage_obstacle = [&](int o, float cx, float cy, float ax, float ay, float th, float e, float vx, float vy) {
@@ -1129,13 +1139,21 @@ static __device__ void optimal_trajectory(const KConst& k, const Inst& in, const
     }
   };
   if (threadIdx.x == 0) {  // trailer angle
+    // step tau + 1's coefficients are loaded before step tau's store, so
+    // the loads overlap the chain (A, V, T and B share one scratch array)
     float q2 = fr.t2;
-#pragma unroll 4
+    float an = A[0], cn = (Ts * V[0]) * k.inv_l2, en = k.k_hitch * T[0];
     for (int tau = 0; tau < H; ++tau) {
+      const float a = an, c = cn, e = en;
+      if (tau + 1 < H) {
+        an = A[tau + 1];
+        cn = (Ts * V[tau + 1]) * k.inv_l2;
+        en = k.k_hitch * T[tau + 1];
+      }
       B[tau] = q2;
       float a2, b2;
-      __sincosf(A[tau] - q2, &a2, &b2);
-      q2 += (Ts * V[tau]) * k.inv_l2 * (a2 - k.k_hitch * b2 * T[tau]);
+      __sincosf(a - q2, &a2, &b2);
+      q2 = fmaf(c, fmaf(-e, b2, a2), q2);
     }
     B[H] = q2;
   }
@@ -1197,15 +1215,23 @@ static __device__ void serial_trajectory(const KConst& k, const Inst& in, const 
 }
 
 static __device__ void merge_instance(const KConst& k, const Inst& in, const Smem& S, Shared& sh) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
   const int nb = in.tiles;
   const int stride = in.part_stride;
   const int H = in.H;
-  if (warp == 0) {
+  // global pair minimum: every thread its tiles (b = tid, tid + blockDim,
+  // ...), then warps, then warp 0; the pair of tile tid stays in registers
+  // for the weights below (one L2 round trip for both)
+  float h0 = CUDART_INF_F, l0 = 0.f;
+  {
     float mh = CUDART_INF_F, ml = 0.f;
-    for (int b = lane; b < nb; b += 32) {
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) {
       const float h = __ldcg(in.part + static_cast<size_t>(b) * stride + 0);
       const float l = __ldcg(in.part + static_cast<size_t>(b) * stride + 1);
+      if (b == static_cast<int>(threadIdx.x)) {
+        h0 = h;
+        l0 = l;
+      }
       if (pair_less(h, l, mh, ml)) { mh = h; ml = l; }
     }
 #pragma unroll
@@ -1214,7 +1240,19 @@ static __device__ void merge_instance(const KConst& k, const Inst& in, const Sme
       const float ol = __shfl_xor_sync(0xffffffffu, ml, m);
       if (pair_less(oh, ol, mh, ml)) { mh = oh; ml = ol; }
     }
-    if (lane == 0) { sh.red_h[1] = mh; sh.red_l[1] = ml; }
+    if (lane == 0) { sh.wred_h[warp] = mh; sh.wred_l[warp] = ml; }
+    __syncthreads();
+    if (warp == 0) {
+      mh = lane < nwarps ? sh.wred_h[lane] : CUDART_INF_F;
+      ml = lane < nwarps ? sh.wred_l[lane] : 0.f;
+#pragma unroll
+      for (int m = 16; m > 0; m >>= 1) {
+        const float oh = __shfl_xor_sync(0xffffffffu, mh, m);
+        const float ol = __shfl_xor_sync(0xffffffffu, ml, m);
+        if (pair_less(oh, ol, mh, ml)) { mh = oh; ml = ol; }
+      }
+      if (lane == 0) { sh.red_h[1] = mh; sh.red_l[1] = ml; }
+    }
   }
   __syncthreads();
   const float gmh = sh.red_h[1], gml = sh.red_l[1];
@@ -1226,7 +1264,8 @@ static __device__ void merge_instance(const KConst& k, const Inst& in, const Sme
     __syncthreads();
     for (int t = threadIdx.x; t < 256 && b0 + t < nb; t += blockDim.x) {
       const size_t base = static_cast<size_t>(b0 + t) * stride;
-      const float h = __ldcg(in.part + base + 0), l = __ldcg(in.part + base + 1);
+      const bool held = b0 == 0 && t == static_cast<int>(threadIdx.x);
+      const float h = held ? h0 : __ldcg(in.part + base + 0), l = held ? l0 : __ldcg(in.part + base + 1);
       S.chunk[t] = (ok && h < CUDART_INF_F) ? expf(-((h - gmh) + (l - gml)) * k.inv_lambda) : 0.f;
     }
     __syncthreads();
