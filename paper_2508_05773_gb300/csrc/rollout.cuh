@@ -387,6 +387,7 @@ struct Shared {
   float wred_h[16], wred_l[16];  // per-warp pair minima (merge)
   int item;
   int last;
+  unsigned err;  // the instance's error bits (merge)
 };
 
 // Asynchronous 4-byte copy global -> shared (cp.async): the copies of a
@@ -396,6 +397,13 @@ __device__ __forceinline__ void cp_async4(float* smem_dst, const float* gmem_src
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(gmem_src) : "memory");
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// L2 prefetch of a global address (no value; null-safe).  Issued early for
+// the outputs that the last CTA writes at the very end, it takes their
+// address translation and line allocation off the solve's tail.
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+  if (p) asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
 
 // grad h . e1' in the obstacle frame.
 __device__ __forceinline__ float gda3(float hx, float hy, float dirx, float diry) { return hx * dirx + hy * diry; }
@@ -432,6 +440,14 @@ __device__ void run_tile(const KConst& k, const Inst& in, int tile, float* uh, c
   const int H = in.H;
   const int n_rows = EXT ? in.n_obs * k.nd : in.n_obs;  // obstacle rows (obstacle x disc)
 
+  if (threadIdx.x == 32) {  // warm the outputs' translations (any CTA may merge)
+    prefetch_l2(in.U_out);
+    prefetch_l2(in.traj_out);
+    prefetch_l2(in.U_next);
+    prefetch_l2(in.status);
+    prefetch_l2(in.part + static_cast<size_t>(tile) * in.part_stride);
+    if (in.J_out) prefetch_l2(in.J_out + static_cast<size_t>(tile) * spb);
+  }
   // --- frame and staging (tables in shared memory, relative coordinates).
   // The raw path, the nominal inputs and each thread's first obstacle are
   // loaded first, so that their global loads overlap warp 0's frame; the
@@ -1223,6 +1239,8 @@ static __device__ void merge_instance(const KConst& k, const Inst& in, const Sme
   // ...), then warps, then warp 0; the pair of tile tid stays in registers
   // for the weights below (one L2 round trip for both)
   float h0 = CUDART_INF_F, l0 = 0.f;
+  // the solve's error bits, read now (an atomic round trip) and used after the sums
+  if (threadIdx.x == 0) sh.err = atomicAdd(in.sync + 1, 0u);
   {
     float mh = CUDART_INF_F, ml = 0.f;
     for (int b = threadIdx.x; b < nb; b += blockDim.x) {
@@ -1272,16 +1290,28 @@ static __device__ void merge_instance(const KConst& k, const Inst& in, const Sme
     const int bend = min(256, nb - b0);
     for (int q = threadIdx.x; q < nrows; q += blockDim.x) {
       // four independent chains (tiles t mod 4), combined in a fixed order;
-      // thirty-two L2 loads in flight per pass
+      // 64 (then 16) L2 loads in flight per pass
       float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
       const float* col = in.part + static_cast<size_t>(b0) * stride + 3 + q;
       int t = 0;
-      for (; t + 32 <= bend; t += 32) {
-        float v[32];
+      for (; t + 64 <= bend; t += 64) {
+        float v[64];
 #pragma unroll
-        for (int m = 0; m < 32; ++m) v[m] = __ldcg(col + static_cast<size_t>(t + m) * stride);
+        for (int m = 0; m < 64; ++m) v[m] = __ldcg(col + static_cast<size_t>(t + m) * stride);
 #pragma unroll
-        for (int m = 0; m < 32; m += 4) {
+        for (int m = 0; m < 64; m += 4) {
+          a0 += S.chunk[t + m + 0] * v[m + 0];
+          a1 += S.chunk[t + m + 1] * v[m + 1];
+          a2 += S.chunk[t + m + 2] * v[m + 2];
+          a3 += S.chunk[t + m + 3] * v[m + 3];
+        }
+      }
+      for (; t + 16 <= bend; t += 16) {
+        float v[16];
+#pragma unroll
+        for (int m = 0; m < 16; ++m) v[m] = __ldcg(col + static_cast<size_t>(t + m) * stride);
+#pragma unroll
+        for (int m = 0; m < 16; m += 4) {
           a0 += S.chunk[t + m + 0] * v[m + 0];
           a1 += S.chunk[t + m + 1] * v[m + 1];
           a2 += S.chunk[t + m + 2] * v[m + 2];
@@ -1300,7 +1330,7 @@ static __device__ void merge_instance(const KConst& k, const Inst& in, const Sme
   }
   __syncthreads();
   const float lsum = ustar[3 * H];
-  const unsigned err = atomicAdd(in.sync + 1, 0u);
+  const unsigned err = sh.err;
   for (int q = threadIdx.x; q < 3 * H; q += blockDim.x) {
     const float u = ok ? ustar[q] / lsum : S.unom[q];
     ustar[q] = u;
