@@ -72,6 +72,28 @@ def test_fuzz_small_cases(pkg, seed):
     assert_solve_matches(out, ref, p, f"S={S} H={H} n_obs={n_obs}")
 
 
+@pytest.mark.parametrize("jerk", [False, True])
+@pytest.mark.parametrize("where,S,n_pts", [("shared memory", 300, None), ("tile partials", 1024, 3),
+                                           ("serial", 64, 3)])
+def test_trajectory_scratch_paths(pkg, where, S, n_pts, jerk):
+    """The merge's optimal trajectory keeps its per-step values in the CTA's
+    table regions when they hold 8 (H+1) floats, else in the consumed tile
+    partials, else runs one serial thread.  A short path and no obstacles
+    (4 lanes x 128 threads: 32 samples per tile, H = 40) shrink the tables
+    below 8 (H+1) floats; S picks between partials (32 tiles) and serial
+    (2 tiles)."""
+    c = sc.small_random(41, S=S, H=40, n_obs=0 if n_pts else 4)
+    if n_pts:
+        c["path"] = c["path"][:n_pts].copy()
+    if jerk:
+        c = sc.jerk_model(c, a0=0.3, seed=5)
+    p, ref = _oracle(c)
+    if jerk:  # the trajectory output holds the 7 kinematic states
+        ref = dict(ref, traj=ref["traj"][:, :7])
+    out = _gpu(pkg, c, tps=4, threads=128)
+    assert_solve_matches(out, ref, p, f"{where} jerk={jerk}")
+
+
 def test_standard_mppi_flag(pkg):
     c = sc.config1b(S=200, H=25)
     p, ref = _oracle(c, flags=sc.FLAG_PROJ_NONE)
