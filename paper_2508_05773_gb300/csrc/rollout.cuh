@@ -1241,6 +1241,14 @@ static __device__ void merge_instance(const KConst& k, const Inst& in, const Sme
   float h0 = CUDART_INF_F, l0 = 0.f;
   // the solve's error bits, read now (an atomic round trip) and used after the sums
   if (threadIdx.x == 0) sh.err = atomicAdd(in.sync + 1, 0u);
+  // the first 64 tiles' entries of this thread's first row, loaded now: their
+  // round trip overlaps the minimum's (instances of at least 64 tiles)
+  const int nrows = 3 * H + 1;
+  const bool pre_ok = static_cast<int>(threadIdx.x) < nrows && nb >= 64;
+  float pre[64];
+#pragma unroll
+  for (int m = 0; m < 64; ++m)
+    pre[m] = pre_ok ? __ldcg(in.part + static_cast<size_t>(m) * stride + 3 + threadIdx.x) : 0.f;
   {
     float mh = CUDART_INF_F, ml = 0.f;
     for (int b = threadIdx.x; b < nb; b += blockDim.x) {
@@ -1275,7 +1283,6 @@ static __device__ void merge_instance(const KConst& k, const Inst& in, const Sme
   __syncthreads();
   const float gmh = sh.red_h[1], gml = sh.red_l[1];
   const bool ok = gmh < CUDART_INF_F;
-  const int nrows = 3 * H + 1;
   float* ustar = S.ustar;
   for (int q = threadIdx.x; q < nrows; q += blockDim.x) ustar[q] = 0.f;
   for (int b0 = 0; b0 < nb; b0 += 256) {
@@ -1295,15 +1302,18 @@ static __device__ void merge_instance(const KConst& k, const Inst& in, const Sme
       const float* col = in.part + static_cast<size_t>(b0) * stride + 3 + q;
       int t = 0;
       for (; t + 64 <= bend; t += 64) {
-        float v[64];
+        // `pre` is the pass buffer: it already holds the first pass of the
+        // thread's first row
+        if (!(pre_ok && b0 == 0 && t == 0 && q == static_cast<int>(threadIdx.x))) {
 #pragma unroll
-        for (int m = 0; m < 64; ++m) v[m] = __ldcg(col + static_cast<size_t>(t + m) * stride);
+          for (int m = 0; m < 64; ++m) pre[m] = __ldcg(col + static_cast<size_t>(t + m) * stride);
+        }
 #pragma unroll
         for (int m = 0; m < 64; m += 4) {
-          a0 += S.chunk[t + m + 0] * v[m + 0];
-          a1 += S.chunk[t + m + 1] * v[m + 1];
-          a2 += S.chunk[t + m + 2] * v[m + 2];
-          a3 += S.chunk[t + m + 3] * v[m + 3];
+          a0 += S.chunk[t + m + 0] * pre[m + 0];
+          a1 += S.chunk[t + m + 1] * pre[m + 1];
+          a2 += S.chunk[t + m + 2] * pre[m + 2];
+          a3 += S.chunk[t + m + 3] * pre[m + 3];
         }
       }
       for (; t + 16 <= bend; t += 16) {
