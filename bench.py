@@ -430,8 +430,9 @@ def measure_variants(dev, reps: int = 20):
                                               "(8 obstacles x 5 discs = 40 barrier rows)",
                                   "ms_per_solve": ms, "rollout_steps_per_s": S * H / (ms * 1e-3),
                                   "launch": solver.launch(8)}
-    # batched stabilizer
-    n = 1 << 20
+    # batched stabilizer: 2^23 states (0.7 GB, larger than L2; a kernel of
+    # ~0.1 ms, so launch latency does not dominate the interval)
+    n = 1 << 23
     rng = np.random.default_rng(3)
     th1 = rng.uniform(-3, 3, n)
     X = np.stack([rng.uniform(-50, 50, n), rng.uniform(-50, 50, n), th1, th1 + rng.uniform(-1.0, 1.0, n),
@@ -484,8 +485,9 @@ def run_profile(args):
     (256 uneven instances, one persistent launch), each with a fixed launch
     shape (--tps / --threads; defaults: the shapes the autotuners pick on
     GB300), `stress` / `stress_stored` = the config-5 solve (S=65536, H=100,
-    64 ellipses) without / with every sample's states stored (185 MB).
-    Four launches with an L2 flush before each; capture the last."""
+    64 ellipses) without / with every sample's states stored (185 MB),
+    `stabilizer` = the batched hitch stabilizer on 2^20 states.  Four
+    launches with an L2 flush before each; capture the last."""
     import torch
     import paper_2508_05773_gb300 as pkg
     from paper_2508_05773_gb300 import scenarios as sc
@@ -503,6 +505,21 @@ def run_profile(args):
             flush.zero_()
             if solver.solve_device(x0, U, obs, path, c["ds"], c["seed"], r, Uo, tr) != 0:
                 raise RuntimeError(pkg.brmppi_last_error(solver.ctx))
+    elif args.profile == "stabilizer":
+        n = 1 << 20
+        rng = np.random.default_rng(3)
+        th1 = rng.uniform(-3, 3, n)
+        X = np.stack([rng.uniform(-50, 50, n), rng.uniform(-50, 50, n), th1, th1 + rng.uniform(-1.0, 1.0, n),
+                      rng.uniform(-2, 2, n), rng.uniform(-0.5, 0.5, n), rng.uniform(0, 30, n)], 1)
+        Ur = np.stack([rng.uniform(-3, 3, n), rng.uniform(-1, 1, n), rng.uniform(0, 3, n)], 1)
+        xd, ud = t(X, torch.float64), t(Ur)
+        od = torch.empty((n, 4), device=dev)
+        solver = pkg.Solver(sc.config2()["params"], max_obstacles=16, max_path_pts=1024)
+        stream = torch.cuda.current_stream(dev)
+        for r in range(4):
+            flush.zero_()
+            solver.hitch_stabilize_device(xd, ud, od, stream)
+        torch.cuda.synchronize()
     elif args.profile in ("stress", "stress_stored"):
         c = sc.config5()
         S, H = int(c["params"]["S"]), int(c["params"]["H"])
@@ -883,7 +900,7 @@ def main():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-stress", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
-    ap.add_argument("--profile", choices=("solve", "batch", "stress", "stress_stored"), default=None,
+    ap.add_argument("--profile", choices=("solve", "batch", "stress", "stress_stored", "stabilizer"), default=None,
                     help="a few launches of one workload for ncu, no timing")
     ap.add_argument("--tps", type=int, default=0, help="--profile: threads per sample")
     ap.add_argument("--threads", type=int, default=0, help="--profile: threads per block")
