@@ -741,6 +741,7 @@ def run_reference(args, world, rank):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": _config_block(c, {"rollouts_per_step": cores * S_sample,
+                                                       "solves_per_step": cores * S_sample / int(p["S"]),
                                                        "l2": "not applicable (host cores)",
                                                        "timing": "host wall clock over the timed steps"}),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
