@@ -225,17 +225,31 @@ bool heuristic_plain(const brmppi_ctx* c, int n_obs, int n_pts, Shape* out) {
   const bool fixed_tps = c->prm.threads_per_sample != 0;
   int tps = c->prm.threads_per_sample;
   if (!fixed_tps) {
+    // latency shape: one Philox block per lane; then, while the GPU stays
+    // full (at least 4 warps per SM), fewer lanes per sample and more blocks
+    // per lane (less work repeated across a team)
     tps = 1;
     while (tps < P && tps < 32) tps <<= 1;
+    int b2 = 0;
+    while (tps > 1 && pick_bpt(tps / 2, P, &b2) &&
+           static_cast<long long>(c->prm.S) * (tps / 2) / 32 >= 4LL * c->num_sms)
+      tps >>= 1;
   }
   int bpt = 0;
   if (!pick_bpt(tps, P, &bpt)) return false;
   int threads = c->prm.block_threads;
   const bool fixed_threads = threads != 0;
   if (!fixed_threads) {
+    // 128 threads, one CTA per SM where the tiles fit; just over one wave:
+    // 64 (a short second wave of small CTAs); more: 256; very few tiles: 64
+    // (shapes measured on GB300; the autotuner refines per workload)
     threads = 128;
-    const int spb = threads / tps;
-    if ((c->prm.S + spb - 1) / spb < 2 * c->num_sms) threads = 64;
+    const long long tiles = (c->prm.S + threads / tps - 1) / (threads / tps);
+    const bool small_ok = 64 / tps >= 2;
+    if (tiles > c->num_sms)
+      threads = (tiles <= c->num_sms + c->num_sms / 4 && small_ok) ? 64 : 256;
+    else if (tiles < c->num_sms / 2 && small_ok)
+      threads = 64;
   }
   if (threads < tps) return false;
   while (smem_bytes(make_caps(n_obs, rows_of(c->prm, n_obs), n_pts, c->prm.H, tps), threads / tps) > c->smem_limit) {
