@@ -54,7 +54,7 @@ L2_FLUSH_BYTES = 256 << 20
 # compensated sums and without team redundancy): every +, -, *, fma, min,
 # max, compare/select, integer mul.lo / mul.hi / xor / add / shift / convert
 # and every elementary function (sin, cos, tan, log, sqrt, exp, reciprocal)
-# counts one.  Tally (the design doc lists it term by term):
+# counts one.  Tally per term:
 PHILOX_BLOCK_OPS = 132    # 10 rounds x 10 int ops, 4 uniform maps x 4, 2 Box-Muller pairs x 8
 STEP_BASE_OPS = 111       # z_des 9, state trig 13, p_u 6, 2x2 solve 14, clip 6, Euler 14, path + cost 49
 HITCH_OPS = 60            # row 27, projection terms 30, alpha update 3

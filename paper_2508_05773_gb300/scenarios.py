@@ -26,7 +26,9 @@ import math
 import numpy as np
 
 #: Default parameters (tractor-trailer geometry and weights of the workloads;
-#: values the paper leaves open are the readings stated in the design doc).
+#: where the paper leaves a value open, the value chosen here is a reading
+#: of it: alpha0 = 0.5, the alpha-input noise and bounds, w_alpha, rho,
+#: h_floor, nu_bar).
 DEFAULT_PARAMS = dict(
     S=256, H=30, flags=0,
     Ts=0.05, **{"lambda": 1.0},
