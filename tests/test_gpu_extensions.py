@@ -456,3 +456,18 @@ def test_jerk_model_batch(pkg, torch):
             assert_solve_matches(out, _ref7(ref), p, f"jerk batch {k}")
     finally:
         s.close()
+
+
+# ------------------------------------------------- three blocks per lane
+@pytest.mark.parametrize("moving", [False, True])
+@pytest.mark.parametrize("tps,n_obs", [(4, 30), (8, 64)])
+def test_three_blocks_per_lane_variants(pkg, tps, n_obs, moving):
+    """Teams of 4 (8) lanes drawing 9..12 (17..24) Philox blocks per step
+    run the variants with three blocks per lane, in both kernel families
+    (moving and e = 4 rows select the extended one)."""
+    c = sc.small_random(131 + n_obs, S=200, H=12, n_obs=n_obs)
+    if moving:
+        c = sc.with_moving(c, seed=7)
+    p, ref = _oracle(c)
+    out = _gpu(pkg, c, tps=tps, threads=128)
+    assert_solve_matches(out, ref, p, f"tps={tps} n_obs={n_obs} moving={moving}")
