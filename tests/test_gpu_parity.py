@@ -60,6 +60,22 @@ def test_every_variant_matches_oracle(pkg, tps, threads):
     assert_solve_matches(out, ref, p, f"tps={tps} threads={threads}")
 
 
+@pytest.mark.parametrize("tps", [2, 4, 8, 16])
+@pytest.mark.parametrize("n_obs", [0, 7, 13, 21, 29, 45, 70, 100])
+def test_blocks_per_lane_grid(pkg, tps, n_obs):
+    # 1 + n_obs constraints -> ceil((4 + n_obs) / 4) Philox blocks per step:
+    # with 2..16 lanes per sample this walks every blocks-per-lane variant
+    # (1, 2, 3, 4 and the producer-warp / lane-staged split) that a team
+    # width offers; S = 96 leaves a ragged last tile at 128 threads.
+    P = (4 + n_obs + 3) // 4
+    if P > (2 if tps == 16 else 4) * tps:
+        pytest.skip("no variant with that many blocks per lane")
+    c = sc.small_random(300 + n_obs, S=96, H=8, n_obs=n_obs)
+    p, ref = _oracle(c)
+    out = _gpu(pkg, c, tps=tps, threads=128)
+    assert_solve_matches(out, ref, p, f"tps={tps} n_obs={n_obs}")
+
+
 @pytest.mark.parametrize("seed", range(8))
 def test_fuzz_small_cases(pkg, seed):
     rng = np.random.default_rng(100 + seed)
