@@ -525,7 +525,7 @@ def run_profile(args):
         S, H = int(c["params"]["S"]), int(c["params"]["H"])
         n_obs = int(c["obs"].shape[0])
         solver = pkg.Solver(c["params"], max_obstacles=n_obs, max_path_pts=c["path"].shape[0],
-                            threads_per_sample=args.tps or 8, block_threads=args.threads or 256)
+                            threads_per_sample=args.tps or 4, block_threads=args.threads or 256)
         inst = dict(x0=t(c["x0"], torch.float64), U_nom=t(c["U_nom"]), obs=t(c["obs"]), path=t(c["path"]),
                     ds=c["ds"], S=S, seed=c["seed"], counter=0,
                     U_out=torch.empty((H, 3), device=dev), traj_out=torch.empty((H + 1, 7), device=dev),

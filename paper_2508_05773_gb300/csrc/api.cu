@@ -206,8 +206,11 @@ brmppi::SmemCaps make_caps(int n_obs, int n_rows, int n_pts, int H, int tps) {
 size_t smem_bytes(const brmppi::SmemCaps& c, int spb) { return sizeof(float) * static_cast<size_t>(c.total(spb)); }
 
 bool pick_bpt(int tps, int P, int* bpt) {
+  // one lane: the lane draws every block (b >= P); wider teams: the row
+  // slots of a lane (4 b) must hold its share of the at most 4 P - 4 rows
+  // (their blocks are drawn by producer warps or staged in passes)
   for (int b : {1, 2, 3, 4, 5, 6, 8})
-    if (tps * b >= P && brmppi::variant_exists(tps, b)) {
+    if ((tps == 1 ? b >= P : (4 * P - 4 + tps - 1) / tps <= 4 * b) && brmppi::variant_exists(tps, b)) {
       *bpt = b;
       return true;
     }
@@ -246,8 +249,11 @@ bool heuristic_plain(const brmppi_ctx* c, int n_obs, int n_pts, Shape* out) {
     threads = 128;
     const long long tiles = (c->prm.S + threads / tps - 1) / (threads / tps);
     const bool small_ok = 64 / tps >= 2;
+    // (producer-warp variants stay at 128: their CTAs grow by up to four
+    // warps, and 256 + 128 threads of 128 registers fit one CTA per SM)
+    const bool producers = tps > 1 && bpt <= 2;
     if (tiles > c->num_sms)
-      threads = (tiles <= c->num_sms + c->num_sms / 4 && small_ok) ? 64 : 256;
+      threads = (tiles <= c->num_sms + c->num_sms / 4 && small_ok) ? 64 : (producers ? 128 : 256);
     else if (tiles < c->num_sms / 2 && small_ok)
       threads = 64;
   }
