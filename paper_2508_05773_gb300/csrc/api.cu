@@ -167,10 +167,10 @@ brmppi::KConst make_kconst(const brmppi_params& q) {
   k.inv_m_u0 = 1.0f / (q.w_u[0] + q.rho);
   k.inv_m_u1 = 1.0f / (q.w_u[1] + q.rho);
   k.inv_m_u2 = 1.0f / (q.w_u[2] + q.rho);
-  k.w_a = q.w_alpha;
-  k.pc_a = 0.5f * q.rho * (q.ua_hi + q.ua_lo);
+  const double m_alpha = static_cast<double>(q.w_alpha) + static_cast<double>(q.rho);
+  k.w_am = static_cast<float>(q.w_alpha / m_alpha);
+  k.pc_am = static_cast<float>(0.5 * q.rho * (static_cast<double>(q.ua_hi) + q.ua_lo) / m_alpha);
   k.m_a = q.w_alpha + q.rho;
-  k.inv_m_a = 1.0f / (q.w_alpha + q.rho);
   k.h_floor = q.h_floor;
   k.q_coll = q.q_coll;
   k.q_abuf = q.q_abuf;

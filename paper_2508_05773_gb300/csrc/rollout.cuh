@@ -42,7 +42,10 @@
 //   S2 = M_u + A_u^T D^-1 A_u (2x2),  g = A_u^T D^-1 r,  y = S2^-1 g,
 //   r  = A M^-1 p - b,  lambda = D^-1 (r - A_u y),
 //   z*_u = M_u^-1 p_u - y,  z*_alpha_i = p_alpha_i/m_alpha - (r_i - a_i.y)/h~_i,
-// algebraically identical to M^-1 [p - A^T K^-1 (A M^-1 p - b)].
+// algebraically identical to M^-1 [p - A^T K^-1 (A M^-1 p - b)].  With
+// u_i = a_i / h~_i and rho_i = r_i / h~_i (one reciprocal per row):
+//   S2 = M_u + m_alpha sum u_i u_i^T,  g = m_alpha sum u_i rho_i,
+// so the rows accumulate the sums and m_alpha is applied once.
 //
 // Numerics: states are carried relative to the initial pose (position
 // relative to (px0, py0), angles relative to theta1_0, progress relative to
@@ -69,7 +72,7 @@ struct KConst {
   float alpha0, sigma_alpha, ua_lo, ua_hi;
   float w_u0, w_u1, w_u2, pc_u0, pc_u1, pc_u2;  // W_u and rho/2 (hi + lo)
   float m_u0, m_u1, inv_m_u0, inv_m_u1, inv_m_u2;
-  float w_a, pc_a, m_a, inv_m_a;
+  float w_am, pc_am, m_a;  // W_alpha / m_alpha, rho (hi + lo) / (2 m_alpha), m_alpha = W_alpha + rho
   float h_floor;
   float q_coll, q_abuf, inv_hbuf;
   float alpha_stab, inv_qs0, inv_qs1;  // hitch stabilizer: CBF rate, Q_h^-1
@@ -721,19 +724,21 @@ __device__ void run_tile(const KConst& k, const Inst& in, int tile, float* uh, c
         const float hm = fmaxf(fabsf(hr.h), k.h_floor);
         const float ht = hr.h >= 0.f ? hm : -hm;
         const float zda = clampf(k.sigma_alpha * n_h, k.ua_lo, k.ua_hi);
-        const float pa = k.w_a * zda + k.pc_a;
+        const float pam = k.w_am * zda + k.pc_am;  // p_alpha / m_alpha
         const float b = -alpha_h * hr.h - hr.c0;
-        const float r = hr.Aa * q0 + hr.Aw * q1 + ht * pa * k.inv_m_a - b;
+        const float r = hr.Aa * q0 + hr.Aw * q1 + ht * pam - b;
         const float iht = __fdividef(1.f, ht);  // MUFU reciprocal (~1 ulp)
-        const float own = (lt == 0) ? k.m_a * iht * iht : 0.f;  // 1/D on lane 0
-        Saa = hr.Aa * hr.Aa * own;
-        Saw = hr.Aa * hr.Aw * own;
-        Sww = hr.Aw * hr.Aw * own;
-        ga = hr.Aa * r * own;
-        gw = hr.Aw * r * own;
+        const float rho = r * iht;
         ca_h = hr.Aa * iht;
         cw_h = hr.Aw * iht;
-        cc_h = pa * k.inv_m_a - r * iht;
+        cc_h = pam - rho;
+        const float own = (lt == 0) ? 1.f : 0.f;  // the sums take the row once (lane 0)
+        const float ua = own * ca_h, uw = own * cw_h;
+        Saa = ua * ua;
+        Saw = ua * uw;
+        Sww = uw * uw;
+        ga = ua * rho;
+        gw = uw * rho;
       }
 
       // obstacle rows in the obstacle frame; the steer rate does not enter
@@ -850,20 +855,22 @@ __device__ void run_tile(const KConst& k, const Inst& in, int tile, float* uh, c
         const float hm = fmaxf(fabsf(h), k.h_floor);
         const float ht = h >= 0.f ? hm : -hm;
         const float zda = clampf(k.sigma_alpha * n_alpha, k.ua_lo, k.ua_hi);
-        const float pa = k.w_a * zda + k.pc_a;
+        const float pam = k.w_am * zda + k.pc_am;  // p_alpha / m_alpha
         const float b = -alpha[slot] * h + brest;
-        const float r = Aa * q0 + Aw * q1 + ht * pa * k.inv_m_a - b;
+        const float r = Aa * q0 + Aw * q1 + ht * pam - b;
         const float iht = __fdividef(1.f, ht);  // MUFU reciprocal (~1 ulp)
-        const float invD = live * k.m_a * iht * iht;
-        Saa += Aa * Aa * invD;
-        ga += Aa * r * invD;
-        ca[slot] = live * (Aa * iht);
-        cc[slot] = live * (pa * k.inv_m_a - r * iht);
+        const float u = live * (Aa * iht);
+        const float rho = r * iht;
+        Saa += u * u;
+        ga += u * rho;
+        ca[slot] = u;
+        cc[slot] = live * (pam - rho);
         if constexpr (EXT) {
-          Saw += Aa * Aw * invD;
-          Sww += Aw * Aw * invD;
-          gw += Aw * r * invD;
-          cw[slot] = live * (Aw * iht);
+          const float w = live * (Aw * iht);
+          Saw += u * w;
+          Sww += w * w;
+          gw += w * rho;
+          cw[slot] = w;
         }
         if (EXT && k.abuf) {
           // buffer zone: positive rates charged with weight clip(1 - h/h_buf)
@@ -914,11 +921,11 @@ __device__ void run_tile(const KConst& k, const Inst& in, int tile, float* uh, c
         }
       }
       if (EXT && k.abuf) acc2(Jh, Jl, team_sum<TPS>(cbuf));
-      Saa = team_sum<TPS>(Saa) + k.m_u0;
-      Saw = team_sum<TPS>(Saw);
-      Sww = team_sum<TPS>(Sww) + k.m_u1;
-      ga = team_sum<TPS>(ga);
-      gw = team_sum<TPS>(gw);
+      Saa = k.m_a * team_sum<TPS>(Saa) + k.m_u0;
+      Saw = k.m_a * team_sum<TPS>(Saw);
+      Sww = k.m_a * team_sum<TPS>(Sww) + k.m_u1;
+      ga = k.m_a * team_sum<TPS>(ga);
+      gw = k.m_a * team_sum<TPS>(gw);
       const float idet = __fdividef(1.f, Saa * Sww - Saw * Saw);  // SPD: det > 0
       const float ya = (Sww * ga - Saw * gw) * idet;
       const float yw = (Saa * gw - Saw * ga) * idet;
