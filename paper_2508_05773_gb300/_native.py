@@ -419,6 +419,77 @@ def brmppi_transfer_bytes(ctx, n_obs: int, n_pts: int):
     return int(h2d.value), int(d2h.value)
 
 
+def brmppi_get_batch_launch(ctx):
+    tps, thr = ctypes.c_int32(), ctypes.c_int32()
+    st = load().brmppi_get_batch_launch(ctx, ctypes.byref(tps), ctypes.byref(thr))
+    if st != BRMPPI_OK:
+        raise BrmppiError(st, brmppi_last_error(ctx))
+    return dict(threads_per_sample=tps.value, block_threads=thr.value)
+
+
+# ---- serving loop: vehicles with device-resident nominal sequences and RNG
+# counters; requests queued by brmppi_submit and collected by brmppi_poll
+def brmppi_vehicle_register(ctx, vehicle_id: int, path, ds: float, H: int, U_init=None,
+                            seed: int = 0) -> None:
+    path = _f32(path).reshape(-1)
+    U = None if U_init is None else _f32(U_init, 3 * int(H))
+    st = load().brmppi_vehicle_register(ctx, int(vehicle_id), path.ctypes.data_as(_F),
+                                        path.size // 3, float(ds),
+                                        None if U is None else U.ctypes.data_as(_F),
+                                        int(seed) & (2**64 - 1))
+    if st != BRMPPI_OK:
+        raise BrmppiError(st, brmppi_last_error(ctx))
+
+
+def brmppi_submit(ctx, vehicle_id: int, x0, obs=None, obs_row: int = 6):
+    """Queue one solve; returns (status, ticket).  obs_row: floats per
+    obstacle row (6, or 8 with BRMPPI_FLAG_OBS8)."""
+    x0 = np.ascontiguousarray(x0, dtype=np.float64)
+    ob = np.zeros(0, np.float32) if obs is None else _f32(obs).reshape(-1)
+    t = ctypes.c_uint64()
+    st = load().brmppi_submit(ctx, int(vehicle_id), x0.ctypes.data_as(_D),
+                              ob.ctypes.data_as(_F) if ob.size else None, ob.size // int(obs_row),
+                              ctypes.byref(t))
+    return st, t.value
+
+
+def brmppi_poll(ctx, ticket: int, H: int, want_traj: bool = False):
+    """(status, U, traj, latency_s); status EAGAIN while the solve runs."""
+    U = np.empty((int(H), 3), np.float32)
+    traj = np.empty((int(H) + 1, 7), np.float32) if want_traj else None
+    lat = ctypes.c_double()
+    st = load().brmppi_poll(ctx, int(ticket), U.ctypes.data_as(_F),
+                            traj.ctypes.data_as(_F) if traj is not None else None,
+                            ctypes.byref(lat))
+    return st, U, traj, lat.value
+
+
+def brmppi_vehicle_export(ctx, vehicle_id: int, H: int):
+    U = np.empty((int(H), 3), np.float32)
+    seed, ctr = ctypes.c_uint64(), ctypes.c_uint64()
+    st = load().brmppi_vehicle_export(ctx, int(vehicle_id), U.ctypes.data_as(_F),
+                                      ctypes.byref(seed), ctypes.byref(ctr))
+    if st != BRMPPI_OK:
+        raise BrmppiError(st, brmppi_last_error(ctx))
+    return U, seed.value, ctr.value
+
+
+def brmppi_vehicle_import(ctx, vehicle_id: int, U_nom, H: int, seed: int, counter: int) -> None:
+    U = _f32(U_nom, 3 * int(H))
+    st = load().brmppi_vehicle_import(ctx, int(vehicle_id), U.ctypes.data_as(_F),
+                                      int(seed) & (2**64 - 1), int(counter) & (2**64 - 1))
+    if st != BRMPPI_OK:
+        raise BrmppiError(st, brmppi_last_error(ctx))
+
+
+def brmppi_server_stats_get(ctx) -> dict:
+    out = brmppi_server_stats()
+    st = load().brmppi_server_stats_get(ctx, ctypes.byref(out))
+    if st != BRMPPI_OK:
+        raise BrmppiError(st, brmppi_last_error(ctx))
+    return {name: getattr(out, name) for name, _ in brmppi_server_stats._fields_}
+
+
 class Solver:
     """Convenience owner of one context."""
 
@@ -463,11 +534,7 @@ class Solver:
         return brmppi_get_launch(self.ctx, n_obs)
 
     def batch_launch(self) -> dict:
-        tps, thr = ctypes.c_int32(), ctypes.c_int32()
-        st = load().brmppi_get_batch_launch(self.ctx, ctypes.byref(tps), ctypes.byref(thr))
-        if st != BRMPPI_OK:
-            raise BrmppiError(st, brmppi_last_error(self.ctx))
-        return dict(threads_per_sample=tps.value, block_threads=thr.value)
+        return brmppi_get_batch_launch(self.ctx)
 
     def transfer_bytes(self, n_obs: int, n_pts: int):
         return brmppi_transfer_bytes(self.ctx, n_obs, n_pts)
@@ -500,58 +567,25 @@ class Solver:
 
     # ---- serving loop
     def register(self, vehicle_id: int, path, ds: float, U_init=None, seed: int = 0):
-        path = _f32(path).reshape(-1)
-        U = None if U_init is None else _f32(U_init, 3 * self.H)
-        st = load().brmppi_vehicle_register(self.ctx, int(vehicle_id), path.ctypes.data_as(_F),
-                                            path.size // 3, float(ds),
-                                            None if U is None else U.ctypes.data_as(_F),
-                                            int(seed) & (2**64 - 1))
-        if st != BRMPPI_OK:
-            raise BrmppiError(st, brmppi_last_error(self.ctx))
+        brmppi_vehicle_register(self.ctx, vehicle_id, path, ds, self.H, U_init, seed)
 
     def submit(self, vehicle_id: int, x0, obs=None):
         """Queue one solve; returns (status, ticket)."""
-        x0 = np.ascontiguousarray(x0, dtype=np.float64)
-        ob = np.zeros(0, np.float32) if obs is None else _f32(obs).reshape(-1)
         row = 8 if int(self.params.get("flags", 0)) & BRMPPI_FLAG_OBS8 else 6
-        t = ctypes.c_uint64()
-        st = load().brmppi_submit(self.ctx, int(vehicle_id), x0.ctypes.data_as(_D),
-                                  ob.ctypes.data_as(_F) if ob.size else None, ob.size // row,
-                                  ctypes.byref(t))
-        return st, t.value
+        return brmppi_submit(self.ctx, vehicle_id, x0, obs, row)
 
     def poll(self, ticket: int, want_traj: bool = False):
         """(status, U, traj, latency_s); status EAGAIN while running."""
-        U = np.empty((self.H, 3), np.float32)
-        traj = np.empty((self.H + 1, 7), np.float32) if want_traj else None
-        lat = ctypes.c_double()
-        st = load().brmppi_poll(self.ctx, int(ticket), U.ctypes.data_as(_F),
-                                traj.ctypes.data_as(_F) if traj is not None else None,
-                                ctypes.byref(lat))
-        return st, U, traj, lat.value
+        return brmppi_poll(self.ctx, ticket, self.H, want_traj)
 
     def vehicle_export(self, vehicle_id: int):
-        U = np.empty((self.H, 3), np.float32)
-        seed, ctr = ctypes.c_uint64(), ctypes.c_uint64()
-        st = load().brmppi_vehicle_export(self.ctx, int(vehicle_id), U.ctypes.data_as(_F),
-                                          ctypes.byref(seed), ctypes.byref(ctr))
-        if st != BRMPPI_OK:
-            raise BrmppiError(st, brmppi_last_error(self.ctx))
-        return U, seed.value, ctr.value
+        return brmppi_vehicle_export(self.ctx, vehicle_id, self.H)
 
     def vehicle_import(self, vehicle_id: int, U_nom, seed: int, counter: int):
-        U = _f32(U_nom, 3 * self.H)
-        st = load().brmppi_vehicle_import(self.ctx, int(vehicle_id), U.ctypes.data_as(_F),
-                                          int(seed) & (2**64 - 1), int(counter) & (2**64 - 1))
-        if st != BRMPPI_OK:
-            raise BrmppiError(st, brmppi_last_error(self.ctx))
+        brmppi_vehicle_import(self.ctx, vehicle_id, U_nom, self.H, seed, counter)
 
     def server_stats(self) -> dict:
-        out = brmppi_server_stats()
-        st = load().brmppi_server_stats_get(self.ctx, ctypes.byref(out))
-        if st != BRMPPI_OK:
-            raise BrmppiError(st, brmppi_last_error(self.ctx))
-        return {name: getattr(out, name) for name, _ in brmppi_server_stats._fields_}
+        return brmppi_server_stats_get(self.ctx)
 
     def autotune_batch(self, insts, reps=3, stream=None):
         st = brmppi_autotune_batch(self.ctx, insts, reps, stream)

@@ -38,6 +38,13 @@ def test_exports_every_declared_symbol(lib):
         assert name in _declared_functions(), name
 
 
+def test_binding_has_every_entry_point_by_its_c_name():
+    # the Python binding mirrors the C ABI name for name (argument marshalling only)
+    import paper_2508_05773_gb300 as pkg
+    for name in _declared_functions():
+        assert callable(getattr(pkg, name, None)), name
+
+
 def test_params_struct_layout_matches(lib):
     import paper_2508_05773_gb300 as pkg
     p = pkg.brmppi_default_params()
