@@ -26,7 +26,9 @@
  *   inputs     U[H][3]      float   (a, omega, nu)
  *   obstacles  obs[n][6]    float   (cx, cy, mx, my, theta_o, e); e must be 2
               obs[n][8]    float   with BRMPPI_FLAG_OBS8: + (vx, vy), e in {2, 4}
- *   path       path[n][3]   float   (x, y, heading unwrapped) at s = j*ds
+ *   path       path[n][3]   float   (x, y, heading unwrapped) at s = j*ds;
+ *                                   consecutive headings at most pi/4 apart
+ *                                   (else BRMPPI_EINVAL)
  *   trajectory traj[H+1][7] float
  *   costs      J[S]         float
  *
@@ -104,7 +106,7 @@ typedef struct brmppi_params {
   uint32_t abi_version;          /* must be BRMPPI_ABI_VERSION */
   int32_t S, H;                  /* samples, horizon steps (S >= 1, 1 <= H <= 1024) */
   int32_t max_obstacles;         /* capacity: obstacles per solve (<= 124) */
-  int32_t max_path_pts;          /* capacity: path rows per solve (>= 2) */
+  int32_t max_path_pts;          /* capacity: path rows per solve, in [2, 8192] */
   int32_t flags;                 /* BRMPPI_FLAG_* */
   int32_t threads_per_sample;    /* plain solves: 0 = tuned/heuristic, else 1, 2, 4, 8, 16, 32 */
   int32_t block_threads;         /* plain solves: 0 = tuned/heuristic, else 64..512, multiple of 32 */

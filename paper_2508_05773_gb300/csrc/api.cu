@@ -66,7 +66,7 @@ std::string check_params(const brmppi_params* p) {
   if (p->S < 1) return "S must be >= 1";
   if (p->H < 1 || p->H > kMaxH) return "H must be in [1, 1024]";
   if (p->max_obstacles < 0 || p->max_obstacles > kMaxObstacles) return "max_obstacles must be in [0, 124]";
-  if (p->max_path_pts < 2 || p->max_path_pts > kMaxPathPts) return "max_path_pts must be in [2, 12000]";
+  if (p->max_path_pts < 2 || p->max_path_pts > kMaxPathPts) return "max_path_pts must be in [2, 8192]";
   if (p->flags & ~static_cast<int32_t>(BRMPPI_FLAG_PROJ_NONE | BRMPPI_FLAG_COLLISION_COST | BRMPPI_FLAG_OBS8 |
                                         BRMPPI_FLAG_ALPHA_BUFFER | BRMPPI_FLAG_THIRD_ORDER | BRMPPI_FLAG_JERK_MODEL))
     return "unknown flag";
@@ -197,6 +197,7 @@ brmppi::SmemCaps make_caps(int n_obs, int n_rows, int n_pts, int H, int tps) {
   brmppi::SmemCaps c{};
   c.obs = 8 * n_obs;
   c.path = brmppi::SmemCaps::pad4(3 * n_pts);
+  c.phead = brmppi::SmemCaps::pad4(2 * n_pts);
   c.unom = brmppi::SmemCaps::pad4(3 * H);
   c.ustar = brmppi::SmemCaps::pad4(3 * H + 1);
   c.noise_per_team = tps > 1 ? 8 * philox_blocks(n_rows) : 0;
@@ -705,6 +706,7 @@ brmppi_status brmppi_solve(brmppi_ctx* c, const double x0[7], const float* U_nom
   const int of = obs_floats(c->prm);
   for (int o = 0; o < n_obs; ++o)
     if (!exponent_ok(c->prm, obs[of * o + 5])) return fail(c, BRMPPI_EINVAL, "unsupported obstacle exponent");
+  if (!path_turns_ok(path, n_pts)) return fail(c, BRMPPI_EINVAL, "path headings of consecutive rows differ by more than pi/4");
   Shape sh;
   if (!plain_shape(c, n_obs, n_pts, &sh)) return fail(c, BRMPPI_EINVAL, "no launch shape for this size");
   const int H = c->prm.H;

@@ -2,6 +2,7 @@
 // C-ABI translation unit (api.cu) and the serving loop (serve.cu).
 #pragma once
 
+#include <cmath>
 #include <cstdint>
 #include <map>
 #include <string>
@@ -12,7 +13,7 @@
 namespace brmppi_host {
 
 constexpr int kMaxObstacles = 124;  // ceil((4 + n)/4) <= 32 Philox blocks
-constexpr int kMaxPathPts = 12000;
+constexpr int kMaxPathPts = 8192;  // 5 floats a row in shared memory
 constexpr int kMaxH = 1024;
 constexpr int kMinThreads = 64;
 constexpr int kMaxThreads = 512;
@@ -29,6 +30,14 @@ inline int rows_of(const brmppi_params& p, int n_obs) { return n_obs * p.n_discs
 inline int obs_floats(const brmppi_params& p) { return (p.flags & BRMPPI_FLAG_OBS8) ? 8 : 6; }
 inline bool exponent_ok(const brmppi_params& p, float e) {
   return e == 2.0f || ((p.flags & BRMPPI_FLAG_OBS8) && e == 4.0f);
+}
+
+// Consecutive path headings at most pi/4 apart (and finite): the kernel
+// turns each row's heading direction by the interpolation angle.
+inline bool path_turns_ok(const float* path, int n_pts) {
+  for (int j = 0; j + 1 < n_pts; ++j)
+    if (!(std::fabs(path[3 * j + 5] - path[3 * j + 2]) <= 0.78539816339744831f)) return false;
+  return true;
 }
 
 struct Shape {

@@ -111,11 +111,11 @@ struct Inst {
 // Every region is a multiple of 4 floats (16 bytes): float4 accesses stay
 // aligned.
 struct SmemCaps {
-  int obs, path, unom, ustar;
+  int obs, path, phead, unom, ustar;
   int noise_per_team;  // teams wider than one lane: staged normals, 2 steps x P blocks x 4
   __host__ __device__ static int pad4(int n) { return (n + 3) & ~3; }
   __host__ __device__ int total(int spb) const {
-    return obs + path + unom + ustar + pad4(3 * spb) + 256 + 16 + noise_per_team * spb;
+    return obs + path + phead + unom + ustar + pad4(3 * spb) + 256 + 16 + noise_per_team * spb;
   }
 };
 
@@ -131,7 +131,11 @@ struct LaunchDesc {
   SmemCaps caps;
 };
 
-enum : unsigned { ERR_EXPONENT = 1u, ERR_NONFINITE_X0 = 2u };
+enum : unsigned { ERR_EXPONENT = 1u, ERR_NONFINITE_X0 = 2u, ERR_PATH_TURN = 4u };
+
+// Largest heading change between consecutive path rows (rad): the stage
+// cost's interpolated heading turns a row's direction by at most this.
+constexpr float kMaxPathTurn = 0.78539816339744831f;  // pi / 4
 
 // ------------------------------------------------------------------- noise
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two 32x32
@@ -163,6 +167,24 @@ __device__ __forceinline__ void box_muller(uint32_t wa, uint32_t wb, float& n0, 
 }
 
 __device__ __forceinline__ float clampf(float v, float lo, float hi) { return fminf(fmaxf(v, lo), hi); }
+
+// sin and cos of the turn within one path segment, |e| <= pi/4 (rows
+// farther apart are rejected when the path is staged): Taylor series of sin
+// to e^9 and of cos to e^10, truncation below 2e-9, no branch.
+__device__ __forceinline__ void turn_sincos(float e, float* s, float* c) {
+  const float e2 = e * e, e4 = e2 * e2;
+  // sin e = e + e^3 (-1/3! + e^2/5! + e^4 (-1/7! + e^2/9!))
+  *s = fmaf(e * e2,
+            fmaf(e4, fmaf(e2, 2.7557318844628753e-06f, -1.9841270113829523e-04f),
+                 fmaf(e2, 8.333333767950535e-03f, -0.1666666716337204f)),
+            e);
+  // cos e = 1 + e^2 (-1/2! + e^2/4! + e^4 (-1/6! + e^2/8!) - e^8/10!)
+  *c = fmaf(e2,
+            fmaf(e4 * e4, -2.755731998149713e-07f,
+                 fmaf(e4, fmaf(e2, 2.4801587642286904e-05f, -1.3888889225199819e-03f),
+                      fmaf(e2, 0.0416666679084301f, -0.5f))),
+            1.0f);
+}
 
 // into [-pi, pi]; only the square of the result is used
 __device__ __forceinline__ float wrap_pi(float a) {
@@ -360,6 +382,7 @@ struct Smem {
                  // k = 1/A^2 (e = 2) or 1/A^4 (e = 4, kx stored negated) and
                  // the velocity in the obstacle frame (zero unless moving)
   float* path;   // 3 per row: x, y, heading (relative frame)
+  float* phead;  // 2 per row: cos, sin of the row's heading in world axes
   float* unom;   // 3H
   float* ustar;  // 3H + 1 (merge)
   float* jh;     // spb
@@ -372,7 +395,8 @@ struct Smem {
   __device__ Smem(float* base, const SmemCaps& c, int spb) {
     obs = base;
     path = obs + c.obs;
-    unom = path + c.path;
+    phead = path + c.path;
+    unom = phead + c.phead;
     ustar = unom + c.unom;
     jh = ustar + c.ustar;
     jl = jh + spb;
@@ -493,7 +517,13 @@ __device__ void run_tile(const KConst& k, const Inst& in, int tile, float* uh, c
     float* d = S.path + 3 * j;
     d[0] = (d[0] - fr.ox_h) - fr.ox_l;
     d[1] = (d[1] - fr.oy_h) - fr.oy_l;
-    d[2] = (d[2] - fr.oth_h) - fr.oth_l;
+    const float th = (d[2] - fr.oth_h) - fr.oth_l;
+    d[2] = th;
+    // the row's heading direction in world axes, once per solve: the stage
+    // cost turns it by the interpolation angle instead of a sincos per step
+    float st, ct;
+    sincosf(th, &st, &ct);
+    *reinterpret_cast<float2*>(S.phead + 2 * j) = make_float2(fr.c0 * ct - fr.s0 * st, fr.s0 * ct + fr.c0 * st);
   }
   if constexpr (EXT) {
 #pragma unroll
@@ -576,11 +606,13 @@ __device__ void run_tile(const KConst& k, const Inst& in, int tile, float* uh, c
     const float* r0 = S.path + 3 * ii;
     const float xr = r0[0] + ff * (r0[3] - r0[0]);
     const float yr = r0[1] + ff * (r0[4] - r0[1]);
-    const float thr = r0[2] + ff * (r0[5] - r0[2]);
-    float st, ct;
-    sincosf(thr, &st, &ct);
-    const float cth = c0 * ct - s0 * st;
-    const float sth = s0 * ct + c0 * st;
+    const float eps = ff * (r0[5] - r0[2]);  // turn from row ii to the interpolated heading
+    const float thr = r0[2] + eps;
+    const float2 hd = *reinterpret_cast<const float2*>(S.phead + 2 * ii);
+    float se, ce;
+    turn_sincos(eps, &se, &ce);
+    const float cth = hd.x * ce - hd.y * se;  // cos / sin of the heading in world axes
+    const float sth = hd.y * ce + hd.x * se;
     const float dxr = (px - xr) + pxl, dyr = (py - yr) + pyl;
     const float ec = sth * dxr - cth * dyr;
     const float el = -cth * dxr - sth * dyr;
@@ -1345,9 +1377,15 @@ static __device__ void merge_instance(const KConst& k, const Inst& in, const Sme
       ustar[q] += (a0 + a1) + (a2 + a3);
     }
   }
-  __syncthreads();
+  // path turns between consecutive rows (this CTA's frame-shifted table;
+  // 1e-4 rad over pi/4 covers the shift's rounding): an out-of-range turn
+  // rejects the solve
+  int turn_bad = 0;
+  for (int j = threadIdx.x; j + 1 < in.n_pts; j += blockDim.x)
+    turn_bad |= !(fabsf(S.path[3 * j + 5] - S.path[3 * j + 2]) <= kMaxPathTurn + 1e-4f);
+  const bool turns_bad = __syncthreads_or(turn_bad);
   const float lsum = ustar[3 * H];
-  const unsigned err = sh.err;
+  const unsigned err = sh.err | (turns_bad ? ERR_PATH_TURN : 0u);
   for (int q = threadIdx.x; q < 3 * H; q += blockDim.x) {
     const float u = ok ? ustar[q] / lsum : S.unom[q];
     ustar[q] = u;
@@ -1363,7 +1401,7 @@ static __device__ void merge_instance(const KConst& k, const Inst& in, const Sme
   if (threadIdx.x == 0) {
     if (in.status) {
       int32_t st = 0;
-      if (err & ERR_EXPONENT) st = -1;
+      if (err & (ERR_EXPONENT | ERR_PATH_TURN)) st = -1;
       else if ((err & ERR_NONFINITE_X0) || !ok) st = -5;
       *in.status = st;
     }

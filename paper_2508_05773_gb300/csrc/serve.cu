@@ -336,6 +336,7 @@ brmppi_status brmppi_vehicle_register(brmppi_ctx* c, uint32_t vid, const float* 
   if (!path) return fail(c, BRMPPI_EINVAL, "NULL path");
   if (n_pts < 2 || n_pts > c->prm.max_path_pts) return fail(c, BRMPPI_EINVAL, "n_pts out of [2, max_path_pts]");
   if (!(ds > 0.f) || !std::isfinite(ds)) return fail(c, BRMPPI_EINVAL, "ds must be positive and finite");
+  if (!path_turns_ok(path, n_pts)) return fail(c, BRMPPI_EINVAL, "path headings of consecutive rows differ by more than pi/4");
   std::lock_guard<std::mutex> lk(sv->mu);
   Vehicle& V = sv->veh[vid];
   if (V.queued > 0) return fail(c, BRMPPI_EBUSY, "vehicle has requests in flight");

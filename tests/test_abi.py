@@ -65,7 +65,7 @@ def test_params_struct_layout_matches(lib):
 
 @pytest.mark.parametrize("field,value", [
     ("S", 0), ("H", 0), ("H", 5000), ("max_obstacles", -1), ("max_obstacles", 125),
-    ("max_path_pts", 1), ("threads_per_sample", 3), ("block_threads", 48), ("Ts", 0.0),
+    ("max_path_pts", 1), ("max_path_pts", 8193), ("threads_per_sample", 3), ("block_threads", 48), ("Ts", 0.0),
     ("lambda_", -1.0), ("h_floor", 0.0), ("flags", 0x40), ("abi_version", 99),
     ("max_batch", -1), ("batch_threads_per_sample", 5), ("batch_block_threads", 1000),
     ("max_vehicles", -2), ("serve_lanes", 99), ("serve_max_batch", -1), ("serve_queue", -5),

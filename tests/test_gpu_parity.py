@@ -171,9 +171,40 @@ def test_invalid_inputs_rejected(pkg):
         st, *_ = pkg.brmppi_solve(s.ctx, c["x0"], c["U_nom"], np.zeros((5, 6), np.float32),
                                   c["path"], c["ds"], 0, 0, 5)
         assert st == pkg.BRMPPI_EINVAL  # more obstacles than the capacity
+        sharp = c["path"].copy()
+        sharp[len(sharp) // 2:, 2] += 1.0  # a 1 rad heading jump between two rows
+        st, *_ = pkg.brmppi_solve(s.ctx, c["x0"], c["U_nom"], c["obs"], sharp, c["ds"], 0, 0, 5)
+        assert st == pkg.BRMPPI_EINVAL
         # the context still works after rejected calls
         out = s.solve(c["x0"], c["U_nom"], c["obs"], c["path"], c["ds"], c["seed"], c["counter"])
         assert out["status"] == 0
+    finally:
+        s.close()
+
+
+def test_device_path_turn_rejected_by_the_kernel(pkg):
+    # device buffers are not checked on the host: the kernel flags a path
+    # whose consecutive headings differ by more than pi/4 and reports EINVAL
+    import torch
+    c = sc.small_random(11, S=64, H=8, n_obs=2)
+    s = pkg.Solver(c["params"], max_obstacles=4, max_path_pts=512)
+    try:
+        dev = torch.device("cuda:0")
+        t = lambda a, dt=torch.float32: torch.tensor(np.asarray(a), dtype=dt, device=dev)
+        U = torch.empty((8, 3), device=dev)
+        st = torch.full((1,), 99, dtype=torch.int32, device=dev)
+        sharp = c["path"].copy()
+        sharp[5:, 2] -= 0.8
+        rc = s.solve_device(t(c["x0"], torch.float64), t(c["U_nom"]), t(c["obs"]), t(sharp),
+                            c["ds"], c["seed"], c["counter"], U, None, None, None, st)
+        assert rc == 0
+        torch.cuda.synchronize()
+        assert int(st.item()) == pkg.BRMPPI_EINVAL
+        # the next solve on the same context starts from clean error bits
+        rc = s.solve_device(t(c["x0"], torch.float64), t(c["U_nom"]), t(c["obs"]), t(c["path"]),
+                            c["ds"], c["seed"], c["counter"], U, None, None, None, st)
+        torch.cuda.synchronize()
+        assert rc == 0 and int(st.item()) == 0
     finally:
         s.close()
 

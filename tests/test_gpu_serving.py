@@ -138,6 +138,10 @@ def test_backpressure_and_errors(pkg):
         assert srv.server_stats()["request_slots"] == 3
         st, _ = srv.submit(0, c["x0"], c["obs"])  # unregistered vehicle
         assert st == pkg.BRMPPI_EINVAL
+        sharp = c["path"].copy()
+        sharp[3:, 2] += 1.0  # consecutive headings more than pi/4 apart
+        with pytest.raises(pkg.BrmppiError):
+            srv.register(0, sharp, c["ds"], c["U_nom"], c["seed"])
         srv.register(0, c["path"], c["ds"], c["U_nom"], c["seed"])
         tickets = [srv.submit(0, c["x0"], c["obs"])[1] for _ in range(3)]
         st, _ = srv.submit(0, c["x0"], c["obs"])  # slots are held until polled
