@@ -186,6 +186,25 @@ __device__ __forceinline__ void turn_sincos(float e, float* s, float* c) {
             1.0f);
 }
 
+// sin and cos of a state angle, without branches.  Cody-Waite reduction by
+// pi/2 (Cody and Waite, 1980): pi/2 split into the float nearest it and the
+// float nearest the remainder; x - k hi is exact for |x| < 2^24 pi/2, so r
+// carries one rounding; then turn_sincos on |r| <= pi/4 and the quadrant.
+// Within 1.3 ulp of the exact values for |x| <= 2^16 (host check against
+// FP64); finite and bounded beyond, NaN for NaN or infinite x.
+__device__ __forceinline__ void state_sincos(float x, float* s, float* c) {
+  const float kf = rintf(x * 0.636619746685028f);  // 2 / pi
+  const int q = static_cast<int>(kf);
+  float r = fmaf(-kf, 1.5707963705062866f, x);
+  r = fmaf(-kf, -4.371138828673793e-08f, r);
+  float sr, cr;
+  turn_sincos(r, &sr, &cr);
+  const bool odd = q & 1;  // x = r + q pi/2
+  const float ss = odd ? cr : sr, cc = odd ? sr : cr;
+  *s = (q & 2) ? -ss : ss;
+  *c = ((q + 1) & 2) ? -cc : cc;
+}
+
 // into [-pi, pi]; only the square of the result is used
 __device__ __forceinline__ float wrap_pi(float a) {
   return a - 6.28318530717958647692f * rintf(a * 0.15915494309189533577f);
@@ -710,13 +729,15 @@ __device__ void run_tile(const KConst& k, const Inst& in, int tile, float* uh, c
 
     // trigonometry of the current state
     float sr, cr;
-    sincosf(t1, &sr, &cr);
+    state_sincos(t1, &sr, &cr);
     const float c1 = c0 * cr - s0 * sr;
     const float s1 = s0 * cr + c0 * sr;
     const float phi = t1 - t2;
     float sp, cp;
-    sincosf(phi, &sp, &cp);
-    const float tn = tanf(dl);
+    state_sincos(phi, &sp, &cp);
+    float sd, cd;
+    state_sincos(dl, &sd, &cd);
+    const float tn = __fdividef(sd, cd);  // |cos| >= 4e-9 below 2^16: MUFU reciprocal (~2 ulp)
     const float vv = v + vl;
     const float th1dot = vv * tn * k.inv_l1;
 
