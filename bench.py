@@ -78,10 +78,10 @@ def _dist_env():
 
 def kernel_source_hash() -> str:
     """First 16 hex digits of the SHA-256 of the solve kernel's device code
-    and launch logic (rollout.cuh, then kernels.cu)."""
+    and launch logic (trig.cuh, rollout.cuh, then kernels.cu)."""
     import hashlib
     h = hashlib.sha256()
-    for name in ("rollout.cuh", "kernels.cu"):
+    for name in ("trig.cuh", "rollout.cuh", "kernels.cu"):
         with open(os.path.join(ROOT, "paper_2508_05773_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]

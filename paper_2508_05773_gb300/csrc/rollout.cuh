@@ -58,6 +58,8 @@
 #include <cuda_runtime.h>
 #include <math_constants.h>
 
+#include "trig.cuh"
+
 namespace brmppi {
 
 // ------------------------------------------------------------ descriptors
@@ -170,42 +172,6 @@ __device__ __forceinline__ void box_muller(uint32_t wa, uint32_t wb, float& n0, 
 
 __device__ __forceinline__ float clampf(float v, float lo, float hi) { return fminf(fmaxf(v, lo), hi); }
 
-// sin and cos of the turn within one path segment, |e| <= pi/4 (rows
-// farther apart are rejected when the path is staged): Taylor series of sin
-// to e^9 and of cos to e^10, truncation below 2e-9, no branch.
-__device__ __forceinline__ void turn_sincos(float e, float* s, float* c) {
-  const float e2 = e * e, e4 = e2 * e2;
-  // sin e = e + e^3 (-1/3! + e^2/5! + e^4 (-1/7! + e^2/9!))
-  *s = fmaf(e * e2,
-            fmaf(e4, fmaf(e2, 2.7557318844628753e-06f, -1.9841270113829523e-04f),
-                 fmaf(e2, 8.333333767950535e-03f, -0.1666666716337204f)),
-            e);
-  // cos e = 1 + e^2 (-1/2! + e^2/4! + e^4 (-1/6! + e^2/8!) - e^8/10!)
-  *c = fmaf(e2,
-            fmaf(e4 * e4, -2.755731998149713e-07f,
-                 fmaf(e4, fmaf(e2, 2.4801587642286904e-05f, -1.3888889225199819e-03f),
-                      fmaf(e2, 0.0416666679084301f, -0.5f))),
-            1.0f);
-}
-
-// sin and cos of a state angle, without branches.  Cody-Waite reduction by
-// pi/2 (Cody and Waite, 1980): pi/2 split into the float nearest it and the
-// float nearest the remainder; x - k hi is exact for |x| < 2^24 pi/2, so r
-// carries one rounding; then turn_sincos on |r| <= pi/4 and the quadrant.
-// Within 1.3 ulp of the exact values for |x| <= 2^16 (host check against
-// FP64); finite and bounded beyond, NaN for NaN or infinite x.
-__device__ __forceinline__ void state_sincos(float x, float* s, float* c) {
-  const float kf = rintf(x * 0.636619746685028f);  // 2 / pi
-  const int q = static_cast<int>(kf);
-  float r = fmaf(-kf, 1.5707963705062866f, x);
-  r = fmaf(-kf, -4.371138828673793e-08f, r);
-  float sr, cr;
-  turn_sincos(r, &sr, &cr);
-  const bool odd = q & 1;  // x = r + q pi/2
-  const float ss = odd ? cr : sr, cc = odd ? sr : cr;
-  *s = (q & 2) ? -ss : ss;
-  *c = ((q + 1) & 2) ? -cc : cc;
-}
 
 // into [-pi, pi]; only the square of the result is used
 __device__ __forceinline__ float wrap_pi(float a) {
