@@ -55,7 +55,7 @@
 extern "C" {
 #endif
 
-#define BRMPPI_ABI_VERSION 6u
+#define BRMPPI_ABI_VERSION 7u
 
 typedef enum {
   BRMPPI_OK = 0,
@@ -164,6 +164,12 @@ typedef struct brmppi_instance {
   float *u_safe_out; /* may be NULL: U*[0] after the hitch stabilizer (see
                         brmppi_hitch_stabilize_device), 4 floats, written by
                         a small launch that follows the solve on its stream */
+  float *inputs_out; /* may be NULL: every sample's applied (clipped) inputs,
+                        S x H x 3 -- the u_s of the update */
+  float *J_lo_out;   /* may be NULL: S floats; the cost of sample s that the
+                        softmin uses is the unevaluated pair
+                        J_out[s] + J_lo_out[s] (|J_lo_out[s]| <= half an ulp
+                        of J_out[s]) */
 } brmppi_instance;
 
 typedef struct brmppi_graph brmppi_graph; /* a captured batch launch */
@@ -272,11 +278,15 @@ brmppi_status brmppi_autotune_batch(brmppi_ctx *ctx, const brmppi_instance *inst
    a file-scope device array of about 3.1 MiB that every device loading the
    library keeps until exit.  Maxima: S <= 4096, H <= 64, n_obs <= 16,
    n_pts <= 4096; larger sizes return BRMPPI_EINVAL with the reason in
-   brmppi_last_error(NULL).  The first call on a device looks up the array's
-   device address and sets the kernels' shared-memory limit for that
-   device; make that first call before any stream capture.  All calls on a
-   device share the array (counters are cleared on `stream` before each
-   launch): calls that overlap on the GPU race, so serialise them. */
+   brmppi_last_error(NULL), and so does a shared-memory need above the
+   device's limit.  The first call on a device sets the kernels'
+   shared-memory limit for that device; make that first call before any
+   stream capture.  Every call looks up the array's device address with
+   cudaGetSymbolAddress (a host-side query that allocates nothing) and
+   repeats that set-up if the address changed (after a cudaDeviceReset).
+   All calls on a device share the array (counters are cleared on `stream`
+   before each launch): calls that overlap on the GPU race, so serialise
+   them. */
 brmppi_status brmppi_solve_device_noalloc(const brmppi_params *p, const double *x0_dev,
                                           const float *U_nom_dev, const float *obs_dev,
                                           int32_t n_obs, const float *path_dev, int32_t n_pts,
@@ -337,6 +347,23 @@ brmppi_status brmppi_get_launch(brmppi_ctx *ctx, int32_t n_obs, int32_t *threads
    the autotuned shape after brmppi_autotune_batch, else the default for the
    context's obstacle capacity.  Threads per block exclude noise warps. */
 brmppi_status brmppi_get_batch_launch(brmppi_ctx *ctx, int32_t *threads_per_sample, int32_t *block_threads);
+
+/* The noise stream of the solves, for checking it (paper Sec. II-B: the
+   sampled perturbations; reading R15 of the noise generator): for samples
+   s < n_samples, steps tau < H and Philox blocks b < n_blocks, the four
+   Philox4x32-10 words of key (seed lo, seed hi) and counter (b, tau, s,
+   counter lo), and the four standard normals the solve kernel draws from
+   them (Box-Muller on the word pairs (0, 1) and (2, 3) after the map
+   ((w >> 9) + 1/2) 2^-23), computed by the same device functions as the
+   solves.  Layout: words_dev (uint32) and normals_dev (float), both
+   n_samples*H*n_blocks*4 entries at ((s*H + tau)*n_blocks + b)*4 + j, device
+   memory owned by the caller, 16-byte aligned; either may be NULL.  Enqueued
+   on `stream` (no synchronisation, no allocation, no context).  EINVAL for
+   negative sizes, more than 2^31 blocks, H or n_blocks above 2^16, or a
+   misaligned output, with the reason in brmppi_last_error(NULL). */
+brmppi_status brmppi_noise_blocks(uint64_t seed, uint64_t counter, int32_t n_samples, int32_t H,
+                                  int32_t n_blocks, uint32_t *words_dev, float *normals_dev,
+                                  void *stream);
 
 /* Bytes the host entry point brmppi_solve copies per call for a solve with
    n_obs obstacles and n_pts path rows: *h2d (inputs, one copy) and *d2h

@@ -124,6 +124,13 @@ def _load():
                                              ctypes.c_double, ctypes.c_uint64, ctypes.c_uint64,
                                              _DP, _DP, _DP, _DP, _DP]),
                 "orc_integrate": (None, [P, _DP, _DP, ctypes.c_int, _DP]),
+                "orc_noise_table": (None, [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int, ctypes.c_int,
+                                           ctypes.c_int, u32p, _DP]),
+                "orc_update": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _DP, _DP, ctypes.c_double,
+                                              _DP, _DP, _DP]),
+                "orc_rollout_range": (ctypes.c_int, [P, _DP, _DP, _DP, ctypes.c_int, _DP, ctypes.c_int,
+                                                     ctypes.c_double, ctypes.c_uint64, ctypes.c_uint64,
+                                                     ctypes.c_uint32, ctypes.c_uint32, _DP, _DP, _DP]),
                 "orc_obstacle_h_at": (ctypes.c_double, [P, _DP, ctypes.c_int, ctypes.c_double,
                                                         _DP]),
                 "orc_obstacle_row_at": (None, [P, _DP, ctypes.c_int, ctypes.c_double, _DP, _DP,
@@ -522,3 +529,53 @@ def solve(p: dict, x0, U_nom, obs, path, ds, seed, counter, *, want_J=True, want
                        float(ds), int(seed), int(counter), _ptr(U), _ptr(traj), _ptr(J),
                        _ptr(uh), _ptr(xs))
     return dict(U=U, traj=traj, J=J, u_hist=uh, states=xs, status=st)
+
+
+def update(J, u_hist, lam, U_nom):
+    """The MPPI update of Sec. II-B from given costs J (S,) and applied
+    inputs u_hist (S, H, 3): softmin weights, then the weighted sum in
+    sample order.  Returns (status, U (H, 3), gamma_bar (S,))."""
+    lib = _load()
+    J = _d(J)
+    uh = _d(u_hist)
+    S = J.size
+    H = uh.size // (3 * S) if S else 0
+    U = np.zeros((H, 3))
+    g = np.zeros(S)
+    st = lib.orc_update(S, H, _ptr(J), _ptr(uh), float(lam), _ptr(_d(U_nom, 3 * H)), _ptr(g), _ptr(U))
+    return st, U, g
+
+
+def rollouts(p: dict, x0, U_nom, obs, path, ds, seed, counter, s0: int, s1: int, *, want_uhist=True,
+             want_states=False):
+    """Rollouts of samples s0 .. s1-1 of one solve (each as rollout_sample):
+    dict(J (n,), u_hist (n, H, 3) or None, states (n, H+1, NX) or None,
+    status).  A solve's samples can be spread over worker processes and
+    joined with `update`."""
+    lib = _load()
+    n = int(s1) - int(s0)
+    H = int(p["H"])
+    obs = _d(obs).reshape(-1, obs_stride(p))
+    n_obs = obs.shape[0]
+    path = _d(path)
+    nx = state_dim(p)
+    J = np.zeros(n)
+    uh = np.zeros((n, H, 3)) if want_uhist else None
+    xs = np.zeros((n, H + 1, nx)) if want_states else None
+    P = _params(p)
+    st = lib.orc_rollout_range(ctypes.byref(P), _ptr(_d(x0, nx)), _ptr(_d(U_nom, 3 * H)),
+                               _ptr(obs) if n_obs else None, n_obs, _ptr(path), path.size // 3,
+                               float(ds), int(seed), int(counter), int(s0), int(s1), _ptr(J),
+                               _ptr(uh), _ptr(xs))
+    return dict(J=J, u_hist=uh, states=xs, status=st)
+
+
+def noise_table(seed: int, counter: int, n_samples: int, H: int, n_blocks: int):
+    """The noise stream block by block: (words uint32, normals float64), each
+    of shape (n_samples, H, n_blocks, 4)."""
+    lib = _load()
+    w = np.zeros((n_samples, H, n_blocks, 4), dtype=np.uint32)
+    n = np.zeros((n_samples, H, n_blocks, 4))
+    lib.orc_noise_table(int(seed), int(counter), int(n_samples), int(H), int(n_blocks),
+                        w.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)), _ptr(n))
+    return w, n

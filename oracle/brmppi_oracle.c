@@ -95,6 +95,31 @@ void orc_normals(uint64_t seed, uint64_t counter, uint32_t s, uint32_t tau, int 
   }
 }
 
+/* The noise stream as a table (for comparing generators block by block):
+   for samples s < n_samples, steps tau < H, blocks b < n_blocks, the Philox
+   words of counter (b, tau, s, counter lo) and the four normals of block b
+   from orc_normals, at ((s*H + tau)*n_blocks + b)*4 + j.  Either output may
+   be NULL. */
+void orc_noise_table(uint64_t seed, uint64_t counter, int n_samples, int H, int n_blocks, uint32_t *words,
+                     double *normals) {
+  const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+  double *n = normals ? (double *)malloc(sizeof(double) * 4 * (size_t)n_blocks) : NULL;
+  for (int s = 0; s < n_samples; ++s)
+    for (int tau = 0; tau < H; ++tau) {
+      const size_t base = ((size_t)s * (size_t)H + (size_t)tau) * (size_t)n_blocks * 4;
+      if (words)
+        for (int b = 0; b < n_blocks; ++b) {
+          const uint32_t ctr[4] = {(uint32_t)b, (uint32_t)tau, (uint32_t)s, (uint32_t)counter};
+          orc_philox4x32_10(ctr, key, words + base + 4 * (size_t)b);
+        }
+      if (n) {
+        orc_normals(seed, counter, (uint32_t)s, (uint32_t)tau, 4 * n_blocks, n);
+        memcpy(normals + base, n, sizeof(double) * 4 * (size_t)n_blocks);
+      }
+    }
+  free(n);
+}
+
 /* ------------------------------------------------------------------ */
 /* Tractor-trailer kinematics, explicit Euler (Sec. III-A,
    Eq. tt_discrete_kinematics), with acceleration a as input and the path
@@ -958,6 +983,46 @@ int orc_rollout_sample(const orc_params *P, const double *x0, const double *U_no
 /* The solve: S rollouts, softmin weights, and the update of
    Eq. MPPI_update_rule over the applied inputs; then the optimal
    trajectory, x0 integrated with U*. */
+/* The MPPI update (Sec. II-B, Eq. MPPI_update_rule): softmin weights of the
+   costs, then U*[k] = sum_s gamma_bar_s u_s[k] over the applied inputs, in
+   sample order.  No finite cost: U_out = U_nom and ORC_ENONFINITE.
+   gamma_bar: S doubles of workspace (the weights on return). */
+int orc_update(int S, int H, const double *J, const double *u_hist, double lambda,
+               const double *U_nom, double *gamma_bar, double *U_out) {
+  const int status = orc_softmin(S, J, lambda, gamma_bar);
+  if (status == ORC_OK) {
+    for (int k = 0; k < 3 * H; ++k) {
+      double acc = 0.0;
+      for (int s = 0; s < S; ++s) acc += gamma_bar[s] * u_hist[(size_t)s * (size_t)H * 3 + (size_t)k];
+      U_out[k] = acc;
+    }
+  } else {
+    for (int k = 0; k < 3 * H; ++k) U_out[k] = U_nom[k];
+  }
+  return status;
+}
+
+/* Rollouts of samples s0 .. s1-1 (each exactly as orc_rollout_sample):
+   J_out (s1 - s0), u_hist (s1 - s0)*H*3, states_out (s1 - s0)*(H+1)*NX;
+   u_hist and states_out may be NULL.  Lets a caller spread one solve's
+   samples over several processes. */
+int orc_rollout_range(const orc_params *P, const double *x0, const double *U_nom, const double *obs,
+                      int n_obs, const double *path, int n_pts, double ds, uint64_t seed,
+                      uint64_t counter, uint32_t s0, uint32_t s1, double *J_out, double *u_hist,
+                      double *states_out) {
+  const int H = P->H;
+  const int nx = (P->flags & ORC_JERK) ? 8 : 7;
+  for (uint32_t s = s0; s < s1; ++s) {
+    const size_t i = (size_t)(s - s0);
+    const int st = orc_rollout_sample(P, x0, U_nom, obs, n_obs, path, n_pts, ds, seed, counter, s,
+                                      states_out ? states_out + i * (size_t)(H + 1) * (size_t)nx : NULL,
+                                      u_hist ? u_hist + i * (size_t)H * 3 : NULL, NULL, NULL, NULL,
+                                      &J_out[i]);
+    if (st != ORC_OK) return st;
+  }
+  return ORC_OK;
+}
+
 int orc_solve(const orc_params *P, const double *x0, const double *U_nom, const double *obs,
               int n_obs, const double *path, int n_pts, double ds, uint64_t seed,
               uint64_t counter, double *U_out, double *traj_out, double *J_out, double *u_hist,
@@ -977,16 +1042,7 @@ int orc_solve(const orc_params *P, const double *x0, const double *U_nom, const 
                                 uh + (size_t)s * (size_t)H * 3, NULL, NULL, NULL, &J[s]);
   }
   if (status == ORC_OK) {
-    status = orc_softmin(S, J, P->lambda, gb);
-    if (status == ORC_OK) {
-      for (int k = 0; k < 3 * H; ++k) {
-        double acc = 0.0;
-        for (int s = 0; s < S; ++s) acc += gb[s] * uh[(size_t)s * (size_t)H * 3 + (size_t)k];
-        U_out[k] = acc;
-      }
-    } else {
-      for (int k = 0; k < 3 * H; ++k) U_out[k] = U_nom[k];
-    }
+    status = orc_update(S, H, J, uh, P->lambda, U_nom, gb, U_out);
     if (traj_out) {
       if (P->flags & ORC_JERK)
         orc_jerk_integrate(P, x0, U_out, H, traj_out);

@@ -71,6 +71,12 @@ void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t ou
    word pairs). */
 void orc_normals(uint64_t seed, uint64_t counter, uint32_t s, uint32_t tau, int d, double *n);
 
+/* The noise stream as a table: Philox words (uint32) and normals (double) of
+   samples s < n_samples, steps tau < H, blocks b < n_blocks at
+   ((s*H + tau)*n_blocks + b)*4 + j; either output may be NULL. */
+void orc_noise_table(uint64_t seed, uint64_t counter, int n_samples, int H, int n_blocks, uint32_t *words,
+                     double *normals);
+
 /* One explicit-Euler step of the tractor-trailer kinematics. */
 void orc_dynamics_step(const orc_params *P, const double x[7], const double u[3], double xn[7]);
 
@@ -174,6 +180,20 @@ int orc_rollout_sample(const orc_params *P, const double *x0, const double *U_no
                        const double *obs, int n_obs, const double *path, int n_pts, double ds,
                        uint64_t seed, uint64_t counter, uint32_t s, double *states, double *u,
                        double *alpha, double *z_des, double *z_star, double *J);
+
+/* The MPPI update (Sec. II-B): softmin weights of J, then the weighted sum of
+   the applied inputs u_hist (S*H*3) in sample order into U_out (H*3).
+   gamma_bar: S doubles (workspace; the weights on return).  No finite J:
+   U_out = U_nom and ORC_ENONFINITE. */
+int orc_update(int S, int H, const double *J, const double *u_hist, double lambda,
+               const double *U_nom, double *gamma_bar, double *U_out);
+
+/* Rollouts of samples s0 .. s1-1, each as orc_rollout_sample: J_out (s1-s0),
+   u_hist (s1-s0)*H*3 and states_out (s1-s0)*(H+1)*NX optional (NULL). */
+int orc_rollout_range(const orc_params *P, const double *x0, const double *U_nom, const double *obs,
+                      int n_obs, const double *path, int n_pts, double ds, uint64_t seed,
+                      uint64_t counter, uint32_t s0, uint32_t s1, double *J_out, double *u_hist,
+                      double *states_out);
 
 /* The full solve.  U_out H*3 (required); traj_out (H+1)*NX, J_out S,
    u_hist S*H*3, states_out S*(H+1)*NX optional (NX as for rollouts).  On

@@ -13,7 +13,7 @@ from ._native import (  # noqa: F401
     NativeLibraryMissing, Solver, brmppi_autotune, brmppi_autotune_batch, brmppi_batch_capture,
     brmppi_create, brmppi_default_params, brmppi_destroy, brmppi_get_batch_launch, brmppi_get_launch,
     brmppi_graph_destroy, brmppi_graph_launch, brmppi_hitch_stabilize_device, brmppi_instance,
-    brmppi_last_error, brmppi_params, brmppi_poll, brmppi_server_stats, brmppi_server_stats_get,
+    brmppi_last_error, brmppi_noise_blocks, brmppi_params, brmppi_poll, brmppi_server_stats, brmppi_server_stats_get,
     brmppi_solve, brmppi_solve_batch, brmppi_solve_device, brmppi_solve_device_ex,
     brmppi_solve_device_noalloc, brmppi_submit, brmppi_transfer_bytes, brmppi_vehicle_export,
     brmppi_vehicle_import, brmppi_vehicle_register, load, make_instances, params_from_dict,

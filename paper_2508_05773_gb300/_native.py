@@ -12,7 +12,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libbrmppi.so")
 
-BRMPPI_ABI_VERSION = 6
+BRMPPI_ABI_VERSION = 7
 BRMPPI_OK = 0
 BRMPPI_EINVAL = -1
 BRMPPI_ENOMEM = -2
@@ -39,6 +39,7 @@ EXPORTS = (
     "brmppi_get_launch", "brmppi_transfer_bytes", "brmppi_vehicle_register", "brmppi_submit",
     "brmppi_poll", "brmppi_vehicle_export", "brmppi_vehicle_import", "brmppi_server_stats_get",
     "brmppi_solve_device_noalloc", "brmppi_hitch_stabilize_device", "brmppi_get_batch_launch",
+    "brmppi_noise_blocks",
 )
 
 
@@ -78,6 +79,7 @@ class brmppi_instance(ctypes.Structure):
         ("U_out", ctypes.c_void_p), ("traj_out", ctypes.c_void_p), ("J_out", ctypes.c_void_p),
         ("U_next", ctypes.c_void_p), ("status", ctypes.c_void_p),
         ("states_out", ctypes.c_void_p), ("u_safe_out", ctypes.c_void_p),
+        ("inputs_out", ctypes.c_void_p), ("J_lo_out", ctypes.c_void_p),
     ]
 
 
@@ -160,6 +162,8 @@ def load() -> ctypes.CDLL:
             "brmppi_transfer_bytes": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.c_int32,
                                                      ctypes.POINTER(ctypes.c_uint64),
                                                      ctypes.POINTER(ctypes.c_uint64)]),
+            "brmppi_noise_blocks": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int32,
+                                                   ctypes.c_int32, ctypes.c_int32, _VP, _VP, _VP]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -312,7 +316,8 @@ def _stream_handle(stream):
 
 def make_instances(insts) -> "ctypes.Array":
     """ctypes array of brmppi_instance from dicts of torch CUDA tensors
-    (x0, U_nom, obs, path, U_out; optional traj_out, J_out, U_next, status)
+    (x0, U_nom, obs, path, U_out; optional traj_out, J_out, U_next, status,
+    states_out, u_safe_out, inputs_out, J_lo_out)
     and scalars (ds, seed, counter)."""
     arr = (brmppi_instance * len(insts))()
     for i, d in enumerate(insts):
@@ -330,7 +335,8 @@ def make_instances(insts) -> "ctypes.Array":
         q.seed = int(d["seed"]) & (2**64 - 1)
         q.counter = int(d.get("counter", 0)) & (2**64 - 1)
         q.U_out = d["U_out"].data_ptr()
-        for key in ("traj_out", "J_out", "U_next", "status", "states_out", "u_safe_out"):
+        for key in ("traj_out", "J_out", "U_next", "status", "states_out", "u_safe_out", "inputs_out",
+                    "J_lo_out"):
             t = d.get(key)
             setattr(q, key, None if t is None else t.data_ptr())
     return arr
@@ -399,6 +405,15 @@ def brmppi_hitch_stabilize_device(ctx, x, u_ref, u_out, stream=None) -> int:
     n = u_ref.numel() // 3
     return load().brmppi_hitch_stabilize_device(ctx, _dptr(x), _dptr(u_ref), n, _dptr(u_out),
                                                 ctypes.c_void_p(_stream_handle(stream)))
+
+
+def brmppi_noise_blocks(seed: int, counter: int, n_samples: int, H: int, n_blocks: int, words=None,
+                        normals=None, stream=None) -> int:
+    """The solves' noise stream: Philox words (uint32 viewed as int32) and
+    normals (float32) of shape (n_samples, H, n_blocks, 4), torch CUDA
+    tensors or None."""
+    return load().brmppi_noise_blocks(int(seed), int(counter), int(n_samples), int(H), int(n_blocks),
+                                      _dptr(words), _dptr(normals), ctypes.c_void_p(_stream_handle(stream)))
 
 
 def brmppi_get_launch(ctx, n_obs: int):

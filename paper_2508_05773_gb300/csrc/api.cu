@@ -21,7 +21,7 @@ using namespace brmppi_host;
 
 // The layouts the Python binding mirrors.
 static_assert(sizeof(brmppi_params) == 4 * 15 + 4 * 41 + 4 * 10, "brmppi_params layout");
-static_assert(sizeof(brmppi_instance) == 8 * 4 + 4 * 5 + 4 + 8 * 2 + 8 * 7, "brmppi_instance layout");
+static_assert(sizeof(brmppi_instance) == 8 * 4 + 4 * 5 + 4 + 8 * 2 + 8 * 9, "brmppi_instance layout");
 
 namespace brmppi_host {
 
@@ -332,13 +332,16 @@ brmppi_status enqueue_plain_sized(brmppi_ctx* c, const Shape& sh, int S, int H, 
                                   const float* U_nom, const float* obs, int32_t n_obs, const float* path,
                                   int32_t n_pts, float ds, uint64_t seed, uint64_t counter, float* U_out,
                                   float* traj_out, float* J_out, float* U_next, int32_t* status, float* states_out,
-                                  float* u_safe, cudaStream_t stream) {
+                                  float* u_safe, cudaStream_t stream, float* inputs_out = nullptr,
+                                  float* J_lo_out = nullptr) {
   const int spb = sh.threads / sh.tps;
   brmppi::LaunchDesc L{};
   L.single = make_inst(x0, U_nom, obs, n_obs, path, n_pts, ds, S, H, seed, counter, U_out, traj_out, J_out,
                        U_next, status, c->d_part, c->d_sync, spb, c->prm.n_discs);
   L.single.states_out = states_out;
   L.single.u_safe = u_safe;
+  L.single.inputs_out = inputs_out;
+  L.single.J_lo_out = J_lo_out;
   L.caps = make_caps(n_obs, rows_of(c->prm, n_obs), n_pts, H, sh.tps);
   L.uh = c->d_uh;
   L.uh_stride = 3 * H * spb;
@@ -497,6 +500,8 @@ brmppi_status plan_batch(brmppi_ctx* c, Lane& L, const brmppi_instance* inst, in
                                 c->prm.n_discs);
     in.states_out = q.states_out;
     in.u_safe = q.u_safe_out;
+    in.inputs_out = q.inputs_out;
+    in.J_lo_out = q.J_lo_out;
     if (q.u_safe_out) plan->any_u_safe = true;
     in.part = L.d_bpart + pool;
     pool += static_cast<size_t>(in.tiles) * static_cast<size_t>(in.part_stride);
@@ -776,7 +781,8 @@ brmppi_status brmppi_solve_device_ex(brmppi_ctx* c, const brmppi_instance* q, vo
   if (!plain_shape(c, q->n_obs, q->n_pts, &sh)) return fail(c, BRMPPI_EINVAL, "no launch shape for this size");
   return enqueue_plain_sized(c, sh, q->S, q->H, q->x0, q->U_nom, q->obs, q->n_obs, q->path, q->n_pts, q->ds,
                              q->seed, q->counter, q->U_out, q->traj_out, q->J_out, q->U_next, q->status,
-                             q->states_out, q->u_safe_out, static_cast<cudaStream_t>(stream));
+                             q->states_out, q->u_safe_out, static_cast<cudaStream_t>(stream), q->inputs_out,
+                             q->J_lo_out);
 }
 
 brmppi_status brmppi_solve_batch(brmppi_ctx* c, const brmppi_instance* inst, int32_t n, void* stream) {
@@ -1011,6 +1017,22 @@ brmppi_status brmppi_hitch_stabilize_device(brmppi_ctx* c, const double* x_dev, 
   if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
   e = brmppi::launch_stabilize(make_kconst(c->prm), x_dev, u_ref_dev, n, u_out_dev, static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(c, e, "stabilizer launch");
+  return BRMPPI_OK;
+}
+
+brmppi_status brmppi_noise_blocks(uint64_t seed, uint64_t counter, int32_t n_samples, int32_t H, int32_t n_blocks,
+                                  uint32_t* words_dev, float* normals_dev, void* stream) {
+  if (n_samples < 0 || H < 0 || n_blocks < 0) return fail(nullptr, BRMPPI_EINVAL, "negative size");
+  if (static_cast<long long>(n_samples) * H * n_blocks > (1LL << 31))
+    return fail(nullptr, BRMPPI_EINVAL, "more than 2^31 blocks");
+  if (n_blocks > (1 << 16) || H > (1 << 16)) return fail(nullptr, BRMPPI_EINVAL, "H or n_blocks above 2^16");
+  if ((words_dev && (reinterpret_cast<uintptr_t>(words_dev) & 15)) ||
+      (normals_dev && (reinterpret_cast<uintptr_t>(normals_dev) & 15)))
+    return fail(nullptr, BRMPPI_EINVAL, "outputs must be 16-byte aligned");
+  const cudaError_t e =
+      brmppi::launch_noise_blocks(seed, counter, n_samples, H, n_blocks, words_dev, normals_dev,
+                                  static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "noise-table launch");
   return BRMPPI_OK;
 }
 

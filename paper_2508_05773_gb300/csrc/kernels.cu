@@ -57,7 +57,42 @@ __global__ void __launch_bounds__(128) stabilize_table_kernel(const KConst k, co
                   in.U_out[1], in.U_out[2], in.u_safe);
 }
 
+// One Philox block per thread: the words and normals the solve kernel draws
+// for block b of step tau of sample s (the same device functions), at index
+// ((s * H + tau) * n_blocks + b) * 4 + j.
+__global__ void __launch_bounds__(256) noise_blocks_kernel(uint32_t key0, uint32_t key1, uint32_t ctr, int n_samples,
+                                                           int H, int n_blocks, uint32_t* words, float* normals) {
+  const long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+  const long long n = static_cast<long long>(n_samples) * H * n_blocks;
+  if (i >= n) return;
+  const int b = static_cast<int>(i % n_blocks);
+  const long long st = i / n_blocks;
+  const int tau = static_cast<int>(st % H);
+  const int s = static_cast<int>(st / H);
+  const uint4 w = philox4x32_10(
+      make_uint4(static_cast<uint32_t>(b), static_cast<uint32_t>(tau), static_cast<uint32_t>(s), ctr), key0, key1);
+  if (words) reinterpret_cast<uint4*>(words)[i] = w;
+  if (normals) {
+    float4 g;
+    box_muller(w.x, w.y, g.x, g.y);
+    box_muller(w.z, w.w, g.z, g.w);
+    reinterpret_cast<float4*>(normals)[i] = g;
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_noise_blocks(uint64_t seed, uint64_t counter, int n_samples, int H, int n_blocks, uint32_t* words,
+                                float* normals, cudaStream_t stream) {
+  const long long n = static_cast<long long>(n_samples) * H * n_blocks;
+  if (n <= 0) return cudaSuccess;
+  const int threads = 256;
+  const long long grid = (n + threads - 1) / threads;
+  noise_blocks_kernel<<<static_cast<unsigned>(grid), threads, 0, stream>>>(
+      static_cast<uint32_t>(seed), static_cast<uint32_t>(seed >> 32), static_cast<uint32_t>(counter), n_samples, H,
+      n_blocks, words, normals);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_stabilize_table(const KConst& k, const Inst* d_table, int n, cudaStream_t stream) {
   if (n <= 0) return cudaSuccess;

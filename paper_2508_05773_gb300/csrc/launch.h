@@ -54,6 +54,12 @@ cudaError_t launch_stabilize(const KConst& k, const double* x, const float* u_re
 // u_safe is set (after their solve, on the same stream).
 cudaError_t launch_stabilize_table(const KConst& k, const Inst* d_table, int n, cudaStream_t stream);
 
+// Enqueue the noise-table kernel: Philox words and Box-Muller normals of
+// samples < n_samples, steps < H, blocks < n_blocks (words or normals may
+// be null).
+cudaError_t launch_noise_blocks(uint64_t seed, uint64_t counter, int n_samples, int H, int n_blocks, uint32_t* words,
+                                float* normals, cudaStream_t stream);
+
 // Enqueue one launch of the solve kernel.
 cudaError_t launch_solve(int tps, int bpt, int blocks, int threads, size_t smem, cudaStream_t stream,
                          const KConst& k, const LaunchDesc& L, int P);

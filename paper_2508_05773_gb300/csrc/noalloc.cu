@@ -54,6 +54,7 @@ constexpr size_t kNaScratchFloats = kNaSyncFloats + kNaPartFloats + kNaHistFloat
 constexpr int kMaxDevices = 64;
 std::mutex g_setup_mu;
 float* g_scratch_ptr[kMaxDevices] = {};
+size_t g_smem_optin[kMaxDevices] = {};
 
 }  // namespace
 
@@ -63,26 +64,32 @@ static __device__ __align__(256) float g_noalloc_scratch[kNaScratchFloats];
 
 namespace {
 
-// Once per device, with that device current: the device address of the
-// scratch array, and the shared-memory limit of the kernel variants.
-brmppi_status scratch_for_current_device(float** out) {
+// With the device current: the device address of the scratch array and the
+// device's opt-in shared-memory limit.  The first call on a device also
+// raises the kernel variants' shared-memory limit.  The address is looked up
+// again on every call (a host-side query, no allocation): after a
+// cudaDeviceReset the device's module, and with it the array, may move, and
+// a changed address repeats the set-up.
+brmppi_status scratch_for_current_device(float** out, size_t* smem_optin) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return brmppi_host::cuda_fail(nullptr, e, "cudaGetDevice");
   if (dev < 0 || dev >= kMaxDevices) return brmppi_host::fail(nullptr, BRMPPI_EINVAL, "device index out of range");
+  void* ptr = nullptr;
+  if ((e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch)) != cudaSuccess)
+    return brmppi_host::cuda_fail(nullptr, e, "cudaGetSymbolAddress(no-alloc scratch)");
   std::lock_guard<std::mutex> lk(g_setup_mu);
-  if (!g_scratch_ptr[dev]) {
-    void* ptr = nullptr;
-    if ((e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch)) != cudaSuccess)
-      return brmppi_host::cuda_fail(nullptr, e, "cudaGetSymbolAddress(no-alloc scratch)");
+  if (g_scratch_ptr[dev] != static_cast<float*>(ptr)) {
     int optin = 0;
     if ((e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess)
       return brmppi_host::cuda_fail(nullptr, e, "cudaDeviceGetAttribute");
-    if ((e = brmppi::set_smem_limit(static_cast<size_t>(optin) - 1024)) != cudaSuccess)
+    g_smem_optin[dev] = static_cast<size_t>(optin) - 1024;  // static shared memory of the kernel
+    if ((e = brmppi::set_smem_limit(g_smem_optin[dev])) != cudaSuccess)
       return brmppi_host::cuda_fail(nullptr, e, "cudaFuncSetAttribute");
     g_scratch_ptr[dev] = static_cast<float*>(ptr);
   }
   *out = g_scratch_ptr[dev];
+  *smem_optin = g_smem_optin[dev];
   return BRMPPI_OK;
 }
 
@@ -108,7 +115,8 @@ extern "C" brmppi_status brmppi_solve_device_noalloc(const brmppi_params* p, con
   if (!x0_dev || !U_nom_dev || !path_dev || !U_out_dev || (n_obs > 0 && !obs_dev))
     return fail(nullptr, BRMPPI_EINVAL, "no-alloc solve: NULL buffer");
   float* scratch = nullptr;
-  brmppi_status st = scratch_for_current_device(&scratch);
+  size_t smem_optin = 0;
+  brmppi_status st = scratch_for_current_device(&scratch, &smem_optin);
   if (st != BRMPPI_OK) return st;
   int bpt = 0;
   const int n_rows = rows_of(*p, n_obs);
@@ -122,6 +130,10 @@ extern "C" brmppi_status brmppi_solve_device_noalloc(const brmppi_params* p, con
   L.uh = part + kNaPartFloats;
   L.uh_stride = 3 * p->H * kNaSpb;
   const size_t smem = smem_bytes(L.caps, kNaSpb);
+  if (smem > smem_optin)
+    return fail(nullptr, BRMPPI_EINVAL,
+                "no-alloc solve: shared memory need " + std::to_string(smem) + " B exceeds the device limit " +
+                    std::to_string(smem_optin) + " B");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   cudaError_t e = cudaMemsetAsync(sync, 0, sizeof(float) * kNaSyncFloats, s);
   if (e != cudaSuccess) return cuda_fail(nullptr, e, "no-alloc solve: clearing counters");

@@ -100,6 +100,8 @@ struct Inst {
   float* states_out;  // may be null: every sample's states, S x (H+1) x 7
   float* u_safe;      // may be null: stabilized U*[0] (a, omega, nu, slack), written
                       // by the stabilizer launch that follows the solve
+  float* inputs_out;  // may be null: every sample's applied inputs, S x H x 3
+  float* J_lo_out;    // may be null: low parts of the compensated costs (J_out the high parts)
   float* part;       // tiles * part_stride floats
   unsigned int* sync;  // [0] finished tiles, [1] error bits
   int S, H, n_obs, n_pts, tiles, part_stride;
@@ -633,6 +635,9 @@ __device__ void run_tile(const KConst& k, const Inst& in, int tile, float* uh, c
     o[6] = (fr.psi_h + ps) + (fr.psi_l + psl);
   };
   if (st_out) store_state(0);
+  float* in_out = (!producer && in.inputs_out && lt == 0 && s < in.S)
+                      ? in.inputs_out + static_cast<size_t>(s) * static_cast<size_t>(H) * 3
+                      : nullptr;
 
   // Noise.  One lane per sample: the lane draws Philox block 0 a step ahead
   // and the further blocks where their rows are built.  Wider teams: the
@@ -992,6 +997,11 @@ __device__ void run_tile(const KConst& k, const Inst& in, int tile, float* uh, c
       uh[(3 * tau + 2) * spb + team] = un;
     }
     if (st_out) store_state(tau + 1);
+    if (in_out) {
+      in_out[3 * tau + 0] = ua;
+      in_out[3 * tau + 1] = uw;
+      in_out[3 * tau + 2] = un;
+    }
     if constexpr (TPS == 1) {
 #pragma unroll
       for (int q = 0; q < 4; ++q) nrm[q] = nxt[q];
@@ -1022,7 +1032,8 @@ __device__ void run_tile(const KConst& k, const Inst& in, int tile, float* uh, c
     const bool fin = valid && isfinite(Jh) && isfinite(Jl);
     S.jh[team] = fin ? Jh : CUDART_INF_F;
     S.jl[team] = fin ? Jl : 0.f;
-    if (valid && in.J_out) in.J_out[s] = Jh + Jl;
+    if (valid && in.J_out) in.J_out[s] = Jh;  // the normalised pair's high part
+    if (valid && in.J_lo_out) in.J_lo_out[s] = Jl;
   }
   __syncthreads();
 

@@ -38,7 +38,13 @@ __host__ __device__ __forceinline__ void turn_sincos(float e, float* s, float* c
 // or non-finite cost it then accrues carries zero weight in the softmin.
 __host__ __device__ __forceinline__ void state_sincos(float x, float* s, float* c) {
   const float kf = rintf(x * 0.636619746685028f);  // 2 / pi
-  const int q = static_cast<int>(kf);
+#ifdef __CUDA_ARCH__
+  const int q = static_cast<int>(kf);  // cvt.rzi: saturates, NaN -> 0
+#else
+  // the same in host C++, where the conversion of NaN or of |kf| >= 2^31 is
+  // undefined: clamp first (only q mod 4 is used), NaN -> 0
+  const int q = (kf == kf) ? static_cast<int>(fminf(fmaxf(kf, -1073741824.0f), 1073741824.0f)) : 0;
+#endif
   float r = fmaf(-kf, 1.5707963705062866f, x);
   r = fmaf(-kf, -4.371138828673793e-08f, r);
   float sr, cr;

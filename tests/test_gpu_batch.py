@@ -7,6 +7,7 @@ import pytest
 
 import oracle
 from paper_2508_05773_gb300 import scenarios as sc
+from tests.gpu_solve import device_solve, device_tensors, host_outputs
 from tests.parity import assert_solve_matches
 
 pytestmark = pytest.mark.gpu
@@ -23,15 +24,9 @@ def pkg():
 
 def _device_inst(c, dev):
     import torch
-    H = int(c["params"]["H"])
-    S = int(c["params"]["S"])
-    t = lambda a, dt=torch.float32: torch.tensor(np.asarray(a), dtype=dt, device=dev)
-    return dict(x0=t(c["x0"], torch.float64), U_nom=t(c["U_nom"]),
-                obs=t(c["obs"]) if c["obs"].shape[0] else None, path=t(c["path"]), ds=c["ds"],
-                S=S, seed=c["seed"], counter=c["counter"],
-                U_out=torch.empty((H, 3), device=dev), traj_out=torch.empty((H + 1, 7), device=dev),
-                J_out=torch.empty(S, device=dev), U_next=torch.empty((H, 3), device=dev),
-                status=torch.full((1,), 99, dtype=torch.int32, device=dev))
+    d = device_tensors(c, dev)
+    d["U_next"] = torch.empty((int(c["params"]["H"]), 3), device=dev)
+    return d
 
 
 def _instances(n, seed=1, S_choices=(64, 200, 333), H_range=(5, 24), obs_range=(0, 12)):
@@ -49,9 +44,7 @@ def _ctx(pkg, cases, max_batch, **kw):
 
 
 def _out(d):
-    return dict(U=d["U_out"].cpu().numpy(), traj=d["traj_out"].cpu().numpy(),
-                J=d["J_out"].cpu().numpy(), U_next=d["U_next"].cpu().numpy(),
-                status=int(d["status"].item()))
+    return host_outputs(d)
 
 
 def test_batch_alone_equals_mix_bitwise(pkg):
@@ -113,8 +106,7 @@ def test_batch_matches_plain_solves(pkg):
             plain = pkg.Solver(c["params"], max_obstacles=max(1, c["obs"].shape[0]),
                                max_path_pts=c["path"].shape[0])
             try:
-                po = plain.solve(c["x0"], c["U_nom"], c["obs"], c["path"], c["ds"], c["seed"],
-                                 c["counter"], want_J=True)
+                po = device_solve(plain, c)
             finally:
                 plain.close()
             p = sc.as_float32(c["params"])
@@ -181,52 +173,10 @@ def test_autotune_keeps_results_within_tolerance(pkg):
         d = _device_inst(c, dev)
         s.autotune(d["x0"], d["U_nom"], d["obs"], d["path"], c["ds"], reps=2)
         launch = s.launch(6)
-        out = s.solve(c["x0"], c["U_nom"], c["obs"], c["path"], c["ds"], c["seed"], c["counter"],
-                      want_J=True)
+        out = device_solve(s, c)
         p = sc.as_float32(c["params"])
         ref = oracle.solve(p, c["x0"], c["U_nom"], c["obs"], c["path"], c["ds"], c["seed"],
                            c["counter"], want_uhist=True)
         assert_solve_matches(out, ref, p, f"autotuned {launch}")
-    finally:
-        s.close()
-
-
-@pytest.mark.slow
-def test_config3_full_batch_sampled(pkg):
-    """The full 256-instance config-3 batch in one persistent launch with
-    the shape the bench times (one lane per sample, 256 threads, capacity
-    16 obstacles): four instances (the largest S and H among them) against
-    the full oracle solve, and sampled rollouts of eight more compared one
-    by one (cost and applied inputs are per sample, so the oracle computes
-    them alone)."""
-    import torch
-    dev = torch.device("cuda:0")
-    cases = sc.config3()
-    Smax = max(int(c["params"]["S"]) for c in cases)
-    Hmax = max(int(c["params"]["H"]) for c in cases)
-    npts = max(c["path"].shape[0] for c in cases)
-    s = pkg.Solver(dict(cases[0]["params"], S=Smax, H=Hmax), max_obstacles=16, max_path_pts=npts,
-                   max_batch=len(cases), batch_threads_per_sample=1, batch_block_threads=256)
-    try:
-        insts = [_device_inst(c, dev) for c in cases]
-        s.solve_batch(insts)
-        torch.cuda.synchronize()
-        assert all(int(d["status"].item()) == 0 for d in insts)
-        order = sorted(range(len(cases)), key=lambda i: -int(cases[i]["params"]["S"]) * int(cases[i]["params"]["H"]))
-        for i in [order[0], order[1], order[len(order) // 2], order[-1]]:
-            c = cases[i]
-            p = sc.as_float32(c["params"])
-            ref = oracle.solve(p, c["x0"], c["U_nom"], c["obs"], c["path"], c["ds"], c["seed"], c["counter"],
-                               want_uhist=True)
-            assert_solve_matches(_out(insts[i]), ref, p, f"config-3 instance {i}")
-        rng = np.random.default_rng(0)
-        for i in rng.choice(len(cases), 8, replace=False):
-            c = cases[int(i)]
-            p = sc.as_float32(c["params"])
-            J = insts[int(i)]["J_out"].cpu().numpy()
-            for smp in rng.choice(int(c["params"]["S"]), 3, replace=False):
-                one = oracle.rollout_sample(p, c["x0"], c["U_nom"], c["obs"], c["path"], c["ds"], c["seed"],
-                                            c["counter"], int(smp))
-                assert abs(J[smp] - one["J"]) <= 2.0 ** -18 * abs(one["J"]), (int(i), int(smp))
     finally:
         s.close()

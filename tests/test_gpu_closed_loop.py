@@ -11,6 +11,7 @@ import pytest
 import oracle
 from paper_2508_05773_gb300 import plant
 from paper_2508_05773_gb300 import scenarios as sc
+from tests.gpu_solve import device_solve
 from tests.parity import assert_solve_matches
 
 pytestmark = pytest.mark.gpu
@@ -40,7 +41,11 @@ def test_closed_loop_1000_ticks(pkg):
             out = solver.solve(x, U, c["obs"], c["path"], c["ds"], c["seed"], k, want_J=k in checks)
             lat.append(time.perf_counter() - t0)
             if k in checks:
-                checks[k] = (x.copy(), U.copy(), out)
+                # the same inputs through the device-instance entry point,
+                # which also returns the cost pairs and applied inputs
+                full = device_solve(solver, c, x0=x, U_nom=U, counter=k)
+                assert np.array_equal(full["U"], out["U"]) and np.array_equal(full["J"], out["J"])
+                checks[k] = (x.copy(), U.copy(), full)
             assert np.all(np.isfinite(out["U"]))
             x = plant.step(p32, x, out["U"][0])
             U = plant.shift(out["U"])
@@ -50,7 +55,9 @@ def test_closed_loop_1000_ticks(pkg):
         ref = oracle.solve(p32, xk, Uk, c["obs"], c["path"], c["ds"], c["seed"], k,
                            want_uhist=True)
         assert ref["status"] == 0
-        assert_solve_matches(out, ref, p32, f"tick {k}")
+        # tick 0 also at the flat 1e-4 against the oracle's own U*; later
+        # ticks hold near-tied samples whose binary32 costs move U* (shift_J)
+        assert_solve_matches(out, ref, p32, f"tick {k}", strict=(k == 0))
     assert np.percentile(lat, 99) < 10e-3  # host-path tick latency under the deadline
     # the loop made progress along the reference path
     assert x[6] > 1.0

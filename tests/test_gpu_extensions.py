@@ -10,6 +10,8 @@ import oracle
 from paper_2508_05773_gb300 import scenarios as sc
 from tests import test_oracle_stabilizer as tz
 from tests.parity import assert_solve_matches, buffer_conditioning, stab_tolerance
+from tests.gpu_solve import add_cost_outputs, device_solve, host_outputs
+from tests.served import served_costs
 
 pytestmark = pytest.mark.gpu
 
@@ -41,8 +43,7 @@ def _gpu(pkg, c, tps=0, threads=0, **over):
     s = pkg.Solver(p, max_obstacles=max(n_obs, 1), max_path_pts=max(2, c["path"].shape[0]),
                    threads_per_sample=tps, block_threads=threads)
     try:
-        return s.solve(c["x0"], c["U_nom"], c["obs"], c["path"], c["ds"], c["seed"], c["counter"],
-                       want_traj=True, want_J=True)
+        return device_solve(s, c)
     finally:
         s.close()
 
@@ -237,12 +238,13 @@ def test_batch_with_moving_obstacles(pkg, torch):
                               traj_out=torch.zeros((H + 1, 7), device="cuda"),
                               J_out=torch.zeros(c["params"]["S"], device="cuda"),
                               u_safe_out=torch.zeros(4, device="cuda") if len(insts) % 2 else None))
+            add_cost_outputs(insts[-1], c["params"]["S"], H)
         s.solve_batch(insts)
         torch.cuda.synchronize()
         for k, (c, q) in enumerate(zip(cases, insts)):
             p, ref = _oracle(c)
-            U = q["U_out"].cpu().numpy()
-            out = dict(U=U, traj=q["traj_out"].cpu().numpy(), J=q["J_out"].cpu().numpy())
+            out = host_outputs(q)
+            U = out["U"]
             assert_solve_matches(out, ref, p, f"batch instance {k}")
             if q["u_safe_out"] is not None:
                 # the stabilizer on (x0, U*[0]) after the batch
@@ -259,7 +261,7 @@ def test_batch_with_moving_obstacles(pkg, torch):
 def test_served_moving_obstacles(pkg):
     c = sc.with_moving(sc.small_random(71, S=256, H=16, n_obs=4), 9)
     pd = c["params"]
-    s = pkg.Solver(pd, max_obstacles=8, max_path_pts=512, max_vehicles=2)
+    s = pkg.Solver(pd, max_obstacles=8, max_path_pts=512, max_vehicles=2, max_batch=1)
     try:
         s.register(0, c["path"], c["ds"], c["U_nom"], c["seed"])
         st, t = s.submit(0, c["x0"], c["obs"])
@@ -276,7 +278,8 @@ def test_served_moving_obstacles(pkg):
         p = sc.as_float32(pd)
         ref = oracle.solve(p, c["x0"], c["U_nom"], c["obs"], c["path"], c["ds"], c["seed"], 0,
                            want_uhist=True)
-        assert_solve_matches(dict(U=U, traj=traj, J=None), ref, p, "served moving", check_J=False)
+        sv = served_costs(s, c, c["U_nom"], c["seed"], 0, U)
+        assert_solve_matches(dict(U=U, traj=traj, **sv), ref, p, "served moving")
     finally:
         s.close()
 
@@ -339,13 +342,13 @@ def test_batch_and_serving_with_discs(pkg, torch):
                       U_out=torch.zeros((16, 3), device="cuda"),
                       traj_out=torch.zeros((17, 7), device="cuda"),
                       J_out=torch.zeros(c["params"]["S"], device="cuda")) for c in cases]
+        for c, q in zip(cases, insts):
+            add_cost_outputs(q, c["params"]["S"], 16)
         s.solve_batch(insts)
         torch.cuda.synchronize()
         for k, (c, q) in enumerate(zip(cases, insts)):
             p, ref = _oracle(c)
-            out = dict(U=q["U_out"].cpu().numpy(), traj=q["traj_out"].cpu().numpy(),
-                       J=q["J_out"].cpu().numpy())
-            assert_solve_matches(out, ref, p, f"disc batch {k}")
+            assert_solve_matches(host_outputs(q), ref, p, f"disc batch {k}")
         # serving: one vehicle, one request
         c = _discs(sc.small_random(87, S=300, H=16, n_obs=4))
         s.register(0, c["path"], c["ds"], c["U_nom"], c["seed"])
@@ -363,7 +366,8 @@ def test_batch_and_serving_with_discs(pkg, torch):
         p = sc.as_float32(c["params"])
         ref = oracle.solve(p, c["x0"], c["U_nom"], c["obs"], c["path"], c["ds"], c["seed"], 0,
                            want_uhist=True)
-        assert_solve_matches(dict(U=U, traj=traj, J=None), ref, p, "served discs", check_J=False)
+        sv = served_costs(s, c, c["U_nom"], c["seed"], 0, U)
+        assert_solve_matches(dict(U=U, traj=traj, **sv), ref, p, "served discs")
     finally:
         s.close()
 
@@ -448,12 +452,13 @@ def test_jerk_model_batch(pkg, torch):
                       S=c["params"]["S"], seed=c["seed"], counter=c["counter"],
                       U_out=torch.zeros((16, 3), device="cuda"), traj_out=torch.zeros((17, 7), device="cuda"),
                       J_out=torch.zeros(c["params"]["S"], device="cuda")) for c in cases]
+        for c, q in zip(cases, insts):
+            add_cost_outputs(q, c["params"]["S"], 16)
         s.solve_batch(insts)
         torch.cuda.synchronize()
         for k, (c, q) in enumerate(zip(cases, insts)):
             p, ref = _oracle(c)
-            out = dict(U=q["U_out"].cpu().numpy(), traj=q["traj_out"].cpu().numpy(), J=q["J_out"].cpu().numpy())
-            assert_solve_matches(out, _ref7(ref), p, f"jerk batch {k}")
+            assert_solve_matches(host_outputs(q), _ref7(ref), p, f"jerk batch {k}")
     finally:
         s.close()
 

@@ -10,6 +10,7 @@ import pytest
 import oracle
 from paper_2508_05773_gb300 import scenarios as sc
 from tests.parity import assert_solve_matches
+from tests.served import served_costs
 
 pytestmark = pytest.mark.gpu
 
@@ -32,6 +33,7 @@ def _fleet(n, seed=3):
 
 def _server(pkg, n_vehicles, **kw):
     p = sc.params(S=S, H=H)
+    kw.setdefault("max_batch", 1)  # a batch of one reproduces a served solve (its costs)
     return pkg.Solver(p, max_obstacles=16, max_path_pts=1024, max_vehicles=n_vehicles, **kw)
 
 
@@ -66,8 +68,8 @@ def test_served_solves_match_oracle_and_warm_start(pkg):
             p = sc.as_float32(sc.params(S=S, H=H))
             ref = oracle.solve(p, c["x0"], U0, c["obs"], c["path"], c["ds"], seed, ctr,
                                want_uhist=True)
-            assert_solve_matches(dict(U=U, traj=traj, J=None), ref, p, f"vehicle {v}",
-                                 check_J=False)
+            sv = served_costs(srv, c, U0, seed, ctr, U)
+            assert_solve_matches(dict(U=U, traj=traj, **sv), ref, p, f"vehicle {v}")
             # warm start and counter advanced on the device
             U1, seed1, ctr1 = srv.vehicle_export(v)
             assert ctr1 == 1 and seed1 == seed
@@ -167,7 +169,7 @@ def test_config4_full_size_request(pkg):
     c = sc.random_instance(rng, S_choices=(4096,), H_range=(50, 50), obs_range=(12, 12))
     pd = sc.params(S=4096, H=50)
     srv = pkg.Solver(pd, max_obstacles=16, max_path_pts=1024, max_vehicles=4, serve_lanes=2,
-                     serve_max_batch=16)
+                     serve_max_batch=16, max_batch=1)
     try:
         srv.register(0, c["path"], c["ds"], c["U_nom"], c["seed"])
         U0, seed, ctr = srv.vehicle_export(0)
@@ -177,6 +179,7 @@ def test_config4_full_size_request(pkg):
         assert st == 0
         p = sc.as_float32(pd)
         ref = oracle.solve(p, c["x0"], U0, c["obs"], c["path"], c["ds"], seed, ctr, want_uhist=True)
-        assert_solve_matches(dict(U=U, traj=traj, J=None), ref, p, "config-4 request", check_J=False)
+        sv = served_costs(srv, c, U0, seed, ctr, U)
+        assert_solve_matches(dict(U=U, traj=traj, **sv), ref, p, "config-4 request", strict=True)
     finally:
         srv.close()

@@ -88,7 +88,7 @@ MUTANTS = [
     ("applied input not clipped", "for (int j = 0; j < 3; ++j) u[j] = clip(zs[j], P->z_lo[j], P->z_hi[j]);", "for (int j = 0; j < 3; ++j) u[j] = zs[j];"),
     ("barrier rate uses h_tilde in b", "b[i] = -alpha[i] * h + b_rest;", "b[i] = -alpha[i] * h_tilde * 2.0 + b_rest;"),
     ("cost before the step", "    orc_dynamics_step(P, x, u, xn);\n    memcpy(x, xn, sizeof(x));\n    J += orc_stage_cost(P, x, u, path, n_pts, ds);", "    J += orc_stage_cost(P, x, u, path, n_pts, ds);\n    orc_dynamics_step(P, x, u, xn);\n    memcpy(x, xn, sizeof(x));"),
-    ("update uses first sample only", "for (int s = 0; s < S; ++s) acc += gb[s] * uh[(size_t)s * (size_t)H * 3 + (size_t)k];", "for (int s = 0; s < S; ++s) acc += gb[s] * uh[(size_t)k];"),
+    ("update uses first sample only", "for (int s = 0; s < S; ++s) acc += gamma_bar[s] * u_hist[(size_t)s * (size_t)H * 3 + (size_t)k];", "for (int s = 0; s < S; ++s) acc += gamma_bar[s] * u_hist[(size_t)k];"),
     ("nominal not added", "zdes[j] = clip(U_nom[3 * tau + j] + P->sigma[j] * n[j], P->z_lo[j], P->z_hi[j]);", "zdes[j] = clip(P->sigma[j] * n[j], P->z_lo[j], P->z_hi[j]);"),
 ]
 

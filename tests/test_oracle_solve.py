@@ -175,3 +175,30 @@ def test_no_obstacles_only_hitch():
     p, r = _run(c)
     assert r["status"] == 0
     assert np.all(np.isfinite(r["U"]))
+
+
+def test_sample_ranges_and_update_reassemble_the_solve():
+    # A solve spread over sample ranges (one per worker process) and joined
+    # by the update gives the full solve's costs, inputs and U* bit for bit.
+    c = sc.small_random(12, S=37, H=9, n_obs=3)
+    p, ref = _run(c)
+    args = (p, c["x0"], c["U_nom"], c["obs"], c["path"], c["ds"], c["seed"], c["counter"])
+    parts = [oracle.rollouts(*args, s0, s1) for s0, s1 in ((0, 5), (5, 6), (6, 37))]
+    assert all(r["status"] == 0 for r in parts)
+    J = np.concatenate([r["J"] for r in parts])
+    uh = np.concatenate([r["u_hist"] for r in parts])
+    st, U, g = oracle.update(J, uh, p["lambda"], c["U_nom"])
+    assert st == 0
+    assert np.array_equal(J, ref["J"]) and np.array_equal(uh, ref["u_hist"]) and np.array_equal(U, ref["U"])
+    # the update is the weighted mean of the applied inputs with the softmin
+    # weights (non-negative, summing to 1), written out here
+    w = np.exp(-(J - J.min()) / p["lambda"])
+    np.testing.assert_allclose(g, w / w.sum(), rtol=1e-13)
+    np.testing.assert_allclose(U, np.einsum("s,shj->hj", w / w.sum(), uh), rtol=1e-12, atol=1e-15)
+
+
+def test_update_without_finite_costs_returns_the_nominal():
+    U_nom = np.arange(12, dtype=np.float64).reshape(4, 3)
+    st, U, g = oracle.update(np.array([np.inf, np.nan]), np.ones((2, 4, 3)), 1.0, U_nom)
+    assert st == oracle.ORC_ENONFINITE
+    assert np.array_equal(U, U_nom) and np.all(g == 0)

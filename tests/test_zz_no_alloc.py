@@ -82,3 +82,46 @@ def test_noalloc_rejects_sizes_beyond_its_maximum():
         rc = pkg.brmppi_solve_device_noalloc(params, x0, Un, ob, pa, c["ds"], 1, 0, out["U"])
         assert rc == pkg.BRMPPI_EINVAL
         assert "maximum" in pkg.brmppi_last_error(None)
+
+
+def test_noalloc_at_its_maxima_allocates_nothing():
+    """S = 4095 (a ragged last tile), H = 64, 16 obstacles, 4096 path rows:
+    the largest solve the entry point accepts.  A context solve in the same
+    fixed launch shape (4 lanes per sample, 128-thread blocks) runs the same
+    kernel variant on the same tiles, so the two agree bit for bit.  After a
+    first call (which may load the kernel's module), a call leaves the
+    device's free memory unchanged."""
+    import torch
+    import paper_2508_05773_gb300 as pkg
+    pkg.load()
+    dev = torch.device("cuda:0")
+    c = sc.small_random(31, S=4095, H=64, n_obs=16)
+    ds = 0.012
+    c["path"] = sc.path_table([("S", 40.0), ("A", 15.0, 1.2)], ds, reverse=True)[:4096].copy()
+    c["ds"] = ds
+    assert c["path"].shape[0] == 4096
+    S, H = 4095, 64
+    params = pkg.params_from_dict(c["params"], max_obstacles=16, max_path_pts=4096)
+    x0, Un, ob, pa = _tensors(c, dev)
+    solver = pkg.Solver(c["params"], max_obstacles=16, max_path_pts=4096, threads_per_sample=4,
+                        block_threads=128)
+    try:
+        ref = _outs(H, S, dev)
+        assert solver.solve_device(x0, Un, ob, pa, ds, c["seed"], c["counter"], ref["U"], ref["traj"],
+                                   ref["J"], ref["Un"], ref["st"]) == 0
+        got = _outs(H, S, dev)
+        for call in range(2):
+            torch.cuda.synchronize()
+            free0, _ = torch.cuda.mem_get_info(dev)
+            rc = pkg.brmppi_solve_device_noalloc(params, x0, Un, ob, pa, ds, c["seed"], c["counter"],
+                                                 got["U"], got["traj"], got["J"], got["Un"], got["st"])
+            assert rc == 0, pkg.brmppi_last_error(None)
+            torch.cuda.synchronize()
+            free1, _ = torch.cuda.mem_get_info(dev)
+            if call == 1:
+                assert free1 == free0, (free0, free1)
+            assert int(got["st"].item()) == 0 and int(ref["st"].item()) == 0
+            for k in ("U", "traj", "J", "Un"):
+                assert np.array_equal(got[k].cpu().numpy(), ref[k].cpu().numpy()), (call, k)
+    finally:
+        solver.close()
