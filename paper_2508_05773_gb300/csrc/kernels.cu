@@ -16,12 +16,16 @@ void for_each_variant(F f) {
   for (int i = 0; i < n; ++i) f(c[i]);
   const Variant* d = variants_wide_ext(&n);
   for (int i = 0; i < n; ++i) f(d[i]);
+  const Variant* e = variants_latency(&n);
+  for (int i = 0; i < n; ++i) f(e[i]);
 }
 
-const Variant* find(int tps, int bpt, bool ext) {
+// rows = 0: the general instantiation of a shape; rows > 0: the one with
+// exactly that many constraint rows a lane (null if not compiled)
+const Variant* find(int tps, int bpt, bool ext, int rows = 0) {
   const Variant* hit = nullptr;
   for_each_variant([&](const Variant& v) {
-    if (v.tps == tps && v.bpt == bpt && v.ext == ext) hit = &v;
+    if (v.tps == tps && v.bpt == bpt && v.ext == ext && v.rows == rows) hit = &v;
   });
   return hit;
 }
@@ -151,6 +155,12 @@ cudaError_t launch_solve(int tps, int bpt, int blocks, int threads, size_t smem,
                          const KConst& k, const LaunchDesc& L, int P) {
   const Variant* v = find(tps, bpt, needs_ext(k));
   if (!v || block_threads(tps, bpt, threads, P) > kMaxBlockThreads) return cudaErrorInvalidValue;
+  if (!L.work && !v->ext && tps > 1 && bpt <= 2 && k.proj) {
+    // a single solve on a noise-warp shape: the instantiation with exactly
+    // the rows a lane holds, where one is compiled
+    const int rows = (L.single.n_obs * k.nd + tps - 1) / tps;
+    if (const Variant* r = rows > 0 ? find(tps, 1, false, rows) : nullptr) v = r;
+  }
   LaunchDesc D = L;
   D.noise_warps = noise_warps(tps, bpt, threads, P);
   v->fn<<<blocks, block_threads(tps, bpt, threads, P), smem, stream>>>(k, D);

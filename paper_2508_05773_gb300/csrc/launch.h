@@ -14,6 +14,7 @@ struct Variant {
   bool ext;  // carries the optional terms (BRMPPI_FLAG_COLLISION_COST, _OBS8, _ALPHA_BUFFER,
              // footprint discs other than the rear-axle point)
   KernelFn fn;
+  int rows = 0;  // > 0: exactly this many constraint rows a lane (single solves)
 };
 
 // Instantiations, one translation unit per group of team widths and family
@@ -23,6 +24,7 @@ const Variant* variants_narrow(int* n);      // 1 and 2 lanes per sample
 const Variant* variants_wide(int* n);        // 4 .. 32 lanes per sample
 const Variant* variants_narrow_ext(int* n);  // the same, with the optional terms
 const Variant* variants_wide_ext(int* n);
+const Variant* variants_latency(int* n);     // exact rows a lane, noise-warp shapes
 
 // Whether a launch with these constants needs the family with the optional terms.
 inline bool needs_ext(const KConst& k) { return k.coll || k.obs8 || k.abuf || k.discs || k.third || k.jerk; }

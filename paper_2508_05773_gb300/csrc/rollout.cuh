@@ -55,6 +55,7 @@
 #pragma once
 
 #include <cstdint>
+#include <type_traits>
 #include <cuda_runtime.h>
 #include <math_constants.h>
 
@@ -441,7 +442,7 @@ constexpr bool kNoiseWarps = TPS > 1 && BPT <= 2;
 __device__ __forceinline__ void step_barrier() { asm volatile("bar.sync 1, %0;" ::"r"(blockDim.x) : "memory"); }
 
 // ----------------------------------------------------------- one sample tile
-template <int TPS, int BPT, bool EXT>
+template <int TPS, int BPT, bool EXT, int ROWS>
 __device__ void run_tile(const KConst& k, const Inst& in, int tile, float* uh, const Smem& S,
                          Shared& sh, int noise_warps) {
   // Teams wider than one lane run with extra warps (the last ones) that
@@ -530,8 +531,10 @@ __device__ void run_tile(const KConst& k, const Inst& in, int tile, float* uh, c
   float px = 0.f, pxl = 0.f, py = 0.f, pyl = 0.f, t1 = 0.f, t2 = fr.t2, v = fr.v_h, vl = fr.v_l,
         dl = fr.dl, ps = 0.f, psl = 0.f;
   // obstacle slots per lane: one lane per sample holds every obstacle of
-  // its Philox blocks 1.. ; wider teams hold obstacles lt, lt + TPS, ...
-  constexpr int OBS_SLOTS = (TPS == 1) ? (BPT > 1 ? 4 * (BPT - 1) : 1) : 4 * BPT;
+  // its Philox blocks 1.. ; wider teams hold obstacles lt, lt + TPS, ...;
+  // ROWS > 0 (latency variants with noise warps): exactly ROWS slots a lane
+  static_assert(ROWS == 0 || kNoiseWarps<TPS, BPT>, "exact row slots need the noise-warp variants");
+  constexpr int OBS_SLOTS = ROWS > 0 ? ROWS : ((TPS == 1) ? (BPT > 1 ? 4 * (BPT - 1) : 1) : 4 * BPT);
   float alpha_h = k.alpha0;  // the hitch's barrier rate (same on every lane)
   float alpha[OBS_SLOTS];
 #pragma unroll
@@ -579,8 +582,9 @@ __device__ void run_tile(const KConst& k, const Inst& in, int tile, float* uh, c
     return xp * xp * X + yp * yp * Y - 1.f;
   };
 
-  // stage cost of the current state (time t) reached with input (ua, uw, un)
-  auto stage_cost = [&](float t, float ce1, float se1, float ce2, float se2) {
+  // stage cost of the current state (time t) reached with input (ua, uw, un);
+  // add = false computes it and adds zero (no branch in the step)
+  auto stage_cost = [&](float t, float ce1, float se1, float ce2, float se2, bool add) {
     const float qf = qf0 + (ps * in.inv_ds + psl * in.inv_ds);
     const float fl = floorf(qf);
     int ii = i0 + static_cast<int>(fl);
@@ -616,7 +620,7 @@ __device__ void run_tile(const KConst& k, const Inst& in, int tile, float* uh, c
       for (int j = lt; j < n_rows; j += TPS) c += fmaxf(-row_h(j, t, ce1, se1, ce2, se2), 0.f);
       rc += k.q_coll * team_sum<TPS>(c);
     }
-    acc2(Jh, Jl, rc);
+    acc2(Jh, Jl, add ? rc : 0.f);
   };
 
   // stored-trajectory variant: the state of this sample after step tau, in
@@ -686,7 +690,24 @@ __device__ void run_tile(const KConst& k, const Inst& in, int tile, float* uh, c
   }
   float nrm[4];
   if constexpr (TPS == 1) draw_first(0, nrm);
-  for (int tau = 0; tau < H && !producer; ++tau) {
+  // trigonometry of the current state, carried from step to step: the state
+  // angles theta1 and phi = theta1 - theta2 of step tau + 1 follow from step
+  // tau's state alone (the input enters only the speed, steer angle and
+  // progress), so their sin / cos are taken before step tau's projection
+  // and stay off its dependency chain; only the steer angle's trigonometry
+  // waits for the projection.
+  float c1, s1, sp, cp;
+  {
+    float sr, cr;
+    state_sincos(t1, &sr, &cr);
+    c1 = c0 * cr - s0 * sr;
+    s1 = s0 * cr + c0 * sr;
+    state_sincos(t1 - t2, &sp, &cp);
+  }
+  // One step; PROJ is fixed for the whole loop (no branch on the flag
+  // inside the step).
+  auto step = [&](int tau, auto proj_c) {
+    constexpr bool PROJ = decltype(proj_c)::value;
     float nxt[4];
     float* cur = nz;
     if constexpr (TPS == 1) {
@@ -700,22 +721,35 @@ __device__ void run_tile(const KConst& k, const Inst& in, int tile, float* uh, c
       cur = nz + (tau & 1) * 4 * in.P;
     }
 
-    // trigonometry of the current state
-    float sr, cr;
-    state_sincos(t1, &sr, &cr);
-    const float c1 = c0 * cr - s0 * sr;
-    const float s1 = s0 * cr + c0 * sr;
-    const float phi = t1 - t2;
-    float sp, cp;
-    state_sincos(phi, &sp, &cp);
+    // trigonometry of the steer angle (the one state angle the previous
+    // projection moved)
     float sd, cd;
     state_sincos(dl, &sd, &cd);
     const float tn = __fdividef(sd, cd);  // |cos| >= 4e-9 below 2^16: MUFU reciprocal (~2 ulp)
     const float vv = v + vl;
     const float th1dot = vv * tn * k.inv_l1;
 
-    // cost of the previous step, at this state (independent of the rows)
-    if (tau > 0) stage_cost(static_cast<float>(tau) * k.Ts, c1, s1, c1 * cp + s1 * sp, s1 * cp - c1 * sp);
+    // cost of the previous step, at this state (independent of the rows);
+    // at tau = 0 there is no previous step and the increment is zero
+    // (adding zero to a compensated pair leaves it unchanged)
+    stage_cost(static_cast<float>(tau) * k.Ts, c1, s1, c1 * cp + s1 * sp, s1 * cp - c1 * sp, tau > 0);
+
+    // explicit Euler, the state-only part (right-hand sides at the current
+    // state), and the next state's theta1 / phi trigonometry
+    const float Tv = k.Ts * vv;
+    float px_n = px, pxl_n = pxl, py_n = py, pyl_n = pyl;
+    acc2(px_n, pxl_n, Tv * c1);
+    acc2(py_n, pyl_n, Tv * s1);
+    const float t1_n = t1 + k.Ts * th1dot;
+    const float t2_n = t2 + Tv * k.inv_l2 * (sp - k.k_hitch * cp * tn);
+    float c1_n, s1_n, sp_n, cp_n;
+    {
+      float sr, cr;
+      state_sincos(t1_n, &sr, &cr);
+      c1_n = c0 * cr - s0 * sr;
+      s1_n = s0 * cr + c0 * sr;
+      state_sincos(t1_n - t2_n, &sp_n, &cp_n);
+    }
 
     float na, nw, nn;
     if constexpr (TPS == 1) {
@@ -732,7 +766,7 @@ __device__ void run_tile(const KConst& k, const Inst& in, int tile, float* uh, c
     const float zd2 = clampf(S.unom[3 * tau + 2] + k.sig2 * nn, k.zlo2, k.zhi2);
 
     float za, zw, zn;
-    if (k.proj) {
+    if constexpr (PROJ) {
       const float pu0 = k.w_u0 * zd0 + k.pc_u0;
       const float pu1 = k.w_u1 * zd1 + k.pc_u1;
       const float pu2 = k.w_u2 * zd2 + k.pc_u2;
@@ -759,12 +793,12 @@ __device__ void run_tile(const KConst& k, const Inst& in, int tile, float* uh, c
         cw_h = hr.Aw * iht;
         cc_h = pam - rho;
         const float own = (lt == 0) ? 1.f : 0.f;  // the sums take the row once (lane 0)
-        const float ua = own * ca_h, uw = own * cw_h;
-        Saa = ua * ua;
-        Saw = ua * uw;
-        Sww = uw * uw;
-        ga = ua * rho;
-        gw = uw * rho;
+        const float ua_ = own * ca_h, uw_ = own * cw_h;
+        Saa = ua_ * ua_;
+        Saw = ua_ * uw_;
+        Sww = uw_ * uw_;
+        ga = ua_ * rho;
+        gw = uw_ * rho;
       }
 
       // obstacle rows in the obstacle frame; the steer rate does not enter
@@ -774,11 +808,13 @@ __device__ void run_tile(const KConst& k, const Inst& in, int tile, float* uh, c
       // `live` = 0 turns a padding slot into a no-op without branching.
       float ca[OBS_SLOTS], cc[OBS_SLOTS];
       float cw[EXT ? OBS_SLOTS : 1];  // steer-rate column (footprint discs off the rear axle)
+      if constexpr (ROWS == 0) {
 #pragma unroll
-      for (int q = 0; q < OBS_SLOTS; ++q) ca[q] = cc[q] = 0.f;
-      if constexpr (EXT) {
+        for (int q = 0; q < OBS_SLOTS; ++q) ca[q] = cc[q] = 0.f;
+        if constexpr (EXT) {
 #pragma unroll
-        for (int q = 0; q < OBS_SLOTS; ++q) cw[q] = 0.f;
+          for (int q = 0; q < OBS_SLOTS; ++q) cw[q] = 0.f;
+        }
       }
       const float tnow = static_cast<float>(tau) * k.Ts;
       float cbuf = 0.f;  // buffer cost of this lane's rows
@@ -930,6 +966,16 @@ __device__ void run_tile(const KConst& k, const Inst& in, int tile, float* uh, c
             }
           }
         }
+      } else if constexpr (ROWS > 0) {
+        // exactly ROWS row slots a lane (row j on lane j % TPS): every slot
+        // runs, padding rows masked by `live`; no branch in the step
+#pragma unroll
+        for (int slot = 0; slot < ROWS; ++slot) {
+          const int j = lt + TPS * slot;
+          const bool live = j < n_rows;
+          const int jj = live ? j : 0;
+          obstacle_row(jj, cur[4 + jj], slot, live ? 1.f : 0.f);
+        }
       } else {
         // row j on lane j % TPS; every lane runs the team's slot count
         const int per_lane = (n_rows + TPS - 1) / TPS;
@@ -976,12 +1022,14 @@ __device__ void run_tile(const KConst& k, const Inst& in, int tile, float* uh, c
     uw = clampf(zw, k.zlo1, k.zhi1);
     un = clampf(zn, k.zlo2, k.zhi2);
 
-    // explicit Euler step, right-hand sides at the current state
-    const float Tv = k.Ts * vv;
-    acc2(px, pxl, Tv * c1);
-    acc2(py, pyl, Tv * s1);
-    t1 += k.Ts * th1dot;
-    t2 += Tv * k.inv_l2 * (sp - k.k_hitch * cp * tn);
+    // explicit Euler, the input-driven part; the state-only part was formed
+    // above from the same right-hand sides
+    px = px_n;
+    pxl = pxl_n;
+    py = py_n;
+    pyl = pyl_n;
+    t1 = t1_n;
+    t2 = t2_n;
     if (EXT && k.jerk) {  // input 0 is the jerk; the acceleration state drives the speed
       acc2(v, vl, k.Ts * acc);
       acc += k.Ts * ua;
@@ -990,6 +1038,10 @@ __device__ void run_tile(const KConst& k, const Inst& in, int tile, float* uh, c
     }
     dl += k.Ts * uw;
     acc2(ps, psl, k.Ts * un);
+    c1 = c1_n;
+    s1 = s1_n;
+    sp = sp_n;
+    cp = cp_n;
 
     if (lt == 0) {
       uh[(3 * tau + 0) * spb + team] = ua;
@@ -1006,6 +1058,13 @@ __device__ void run_tile(const KConst& k, const Inst& in, int tile, float* uh, c
 #pragma unroll
       for (int q = 0; q < 4; ++q) nrm[q] = nxt[q];
     }
+  };
+  if (!producer) {
+    if (k.proj) {
+      for (int tau = 0; tau < H; ++tau) step(tau, std::true_type{});
+    } else {
+      for (int tau = 0; tau < H; ++tau) step(tau, std::false_type{});
+    }
   }
   if (!producer) {  // cost of the last step
     float ce1 = 0.f, se1 = 0.f, ce2 = 0.f, se2 = 0.f;
@@ -1018,7 +1077,7 @@ __device__ void run_tile(const KConst& k, const Inst& in, int tile, float* uh, c
       ce2 = ce1 * cq + se1 * sq;
       se2 = se1 * cq - ce1 * sq;
     }
-    stage_cost(static_cast<float>(H) * k.Ts, ce1, se1, ce2, se2);
+    stage_cost(static_cast<float>(H) * k.Ts, ce1, se1, ce2, se2, true);
   }
 
   // --- per-sample cost: normalise the pair
@@ -1425,7 +1484,7 @@ static __device__ void merge_instance(const KConst& k, const Inst& in, const Sme
 // -------------------------------------------------------------- the kernel
 // EXT: the instantiations that also carry the optional terms (moving and
 // e = 4 obstacles, collision cost, buffer cost); the others compile them out.
-template <int TPS, int BPT, bool EXT>
+template <int TPS, int BPT, bool EXT, int ROWS = 0>
 __global__ void __launch_bounds__(512) solve_kernel(const KConst k, const LaunchDesc L) {
   extern __shared__ float dyn[];
   __shared__ Shared sh;
@@ -1451,7 +1510,7 @@ __global__ void __launch_bounds__(512) solve_kernel(const KConst k, const Launch
     Inst in;
     if (L.work) in = L.inst[inst_id];
     else in = L.single;
-    run_tile<TPS, BPT, EXT>(k, in, tile, uh, S, sh, L.noise_warps);
+    run_tile<TPS, BPT, EXT, ROWS>(k, in, tile, uh, S, sh, L.noise_warps);
 
     // the CTA that completes an instance's last tile merges its partials
     __threadfence();
