@@ -201,6 +201,8 @@ brmppi::SmemCaps make_caps(int n_obs, int n_rows, int n_pts, int H, int tps) {
   c.unom = brmppi::SmemCaps::pad4(3 * H);
   c.ustar = brmppi::SmemCaps::pad4(3 * H + 1);
   c.noise_per_team = tps > 1 ? 8 * philox_blocks(n_rows) : 0;
+  c.uh_per_team = 0;
+  c.merge = 0;
   return c;
 }
 
@@ -321,6 +323,23 @@ brmppi::Inst make_inst(const double* x0, const float* U_nom, const float* obs, i
   return in;
 }
 
+void single_launch_options(brmppi::LaunchDesc& L, const Shape& sh, const brmppi::KConst& k, int n_rows, int H,
+                           size_t smem_limit) {
+  // a single solve on a noise-warp shape: the instantiation with exactly the
+  // rows a lane holds, with the tile's applied-input history in shared
+  // memory, where both the variant exists and the history fits
+  const int spb = sh.threads / sh.tps;
+  const int rows = brmppi::exact_rows_variant(sh.tps, sh.bpt, k, n_rows);
+  if (rows <= 0) return;
+  brmppi::SmemCaps caps = L.caps;
+  caps.uh_per_team = 3 * H;
+  // those variants merge the instance's tile partials in shared memory
+  caps.merge = L.single.tiles * L.single.part_stride;
+  if (smem_bytes(caps, spb) > smem_limit) return;
+  L.caps = caps;
+  L.rows = rows;
+}
+
 brmppi_status check_sizes(brmppi_ctx* c, int32_t n_obs, int32_t n_pts, float ds) {
   if (n_obs < 0 || n_obs > c->prm.max_obstacles) return fail(c, BRMPPI_EINVAL, "n_obs out of [0, max_obstacles]");
   if (n_pts < 2 || n_pts > c->prm.max_path_pts) return fail(c, BRMPPI_EINVAL, "n_pts out of [2, max_path_pts]");
@@ -345,13 +364,14 @@ brmppi_status enqueue_plain_sized(brmppi_ctx* c, const Shape& sh, int S, int H, 
   L.caps = make_caps(n_obs, rows_of(c->prm, n_obs), n_pts, H, sh.tps);
   L.uh = c->d_uh;
   L.uh_stride = 3 * H * spb;
+  const brmppi::KConst k = make_kconst(c->prm);
+  single_launch_options(L, sh, k, rows_of(c->prm, n_obs), H, c->smem_limit);
   const size_t smem = smem_bytes(L.caps, spb);
   const int tiles = L.single.tiles;
   if (smem > c->smem_limit) return fail(c, BRMPPI_EINVAL, "shared memory need exceeds the device limit");
   if (static_cast<size_t>(tiles) > c->part_tiles ||
       static_cast<size_t>(tiles) * static_cast<size_t>(L.uh_stride) > c->uh_floats)
     return fail(c, BRMPPI_EINVAL, "launch shape exceeds the context's scratch");
-  const brmppi::KConst k = make_kconst(c->prm);
   cudaError_t e = brmppi::launch_solve(sh.tps, sh.bpt, tiles, sh.threads, smem, stream, k, L, L.single.P);
   if (e != cudaSuccess) return cuda_fail(c, e, "kernel launch");
   if (u_safe) {

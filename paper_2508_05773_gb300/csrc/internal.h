@@ -124,6 +124,12 @@ int part_stride_for(int H);
 // two Philox blocks per lane.
 int ext_team_width(int P);
 brmppi_status check_sizes(brmppi_ctx* c, int32_t n_obs, int32_t n_pts, float ds);
+// Options of a single (non-batch) solve launch: the exact-rows variant, with
+// the applied-input history and the merge of the tile partials in shared
+// memory, when the variant exists and the room fits (L.rows,
+// L.caps.uh_per_team, L.caps.merge); L.caps and L.single must be set.
+void single_launch_options(brmppi::LaunchDesc& L, const Shape& sh, const brmppi::KConst& k, int n_rows, int H,
+                           size_t smem_limit);
 
 // Allocate / free the buffers of a lane for max_batch instances of at most
 // S samples and H steps.

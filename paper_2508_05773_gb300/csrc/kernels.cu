@@ -141,6 +141,12 @@ int noise_warps(int tps, int bpt, int threads, int P) {
 
 int block_threads(int tps, int bpt, int threads, int P) { return threads + 32 * noise_warps(tps, bpt, threads, P); }
 
+int exact_rows_variant(int tps, int bpt, const KConst& k, int n_rows) {
+  if (needs_ext(k) || !k.proj || tps <= 1 || bpt > 2 || n_rows <= 0) return 0;
+  const int rows = (n_rows + tps - 1) / tps;
+  return find(tps, 1, false, rows) ? rows : 0;
+}
+
 int variant_occupancy(int tps, int bpt, int threads, size_t smem, bool ext, int P) {
   const Variant* v = find(tps, bpt, ext);
   if (!v || block_threads(tps, bpt, threads, P) > kMaxBlockThreads) return 0;
@@ -155,11 +161,14 @@ cudaError_t launch_solve(int tps, int bpt, int blocks, int threads, size_t smem,
                          const KConst& k, const LaunchDesc& L, int P) {
   const Variant* v = find(tps, bpt, needs_ext(k));
   if (!v || block_threads(tps, bpt, threads, P) > kMaxBlockThreads) return cudaErrorInvalidValue;
-  if (!L.work && !v->ext && tps > 1 && bpt <= 2 && k.proj) {
-    // a single solve on a noise-warp shape: the instantiation with exactly
-    // the rows a lane holds, where one is compiled
-    const int rows = (L.single.n_obs * k.nd + tps - 1) / tps;
-    if (const Variant* r = rows > 0 ? find(tps, 1, false, rows) : nullptr) v = r;
+  if (L.rows > 0) {
+    // the exact-rows variants merge in shared memory: the launch must have
+    // reserved the room for the instance's partials
+    v = (L.work || L.caps.merge < L.single.tiles * L.single.part_stride ||
+         L.caps.uh_per_team < 3 * L.single.H)
+            ? nullptr
+            : find(tps, 1, false, L.rows);
+    if (!v) return cudaErrorInvalidValue;
   }
   LaunchDesc D = L;
   D.noise_warps = noise_warps(tps, bpt, threads, P);

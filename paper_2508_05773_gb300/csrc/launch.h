@@ -39,6 +39,11 @@ constexpr int kMaxBlockThreads = 512;
 int noise_warps(int tps, int bpt, int threads, int P);
 int block_threads(int tps, int bpt, int threads, int P);
 
+// The rows a lane holds in a single solve of n_rows constraint rows on a
+// noise-warp shape, if the instantiation with exactly that many is compiled
+// (LaunchDesc::rows), else 0.
+int exact_rows_variant(int tps, int bpt, const KConst& k, int n_rows);
+
 // Supported (threads per sample, Philox blocks per lane) pairs.
 bool variant_exists(int tps, int bpt);
 

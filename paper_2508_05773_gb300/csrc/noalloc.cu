@@ -129,6 +129,12 @@ extern "C" brmppi_status brmppi_solve_device_noalloc(const brmppi_params* p, con
   L.caps = make_caps(n_obs, n_rows, n_pts, p->H, kNaTps);
   L.uh = part + kNaPartFloats;
   L.uh_stride = 3 * p->H * kNaSpb;
+  Shape sh;
+  sh.tps = kNaTps;
+  sh.bpt = bpt;
+  sh.threads = kNaThreads;
+  const brmppi::KConst k = make_kconst(*p);
+  single_launch_options(L, sh, k, n_rows, p->H, smem_optin);
   const size_t smem = smem_bytes(L.caps, kNaSpb);
   if (smem > smem_optin)
     return fail(nullptr, BRMPPI_EINVAL,
@@ -137,7 +143,7 @@ extern "C" brmppi_status brmppi_solve_device_noalloc(const brmppi_params* p, con
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   cudaError_t e = cudaMemsetAsync(sync, 0, sizeof(float) * kNaSyncFloats, s);
   if (e != cudaSuccess) return cuda_fail(nullptr, e, "no-alloc solve: clearing counters");
-  e = brmppi::launch_solve(kNaTps, bpt, L.single.tiles, kNaThreads, smem, s, make_kconst(*p), L, L.single.P);
+  e = brmppi::launch_solve(kNaTps, bpt, L.single.tiles, kNaThreads, smem, s, k, L, L.single.P);
   if (e != cudaSuccess) return cuda_fail(nullptr, e, "no-alloc solve: kernel launch");
   return BRMPPI_OK;
 }

@@ -118,9 +118,12 @@ struct Inst {
 struct SmemCaps {
   int obs, path, phead, unom, ustar;
   int noise_per_team;  // teams wider than one lane: staged normals, 2 steps x P blocks x 4
+  int uh_per_team;     // 3 H when the applied-input history stays in shared memory, else 0
+  int merge;           // > 0: room for an instance's tile partials (merged in shared memory)
   __host__ __device__ static int pad4(int n) { return (n + 3) & ~3; }
   __host__ __device__ int total(int spb) const {
-    return obs + path + phead + unom + ustar + pad4(3 * spb) + 256 + 16 + noise_per_team * spb;
+    const int tail = noise_per_team * spb + pad4(uh_per_team * spb);  // noise, history; then the partials
+    return obs + path + phead + unom + ustar + pad4(3 * spb) + 256 + 16 + (tail > merge ? tail : merge);
   }
 };
 
@@ -131,8 +134,10 @@ struct LaunchDesc {
   int n_work;
   unsigned int* work_ctr;  // [0] next item, [1] CTAs that ran out of work
   float* uh;            // per-CTA applied-input history: gridDim.x * uh_stride floats
+                        // (unused by the exact-rows variants: their history is in shared memory)
   int uh_stride;        // 3 * H_max * samples per CTA
   int noise_warps;      // teams wider than one lane: warps that produce the noise
+  int rows;             // > 0: the instantiation with exactly this many rows a lane
   SmemCaps caps;
 };
 
@@ -380,7 +385,8 @@ struct Smem {
   float* w;      // spb
   float* chunk;  // 256
   float* disc;   // 16: lever arms (along e1, along e2) of the footprint discs
-  float* noise;  // spb x noise_per_team
+  float* noise;  // spb x noise_per_team, then (exact-rows variants) the
+                 // applied-input history, 3H x spb
   int noise_per_team;
   __device__ Smem(float* base, const SmemCaps& c, int spb) {
     obs = base;
@@ -743,7 +749,20 @@ __device__ void run_tile(const KConst& k, const Inst& in, int tile, float* uh, c
     const float t1_n = t1 + k.Ts * th1dot;
     const float t2_n = t2 + Tv * k.inv_l2 * (sp - k.k_hitch * cp * tn);
     float c1_n, s1_n, sp_n, cp_n;
-    {
+    if constexpr (TPS > 1) {
+      // even lanes take theta1, odd lanes phi, and each pair trades the
+      // results: one sin / cos sequence in the warp's stream instead of two
+      const bool odd = lt & 1;
+      float sa, ca;
+      state_sincos(odd ? t1_n - t2_n : t1_n, &sa, &ca);
+      const float sb = __shfl_xor_sync(0xffffffffu, sa, 1);
+      const float cb = __shfl_xor_sync(0xffffffffu, ca, 1);
+      const float sr = odd ? sb : sa, cr = odd ? cb : ca;
+      sp_n = odd ? sa : sb;
+      cp_n = odd ? ca : cb;
+      c1_n = c0 * cr - s0 * sr;
+      s1_n = s0 * cr + c0 * sr;
+    } else {
       float sr, cr;
       state_sincos(t1_n, &sr, &cr);
       c1_n = c0 * cr - s0 * sr;
@@ -1328,112 +1347,196 @@ static __device__ void serial_trajectory(const KConst& k, const Inst& in, const 
   }
 }
 
-static __device__ void merge_instance(const KConst& k, const Inst& in, const Smem& S, Shared& sh) {
+// 16-byte asynchronous copy global -> shared through L2 (cp.async.cg).
+__device__ __forceinline__ void cp_async16(float* smem_dst, const float* gmem_src) {
+  const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(smem_dst));
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(gmem_src) : "memory");
+}
+
+// Minimum pair over the partials of an instance held in shared memory
+// (tile b at mp + b * stride), into sh.red_h[1] / sh.red_l[1].
+static __device__ void smem_pair_min(const float* mp, int nb, int stride, Shared& sh) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
-  const int nb = in.tiles;
-  const int stride = in.part_stride;
-  const int H = in.H;
-  // global pair minimum: every thread its tiles (b = tid, tid + blockDim,
-  // ...), then warps, then warp 0; the pair of tile tid stays in registers
-  // for the weights below (one L2 round trip for both)
-  float h0 = CUDART_INF_F, l0 = 0.f;
-  // the solve's error bits, read now (an atomic round trip) and used after the sums
-  if (threadIdx.x == 0) sh.err = atomicAdd(in.sync + 1, 0u);
-  // the first 64 tiles' entries of this thread's first row, loaded now: their
-  // round trip overlaps the minimum's (instances of at least 64 tiles)
-  const int nrows = 3 * H + 1;
-  const bool pre_ok = static_cast<int>(threadIdx.x) < nrows && nb >= 64;
-  float pre[64];
+  float mh = CUDART_INF_F, ml = 0.f;
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+    const float h = mp[static_cast<size_t>(b) * stride + 0], l = mp[static_cast<size_t>(b) * stride + 1];
+    if (pair_less(h, l, mh, ml)) { mh = h; ml = l; }
+  }
 #pragma unroll
-  for (int m = 0; m < 64; ++m)
-    pre[m] = pre_ok ? __ldcg(in.part + static_cast<size_t>(m) * stride + 3 + threadIdx.x) : 0.f;
-  {
-    float mh = CUDART_INF_F, ml = 0.f;
-    for (int b = threadIdx.x; b < nb; b += blockDim.x) {
-      const float h = __ldcg(in.part + static_cast<size_t>(b) * stride + 0);
-      const float l = __ldcg(in.part + static_cast<size_t>(b) * stride + 1);
-      if (b == static_cast<int>(threadIdx.x)) {
-        h0 = h;
-        l0 = l;
-      }
-      if (pair_less(h, l, mh, ml)) { mh = h; ml = l; }
-    }
+  for (int m = 16; m > 0; m >>= 1) {
+    const float oh = __shfl_xor_sync(0xffffffffu, mh, m);
+    const float ol = __shfl_xor_sync(0xffffffffu, ml, m);
+    if (pair_less(oh, ol, mh, ml)) { mh = oh; ml = ol; }
+  }
+  if (lane == 0) { sh.wred_h[warp] = mh; sh.wred_l[warp] = ml; }
+  __syncthreads();
+  if (warp == 0) {
+    mh = lane < nwarps ? sh.wred_h[lane] : CUDART_INF_F;
+    ml = lane < nwarps ? sh.wred_l[lane] : 0.f;
 #pragma unroll
     for (int m = 16; m > 0; m >>= 1) {
       const float oh = __shfl_xor_sync(0xffffffffu, mh, m);
       const float ol = __shfl_xor_sync(0xffffffffu, ml, m);
       if (pair_less(oh, ol, mh, ml)) { mh = oh; ml = ol; }
     }
-    if (lane == 0) { sh.wred_h[warp] = mh; sh.wred_l[warp] = ml; }
+    if (lane == 0) { sh.red_h[1] = mh; sh.red_l[1] = ml; }
+  }
+  __syncthreads();
+}
+
+// SMEM_PARTS: the instance's tile partials are copied into the CTA's shared
+// memory at once (one L2 round trip; the launch reserved the room) and
+// merged from there; else they are read from L2 in passes.  Both sum each
+// row in the same order (four chains, tiles t mod 4, the tail on the first),
+// so they give the same bits.
+template <bool SMEM_PARTS>
+static __device__ void merge_instance(const KConst& k, const Inst& in, const Smem& S, Shared& sh) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+  const int nb = in.tiles;
+  const int stride = in.part_stride;
+  const int H = in.H;
+  const int nrows = 3 * H + 1;
+  float* ustar = S.ustar;
+  bool ok;
+  if constexpr (SMEM_PARTS) {
+    // the partials region (nb * stride floats, a multiple of 4, 16-byte
+    // aligned) into the regions after the disc table (noise, history: no
+    // longer read); the error bits' atomic round trip overlaps the copy
+    float* mp = S.noise;
+    const int nf = nb * stride;
+    for (int i = 4 * static_cast<int>(threadIdx.x); i < nf; i += 4 * static_cast<int>(blockDim.x))
+      cp_async16(mp + i, in.part + i);
+    if (threadIdx.x == 0) sh.err = atomicAdd(in.sync + 1, 0u);
+    cp_async_wait_all();
     __syncthreads();
-    if (warp == 0) {
-      mh = lane < nwarps ? sh.wred_h[lane] : CUDART_INF_F;
-      ml = lane < nwarps ? sh.wred_l[lane] : 0.f;
+    smem_pair_min(mp, nb, stride, sh);
+    const float gmh = sh.red_h[1], gml = sh.red_l[1];
+    ok = gmh < CUDART_INF_F;
+    for (int q = threadIdx.x; q < nrows; q += blockDim.x) ustar[q] = 0.f;
+    for (int b0 = 0; b0 < nb; b0 += 256) {
+      __syncthreads();
+      for (int t = threadIdx.x; t < 256 && b0 + t < nb; t += blockDim.x) {
+        const float* pt = mp + static_cast<size_t>(b0 + t) * stride;
+        const float h = pt[0], l = pt[1];
+        S.chunk[t] = (ok && h < CUDART_INF_F) ? expf(-((h - gmh) + (l - gml)) * k.inv_lambda) : 0.f;
+      }
+      __syncthreads();
+      const int bend = min(256, nb - b0);
+      for (int q = threadIdx.x; q < nrows; q += blockDim.x) {
+        float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+        const float* col = mp + static_cast<size_t>(b0) * stride + 3 + q;
+        int t = 0;
+        for (; t + 4 <= bend; t += 4) {
+          a0 += S.chunk[t + 0] * col[static_cast<size_t>(t + 0) * stride];
+          a1 += S.chunk[t + 1] * col[static_cast<size_t>(t + 1) * stride];
+          a2 += S.chunk[t + 2] * col[static_cast<size_t>(t + 2) * stride];
+          a3 += S.chunk[t + 3] * col[static_cast<size_t>(t + 3) * stride];
+        }
+        for (; t < bend; ++t) a0 += S.chunk[t] * col[static_cast<size_t>(t) * stride];
+        ustar[q] += (a0 + a1) + (a2 + a3);
+      }
+    }
+  } else {
+    // global pair minimum: every thread its tiles (b = tid, tid + blockDim,
+    // ...), then warps, then warp 0; the pair of tile tid stays in registers
+    // for the weights below (one L2 round trip for both)
+    float h0 = CUDART_INF_F, l0 = 0.f;
+    // the solve's error bits, read now (an atomic round trip) and used after the sums
+    if (threadIdx.x == 0) sh.err = atomicAdd(in.sync + 1, 0u);
+    // the first 64 tiles' entries of this thread's first row, loaded now: their
+    // round trip overlaps the minimum's (instances of at least 64 tiles)
+    const bool pre_ok = static_cast<int>(threadIdx.x) < nrows && nb >= 64;
+    float pre[64];
+#pragma unroll
+    for (int m = 0; m < 64; ++m)
+      pre[m] = pre_ok ? __ldcg(in.part + static_cast<size_t>(m) * stride + 3 + threadIdx.x) : 0.f;
+    {
+      float mh = CUDART_INF_F, ml = 0.f;
+      for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+        const float h = __ldcg(in.part + static_cast<size_t>(b) * stride + 0);
+        const float l = __ldcg(in.part + static_cast<size_t>(b) * stride + 1);
+        if (b == static_cast<int>(threadIdx.x)) {
+          h0 = h;
+          l0 = l;
+        }
+        if (pair_less(h, l, mh, ml)) { mh = h; ml = l; }
+      }
 #pragma unroll
       for (int m = 16; m > 0; m >>= 1) {
         const float oh = __shfl_xor_sync(0xffffffffu, mh, m);
         const float ol = __shfl_xor_sync(0xffffffffu, ml, m);
         if (pair_less(oh, ol, mh, ml)) { mh = oh; ml = ol; }
       }
-      if (lane == 0) { sh.red_h[1] = mh; sh.red_l[1] = ml; }
-    }
-  }
-  __syncthreads();
-  const float gmh = sh.red_h[1], gml = sh.red_l[1];
-  const bool ok = gmh < CUDART_INF_F;
-  float* ustar = S.ustar;
-  for (int q = threadIdx.x; q < nrows; q += blockDim.x) ustar[q] = 0.f;
-  for (int b0 = 0; b0 < nb; b0 += 256) {
-    __syncthreads();
-    for (int t = threadIdx.x; t < 256 && b0 + t < nb; t += blockDim.x) {
-      const size_t base = static_cast<size_t>(b0 + t) * stride;
-      const bool held = b0 == 0 && t == static_cast<int>(threadIdx.x);
-      const float h = held ? h0 : __ldcg(in.part + base + 0), l = held ? l0 : __ldcg(in.part + base + 1);
-      S.chunk[t] = (ok && h < CUDART_INF_F) ? expf(-((h - gmh) + (l - gml)) * k.inv_lambda) : 0.f;
+      if (lane == 0) { sh.wred_h[warp] = mh; sh.wred_l[warp] = ml; }
+      __syncthreads();
+      if (warp == 0) {
+        mh = lane < nwarps ? sh.wred_h[lane] : CUDART_INF_F;
+        ml = lane < nwarps ? sh.wred_l[lane] : 0.f;
+#pragma unroll
+        for (int m = 16; m > 0; m >>= 1) {
+          const float oh = __shfl_xor_sync(0xffffffffu, mh, m);
+          const float ol = __shfl_xor_sync(0xffffffffu, ml, m);
+          if (pair_less(oh, ol, mh, ml)) { mh = oh; ml = ol; }
+        }
+        if (lane == 0) { sh.red_h[1] = mh; sh.red_l[1] = ml; }
+      }
     }
     __syncthreads();
-    const int bend = min(256, nb - b0);
-    for (int q = threadIdx.x; q < nrows; q += blockDim.x) {
-      // four independent chains (tiles t mod 4), combined in a fixed order;
-      // 64 (then 16) L2 loads in flight per pass
-      float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
-      const float* col = in.part + static_cast<size_t>(b0) * stride + 3 + q;
-      int t = 0;
-      for (; t + 64 <= bend; t += 64) {
-        // `pre` is the pass buffer: it already holds the first pass of the
-        // thread's first row
-        if (!(pre_ok && b0 == 0 && t == 0 && q == static_cast<int>(threadIdx.x))) {
-#pragma unroll
-          for (int m = 0; m < 64; ++m) pre[m] = __ldcg(col + static_cast<size_t>(t + m) * stride);
-        }
-#pragma unroll
-        for (int m = 0; m < 64; m += 4) {
-          a0 += S.chunk[t + m + 0] * pre[m + 0];
-          a1 += S.chunk[t + m + 1] * pre[m + 1];
-          a2 += S.chunk[t + m + 2] * pre[m + 2];
-          a3 += S.chunk[t + m + 3] * pre[m + 3];
-        }
+    const float gmh = sh.red_h[1], gml = sh.red_l[1];
+    ok = gmh < CUDART_INF_F;
+    for (int q = threadIdx.x; q < nrows; q += blockDim.x) ustar[q] = 0.f;
+    for (int b0 = 0; b0 < nb; b0 += 256) {
+      __syncthreads();
+      for (int t = threadIdx.x; t < 256 && b0 + t < nb; t += blockDim.x) {
+        const size_t base = static_cast<size_t>(b0 + t) * stride;
+        const bool held = b0 == 0 && t == static_cast<int>(threadIdx.x);
+        const float h = held ? h0 : __ldcg(in.part + base + 0), l = held ? l0 : __ldcg(in.part + base + 1);
+        S.chunk[t] = (ok && h < CUDART_INF_F) ? expf(-((h - gmh) + (l - gml)) * k.inv_lambda) : 0.f;
       }
-      for (; t + 16 <= bend; t += 16) {
-        float v[16];
+      __syncthreads();
+      const int bend = min(256, nb - b0);
+      for (int q = threadIdx.x; q < nrows; q += blockDim.x) {
+        // four independent chains (tiles t mod 4), combined in a fixed order;
+        // 64 (then 16) L2 loads in flight per pass
+        float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+        const float* col = in.part + static_cast<size_t>(b0) * stride + 3 + q;
+        int t = 0;
+        for (; t + 64 <= bend; t += 64) {
+          // `pre` is the pass buffer: it already holds the first pass of the
+          // thread's first row
+          if (!(pre_ok && b0 == 0 && t == 0 && q == static_cast<int>(threadIdx.x))) {
 #pragma unroll
-        for (int m = 0; m < 16; ++m) v[m] = __ldcg(col + static_cast<size_t>(t + m) * stride);
+            for (int m = 0; m < 64; ++m) pre[m] = __ldcg(col + static_cast<size_t>(t + m) * stride);
+          }
 #pragma unroll
-        for (int m = 0; m < 16; m += 4) {
-          a0 += S.chunk[t + m + 0] * v[m + 0];
-          a1 += S.chunk[t + m + 1] * v[m + 1];
-          a2 += S.chunk[t + m + 2] * v[m + 2];
-          a3 += S.chunk[t + m + 3] * v[m + 3];
+          for (int m = 0; m < 64; m += 4) {
+            a0 += S.chunk[t + m + 0] * pre[m + 0];
+            a1 += S.chunk[t + m + 1] * pre[m + 1];
+            a2 += S.chunk[t + m + 2] * pre[m + 2];
+            a3 += S.chunk[t + m + 3] * pre[m + 3];
+          }
         }
+        for (; t + 16 <= bend; t += 16) {
+          float v[16];
+#pragma unroll
+          for (int m = 0; m < 16; ++m) v[m] = __ldcg(col + static_cast<size_t>(t + m) * stride);
+#pragma unroll
+          for (int m = 0; m < 16; m += 4) {
+            a0 += S.chunk[t + m + 0] * v[m + 0];
+            a1 += S.chunk[t + m + 1] * v[m + 1];
+            a2 += S.chunk[t + m + 2] * v[m + 2];
+            a3 += S.chunk[t + m + 3] * v[m + 3];
+          }
+        }
+        for (; t + 4 <= bend; t += 4) {
+          a0 += S.chunk[t + 0] * __ldcg(col + static_cast<size_t>(t + 0) * stride);
+          a1 += S.chunk[t + 1] * __ldcg(col + static_cast<size_t>(t + 1) * stride);
+          a2 += S.chunk[t + 2] * __ldcg(col + static_cast<size_t>(t + 2) * stride);
+          a3 += S.chunk[t + 3] * __ldcg(col + static_cast<size_t>(t + 3) * stride);
+        }
+        for (; t < bend; ++t) a0 += S.chunk[t] * __ldcg(col + static_cast<size_t>(t) * stride);
+        ustar[q] += (a0 + a1) + (a2 + a3);
       }
-      for (; t + 4 <= bend; t += 4) {
-        a0 += S.chunk[t + 0] * __ldcg(col + static_cast<size_t>(t + 0) * stride);
-        a1 += S.chunk[t + 1] * __ldcg(col + static_cast<size_t>(t + 1) * stride);
-        a2 += S.chunk[t + 2] * __ldcg(col + static_cast<size_t>(t + 2) * stride);
-        a3 += S.chunk[t + 3] * __ldcg(col + static_cast<size_t>(t + 3) * stride);
-      }
-      for (; t < bend; ++t) a0 += S.chunk[t] * __ldcg(col + static_cast<size_t>(t) * stride);
-      ustar[q] += (a0 + a1) + (a2 + a3);
     }
   }
   // path turns between consecutive rows (this CTA's frame-shifted table;
@@ -1490,7 +1593,14 @@ __global__ void __launch_bounds__(512) solve_kernel(const KConst k, const Launch
   __shared__ Shared sh;
   const int spb = compute_threads<TPS>(L.noise_warps) / TPS;
   const Smem S(dyn, L.caps, spb);
-  float* uh = L.uh + static_cast<size_t>(blockIdx.x) * L.uh_stride;
+  // applied-input history of the CTA's tile: shared memory in the exact-rows
+  // variants (the launch reserved it), else the CTA's global slot
+  float* uh;
+  if constexpr (ROWS > 0) {
+    uh = S.noise + L.caps.noise_per_team * spb;
+  } else {
+    uh = L.uh + static_cast<size_t>(blockIdx.x) * L.uh_stride;
+  }
 
   for (int iter = 0;; ++iter) {
     int inst_id = 0, tile;
@@ -1519,7 +1629,7 @@ __global__ void __launch_bounds__(512) solve_kernel(const KConst k, const Launch
     __syncthreads();
     if (sh.last) {
       __threadfence();
-      merge_instance(k, in, S, sh);
+      merge_instance<(ROWS > 0)>(k, in, S, sh);
     }
     __syncthreads();
   }
