@@ -43,8 +43,6 @@ import numpy as np  # noqa: E402
 
 METRIC = "rollout-steps/s (S·H·solves/s) batched vs plain; p50/p99 solve latency"
 UNIT = "rollout-steps/s"
-N_SM = 152
-FP32_LANES_PER_SM = 128
 L2_FLUSH_BYTES = 256 << 20
 
 
@@ -66,6 +64,72 @@ def ops_per_rollout_step(n_obs: int, proj: bool = True) -> int:
         return PHILOX_BLOCK_OPS + STEP_BASE_OPS - 6
     P = (3 + 1 + n_obs + 3) // 4
     return PHILOX_BLOCK_OPS * P + STEP_BASE_OPS + HITCH_OPS + OBSTACLE_OPS * n_obs
+
+
+# Of those, the elementary functions the step evaluates on the XU (the
+# special-function pipe, 16 lanes a clock per SM against 128 for FP32): per
+# Philox block the two Box-Muller logarithms and radii (reciprocal square
+# root); per constraint row one reciprocal (1 / h~); per step the steer
+# angle's tangent and the 2x2 determinant (one reciprocal each).  Box-Muller's
+# sin / cos of pi u and the state angles' sin / cos are FP32 polynomials.
+def xu_ops_per_rollout_step(n_obs: int, proj: bool = True) -> int:
+    if not proj:
+        return 4 + 1
+    P = (3 + 1 + n_obs + 3) // 4
+    return 4 * P + 2 + (1 + n_obs)
+
+
+# ----------------------------------------------------------------------------
+# Measured pipe peaks (issue-rate microbenchmarks, brmppi_measure_pipe): the
+# roofline denominators of the ALU-bound kernels, measured on the device the
+# bench runs on, with the clocks sampled while they run.
+_PIPE_PEAKS = None
+
+
+def pipe_peaks(local: int = 0):
+    global _PIPE_PEAKS
+    if _PIPE_PEAKS is not None:
+        return _PIPE_PEAKS
+    import torch
+    import paper_2508_05773_gb300 as pkg
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.2)
+    fma, t_fma = pkg.brmppi_measure_pipe(pkg.PIPE_FMA, 300000)
+    imad, t_imad = pkg.brmppi_measure_pipe(pkg.PIPE_IMAD, 150000)
+    xu, t_xu = pkg.brmppi_measure_pipe(pkg.PIPE_XU, 40000)
+    clk = clocks.stop()
+    _PIPE_PEAKS = {
+        "fp32_fma_lane_ops_per_s": fma, "int_imad_lane_ops_per_s": imad, "xu_lane_ops_per_s": xu,
+        "seconds": {"fma": t_fma, "imad": t_imad, "xu": t_xu}, "sms": sms, "clocks": clk,
+        "how": "brmppi_measure_pipe: 4 CTAs x 512 threads per SM, 8 independent chains a thread of FFMA / "
+               "IMAD / MUFU.RSQ; lane operations per second of the timed launch (CUDA events)",
+    }
+    return _PIPE_PEAKS
+
+
+def alu_roofline(ops: float, xu_ops: float, seconds: float, kernel: str, kernel_mhz=None) -> dict:
+    """Roofline of an ALU-bound launch against the measured peaks: every
+    algorithmic lane operation takes an issue slot (peak = the FP32 FMA issue
+    rate); the XU operations also against the XU pipe's own measured rate.
+    If the kernel ran at a higher SM clock than the microbenchmark (which can
+    meet the power cap), the peaks are scaled up to the kernel's clock (never
+    down), so that the fraction is not flattered."""
+    pk = pipe_peaks()
+    fma, xu = pk["fp32_fma_lane_ops_per_s"], pk["xu_lane_ops_per_s"]
+    peak_mhz = (pk.get("clocks") or {}).get("sm_mhz")
+    scale = 1.0
+    if kernel_mhz and peak_mhz and kernel_mhz > peak_mhz:
+        scale = kernel_mhz / peak_mhz
+    achieved = ops / seconds
+    return {"bound": "alu", "achieved": achieved / 1e12, "peak": scale * fma / 1e12, "unit": "Tops/s (FP32 lane ops)",
+            "frac": achieved / (scale * fma), "kernel": kernel, "ops_per_launch": ops,
+            "peak_note": "of measured: FP32 FFMA issue-rate microbenchmark on this GPU "
+                         f"({fma / 1e12:.2f} T lane-ops/s at a median {peak_mhz} MHz, {pk['sms']} SMs)"
+                         + (f", scaled to the kernel's {kernel_mhz:.0f} MHz" if scale > 1.0 else ""),
+            "xu": {"achieved": xu_ops / seconds / 1e12, "peak": scale * xu / 1e12,
+                   "frac": xu_ops / seconds / (scale * xu), "ops_per_launch": xu_ops}}
 
 
 # ----------------------------------------------------------------------------
@@ -266,17 +330,15 @@ def measure_batched(dev, reps: int = 10):
     plain_ms = float(np.median(plain_times))
     ops = sum(int(c["params"]["S"]) * int(c["params"]["H"]) * ops_per_rollout_step(int(c["obs"].shape[0]))
               for c in cases)
-    peak_ops = N_SM * FP32_LANES_PER_SM * float(_measured_peaks().get("sm_max_mhz", 2070.0)) * 1e6
-    achieved = ops / (batched_ms * 1e-3)
+    xu_ops = sum(int(c["params"]["S"]) * int(c["params"]["H"]) * xu_ops_per_rollout_step(int(c["obs"].shape[0]))
+                 for c in cases)
     return {"workload": "256 uneven solves: S in {1024,2048,4096,8192}, H in [30,80], "
                         "0-16 ellipses, random straight+arc paths (seed 1)",
             "rollout_steps": work, "value": work / (batched_ms * 1e-3), "unit": UNIT,
             "ms_per_batch": batched_ms, "plain_value": work / (plain_ms * 1e-3),
             "plain_ms_per_batch": plain_ms, "speedup_vs_plain": plain_ms / batched_ms,
             "launches_per_batch": 1, "plain_launches_per_batch": len(cases), "launch": batch_launch,
-            "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
-                         "unit": "Tops/s (FP32 lane ops)", "frac": achieved / peak_ops,
-                         "ops_per_launch": ops, "kernel": "solve_kernel (persistent batch launch)"},
+            "roofline": alu_roofline(ops, xu_ops, batched_ms * 1e-3, "solve_kernel (persistent batch launch)"),
             "how": "CUDA-graph replay of one persistent launch vs brmppi_solve_device per "
                    "instance on one stream; L2 flushed between batches; median"}
 
@@ -323,15 +385,14 @@ def measure_stress(dev, reps: int = 5):
     solver.close()
     peaks = _measured_peaks()
     hbm = float(peaks.get("hbm_gbs", 6800.0))
-    sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
-    peak_ops = N_SM * FP32_LANES_PER_SM * sm_mhz * 1e6
     ops = S * H * ops_per_rollout_step(n_obs)
+    roof = alu_roofline(ops, S * H * xu_ops_per_rollout_step(n_obs), res["plain"] * 1e-3, "solve_kernel")
     state_bytes = S * (H + 1) * 7 * 4
     gbs = state_bytes / (res["stored"] * 1e-3) / 1e9
     return {"workload": "S=65536, H=100, 64 ellipses (60x60 m lot), 120 m multi-arc path, ds=0.05",
             "launch": launch, "ms_per_solve": res["plain"], "ms_per_solve_stored": res["stored"],
             "rollout_steps_per_s": S * H / (res["plain"] * 1e-3),
-            "alu_frac": ops / (res["plain"] * 1e-3) / peak_ops,
+            "alu_frac": roof["frac"], "roofline": roof,
             "stored_bytes": state_bytes, "stored_hbm_gbs": gbs,
             "stored_hbm_frac": gbs / hbm,
             "note": "the stored variant writes 185 MB per solve at the solve's compute rate; "
@@ -782,6 +843,8 @@ def run_ours(args, world, rank, local):
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
 
+    if rank == 0:
+        pipe_peaks(local)  # the roofline denominators, measured before anything is timed
     solver.autotune(x0, Ubuf[0], obs, path, c["ds"], reps=3, stream=stream)
 
     def solve(tick: int):
@@ -848,12 +911,11 @@ def run_ours(args, world, rank, local):
            "what": "closed loop: brmppi_solve on host buffers + FP64 host plant + shift"}
 
     if rank == 0:
-        peaks = _measured_peaks()
-        sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
-        peak_ops = N_SM * FP32_LANES_PER_SM * sm_mhz * 1e6
         ops = S * H * ops_per_rollout_step(n_obs)
-        kernel_s = total_ms * 1e-3 / args.steps / world if world > 1 else total_ms * 1e-3 / args.steps
-        achieved = ops / kernel_s
+        kernel_s = total_ms * 1e-3 / args.steps
+        roof = alu_roofline(ops, S * H * xu_ops_per_rollout_step(n_obs), kernel_s, "solve_kernel",
+                            kernel_mhz=(clk or {}).get("sm_mhz"))
+        roof["traffic"] = _traffic_for_current_kernel()
         launch = solver.launch(n_obs)
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -863,12 +925,8 @@ def run_ours(args, world, rank, local):
             "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                            "p999": float(np.percentile(lat, 99.9)), "deadline": 10.0,
                            "misses": int(np.sum(lat > 10.0))},
-            "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
-                         "unit": "Tops/s (FP32 lane ops)", "frac": achieved / peak_ops,
-                         "traffic": _traffic_for_current_kernel(), "kernel": "solve_kernel",
-                         "ops_per_launch": ops,
-                         "peak_note": f"152 SMs x 128 FP32 lanes x {sm_mhz:.0f} MHz (sm_max_mhz of "
-                                      "MEASURED_PEAKS.json); derived, not measured"},
+            "roofline": roof,
+            "pipe_peaks": pipe_peaks(local),
             "e2e": e2e,
             "gpu_launches": args.steps,
             "clocks": clk,

@@ -365,6 +365,19 @@ brmppi_status brmppi_noise_blocks(uint64_t seed, uint64_t counter, int32_t n_sam
                                   int32_t n_blocks, uint32_t *words_dev, float *normals_dev,
                                   void *stream);
 
+/* Issue-rate microbenchmark of one SM pipe on the current device, for the
+   roofline denominators of the solve (no paper counterpart): pipe 0 = FP32
+   fused multiply-add, 1 = 32-bit integer multiply-add, 2 = the XU's
+   reciprocal square root (the special-function unit that also evaluates
+   log, sin, cos, exp and reciprocals).  4 CTAs of 512 threads per SM, each
+   thread eight independent chains of `iters` x 16 operations; one untimed
+   warm-up launch, then one launch timed with CUDA events on `stream` (waits
+   for it).  *lane_ops_per_s = lane operations of the pipe per second,
+   *seconds (may be NULL) the timed launch.  Changes no device setting;
+   allocates nothing.  EINVAL for a bad pipe or iters < 1. */
+brmppi_status brmppi_measure_pipe(int32_t pipe, int64_t iters, double *lane_ops_per_s, double *seconds,
+                                  void *stream);
+
 /* Bytes the host entry point brmppi_solve copies per call for a solve with
    n_obs obstacles and n_pts path rows: *h2d (inputs, one copy) and *d2h
    (U*, trajectory and status, one copy; plus 4*S when costs are asked

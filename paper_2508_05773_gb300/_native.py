@@ -39,7 +39,7 @@ EXPORTS = (
     "brmppi_get_launch", "brmppi_transfer_bytes", "brmppi_vehicle_register", "brmppi_submit",
     "brmppi_poll", "brmppi_vehicle_export", "brmppi_vehicle_import", "brmppi_server_stats_get",
     "brmppi_solve_device_noalloc", "brmppi_hitch_stabilize_device", "brmppi_get_batch_launch",
-    "brmppi_noise_blocks",
+    "brmppi_noise_blocks", "brmppi_measure_pipe",
 )
 
 
@@ -164,6 +164,9 @@ def load() -> ctypes.CDLL:
                                                      ctypes.POINTER(ctypes.c_uint64)]),
             "brmppi_noise_blocks": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int32,
                                                    ctypes.c_int32, ctypes.c_int32, _VP, _VP, _VP]),
+            "brmppi_measure_pipe": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int64,
+                                                   ctypes.POINTER(ctypes.c_double),
+                                                   ctypes.POINTER(ctypes.c_double), _VP]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -414,6 +417,20 @@ def brmppi_noise_blocks(seed: int, counter: int, n_samples: int, H: int, n_block
     tensors or None."""
     return load().brmppi_noise_blocks(int(seed), int(counter), int(n_samples), int(H), int(n_blocks),
                                       _dptr(words), _dptr(normals), ctypes.c_void_p(_stream_handle(stream)))
+
+
+PIPE_FMA, PIPE_IMAD, PIPE_XU = 0, 1, 2
+
+
+def brmppi_measure_pipe(pipe: int, iters: int, stream=None):
+    """(lane operations per second, seconds) of one SM pipe's issue-rate
+    microbenchmark on the current device (PIPE_FMA, PIPE_IMAD, PIPE_XU)."""
+    rate, sec = ctypes.c_double(), ctypes.c_double()
+    st = load().brmppi_measure_pipe(int(pipe), int(iters), ctypes.byref(rate), ctypes.byref(sec),
+                                    ctypes.c_void_p(_stream_handle(stream)))
+    if st != BRMPPI_OK:
+        raise BrmppiError(st, brmppi_last_error(None))
+    return rate.value, sec.value
 
 
 def brmppi_get_launch(ctx, n_obs: int):

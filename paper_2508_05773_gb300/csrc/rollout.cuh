@@ -1584,6 +1584,23 @@ static __device__ void merge_instance(const KConst& k, const Inst& in, const Sme
   __syncthreads();
 }
 
+// The tile's applied-input history in global memory is dead once the tile's
+// weighted sums have read it: its L2 lines are dropped without being written
+// back to DRAM (discard.global.L2, whole 128-byte lines only, so a line
+// shared with the neighbouring CTA's slot is left alone).  Every read of the
+// history must be complete (after a CTA barrier); the next tile writes
+// before it reads.
+__device__ __forceinline__ void discard_history(const float* uh, int n_floats) {
+  const unsigned long long b0 = reinterpret_cast<unsigned long long>(uh);
+  const unsigned long long b1 = b0 + 4ull * static_cast<unsigned long long>(n_floats);
+  const unsigned long long first = (b0 + 127ull) & ~127ull, last = b1 & ~127ull;
+  for (unsigned long long a = first + 128ull * threadIdx.x; a < last; a += 128ull * blockDim.x) {
+    unsigned long long g;
+    asm volatile("cvta.to.global.u64 %0, %1;" : "=l"(g) : "l"(a));
+    asm volatile("discard.global.L2 [%0], 128;" ::"l"(g) : "memory");
+  }
+}
+
 // -------------------------------------------------------------- the kernel
 // EXT: the instantiations that also carry the optional terms (moving and
 // e = 4 obstacles, collision cost, buffer cost); the others compile them out.
@@ -1625,6 +1642,7 @@ __global__ void __launch_bounds__(512) solve_kernel(const KConst k, const Launch
     // the CTA that completes an instance's last tile merges its partials
     __threadfence();
     __syncthreads();
+    if constexpr (ROWS == 0) discard_history(uh, 3 * in.H * (compute_threads<TPS>(L.noise_warps) / TPS));
     if (threadIdx.x == 0) sh.last = (atomicAdd(in.sync, 1u) == static_cast<unsigned>(in.tiles - 1));
     __syncthreads();
     if (sh.last) {
