@@ -118,6 +118,8 @@ typedef struct brmppi_params {
   int32_t serve_max_batch;       /* serving: solves per launch (0 = 64) */
   int32_t serve_queue;           /* serving: request slots, further capped by free
                                     device memory at create (0 = 1024) */
+  int32_t wait_timeout_ms;       /* limit of the library's host-side waits for the
+                                    GPU (serving completions, destroy): 0 = 10000 */
   float Ts, lambda;              /* sample time [s]; softmin temperature */
   float l1, lh, l2;              /* wheelbase, hitch offset, trailer length [m] */
   float dtheta_max, kappa;       /* hitch limit dtheta_max - kappa*v */
@@ -181,8 +183,21 @@ void brmppi_default_params(brmppi_params *p);
    of the given capacities needs (device + pinned host). */
 brmppi_status brmppi_create(const brmppi_params *p, int device, brmppi_ctx **out);
 
-/* Destroy a context (NULL is a no-op). Waits for its work to finish. */
-void brmppi_destroy(brmppi_ctx *ctx);
+/* Destroy a context (NULL is a no-op): waits for its work to finish, at
+   most params.wait_timeout_ms for each of its streams and batch lanes, then
+   frees everything.  BRMPPI_ETIMEDOUT if a wait gave up: the buffers that
+   the unfinished work may still use are then left allocated (leaked) rather
+   than freed under it; the context itself is released either way.  Returns
+   BRMPPI_OK otherwise. */
+brmppi_status brmppi_destroy(brmppi_ctx *ctx);
+
+/* Testing hook for the out-of-memory paths (no paper counterpart): the n-th
+   device or pinned-host allocation that the library makes from now on
+   (counting every context, batch lane, serving slot and vehicle buffer)
+   fails as if the device were out of memory, without calling CUDA; n <= 0
+   disarms it.  The failing call returns BRMPPI_ENOMEM and unwinds what it had
+   allocated.  Process-wide; not for production use. */
+void brmppi_inject_alloc_failure(int32_t n);
 
 /* Message of the last failure on this context ("" if none); valid until the
    next call on the context. A NULL ctx gives the last create() failure. */

@@ -12,7 +12,8 @@ from ._native import (  # noqa: F401
     BRMPPI_FLAG_OBS8, BRMPPI_FLAG_PROJ_NONE, BRMPPI_FLAG_THIRD_ORDER, BRMPPI_OK, EXPORTS, PIPE_FMA, PIPE_IMAD, PIPE_XU, BrmppiError,
     NativeLibraryMissing, Solver, brmppi_autotune, brmppi_autotune_batch, brmppi_batch_capture,
     brmppi_create, brmppi_default_params, brmppi_destroy, brmppi_get_batch_launch, brmppi_get_launch,
-    brmppi_graph_destroy, brmppi_graph_launch, brmppi_hitch_stabilize_device, brmppi_instance,
+    brmppi_graph_destroy, brmppi_graph_launch, brmppi_hitch_stabilize_device, brmppi_inject_alloc_failure,
+    brmppi_instance,
     brmppi_last_error, brmppi_measure_pipe, brmppi_noise_blocks, brmppi_params, brmppi_poll, brmppi_server_stats, brmppi_server_stats_get,
     brmppi_solve, brmppi_solve_batch, brmppi_solve_device, brmppi_solve_device_ex,
     brmppi_solve_device_noalloc, brmppi_submit, brmppi_transfer_bytes, brmppi_vehicle_export,

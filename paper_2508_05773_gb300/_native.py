@@ -39,7 +39,7 @@ EXPORTS = (
     "brmppi_get_launch", "brmppi_transfer_bytes", "brmppi_vehicle_register", "brmppi_submit",
     "brmppi_poll", "brmppi_vehicle_export", "brmppi_vehicle_import", "brmppi_server_stats_get",
     "brmppi_solve_device_noalloc", "brmppi_hitch_stabilize_device", "brmppi_get_batch_launch",
-    "brmppi_noise_blocks", "brmppi_measure_pipe",
+    "brmppi_noise_blocks", "brmppi_measure_pipe", "brmppi_inject_alloc_failure",
 )
 
 
@@ -53,6 +53,7 @@ class brmppi_params(ctypes.Structure):
         ("batch_threads_per_sample", ctypes.c_int32), ("batch_block_threads", ctypes.c_int32),
         ("max_vehicles", ctypes.c_int32), ("serve_lanes", ctypes.c_int32),
         ("serve_max_batch", ctypes.c_int32), ("serve_queue", ctypes.c_int32),
+        ("wait_timeout_ms", ctypes.c_int32),
         ("Ts", ctypes.c_float), ("lambda_", ctypes.c_float),
         ("l1", ctypes.c_float), ("lh", ctypes.c_float), ("l2", ctypes.c_float),
         ("dtheta_max", ctypes.c_float), ("kappa", ctypes.c_float), ("r_inflate", ctypes.c_float),
@@ -120,7 +121,8 @@ def load() -> ctypes.CDLL:
         sig = {
             "brmppi_default_params": (None, [P]),
             "brmppi_create": (ctypes.c_int, [P, ctypes.c_int, ctypes.POINTER(_VP)]),
-            "brmppi_destroy": (None, [_VP]),
+            "brmppi_destroy": (ctypes.c_int, [_VP]),
+            "brmppi_inject_alloc_failure": (None, [ctypes.c_int32]),
             "brmppi_last_error": (ctypes.c_char_p, [_VP]),
             "brmppi_solve": (ctypes.c_int, [_VP, _D, _F, _F, ctypes.c_int32, _F, ctypes.c_int32,
                                             ctypes.c_float, ctypes.c_uint64, ctypes.c_uint64, _F, _F,
@@ -192,7 +194,7 @@ def params_from_dict(d: dict, max_obstacles: int = 16, max_path_pts: int = 4096,
                      threads_per_sample: int = 0, block_threads: int = 0, max_batch: int = 0,
                      batch_threads_per_sample: int = 0, batch_block_threads: int = 0,
                      max_vehicles: int = 0, serve_lanes: int = 0, serve_max_batch: int = 0,
-                     serve_queue: int = 0) -> brmppi_params:
+                     serve_queue: int = 0, wait_timeout_ms: int = 0) -> brmppi_params:
     """brmppi_params from the parameter dict of ``scenarios`` (values are
     rounded to binary32 by the struct)."""
     p = brmppi_default_params()
@@ -219,6 +221,7 @@ def params_from_dict(d: dict, max_obstacles: int = 16, max_path_pts: int = 4096,
     p.serve_lanes = int(serve_lanes)
     p.serve_max_batch = int(serve_max_batch)
     p.serve_queue = int(serve_queue)
+    p.wait_timeout_ms = int(wait_timeout_ms)
     p.abi_version = BRMPPI_ABI_VERSION
     return p
 
@@ -232,9 +235,18 @@ def brmppi_create(params: brmppi_params, device: int = 0) -> ctypes.c_void_p:
     return h
 
 
-def brmppi_destroy(ctx) -> None:
+def brmppi_destroy(ctx) -> int:
+    """Destroy a context; BRMPPI_ETIMEDOUT if a bounded wait for its work
+    gave up (its buffers are then left allocated)."""
     if ctx:
-        load().brmppi_destroy(ctx)
+        return load().brmppi_destroy(ctx)
+    return BRMPPI_OK
+
+
+def brmppi_inject_alloc_failure(n: int) -> None:
+    """Testing hook: the n-th library allocation from now on fails as out of
+    memory (n <= 0 disarms)."""
+    load().brmppi_inject_alloc_failure(int(n))
 
 
 def brmppi_last_error(ctx) -> str:
@@ -529,7 +541,7 @@ class Solver:
                  max_path_pts: int = 4096, threads_per_sample: int = 0, block_threads: int = 0,
                  max_batch: int = 0, batch_threads_per_sample: int = 0,
                  batch_block_threads: int = 0, max_vehicles: int = 0, serve_lanes: int = 0,
-                 serve_max_batch: int = 0, serve_queue: int = 0):
+                 serve_max_batch: int = 0, serve_queue: int = 0, wait_timeout_ms: int = 0):
         self.ctx = None
         self.params = dict(params)
         self.S = int(params["S"])
@@ -537,13 +549,16 @@ class Solver:
         self._p = params_from_dict(params, max_obstacles, max_path_pts, threads_per_sample,
                                    block_threads, max_batch, batch_threads_per_sample,
                                    batch_block_threads, max_vehicles, serve_lanes,
-                                   serve_max_batch, serve_queue)
+                                   serve_max_batch, serve_queue, wait_timeout_ms)
         self.ctx = brmppi_create(self._p, device)
 
-    def close(self):
+    def close(self) -> int:
+        """Destroy the context; the status of brmppi_destroy."""
+        st = BRMPPI_OK
         if self.ctx:
-            brmppi_destroy(self.ctx)
+            st = brmppi_destroy(self.ctx)
             self.ctx = None
+        return st
 
     def __del__(self):
         try:

@@ -7,12 +7,15 @@
 // for).  Batches upload an instance table and a longest-first work list and
 // run one persistent launch.
 #include <algorithm>
+#include <atomic>
+#include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <map>
 #include <mutex>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "internal.h"
@@ -20,7 +23,7 @@
 using namespace brmppi_host;
 
 // The layouts the Python binding mirrors.
-static_assert(sizeof(brmppi_params) == 4 * 15 + 4 * 41 + 4 * 10, "brmppi_params layout");
+static_assert(sizeof(brmppi_params) == 4 * 16 + 4 * 41 + 4 * 10, "brmppi_params layout");
 static_assert(sizeof(brmppi_instance) == 8 * 4 + 4 * 5 + 4 + 8 * 2 + 8 * 9, "brmppi_instance layout");
 
 namespace brmppi_host {
@@ -32,6 +35,50 @@ std::string g_create_err;
 }  // namespace
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+namespace {
+std::atomic<int> g_fail_alloc_in{0};  // > 0: the allocation that brings it to 0 fails
+
+bool injected_alloc_failure() {
+  int n = g_fail_alloc_in.load();
+  while (n > 0) {
+    if (g_fail_alloc_in.compare_exchange_weak(n, n - 1)) return n == 1;
+  }
+  return false;
+}
+}  // namespace
+
+cudaError_t dev_alloc(void** p, size_t bytes) {
+  *p = nullptr;
+  if (injected_alloc_failure()) return cudaErrorMemoryAllocation;
+  return cudaMalloc(p, bytes);
+}
+
+cudaError_t host_alloc(void** p, size_t bytes) {
+  *p = nullptr;
+  if (injected_alloc_failure()) return cudaErrorMemoryAllocation;
+  return cudaMallocHost(p, bytes);
+}
+
+cudaError_t wait_event(cudaEvent_t ev, int timeout_ms) {
+  const auto t0 = std::chrono::steady_clock::now();
+  for (;;) {
+    const cudaError_t q = cudaEventQuery(ev);
+    if (q != cudaErrorNotReady) return q;
+    if (std::chrono::steady_clock::now() - t0 > std::chrono::milliseconds(timeout_ms)) return cudaErrorNotReady;
+    std::this_thread::yield();
+  }
+}
+
+cudaError_t wait_stream(cudaStream_t s, int timeout_ms) {
+  const auto t0 = std::chrono::steady_clock::now();
+  for (;;) {
+    const cudaError_t q = cudaStreamQuery(s);
+    if (q != cudaErrorNotReady) return q;
+    if (std::chrono::steady_clock::now() - t0 > std::chrono::milliseconds(timeout_ms)) return cudaErrorNotReady;
+    std::this_thread::yield();
+  }
+}
 
 brmppi_status fail(brmppi_ctx* c, brmppi_status st, const std::string& msg) {
   if (c) {
@@ -84,6 +131,7 @@ std::string check_params(const brmppi_params* p) {
   if (p->serve_lanes < 0 || p->serve_lanes > 16) return "serve_lanes must be in [0, 16]";
   if (p->serve_max_batch < 0 || p->serve_max_batch > 4096) return "serve_max_batch must be in [0, 4096]";
   if (p->serve_queue < 0 || p->serve_queue > (1 << 20)) return "serve_queue must be in [0, 2^20]";
+  if (p->wait_timeout_ms < 0) return "wait_timeout_ms must be >= 0";
   const float pos[] = {p->Ts, p->lambda, p->l1, p->l2, p->h_floor};
   for (float v : pos)
     if (!(v > 0.f) || !std::isfinite(v)) return "Ts, lambda, l1, l2, h_floor must be positive and finite";
@@ -399,23 +447,28 @@ cudaError_t lane_alloc(Lane& L, int max_batch, size_t S, size_t H, int num_sms, 
   L.bpart_floats = L.max_work * part_stride;
   L.buh_floats = static_cast<size_t>(num_sms) * kMaxResidentThreads * 3 * H;
   cudaError_t e;
-  if ((e = cudaMalloc(&L.d_inst, sizeof(brmppi::Inst) * nb)) != cudaSuccess) return e;
-  if ((e = cudaMalloc(&L.d_work, sizeof(int2) * L.max_work)) != cudaSuccess) return e;
-  if ((e = cudaMalloc(&L.d_work_ctr, sizeof(unsigned int) * 2)) != cudaSuccess) return e;
+  if ((e = dev_alloc(&L.d_inst, sizeof(brmppi::Inst) * nb)) != cudaSuccess) return e;
+  if ((e = dev_alloc(&L.d_work, sizeof(int2) * L.max_work)) != cudaSuccess) return e;
+  if ((e = dev_alloc(&L.d_work_ctr, sizeof(unsigned int) * 2)) != cudaSuccess) return e;
   if ((e = cudaMemset(L.d_work_ctr, 0, sizeof(unsigned int) * 2)) != cudaSuccess) return e;
-  if ((e = cudaMalloc(&L.d_bpart, sizeof(float) * L.bpart_floats)) != cudaSuccess) return e;
-  if ((e = cudaMalloc(&L.d_bsync, sizeof(unsigned int) * 2 * nb)) != cudaSuccess) return e;
+  if ((e = dev_alloc(&L.d_bpart, sizeof(float) * L.bpart_floats)) != cudaSuccess) return e;
+  if ((e = dev_alloc(&L.d_bsync, sizeof(unsigned int) * 2 * nb)) != cudaSuccess) return e;
   if ((e = cudaMemset(L.d_bsync, 0, sizeof(unsigned int) * 2 * nb)) != cudaSuccess) return e;
-  if ((e = cudaMalloc(&L.d_buh, sizeof(float) * L.buh_floats)) != cudaSuccess) return e;
-  if ((e = cudaMallocHost(&L.h_inst, sizeof(brmppi::Inst) * nb)) != cudaSuccess) return e;
-  if ((e = cudaMallocHost(&L.h_work, sizeof(int2) * L.max_work)) != cudaSuccess) return e;
+  if ((e = dev_alloc(&L.d_buh, sizeof(float) * L.buh_floats)) != cudaSuccess) return e;
+  if ((e = host_alloc(&L.h_inst, sizeof(brmppi::Inst) * nb)) != cudaSuccess) return e;
+  if ((e = host_alloc(&L.h_work, sizeof(int2) * L.max_work)) != cudaSuccess) return e;
   if ((e = cudaEventCreateWithFlags(&L.upload_done, cudaEventDisableTiming)) != cudaSuccess) return e;
   if ((e = cudaEventCreateWithFlags(&L.batch_done, cudaEventDisableTiming)) != cudaSuccess) return e;
   return cudaSuccess;
 }
 
-void lane_free(Lane& L) {
-  if (L.pending && L.batch_done) cudaEventSynchronize(L.batch_done);
+bool lane_free(Lane& L, int timeout_ms) {
+  if (L.pending && L.batch_done && wait_event(L.batch_done, timeout_ms) == cudaErrorNotReady) {
+    // the lane's last batch is still running: leave its buffers allocated
+    if (L.stream) cudaStreamDestroy(L.stream);
+    L = Lane();
+    return false;
+  }
   cudaFree(L.d_inst);
   cudaFree(L.d_work);
   cudaFree(L.d_work_ctr);
@@ -428,6 +481,7 @@ void lane_free(Lane& L) {
   if (L.batch_done) cudaEventDestroy(L.batch_done);
   if (L.stream) cudaStreamDestroy(L.stream);
   L = Lane();
+  return true;
 }
 
 namespace {
@@ -664,16 +718,16 @@ brmppi_status brmppi_create(const brmppi_params* p, int device, brmppi_ctx** out
   c->uh_floats = (S + kMaxThreads) * 3 * H;  // one tile slot per CTA, rounded up
   if ((e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking)) != cudaSuccess)
     return bail(e, "cudaStreamCreate");
-  if ((e = cudaMalloc(&c->d_in, c->in_bytes)) != cudaSuccess) return bail(e, "cudaMalloc(in)");
-  if ((e = cudaMalloc(&c->d_out, sizeof(float) * c->out_floats)) != cudaSuccess) return bail(e, "cudaMalloc(out)");
-  if ((e = cudaMalloc(&c->d_J, sizeof(float) * S)) != cudaSuccess) return bail(e, "cudaMalloc(J)");
-  if ((e = cudaMalloc(&c->d_part, sizeof(float) * c->part_stride * c->part_tiles)) != cudaSuccess)
+  if ((e = dev_alloc(&c->d_in, c->in_bytes)) != cudaSuccess) return bail(e, "cudaMalloc(in)");
+  if ((e = dev_alloc(&c->d_out, sizeof(float) * c->out_floats)) != cudaSuccess) return bail(e, "cudaMalloc(out)");
+  if ((e = dev_alloc(&c->d_J, sizeof(float) * S)) != cudaSuccess) return bail(e, "cudaMalloc(J)");
+  if ((e = dev_alloc(&c->d_part, sizeof(float) * c->part_stride * c->part_tiles)) != cudaSuccess)
     return bail(e, "cudaMalloc(partials)");
-  if ((e = cudaMalloc(&c->d_uh, sizeof(float) * c->uh_floats)) != cudaSuccess) return bail(e, "cudaMalloc(history)");
-  if ((e = cudaMalloc(&c->d_sync, sizeof(unsigned int) * 4)) != cudaSuccess) return bail(e, "cudaMalloc(sync)");
+  if ((e = dev_alloc(&c->d_uh, sizeof(float) * c->uh_floats)) != cudaSuccess) return bail(e, "cudaMalloc(history)");
+  if ((e = dev_alloc(&c->d_sync, sizeof(unsigned int) * 4)) != cudaSuccess) return bail(e, "cudaMalloc(sync)");
   if ((e = cudaMemset(c->d_sync, 0, sizeof(unsigned int) * 4)) != cudaSuccess) return bail(e, "cudaMemset");
-  if ((e = cudaMallocHost(&c->h_in, c->in_bytes)) != cudaSuccess) return bail(e, "cudaMallocHost(in)");
-  if ((e = cudaMallocHost(&c->h_out, sizeof(float) * c->out_floats)) != cudaSuccess)
+  if ((e = host_alloc(&c->h_in, c->in_bytes)) != cudaSuccess) return bail(e, "cudaMallocHost(in)");
+  if ((e = host_alloc(&c->h_out, sizeof(float) * c->out_floats)) != cudaSuccess)
     return bail(e, "cudaMallocHost(out)");
   if (p->max_batch > 0 && (e = lane_alloc(c->batch, p->max_batch, S, H, c->num_sms, c->part_stride)) != cudaSuccess)
     return bail(e, "batch buffers");
@@ -691,23 +745,33 @@ brmppi_status brmppi_create(const brmppi_params* p, int device, brmppi_ctx** out
   return BRMPPI_OK;
 }
 
-void brmppi_destroy(brmppi_ctx* c) {
-  if (!c) return;
+brmppi_status brmppi_destroy(brmppi_ctx* c) {
+  if (!c) return BRMPPI_OK;
   cudaSetDevice(c->device);
-  if (c->server) server_destroy(c);
-  if (c->stream) cudaStreamSynchronize(c->stream);
-  lane_free(c->batch);
-  cudaFree(c->d_in);
-  cudaFree(c->d_out);
-  cudaFree(c->d_J);
-  cudaFree(c->d_part);
-  cudaFree(c->d_uh);
-  cudaFree(c->d_sync);
-  cudaFreeHost(c->h_in);
-  cudaFreeHost(c->h_out);
+  const int limit = wait_limit_ms(c->prm);
+  // every wait bounded; once one gives up nothing more is freed (a free may
+  // wait for the device), the buffers stay allocated and the context goes
+  bool done = server_destroy(c);
+  if (done && c->stream && wait_stream(c->stream, limit) != cudaSuccess) done = false;
+  if (done) done = lane_free(c->batch, limit);
+  if (done) {
+    cudaFree(c->d_in);
+    cudaFree(c->d_out);
+    cudaFree(c->d_J);
+    cudaFree(c->d_part);
+    cudaFree(c->d_uh);
+    cudaFree(c->d_sync);
+    cudaFreeHost(c->h_in);
+    cudaFreeHost(c->h_out);
+  } else if (c->batch.stream) {
+    cudaStreamDestroy(c->batch.stream);
+  }
   if (c->stream) cudaStreamDestroy(c->stream);
   delete c;
+  return done ? BRMPPI_OK : BRMPPI_ETIMEDOUT;
 }
+
+void brmppi_inject_alloc_failure(int32_t n) { g_fail_alloc_in.store(n > 0 ? n : 0); }
 
 const char* brmppi_last_error(const brmppi_ctx* c) {
   if (!c) {
@@ -839,9 +903,9 @@ brmppi_status brmppi_batch_capture(brmppi_ctx* c, const brmppi_instance* inst, i
     brmppi_graph_destroy(g);
     return st;
   };
-  if ((e = cudaMallocHost(&g->h_inst, sizeof(brmppi::Inst) * L.max_batch)) != cudaSuccess)
+  if ((e = host_alloc(&g->h_inst, sizeof(brmppi::Inst) * L.max_batch)) != cudaSuccess)
     return bail(cuda_fail(c, e, "cudaMallocHost(graph table)"));
-  if ((e = cudaMallocHost(&g->h_work, sizeof(int2) * L.max_work)) != cudaSuccess)
+  if ((e = host_alloc(&g->h_work, sizeof(int2) * L.max_work)) != cudaSuccess)
     return bail(cuda_fail(c, e, "cudaMallocHost(graph work)"));
   BatchPlan plan;
   brmppi_status st = plan_batch(c, L, inst, n, nullptr, g->h_inst, g->h_work, &plan);

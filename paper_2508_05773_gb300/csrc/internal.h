@@ -115,6 +115,30 @@ struct brmppi_graph {
 namespace brmppi_host {
 
 size_t align_up(size_t v, size_t a);
+
+// Every device and pinned-host allocation of the library goes through these
+// two.  A test hook (brmppi_inject_alloc_failure) makes the n-th allocation
+// from then on fail with cudaErrorMemoryAllocation without calling CUDA, so
+// that the out-of-memory paths (BRMPPI_ENOMEM, clean unwinding) can be
+// exercised without exhausting a device.
+cudaError_t dev_alloc(void** p, size_t bytes);
+cudaError_t host_alloc(void** p, size_t bytes);
+template <typename T>
+cudaError_t dev_alloc(T** p, size_t bytes) {
+  return dev_alloc(reinterpret_cast<void**>(p), bytes);
+}
+template <typename T>
+cudaError_t host_alloc(T** p, size_t bytes) {
+  return host_alloc(reinterpret_cast<void**>(p), bytes);
+}
+
+// Bounded waits of the host threads: poll an event or a stream until it
+// completes (cudaSuccess), fails (its error) or `timeout_ms` passes
+// (cudaErrorNotReady).
+cudaError_t wait_event(cudaEvent_t ev, int timeout_ms);
+cudaError_t wait_stream(cudaStream_t s, int timeout_ms);
+// The host-wait limit of a context (params.wait_timeout_ms, 0 = 10 s).
+inline int wait_limit_ms(const brmppi_params& p) { return p.wait_timeout_ms > 0 ? p.wait_timeout_ms : 10000; }
 brmppi_status fail(brmppi_ctx* c, brmppi_status st, const std::string& msg);
 brmppi_status cuda_fail(brmppi_ctx* c, cudaError_t e, const char* what);
 int philox_blocks(int n_rows);  // per step, for n_rows obstacle rows
@@ -134,7 +158,9 @@ void single_launch_options(brmppi::LaunchDesc& L, const Shape& sh, const brmppi:
 // Allocate / free the buffers of a lane for max_batch instances of at most
 // S samples and H steps.
 cudaError_t lane_alloc(Lane& L, int max_batch, size_t S, size_t H, int num_sms, size_t part_stride);
-void lane_free(Lane& L);
+// Free a lane; false (nothing freed) if its last batch did not finish within
+// timeout_ms.
+bool lane_free(Lane& L, int timeout_ms);
 
 // Validate instances and fill a lane's host staging (table + longest-first
 // work list); `forced` fixes the launch shape (else the context's batch shape).
@@ -146,6 +172,8 @@ brmppi_status upload_and_launch(brmppi_ctx* c, Lane& L, const BatchPlan& plan, c
 
 // Serving loop (serve.cu).
 brmppi_status server_create(brmppi_ctx* c);
-void server_destroy(brmppi_ctx* c);
+// Stop and free the serving loop; false if a lane did not finish within the
+// context's wait limit (its buffers are then left allocated).
+bool server_destroy(brmppi_ctx* c);
 
 }  // namespace brmppi_host

@@ -58,6 +58,8 @@ struct Slot {
   int n_obs = 0;
   double t_submit = 0.0, t_done = 0.0;
   int32_t status = 0;
+  bool held = false;    // its batch's wait gave up: the GPU may still use the slot
+  bool polled = false;  // handed out while held: free it when the batch finishes
 };
 
 struct InFlight {
@@ -87,6 +89,10 @@ struct Server {
   std::vector<Lane> lanes;
   std::vector<bool> lane_busy;
   std::deque<InFlight> inflight;
+  // batches whose bounded wait gave up (their requests answered ETIMEDOUT):
+  // their lane, vehicles and request slots stay reserved until they finish
+  std::deque<InFlight> stuck;
+  int wait_ms = 10000;
   Shape shape;
   int max_batch = 0;
   std::mutex mu;
@@ -98,7 +104,37 @@ struct Server {
 
   void scheduler_loop();
   void completion_loop();
+  void release(const InFlight& f);  // a stuck batch finished (mu held)
+  void reap_stuck();                // release the stuck batches that have finished (mu held)
 };
+
+void Server::release(const InFlight& f) {
+  for (int s : f.slots) {
+    Slot& sl = slots[s];
+    veh[sl.vid].running = false;
+    sl.held = false;
+    if (sl.polled) {
+      sl.polled = false;
+      sl.state = kFree;
+      free_slots.push_back(s);
+    }
+  }
+  lane_busy[f.lane] = false;
+  lanes[f.lane].pending = false;
+  --running_batches;
+  cv_sched.notify_one();
+}
+
+void Server::reap_stuck() {
+  for (auto it = stuck.begin(); it != stuck.end();) {
+    if (cudaEventQuery(lanes[it->lane].batch_done) != cudaErrorNotReady) {
+      release(*it);
+      it = stuck.erase(it);
+    } else {
+      ++it;
+    }
+  }
+}
 
 void Server::scheduler_loop() {
   cudaSetDevice(shadow.device);
@@ -210,25 +246,39 @@ void Server::completion_loop() {
   cudaSetDevice(shadow.device);
   std::unique_lock<std::mutex> lk(mu);
   for (;;) {
-    while (inflight.empty() && !stop) cv_comp.wait(lk);
+    reap_stuck();
+    while (inflight.empty() && !stop) {
+      if (stuck.empty()) {
+        cv_comp.wait(lk);
+      } else {
+        cv_comp.wait_for(lk, std::chrono::milliseconds(1));
+        reap_stuck();
+      }
+    }
     if (inflight.empty() && stop) return;
     const int lane = inflight.front().lane;
     lk.unlock();
-    const cudaError_t e = cudaEventSynchronize(lanes[lane].batch_done);
+    const cudaError_t e = wait_event(lanes[lane].batch_done, wait_ms);
     const double t = now_s();
     lk.lock();
     InFlight f = std::move(inflight.front());
     inflight.pop_front();
+    const bool timed_out = e == cudaErrorNotReady;
     for (int s : f.slots) {
       Slot& sl = slots[s];
-      int32_t kst = BRMPPI_ECUDA;
+      int32_t kst = timed_out ? BRMPPI_ETIMEDOUT : BRMPPI_ECUDA;
       if (e == cudaSuccess) std::memcpy(&kst, h_out + static_cast<size_t>(s) * out_stride + 3 * H + 7 * (H + 1), 4);
       sl.status = kst;
       sl.t_done = t;
       sl.state = kDone;
-      veh[sl.vid].running = false;
+      sl.held = timed_out;
+      if (!timed_out) veh[sl.vid].running = false;
       veh[sl.vid].queued -= 1;
       ++completed;
+    }
+    if (timed_out) {
+      stuck.push_back(std::move(f));  // the lane stays busy until the batch finishes
+      continue;
     }
     lane_busy[f.lane] = false;
     --running_batches;
@@ -248,6 +298,7 @@ brmppi_status server_create(brmppi_ctx* c) {
   sv->S = p.S;
   sv->max_obs = p.max_obstacles;
   sv->max_batch = p.serve_max_batch > 0 ? p.serve_max_batch : 64;
+  sv->wait_ms = wait_limit_ms(p);
   if (brmppi::needs_ext(make_kconst(p))) {
     // rows with a steer-rate column: at most two Philox blocks per lane
     sv->shape.tps = ext_team_width(philox_blocks(rows_of(p, p.max_obstacles)));
@@ -279,11 +330,11 @@ brmppi_status server_create(brmppi_ctx* c) {
   sv->n_slots = static_cast<int>(want < fit ? want : fit);
   if (sv->n_slots < 1) return fail(c, BRMPPI_ENOMEM, "no device memory for request slots");
   const size_t ns = static_cast<size_t>(sv->n_slots);
-  if ((e = cudaMalloc(&sv->d_in, sv->in_stride * ns)) != cudaSuccess) return cuda_fail(c, e, "request slots");
-  if ((e = cudaMalloc(&sv->d_out, sizeof(float) * sv->out_stride * ns)) != cudaSuccess)
+  if ((e = dev_alloc(&sv->d_in, sv->in_stride * ns)) != cudaSuccess) return cuda_fail(c, e, "request slots");
+  if ((e = dev_alloc(&sv->d_out, sizeof(float) * sv->out_stride * ns)) != cudaSuccess)
     return cuda_fail(c, e, "request slots");
-  if ((e = cudaMallocHost(&sv->h_in, sv->in_stride * ns)) != cudaSuccess) return cuda_fail(c, e, "request slots");
-  if ((e = cudaMallocHost(&sv->h_out, sizeof(float) * sv->out_stride * ns)) != cudaSuccess)
+  if ((e = host_alloc(&sv->h_in, sv->in_stride * ns)) != cudaSuccess) return cuda_fail(c, e, "request slots");
+  if ((e = host_alloc(&sv->h_out, sizeof(float) * sv->out_stride * ns)) != cudaSuccess)
     return cuda_fail(c, e, "request slots");
   sv->slots.resize(ns);
   sv->free_slots.reserve(ns);
@@ -294,9 +345,9 @@ brmppi_status server_create(brmppi_ctx* c) {
   return BRMPPI_OK;
 }
 
-void server_destroy(brmppi_ctx* c) {
+bool server_destroy(brmppi_ctx* c) {
   Server* sv = c->server;
-  if (!sv) return;
+  if (!sv) return true;
   {
     std::lock_guard<std::mutex> lk(sv->mu);
     sv->stop = true;
@@ -305,20 +356,29 @@ void server_destroy(brmppi_ctx* c) {
   sv->cv_comp.notify_all();
   if (sv->sched.joinable()) sv->sched.join();
   if (sv->comp.joinable()) sv->comp.join();
-  for (Lane& L : sv->lanes) {
-    if (L.stream) cudaStreamSynchronize(L.stream);
-    lane_free(L);
+  // every lane's last batch, within the limit; a lane still running keeps its
+  // buffers, and then nothing else is freed either (a free may wait for the
+  // device)
+  bool done = true;
+  for (Lane& L : sv->lanes)
+    if (L.stream && wait_stream(L.stream, sv->wait_ms) != cudaSuccess) done = false;
+  if (done) {
+    for (Lane& L : sv->lanes) lane_free(L, sv->wait_ms);
+    for (Vehicle& V : sv->veh) {
+      cudaFree(V.d_path);
+      cudaFree(V.d_unom);
+    }
+    cudaFree(sv->d_in);
+    cudaFree(sv->d_out);
+    cudaFreeHost(sv->h_in);
+    cudaFreeHost(sv->h_out);
+  } else {
+    for (Lane& L : sv->lanes)
+      if (L.stream) cudaStreamDestroy(L.stream);  // released once its work is done
   }
-  for (Vehicle& V : sv->veh) {
-    cudaFree(V.d_path);
-    cudaFree(V.d_unom);
-  }
-  cudaFree(sv->d_in);
-  cudaFree(sv->d_out);
-  cudaFreeHost(sv->h_in);
-  cudaFreeHost(sv->h_out);
   delete sv;
   c->server = nullptr;
+  return done;
 }
 
 }  // namespace brmppi_host
@@ -339,12 +399,12 @@ brmppi_status brmppi_vehicle_register(brmppi_ctx* c, uint32_t vid, const float* 
   if (!path_turns_ok(path, n_pts)) return fail(c, BRMPPI_EINVAL, "path headings of consecutive rows differ by more than pi/4");
   std::lock_guard<std::mutex> lk(sv->mu);
   Vehicle& V = sv->veh[vid];
-  if (V.queued > 0) return fail(c, BRMPPI_EBUSY, "vehicle has requests in flight");
+  if (V.queued > 0 || V.running) return fail(c, BRMPPI_EBUSY, "vehicle has requests in flight");
   cudaError_t e;
   cudaSetDevice(c->device);
-  if (!V.d_path && (e = cudaMalloc(&V.d_path, sizeof(float) * 3 * static_cast<size_t>(c->prm.max_path_pts))) != cudaSuccess)
+  if (!V.d_path && (e = dev_alloc(&V.d_path, sizeof(float) * 3 * static_cast<size_t>(c->prm.max_path_pts))) != cudaSuccess)
     return cuda_fail(c, e, "vehicle path");
-  if (!V.d_unom && (e = cudaMalloc(&V.d_unom, sizeof(float) * 3 * static_cast<size_t>(sv->H))) != cudaSuccess)
+  if (!V.d_unom && (e = dev_alloc(&V.d_unom, sizeof(float) * 3 * static_cast<size_t>(sv->H))) != cudaSuccess)
     return cuda_fail(c, e, "vehicle nominal");
   if ((e = cudaMemcpy(V.d_path, path, sizeof(float) * 3 * n_pts, cudaMemcpyHostToDevice)) != cudaSuccess)
     return cuda_fail(c, e, "vehicle path upload");
@@ -415,9 +475,13 @@ brmppi_status brmppi_poll(brmppi_ctx* c, uint64_t ticket, float* U_out, float* t
     if (traj_out) std::memcpy(traj_out, out + 3 * sv->H, sizeof(float) * 7 * (sv->H + 1));
   }
   if (latency_s) *latency_s = sl.t_done - sl.t_submit;
-  sl.state = kFree;
   sv->by_ticket.erase(it);
-  sv->free_slots.push_back(s);
+  if (sl.held) {
+    sl.polled = true;  // freed when its batch finishes
+  } else {
+    sl.state = kFree;
+    sv->free_slots.push_back(s);
+  }
   return static_cast<brmppi_status>(st);
 }
 
@@ -428,7 +492,7 @@ brmppi_status brmppi_vehicle_export(brmppi_ctx* c, uint32_t vid, float* U_nom, u
   std::lock_guard<std::mutex> lk(sv->mu);
   Vehicle& V = sv->veh[vid];
   if (!V.registered) return BRMPPI_EINVAL;
-  if (V.queued > 0) return BRMPPI_EBUSY;
+  if (V.queued > 0 || V.running) return BRMPPI_EBUSY;
   cudaSetDevice(c->device);
   if (U_nom && cudaMemcpy(U_nom, V.d_unom, sizeof(float) * 3 * sv->H, cudaMemcpyDeviceToHost) != cudaSuccess)
     return BRMPPI_ECUDA;
@@ -444,7 +508,7 @@ brmppi_status brmppi_vehicle_import(brmppi_ctx* c, uint32_t vid, const float* U_
   std::lock_guard<std::mutex> lk(sv->mu);
   Vehicle& V = sv->veh[vid];
   if (!V.registered) return BRMPPI_EINVAL;
-  if (V.queued > 0) return BRMPPI_EBUSY;
+  if (V.queued > 0 || V.running) return BRMPPI_EBUSY;
   cudaSetDevice(c->device);
   if (cudaMemcpy(V.d_unom, U_nom, sizeof(float) * 3 * sv->H, cudaMemcpyHostToDevice) != cudaSuccess)
     return BRMPPI_ECUDA;

@@ -59,7 +59,7 @@ def test_params_struct_layout_matches(lib):
     assert p.q_abuf == 10.0 and p.h_buf == 0.5
     # the library checks the same sizes at compile time
     assert p.n_discs == 1 and p.disc_trailer_mask == 0 and list(p.disc_off) == [0.0] * 8
-    assert ctypes.sizeof(pkg.brmppi_params) == 4 * 15 + 4 * 41 + 4 * 10
+    assert ctypes.sizeof(pkg.brmppi_params) == 4 * 16 + 4 * 41 + 4 * 10
     assert ctypes.sizeof(pkg.brmppi_instance) == 8 * 4 + 4 * 5 + 4 + 8 * 2 + 8 * 9
 
 
