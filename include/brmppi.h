@@ -380,6 +380,41 @@ brmppi_status brmppi_noise_blocks(uint64_t seed, uint64_t counter, int32_t n_sam
                                   int32_t n_blocks, uint32_t *words_dev, float *normals_dev,
                                   void *stream);
 
+/* ---- One solve partitioned by samples (several GPUs; SURVEY's only
+   exchange of the path: the softmin and update of Sec. II-B, Eq.
+   MPPI_update_rule, need every sample's cost).  The samples of a solve are
+   cut into tiles of the context's plain launch shape; rank r runs a
+   contiguous range of tiles (brmppi_solve_tiles), the ranks all-gather
+   their tile partials in rank order (tile order), and every rank merges
+   the complete set (brmppi_merge_tiles).  The merge is the one a single
+   launch ends with, over the same tiles in the same order: U*, the optimal
+   trajectory and the warm start are bit-identical to brmppi_solve_device_ex
+   on one GPU.  Every rank's context must have the same parameters. */
+
+/* The partition's layout for instance q: *n_tiles tiles of *tile_floats
+   floats each (the launch shape of the context's plain solves). */
+brmppi_status brmppi_tile_layout(brmppi_ctx *ctx, const brmppi_instance *q, int32_t *n_tiles,
+                                 int32_t *tile_floats);
+
+/* Roll out tiles [tile0, tile0 + n_tiles) of instance q (device buffers;
+   U_out, traj_out, U_next, status and u_safe_out are not used) and write
+   their partials to tiles_out (device, n_tiles * tile_floats floats,
+   16-byte aligned, tile tile0 first); J_out, J_lo_out, inputs_out and
+   states_out, if given (sized for all S samples), receive the range's
+   samples.  Enqueued on `stream`, no synchronisation.  An input error
+   (exponent, non-finite x0) is recorded on the context and reported by the
+   next brmppi_merge_tiles on it. */
+brmppi_status brmppi_solve_tiles(brmppi_ctx *ctx, const brmppi_instance *q, int32_t tile0,
+                                 int32_t n_tiles, float *tiles_out, void *stream);
+
+/* Merge all n_tiles tile partials of instance q (device, in tile order, as
+   brmppi_solve_tiles wrote them) into U_out and, if given, traj_out,
+   U_next and the status word (q's x0, U_nom, obstacles and path must be the
+   solve's).  EINVAL unless n_tiles is the instance's tile count.  One CTA,
+   enqueued on `stream`. */
+brmppi_status brmppi_merge_tiles(brmppi_ctx *ctx, const brmppi_instance *q, const float *tiles,
+                                 int32_t n_tiles, void *stream);
+
 /* Issue-rate microbenchmark of one SM pipe on the current device, for the
    roofline denominators of the solve (no paper counterpart): pipe 0 = FP32
    fused multiply-add, 1 = 32-bit integer multiply-add, 2 = the XU's

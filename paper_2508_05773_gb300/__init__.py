@@ -16,7 +16,9 @@ from ._native import (  # noqa: F401
     brmppi_instance,
     brmppi_last_error, brmppi_measure_pipe, brmppi_noise_blocks, brmppi_params, brmppi_poll, brmppi_server_stats, brmppi_server_stats_get,
     brmppi_solve, brmppi_solve_batch, brmppi_solve_device, brmppi_solve_device_ex,
-    brmppi_solve_device_noalloc, brmppi_submit, brmppi_transfer_bytes, brmppi_vehicle_export,
+    brmppi_merge_tiles, brmppi_solve_device_noalloc, brmppi_solve_tiles, brmppi_submit, brmppi_tile_layout,
+    brmppi_transfer_bytes, brmppi_vehicle_export,
     brmppi_vehicle_import, brmppi_vehicle_register, load, make_instances, params_from_dict,
 )
 from . import scenarios  # noqa: F401
+from .sharded import rank_tiles, solve_sharded  # noqa: F401

@@ -40,6 +40,7 @@ EXPORTS = (
     "brmppi_poll", "brmppi_vehicle_export", "brmppi_vehicle_import", "brmppi_server_stats_get",
     "brmppi_solve_device_noalloc", "brmppi_hitch_stabilize_device", "brmppi_get_batch_launch",
     "brmppi_noise_blocks", "brmppi_measure_pipe", "brmppi_inject_alloc_failure",
+    "brmppi_tile_layout", "brmppi_solve_tiles", "brmppi_merge_tiles",
 )
 
 
@@ -123,6 +124,13 @@ def load() -> ctypes.CDLL:
             "brmppi_create": (ctypes.c_int, [P, ctypes.c_int, ctypes.POINTER(_VP)]),
             "brmppi_destroy": (ctypes.c_int, [_VP]),
             "brmppi_inject_alloc_failure": (None, [ctypes.c_int32]),
+            "brmppi_tile_layout": (ctypes.c_int, [_VP, ctypes.POINTER(brmppi_instance),
+                                                  ctypes.POINTER(ctypes.c_int32),
+                                                  ctypes.POINTER(ctypes.c_int32)]),
+            "brmppi_solve_tiles": (ctypes.c_int, [_VP, ctypes.POINTER(brmppi_instance), ctypes.c_int32,
+                                                  ctypes.c_int32, _VP, _VP]),
+            "brmppi_merge_tiles": (ctypes.c_int, [_VP, ctypes.POINTER(brmppi_instance), _VP,
+                                                  ctypes.c_int32, _VP]),
             "brmppi_last_error": (ctypes.c_char_p, [_VP]),
             "brmppi_solve": (ctypes.c_int, [_VP, _D, _F, _F, ctypes.c_int32, _F, ctypes.c_int32,
                                             ctypes.c_float, ctypes.c_uint64, ctypes.c_uint64, _F, _F,
@@ -349,7 +357,7 @@ def make_instances(insts) -> "ctypes.Array":
         q.S = int(d["S"])
         q.seed = int(d["seed"]) & (2**64 - 1)
         q.counter = int(d.get("counter", 0)) & (2**64 - 1)
-        q.U_out = d["U_out"].data_ptr()
+        q.U_out = d["U_out"].data_ptr() if d.get("U_out") is not None else None
         for key in ("traj_out", "J_out", "U_next", "status", "states_out", "u_safe_out", "inputs_out",
                     "J_lo_out"):
             t = d.get(key)
@@ -362,6 +370,32 @@ def brmppi_solve_device_ex(ctx, inst, stream=None) -> int:
     ``states_out`` of shape (S, H+1, 7))."""
     arr = make_instances([inst])
     return load().brmppi_solve_device_ex(ctx, arr, ctypes.c_void_p(_stream_handle(stream)))
+
+
+def brmppi_tile_layout(ctx, inst):
+    """(n_tiles, tile_floats) of a sample-partitioned solve of `inst`."""
+    arr = make_instances([inst])
+    nt, tf = ctypes.c_int32(), ctypes.c_int32()
+    st = load().brmppi_tile_layout(ctx, arr, ctypes.byref(nt), ctypes.byref(tf))
+    if st != BRMPPI_OK:
+        raise BrmppiError(st, brmppi_last_error(ctx))
+    return nt.value, tf.value
+
+
+def brmppi_solve_tiles(ctx, inst, tile0: int, n_tiles: int, tiles_out, stream=None) -> int:
+    """Tiles [tile0, tile0 + n_tiles) of `inst` (dict of torch CUDA tensors,
+    U_out optional) into tiles_out (float32, n_tiles x tile_floats)."""
+    arr = make_instances([inst])
+    return load().brmppi_solve_tiles(ctx, arr, int(tile0), int(n_tiles), _dptr(tiles_out),
+                                     ctypes.c_void_p(_stream_handle(stream)))
+
+
+def brmppi_merge_tiles(ctx, inst, tiles, stream=None) -> int:
+    """Merge every tile of `inst` (tiles: float32, n_tiles x tile_floats, in
+    tile order) into its U_out (and traj_out, U_next, status if given)."""
+    arr = make_instances([inst])
+    n = tiles.shape[0]
+    return load().brmppi_merge_tiles(ctx, arr, _dptr(tiles), int(n), ctypes.c_void_p(_stream_handle(stream)))
 
 
 def brmppi_solve_batch(ctx, insts, stream=None) -> int:

@@ -382,7 +382,8 @@ void single_launch_options(brmppi::LaunchDesc& L, const Shape& sh, const brmppi:
   brmppi::SmemCaps caps = L.caps;
   caps.uh_per_team = 3 * H;
   // those variants merge the instance's tile partials in shared memory
-  caps.merge = L.single.tiles * L.single.part_stride;
+  // (unless the launch only produces its share of the tiles)
+  caps.merge = L.single.no_merge ? 0 : L.single.tiles * L.single.part_stride;
   if (smem_bytes(caps, spb) > smem_limit) return;
   L.caps = caps;
   L.rows = rows;
@@ -400,7 +401,8 @@ brmppi_status enqueue_plain_sized(brmppi_ctx* c, const Shape& sh, int S, int H, 
                                   int32_t n_pts, float ds, uint64_t seed, uint64_t counter, float* U_out,
                                   float* traj_out, float* J_out, float* U_next, int32_t* status, float* states_out,
                                   float* u_safe, cudaStream_t stream, float* inputs_out = nullptr,
-                                  float* J_lo_out = nullptr) {
+                                  float* J_lo_out = nullptr, float* tiles_out = nullptr, int tile0 = 0,
+                                  int n_tiles = 0) {
   const int spb = sh.threads / sh.tps;
   brmppi::LaunchDesc L{};
   L.single = make_inst(x0, U_nom, obs, n_obs, path, n_pts, ds, S, H, seed, counter, U_out, traj_out, J_out,
@@ -409,15 +411,21 @@ brmppi_status enqueue_plain_sized(brmppi_ctx* c, const Shape& sh, int S, int H, 
   L.single.u_safe = u_safe;
   L.single.inputs_out = inputs_out;
   L.single.J_lo_out = J_lo_out;
+  if (tiles_out) {
+    // a share of the instance's tiles: partials to the caller, no merge
+    L.single.part = tiles_out;
+    L.single.tile_base = tile0;
+    L.single.no_merge = 1;
+  }
   L.caps = make_caps(n_obs, rows_of(c->prm, n_obs), n_pts, H, sh.tps);
   L.uh = c->d_uh;
   L.uh_stride = 3 * H * spb;
   const brmppi::KConst k = make_kconst(c->prm);
   single_launch_options(L, sh, k, rows_of(c->prm, n_obs), H, c->smem_limit);
   const size_t smem = smem_bytes(L.caps, spb);
-  const int tiles = L.single.tiles;
+  const int tiles = tiles_out ? n_tiles : L.single.tiles;  // CTAs of the launch
   if (smem > c->smem_limit) return fail(c, BRMPPI_EINVAL, "shared memory need exceeds the device limit");
-  if (static_cast<size_t>(tiles) > c->part_tiles ||
+  if ((!tiles_out && static_cast<size_t>(tiles) > c->part_tiles) ||
       static_cast<size_t>(tiles) * static_cast<size_t>(L.uh_stride) > c->uh_floats)
     return fail(c, BRMPPI_EINVAL, "launch shape exceeds the context's scratch");
   cudaError_t e = brmppi::launch_solve(sh.tps, sh.bpt, tiles, sh.threads, smem, stream, k, L, L.single.P);
@@ -867,6 +875,77 @@ brmppi_status brmppi_solve_device_ex(brmppi_ctx* c, const brmppi_instance* q, vo
                              q->seed, q->counter, q->U_out, q->traj_out, q->J_out, q->U_next, q->status,
                              q->states_out, q->u_safe_out, static_cast<cudaStream_t>(stream), q->inputs_out,
                              q->J_lo_out);
+}
+
+namespace {
+
+// Validation and launch shape shared by the tile-partition entry points.
+brmppi_status tile_plan(brmppi_ctx* c, const brmppi_instance* q, bool need_u_out, Shape* sh, int* n_tiles) {
+  if (!q) return fail(c, BRMPPI_EINVAL, "NULL instance");
+  if (!q->x0 || !q->U_nom || !q->path || (need_u_out && !q->U_out) || (q->n_obs > 0 && !q->obs))
+    return fail(c, BRMPPI_EINVAL, "NULL buffer");
+  if (q->S < 1 || q->S > c->prm.S || q->H < 1 || q->H > c->prm.H)
+    return fail(c, BRMPPI_EINVAL, "S or H beyond the context's capacity");
+  brmppi_status st = check_sizes(c, q->n_obs, q->n_pts, q->ds);
+  if (st != BRMPPI_OK) return st;
+  if (!plain_shape(c, q->n_obs, q->n_pts, sh)) return fail(c, BRMPPI_EINVAL, "no launch shape for this size");
+  const int spb = sh->threads / sh->tps;
+  *n_tiles = (q->S + spb - 1) / spb;
+  return BRMPPI_OK;
+}
+
+}  // namespace
+
+brmppi_status brmppi_tile_layout(brmppi_ctx* c, const brmppi_instance* q, int32_t* n_tiles, int32_t* tile_floats) {
+  if (!c) return BRMPPI_EINVAL;
+  c->err.clear();
+  Shape sh;
+  int nt = 0;
+  brmppi_status st = tile_plan(c, q, false, &sh, &nt);
+  if (st != BRMPPI_OK) return st;
+  if (n_tiles) *n_tiles = nt;
+  if (tile_floats) *tile_floats = part_stride_for(q->H);
+  return BRMPPI_OK;
+}
+
+brmppi_status brmppi_solve_tiles(brmppi_ctx* c, const brmppi_instance* q, int32_t tile0, int32_t n_tiles,
+                                 float* tiles_out, void* stream) {
+  if (!c) return BRMPPI_EINVAL;
+  c->err.clear();
+  Shape sh;
+  int nt = 0;
+  brmppi_status st = tile_plan(c, q, false, &sh, &nt);
+  if (st != BRMPPI_OK) return st;
+  if (!tiles_out) return fail(c, BRMPPI_EINVAL, "NULL tiles_out");
+  if ((reinterpret_cast<uintptr_t>(tiles_out) & 15) != 0) return fail(c, BRMPPI_EINVAL, "tiles_out not 16-byte aligned");
+  if (tile0 < 0 || n_tiles < 1 || tile0 + n_tiles > nt)
+    return fail(c, BRMPPI_EINVAL, "tile range out of [0, " + std::to_string(nt) + ")");
+  return enqueue_plain_sized(c, sh, q->S, q->H, q->x0, q->U_nom, q->obs, q->n_obs, q->path, q->n_pts, q->ds,
+                             q->seed, q->counter, q->U_out, nullptr, q->J_out, nullptr, nullptr, q->states_out,
+                             nullptr, static_cast<cudaStream_t>(stream), q->inputs_out, q->J_lo_out, tiles_out, tile0,
+                             n_tiles);
+}
+
+brmppi_status brmppi_merge_tiles(brmppi_ctx* c, const brmppi_instance* q, const float* tiles, int32_t n_tiles,
+                                 void* stream) {
+  if (!c) return BRMPPI_EINVAL;
+  c->err.clear();
+  Shape sh;
+  int nt = 0;
+  brmppi_status st = tile_plan(c, q, true, &sh, &nt);
+  if (st != BRMPPI_OK) return st;
+  if (!tiles) return fail(c, BRMPPI_EINVAL, "NULL tiles");
+  if (n_tiles != nt) return fail(c, BRMPPI_EINVAL, "the merge needs all " + std::to_string(nt) + " tiles of the instance");
+  const int spb = sh.threads / sh.tps;
+  brmppi::Inst in = make_inst(q->x0, q->U_nom, q->obs, q->n_obs, q->path, q->n_pts, q->ds, q->S, q->H, q->seed,
+                              q->counter, q->U_out, q->traj_out, q->J_out, q->U_next, q->status,
+                              const_cast<float*>(tiles), c->d_sync, spb, c->prm.n_discs);
+  const brmppi::SmemCaps caps = make_caps(q->n_obs, rows_of(c->prm, q->n_obs), q->n_pts, q->H, sh.tps);
+  const size_t smem = smem_bytes(caps, 1);
+  if (smem > c->smem_limit) return fail(c, BRMPPI_EINVAL, "shared memory need exceeds the device limit");
+  const cudaError_t e = brmppi::launch_merge_tiles(make_kconst(c->prm), in, caps, smem, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(c, e, "merge launch");
+  return BRMPPI_OK;
 }
 
 brmppi_status brmppi_solve_batch(brmppi_ctx* c, const brmppi_instance* inst, int32_t n, void* stream) {

@@ -98,6 +98,22 @@ cudaError_t launch_noise_blocks(uint64_t seed, uint64_t counter, int n_samples, 
   return cudaGetLastError();
 }
 
+cudaError_t launch_merge_tiles(const KConst& k, const Inst& in, const SmemCaps& caps, size_t smem,
+                               cudaStream_t stream) {
+  if (needs_ext(k)) {
+    cudaError_t e = cudaFuncSetAttribute(reinterpret_cast<const void*>(&merge_tiles_kernel<true>),
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+    merge_tiles_kernel<true><<<1, 256, smem, stream>>>(k, in, caps);
+  } else {
+    cudaError_t e = cudaFuncSetAttribute(reinterpret_cast<const void*>(&merge_tiles_kernel<false>),
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+    merge_tiles_kernel<false><<<1, 256, smem, stream>>>(k, in, caps);
+  }
+  return cudaGetLastError();
+}
+
 cudaError_t launch_stabilize_table(const KConst& k, const Inst* d_table, int n, cudaStream_t stream) {
   if (n <= 0) return cudaSuccess;
   stabilize_table_kernel<<<(n + 127) / 128, 128, 0, stream>>>(k, d_table, n);
@@ -164,7 +180,7 @@ cudaError_t launch_solve(int tps, int bpt, int blocks, int threads, size_t smem,
   if (L.rows > 0) {
     // the exact-rows variants merge in shared memory: the launch must have
     // reserved the room for the instance's partials
-    v = (L.work || L.caps.merge < L.single.tiles * L.single.part_stride ||
+    v = (L.work || (!L.single.no_merge && L.caps.merge < L.single.tiles * L.single.part_stride) ||
          L.caps.uh_per_team < 3 * L.single.H)
             ? nullptr
             : find(tps, 1, false, L.rows);

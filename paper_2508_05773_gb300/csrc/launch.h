@@ -67,6 +67,11 @@ cudaError_t launch_stabilize_table(const KConst& k, const Inst* d_table, int n, 
 cudaError_t launch_noise_blocks(uint64_t seed, uint64_t counter, int n_samples, int H, int n_blocks, uint32_t* words,
                                 float* normals, cudaStream_t stream);
 
+// Enqueue the one-CTA merge of an instance's gathered tile partials
+// (in.part, in.tiles; caps: the instance's tables; smem: their bytes).
+cudaError_t launch_merge_tiles(const KConst& k, const Inst& in, const SmemCaps& caps, size_t smem,
+                               cudaStream_t stream);
+
 // Enqueue one launch of the solve kernel.
 cudaError_t launch_solve(int tps, int bpt, int blocks, int threads, size_t smem, cudaStream_t stream,
                          const KConst& k, const LaunchDesc& L, int P);

@@ -110,6 +110,9 @@ struct Inst {
   double inv_ds_d;   // 1 / ds in FP64 (path cell of psi0)
   uint32_t key0, key1, ctr;
   int P;             // Philox blocks per step, ceil((4 + n_obs) / 4)
+  int tile_base;     // single launches: tile index of the first CTA (a rank's share of the tiles)
+  int no_merge;      // 1: write the tile partials (at part + (tile - tile_base) * part_stride) and
+                     // stop; the instance's tiles are merged by merge_tiles_kernel
 };
 
 // Shared-memory capacities of a launch (floats).
@@ -468,7 +471,7 @@ __device__ void run_tile(const KConst& k, const Inst& in, int tile, float* uh, c
     prefetch_l2(in.traj_out);
     prefetch_l2(in.U_next);
     prefetch_l2(in.status);
-    prefetch_l2(in.part + static_cast<size_t>(tile) * in.part_stride);
+    prefetch_l2(in.part + static_cast<size_t>(tile - in.tile_base) * in.part_stride);
     if (in.J_out) prefetch_l2(in.J_out + static_cast<size_t>(tile) * spb);
   }
   // --- frame and staging (tables in shared memory, relative coordinates).
@@ -1141,7 +1144,7 @@ __device__ void run_tile(const KConst& k, const Inst& in, int tile, float* uh, c
     S.w[t] = w;
   }
   __syncthreads();
-  float* part = in.part + static_cast<size_t>(tile) * in.part_stride;
+  float* part = in.part + static_cast<size_t>(tile - in.tile_base) * in.part_stride;
   const int nrows = 3 * H + 1;  // row 3H: the weight sum
   // one thread per row: its spb weighted inputs in sample order, four
   // chains (samples t mod 4) combined in a fixed order; the row's loads are
@@ -1632,7 +1635,7 @@ __global__ void __launch_bounds__(512) solve_kernel(const KConst k, const Launch
       tile = w.y;
     } else {
       if (iter > 0) break;
-      tile = blockIdx.x;
+      tile = L.single.tile_base + static_cast<int>(blockIdx.x);
     }
     Inst in;
     if (L.work) in = L.inst[inst_id];
@@ -1643,6 +1646,7 @@ __global__ void __launch_bounds__(512) solve_kernel(const KConst k, const Launch
     __threadfence();
     __syncthreads();
     if constexpr (ROWS == 0) discard_history(uh, 3 * in.H * (compute_threads<TPS>(L.noise_warps) / TPS));
+    if (in.no_merge) continue;  // a share of the tiles: merged elsewhere (single launches only)
     if (threadIdx.x == 0) sh.last = (atomicAdd(in.sync, 1u) == static_cast<unsigned>(in.tiles - 1));
     __syncthreads();
     if (sh.last) {
@@ -1662,6 +1666,37 @@ __global__ void __launch_bounds__(512) solve_kernel(const KConst k, const Launch
       }
     }
   }
+}
+
+// ------------------------------------------------ merge of gathered tiles
+// One CTA merges an instance's complete set of tile partials, produced by
+// no-merge launches (one per rank of a sample-partitioned solve) and
+// gathered in tile order: the same frame, tables and merge as the CTA that
+// finishes a single launch's last tile, so the results are the same bits.
+template <bool EXT>
+__global__ void __launch_bounds__(256) merge_tiles_kernel(const KConst k, const Inst in, const SmemCaps caps) {
+  extern __shared__ float dyn[];
+  __shared__ Shared sh;
+  const Smem S(dyn, caps, 1);
+  for (int j = threadIdx.x; j < 3 * in.n_pts; j += blockDim.x) cp_async4(S.path + j, in.path + j);
+  for (int j = threadIdx.x; j < 3 * in.H; j += blockDim.x) cp_async4(S.unom + j, in.U_nom + j);
+  if (threadIdx.x < 32) make_frame_warp(in.x0, in.inv_ds_d, in.sync + 1, sh.fr, EXT && k.jerk);
+  const bool obs8 = EXT && k.obs8;
+  for (int o = threadIdx.x; o < in.n_obs; o += blockDim.x) {
+    const float e = in.obs[(obs8 ? 8 : 6) * o + 5];
+    if (e != 2.0f && !(obs8 && e == 4.0f)) atomicOr(in.sync + 1, ERR_EXPONENT);
+  }
+  cp_async_wait_all();
+  __syncthreads();
+  const Frame& fr = sh.fr;
+  for (int j = threadIdx.x; j < in.n_pts; j += blockDim.x) {  // the path in the frame, as the tiles stage it
+    float* d = S.path + 3 * j;
+    d[0] = (d[0] - fr.ox_h) - fr.ox_l;
+    d[1] = (d[1] - fr.oy_h) - fr.oy_l;
+    d[2] = (d[2] - fr.oth_h) - fr.oth_l;
+  }
+  __syncthreads();
+  merge_instance<false>(k, in, S, sh);
 }
 
 }  // namespace brmppi
