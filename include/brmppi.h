@@ -317,7 +317,10 @@ brmppi_status brmppi_solve_device_noalloc(const brmppi_params *p, const double *
    sequence (shifted in place on the device after each solve) and its noise
    counter (+1 per solve) resident; requests of one vehicle run in
    submission order.  Results do not depend on what else is in a batch: the
-   serving launch shape (one lane per sample, 128-thread blocks) is fixed. */
+   serving launch shape is fixed at create (params.batch_threads_per_sample
+   and batch_block_threads when set, else one lane per sample in 128-thread
+   blocks), and a batch of one on the same context (batch shape not changed
+   by brmppi_autotune_batch) reproduces a served solve bit for bit. */
 
 /* Register (or re-register) a vehicle: its reference path (host, n_pts*3),
    initial nominal sequence (host H*3, NULL = zeros) and noise seed; its

@@ -299,13 +299,20 @@ brmppi_status server_create(brmppi_ctx* c) {
   sv->max_obs = p.max_obstacles;
   sv->max_batch = p.serve_max_batch > 0 ? p.serve_max_batch : 64;
   sv->wait_ms = wait_limit_ms(p);
-  if (brmppi::needs_ext(make_kconst(p))) {
-    // rows with a steer-rate column: at most two Philox blocks per lane
-    sv->shape.tps = ext_team_width(philox_blocks(rows_of(p, p.max_obstacles)));
-    sv->shape.threads = std::max(128, kMinBatchSpb * sv->shape.tps);
-  } else {
-    sv->shape.tps = 1;
-    sv->shape.threads = 128;
+  // the launch shape of every serving batch, fixed here so that a solve's
+  // bits do not depend on what else is in its batch: the context's batch
+  // shape parameters when given, else one lane per sample (teams just wide
+  // enough for two Philox blocks a lane when rows carry a steer-rate column)
+  // in 128-thread blocks
+  const int P_cap = philox_blocks(rows_of(p, p.max_obstacles));
+  sv->shape.tps = p.batch_threads_per_sample != 0
+                      ? p.batch_threads_per_sample
+                      : (brmppi::needs_ext(make_kconst(p)) ? ext_team_width(P_cap) : 1);
+  sv->shape.threads =
+      p.batch_block_threads != 0 ? p.batch_block_threads : std::max(128, kMinBatchSpb * sv->shape.tps);
+  if (!pick_bpt(sv->shape.tps, P_cap, &sv->shape.bpt) || sv->shape.threads / sv->shape.tps < kMinBatchSpb) {
+    c->server = sv;
+    return fail(c, BRMPPI_EINVAL, "no serving launch shape for the batch shape parameters");
   }
   const int n_lanes = p.serve_lanes > 0 ? p.serve_lanes : 2;
   sv->in_stride = align_up(64 + sizeof(float) * obs_floats(p) * static_cast<size_t>(p.max_obstacles), 256);
