@@ -744,34 +744,44 @@ __device__ void run_tile(const KConst& k, const Inst& in, int tile, float* uh, c
     stage_cost(static_cast<float>(tau) * k.Ts, c1, s1, c1 * cp + s1 * sp, s1 * cp - c1 * sp, tau > 0);
 
     // explicit Euler, the state-only part (right-hand sides at the current
-    // state), and the next state's theta1 / phi trigonometry
+    // state), and the next state's theta1 / phi trigonometry.  Latency
+    // shapes (teams) form it before the projection, off its dependency
+    // chain; one-lane shapes (issue-bound, many warps) after it, so that the
+    // current and next values need not be live at once (no register copies
+    // at the end of the step)
     const float Tv = k.Ts * vv;
-    float px_n = px, pxl_n = pxl, py_n = py, pyl_n = pyl;
-    acc2(px_n, pxl_n, Tv * c1);
-    acc2(py_n, pyl_n, Tv * s1);
-    const float t1_n = t1 + k.Ts * th1dot;
-    const float t2_n = t2 + Tv * k.inv_l2 * (sp - k.k_hitch * cp * tn);
-    float c1_n, s1_n, sp_n, cp_n;
-    if constexpr (TPS > 1) {
-      // even lanes take theta1, odd lanes phi, and each pair trades the
-      // results: one sin / cos sequence in the warp's stream instead of two
-      const bool odd = lt & 1;
-      float sa, ca;
-      state_sincos(odd ? t1_n - t2_n : t1_n, &sa, &ca);
-      const float sb = __shfl_xor_sync(0xffffffffu, sa, 1);
-      const float cb = __shfl_xor_sync(0xffffffffu, ca, 1);
-      const float sr = odd ? sb : sa, cr = odd ? cb : ca;
-      sp_n = odd ? sa : sb;
-      cp_n = odd ? ca : cb;
-      c1_n = c0 * cr - s0 * sr;
-      s1_n = s0 * cr + c0 * sr;
-    } else {
-      float sr, cr;
-      state_sincos(t1_n, &sr, &cr);
-      c1_n = c0 * cr - s0 * sr;
-      s1_n = s0 * cr + c0 * sr;
-      state_sincos(t1_n - t2_n, &sp_n, &cp_n);
-    }
+    float px_n, pxl_n, py_n, pyl_n, t1_n, t2_n, c1_n, s1_n, sp_n, cp_n;
+    auto state_part = [&]() {
+      px_n = px;
+      pxl_n = pxl;
+      py_n = py;
+      pyl_n = pyl;
+      acc2(px_n, pxl_n, Tv * c1);
+      acc2(py_n, pyl_n, Tv * s1);
+      t1_n = t1 + k.Ts * th1dot;
+      t2_n = t2 + Tv * k.inv_l2 * (sp - k.k_hitch * cp * tn);
+      if constexpr (TPS > 1) {
+        // even lanes take theta1, odd lanes phi, and each pair trades the
+        // results: one sin / cos sequence in the warp's stream instead of two
+        const bool odd = lt & 1;
+        float sa, ca;
+        state_sincos(odd ? t1_n - t2_n : t1_n, &sa, &ca);
+        const float sb = __shfl_xor_sync(0xffffffffu, sa, 1);
+        const float cb = __shfl_xor_sync(0xffffffffu, ca, 1);
+        const float sr = odd ? sb : sa, cr = odd ? cb : ca;
+        sp_n = odd ? sa : sb;
+        cp_n = odd ? ca : cb;
+        c1_n = c0 * cr - s0 * sr;
+        s1_n = s0 * cr + c0 * sr;
+      } else {
+        float sr, cr;
+        state_sincos(t1_n, &sr, &cr);
+        c1_n = c0 * cr - s0 * sr;
+        s1_n = s0 * cr + c0 * sr;
+        state_sincos(t1_n - t2_n, &sp_n, &cp_n);
+      }
+    };
+    if constexpr (TPS > 1) state_part();
 
     float na, nw, nn;
     if constexpr (TPS == 1) {
@@ -830,14 +840,8 @@ __device__ void run_tile(const KConst& k, const Inst& in, int tile, float* uh, c
       // `live` = 0 turns a padding slot into a no-op without branching.
       float ca[OBS_SLOTS], cc[OBS_SLOTS];
       float cw[EXT ? OBS_SLOTS : 1];  // steer-rate column (footprint discs off the rear axle)
-      if constexpr (ROWS == 0) {
-#pragma unroll
-        for (int q = 0; q < OBS_SLOTS; ++q) ca[q] = cc[q] = 0.f;
-        if constexpr (EXT) {
-#pragma unroll
-          for (int q = 0; q < OBS_SLOTS; ++q) cw[q] = 0.f;
-        }
-      }
+      // every slot that the alpha update reads is written below (padding
+      // rows as zeros)
       const float tnow = static_cast<float>(tau) * k.Ts;
       float cbuf = 0.f;  // buffer cost of this lane's rows
       // heading rates and accelerations of the bodies (footprint discs):
@@ -979,13 +983,6 @@ __device__ void run_tile(const KConst& k, const Inst& in, int tile, float* uh, c
               if constexpr (EXT) cw[j] = 0.f;
               if (j < n_rows) obstacle_row(j, nb[m], j, 1.f);
             }
-          } else {
-#pragma unroll
-            for (int m = 0; m < 4; ++m) {
-              ca[4 * (b8 - 1) + m] = 0.f;
-              cc[4 * (b8 - 1) + m] = 0.f;
-              if constexpr (EXT) cw[4 * (b8 - 1) + m] = 0.f;
-            }
           }
         }
       } else if constexpr (ROWS > 0) {
@@ -1027,13 +1024,25 @@ __device__ void run_tile(const KConst& k, const Inst& in, int tile, float* uh, c
       zw = q1 - yw;
       zn = pu2 * k.inv_m_u2;
       alpha_h += cc_h + ca_h * ya + cw_h * yw;
-#pragma unroll
-      for (int slot = 0; slot < OBS_SLOTS; ++slot) {
+      auto alpha_update = [&](int slot) {
         if constexpr (EXT) {
           alpha[slot] += cc[slot] + ca[slot] * ya + cw[slot] * yw;
         } else {
           alpha[slot] += cc[slot] + ca[slot] * ya;
         }
+      };
+      if constexpr (TPS == 1) {
+        // the blocks this instance draws (a uniform branch per block): rows
+        // of the blocks beyond it are never read
+#pragma unroll
+        for (int b8 = 1; b8 < BPT; ++b8)
+          if (b8 < in.P) {
+#pragma unroll
+            for (int m = 0; m < 4; ++m) alpha_update(4 * (b8 - 1) + m);
+          }
+      } else {
+#pragma unroll
+        for (int slot = 0; slot < OBS_SLOTS; ++slot) alpha_update(slot);
       }
     } else {
       za = zd0;
@@ -1043,9 +1052,10 @@ __device__ void run_tile(const KConst& k, const Inst& in, int tile, float* uh, c
     ua = clampf(za, k.zlo0, k.zhi0);
     uw = clampf(zw, k.zlo1, k.zhi1);
     un = clampf(zn, k.zlo2, k.zhi2);
+    if constexpr (TPS == 1) state_part();
 
     // explicit Euler, the input-driven part; the state-only part was formed
-    // above from the same right-hand sides
+    // from the same right-hand sides
     px = px_n;
     pxl = pxl_n;
     py = py_n;
