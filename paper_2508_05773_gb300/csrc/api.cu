@@ -176,6 +176,7 @@ brmppi::KConst make_kconst(const brmppi_params& q) {
   k.abuf = (q.flags & BRMPPI_FLAG_ALPHA_BUFFER) ? 1 : 0;
   k.Ts = q.Ts;
   k.hTs2 = 0.5f * q.Ts * q.Ts;
+  k.Ts2 = q.Ts * q.Ts;
   k.inv_lambda = 1.0f / q.lambda;
   k.inv_l1 = 1.0f / q.l1;
   k.inv_l2 = 1.0f / q.l2;

@@ -68,7 +68,7 @@ namespace brmppi {
 struct KConst {
   int proj;
   int coll, obs8, abuf;  // collision cost, moving / e = 4 obstacle rows, buffer cost
-  float Ts, hTs2, inv_lambda;
+  float Ts, hTs2, Ts2, inv_lambda;  // Ts, Ts^2 / 2, Ts^2
   float inv_l1, inv_l2, k_hitch, dtheta_max, kappa, r_inflate;
   float Qc, Ql, Qth, R0, R1, R2, mu, nu_bar;
   float zlo0, zlo1, zlo2, zhi0, zhi1, zhi2, sig0, sig1, sig2;
@@ -860,6 +860,8 @@ __device__ void run_tile(const KConst& k, const Inst& in, int tile, float* uh, c
         a2w = -vv * k.k_hitch * cp * sec2 * k.inv_l2;
         a20 = vv * k.inv_l2 * (cp + k.k_hitch * tn * sp) * (th1dot - th2dot);
       }
+      // per-step factors of the parked-ellipse rows
+      const float cg_row = -2.f * k.Ts * vv, vth_row = vv * th1dot, vv2_row = vv * vv;
       auto obstacle_row = [&](int j, float n_alpha, int slot, float live) {
         float h, Aa, Aw = 0.f, brest;
         if constexpr (!EXT) {
@@ -869,14 +871,20 @@ __device__ void run_tile(const KConst& k, const Inst& in, int tile, float* uh, c
           const float co = o0.z, so = o0.w, iax = o1.x, iay = o1.y;
           const float xp = co * dx + so * dy;
           const float yp = co * dy - so * dx;
-          h = xp * xp * iax + yp * yp * iay - 1.f;
-          const float hx = 2.f * xp * iax, hy = 2.f * yp * iay;
+          // with (ax, ay) = grad h / 2 and the heading e1' = (dirx, diry):
+          // h = xp ax + yp ay - 1; hdot = 2 v g, g = grad h . e1' / 2;
+          // hddot (input part aside) = 2 v th1dot turn + 2 v^2 curv, turn =
+          // grad h . n1' / 2, curv = e1'^T (Hess h / 2) e1'; so the row's
+          // a-column Ts^2/2 dh/da = Ts^2 g and its rest
+          // -(Ts hdot + Ts^2/2 hddot0) = -2 Ts v g - Ts^2 (v th1dot turn + v^2 curv)
+          const float ax = xp * iax, ay = yp * iay;
+          h = fmaf(ax, xp, fmaf(ay, yp, -1.f));
           const float dirx = co * c1 + so * s1, diry = co * s1 - so * c1;
-          const float gda = hx * dirx + hy * diry;  // dh along the heading
-          const float hdd0 = vv * th1dot * (hy * dirx - hx * diry) +
-                             2.f * vv * vv * (iax * dirx * dirx + iay * diry * diry);
-          Aa = k.hTs2 * gda;
-          brest = -k.Ts * vv * gda - k.hTs2 * hdd0;
+          const float g = fmaf(ax, dirx, ay * diry);
+          const float turn = fmaf(ay, dirx, -(ax * diry));
+          const float curv = fmaf(iax * dirx, dirx, iay * diry * diry);
+          Aa = k.Ts2 * g;
+          brest = fmaf(cg_row, g, -k.Ts2 * fmaf(vth_row, turn, vv2_row * curv));
         } else {
           // row j: obstacle o seen from footprint disc m (obstacle-major)
           const int o = (k.nd == 1) ? j : __float2int_rz((static_cast<float>(j) + 0.5f) * k.inv_nd);
@@ -945,7 +953,8 @@ __device__ void run_tile(const KConst& k, const Inst& in, int tile, float* uh, c
         const float zda = clampf(k.sigma_alpha * n_alpha, k.ua_lo, k.ua_hi);
         const float pam = k.w_am * zda + k.pc_am;  // p_alpha / m_alpha
         const float b = -alpha[slot] * h + brest;
-        const float r = Aa * q0 + Aw * q1 + ht * pam - b;
+        float r = fmaf(Aa, q0, fmaf(ht, pam, -b));
+        if constexpr (EXT) r = fmaf(Aw, q1, r);
         const float iht = __fdividef(1.f, ht);  // MUFU reciprocal (~1 ulp)
         const float u = live * (Aa * iht);
         const float rho = r * iht;
