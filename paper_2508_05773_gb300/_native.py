@@ -132,9 +132,12 @@ def load() -> ctypes.CDLL:
             "brmppi_merge_tiles": (ctypes.c_int, [_VP, ctypes.POINTER(brmppi_instance), _VP,
                                                   ctypes.c_int32, _VP]),
             "brmppi_last_error": (ctypes.c_char_p, [_VP]),
-            "brmppi_solve": (ctypes.c_int, [_VP, _D, _F, _F, ctypes.c_int32, _F, ctypes.c_int32,
-                                            ctypes.c_float, ctypes.c_uint64, ctypes.c_uint64, _F, _F,
-                                            _F]),
+            # pointers as plain addresses: the host entry point is the
+            # closed loop's per-tick call, and typed pointer objects cost
+            # microseconds each
+            "brmppi_solve": (ctypes.c_int, [_VP, _VP, _VP, _VP, ctypes.c_int32, _VP, ctypes.c_int32,
+                                            ctypes.c_float, ctypes.c_uint64, ctypes.c_uint64, _VP, _VP,
+                                            _VP]),
             "brmppi_solve_device": (ctypes.c_int, [_VP, _VP, _VP, _VP, ctypes.c_int32, _VP,
                                                    ctypes.c_int32, ctypes.c_float, ctypes.c_uint64,
                                                    ctypes.c_uint64, _VP, _VP, _VP, _VP, _VP, _VP]),
@@ -282,24 +285,23 @@ def _f32(a, n=None):
 def brmppi_solve(ctx, x0, U_nom, obs, path, ds, seed, counter, H, S=None, want_traj=True,
                  want_J=False):
     """Host-buffer solve. Returns (status, U[H,3], traj[H+1,7] or None, J[S] or None)."""
-    lib = load()
+    lib = _lib or load()
     x0 = np.ascontiguousarray(x0, dtype=np.float64)
     if x0.size not in (7, 8):
         raise ValueError("x0 must have 7 entries (8 under the jerk-input model)")
     U_nom = _f32(U_nom, 3 * H)
     n_obs = _rows(None if obs is None else np.asarray(obs))
-    obs = _f32(obs).reshape(-1) if obs is not None else np.zeros(0, np.float32)
-    path = _f32(path).reshape(-1)
+    obs = _f32(obs) if n_obs else None
+    path = _f32(path)
     n_pts = path.size // 3
     U = np.zeros((H, 3), dtype=np.float32)
     traj = np.zeros((H + 1, 7), dtype=np.float32) if want_traj else None
     J = np.zeros(S, dtype=np.float32) if want_J else None
-    st = lib.brmppi_solve(ctx, x0.ctypes.data_as(_D), U_nom.ctypes.data_as(_F),
-                          obs.ctypes.data_as(_F) if n_obs else None, n_obs,
-                          path.ctypes.data_as(_F), n_pts, float(ds), int(seed) & (2**64 - 1),
-                          int(counter) & (2**64 - 1), U.ctypes.data_as(_F),
-                          traj.ctypes.data_as(_F) if traj is not None else None,
-                          J.ctypes.data_as(_F) if J is not None else None)
+    st = lib.brmppi_solve(ctx, x0.ctypes.data, U_nom.ctypes.data, obs.ctypes.data if n_obs else None, n_obs,
+                          path.ctypes.data, n_pts, float(ds), int(seed) & (2**64 - 1),
+                          int(counter) & (2**64 - 1), U.ctypes.data,
+                          traj.ctypes.data if traj is not None else None,
+                          J.ctypes.data if J is not None else None)
     return st, U, traj, J
 
 
@@ -600,10 +602,49 @@ class Solver:
         except Exception:
             pass
 
+    def _host_buffers(self):
+        """Host staging owned by the Solver for brmppi_solve: the inputs are
+        copied into it and the outputs read from it, so that the per-call
+        marshalling (the closed loop's per-tick cost) only copies arrays;
+        every address is taken once."""
+        if getattr(self, "_hb", None) is None:
+            nx = 8 if int(self.params.get("flags", 0)) & BRMPPI_FLAG_JERK_MODEL else 7
+            row = 8 if int(self.params.get("flags", 0)) & BRMPPI_FLAG_OBS8 else 6
+            bufs = dict(x0=np.zeros(nx), U_nom=np.zeros((self.H, 3), np.float32),
+                        obs=np.zeros((max(1, int(self._p.max_obstacles)), row), np.float32),
+                        path=np.zeros((int(self._p.max_path_pts), 3), np.float32),
+                        U=np.zeros((self.H, 3), np.float32), traj=np.zeros((self.H + 1, 7), np.float32),
+                        J=np.zeros(self.S, np.float32))
+            self._hb = (bufs, {k: v.ctypes.data for k, v in bufs.items()}, nx, row)
+        return self._hb
+
     def solve(self, x0, U_nom, obs, path, ds, seed, counter, want_traj=True, want_J=False,
               check=True):
-        st, U, traj, J = brmppi_solve(self.ctx, x0, U_nom, obs, path, ds, seed, counter, self.H,
-                                      self.S, want_traj, want_J)
+        bufs, adr, nx, row = self._host_buffers()
+        x0 = np.asarray(x0)
+        if x0.size != nx:
+            raise ValueError(f"x0 must have {nx} entries")
+        n_obs = _rows(None if obs is None else np.asarray(obs))
+        path = np.asarray(path)
+        n_pts = path.size // 3
+        if n_obs > bufs["obs"].shape[0] or n_pts > bufs["path"].shape[0] or n_pts * 3 != path.size:
+            # beyond the context's capacities: the library reports it
+            st, U, traj, J = brmppi_solve(self.ctx, x0, U_nom, obs, path, ds, seed, counter, self.H,
+                                          self.S, want_traj, want_J)
+        else:
+            np.copyto(bufs["x0"], x0.reshape(-1), casting="unsafe")
+            np.copyto(bufs["U_nom"], np.asarray(U_nom).reshape(self.H, 3), casting="unsafe")
+            if n_obs:
+                np.copyto(bufs["obs"][:n_obs], np.asarray(obs).reshape(n_obs, row), casting="unsafe")
+            np.copyto(bufs["path"][:n_pts], path.reshape(n_pts, 3), casting="unsafe")
+            lib = _lib or load()
+            st = lib.brmppi_solve(self.ctx, adr["x0"], adr["U_nom"], adr["obs"] if n_obs else None, n_obs,
+                                  adr["path"], n_pts, float(ds), int(seed) & (2**64 - 1),
+                                  int(counter) & (2**64 - 1), adr["U"], adr["traj"] if want_traj else None,
+                                  adr["J"] if want_J else None)
+            U = bufs["U"].copy()
+            traj = bufs["traj"].copy() if want_traj else None
+            J = bufs["J"].copy() if want_J else None
         if check and st != BRMPPI_OK:
             raise BrmppiError(st, brmppi_last_error(self.ctx))
         return dict(status=st, U=U, traj=traj, J=J)

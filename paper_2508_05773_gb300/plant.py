@@ -15,16 +15,18 @@ import numpy as np
 
 
 def step(p: dict, x, u) -> np.ndarray:
-    px, py, th1, th2, v, dl, psi = (float(a) for a in x)
-    a, om, nu = (float(b) for b in u)
-    Ts = float(p["Ts"])
+    px, py, th1, th2, v, dl, psi = np.asarray(x, dtype=np.float64).tolist()
+    a, om, nu = np.asarray(u, dtype=np.float64).tolist()[:3]
+    Ts, l1, l2 = float(p["Ts"]), float(p["l1"]), float(p["l2"])
     t = math.tan(dl)
-    k = float(p["lh"]) / float(p["l1"])
+    k = float(p["lh"]) / l1
+    phi = th1 - th2
+    Tv = Ts * v
     return np.array([
-        px + Ts * v * math.cos(th1),
-        py + Ts * v * math.sin(th1),
-        th1 + Ts * v * t / float(p["l1"]),
-        th2 + Ts * v / float(p["l2"]) * (math.sin(th1 - th2) - k * math.cos(th1 - th2) * t),
+        px + Tv * math.cos(th1),
+        py + Tv * math.sin(th1),
+        th1 + Tv * t / l1,
+        th2 + Tv / l2 * (math.sin(phi) - k * math.cos(phi) * t),
         v + Ts * a,
         dl + Ts * om,
         psi + Ts * nu,
@@ -33,4 +35,7 @@ def step(p: dict, x, u) -> np.ndarray:
 
 def shift(U) -> np.ndarray:
     U = np.asarray(U)
-    return np.concatenate([U[1:], U[-1:]], axis=0)
+    out = np.empty_like(U)
+    out[:-1] = U[1:]
+    out[-1] = U[-1]
+    return out
