@@ -380,6 +380,9 @@ void single_launch_options(brmppi::LaunchDesc& L, const Shape& sh, const brmppi:
   const int spb = sh.threads / sh.tps;
   const int rows = brmppi::exact_rows_variant(sh.tps, sh.bpt, k, n_rows);
   if (rows <= 0) return;
+  // those instantiations are compiled for blocks of at most 384 threads
+  // (more registers a thread)
+  if (brmppi::block_threads(sh.tps, sh.bpt, sh.threads, L.single.P) > brmppi::kMaxRowsBlockThreads) return;
   brmppi::SmemCaps caps = L.caps;
   caps.uh_per_team = 3 * H;
   // those variants merge the instance's tile partials in shared memory

@@ -36,6 +36,7 @@ inline bool needs_ext(const KConst& k) { return k.coll || k.obs8 || k.abuf || k.
 // lanes (0 noise warps).  At most kMaxBlockThreads (the kernels' launch
 // bound).
 constexpr int kMaxBlockThreads = 512;
+constexpr int kMaxRowsBlockThreads = 384;  // the exact-rows instantiations' launch bound
 int noise_warps(int tps, int bpt, int threads, int P);
 int block_threads(int tps, int bpt, int threads, int P);
 

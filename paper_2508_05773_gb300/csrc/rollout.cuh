@@ -1627,7 +1627,10 @@ __device__ __forceinline__ void discard_history(const float* uh, int n_floats) {
 // EXT: the instantiations that also carry the optional terms (moving and
 // e = 4 obstacles, collision cost, buffer cost); the others compile them out.
 template <int TPS, int BPT, bool EXT, int ROWS = 0>
-__global__ void __launch_bounds__(512) solve_kernel(const KConst k, const LaunchDesc L) {
+// Launch bound: 512 threads (128 registers a thread); the exact-rows
+// single-solve instantiations 384 (up to 170 registers: one CTA per SM on
+// the latency shapes, where registers buy a longer schedule)
+__global__ void __launch_bounds__(ROWS > 0 ? 384 : 512) solve_kernel(const KConst k, const LaunchDesc L) {
   extern __shared__ float dyn[];
   __shared__ Shared sh;
   const int spb = compute_threads<TPS>(L.noise_warps) / TPS;
