@@ -18,6 +18,8 @@ void for_each_variant(F f) {
   for (int i = 0; i < n; ++i) f(d[i]);
   const Variant* e = variants_latency(&n);
   for (int i = 0; i < n; ++i) f(e[i]);
+  const Variant* g = variants_latency_ext(&n);
+  for (int i = 0; i < n; ++i) f(g[i]);
 }
 
 // rows = 0: the general instantiation of a shape; rows > 0: the one with
@@ -158,9 +160,9 @@ int noise_warps(int tps, int bpt, int threads, int P) {
 int block_threads(int tps, int bpt, int threads, int P) { return threads + 32 * noise_warps(tps, bpt, threads, P); }
 
 int exact_rows_variant(int tps, int bpt, const KConst& k, int n_rows) {
-  if (needs_ext(k) || !k.proj || tps <= 1 || bpt > 2 || n_rows <= 0) return 0;
+  if (!k.proj || tps <= 1 || bpt > 2 || n_rows <= 0) return 0;
   const int rows = (n_rows + tps - 1) / tps;
-  return find(tps, 1, false, rows) ? rows : 0;
+  return find(tps, 1, needs_ext(k), rows) ? rows : 0;
 }
 
 int variant_occupancy(int tps, int bpt, int threads, size_t smem, bool ext, int P) {
@@ -183,7 +185,7 @@ cudaError_t launch_solve(int tps, int bpt, int blocks, int threads, size_t smem,
     v = (L.work || (!L.single.no_merge && L.caps.merge < L.single.tiles * L.single.part_stride) ||
          L.caps.uh_per_team < 3 * L.single.H)
             ? nullptr
-            : find(tps, 1, false, L.rows);
+            : find(tps, 1, needs_ext(k), L.rows);
     if (!v) return cudaErrorInvalidValue;
   }
   LaunchDesc D = L;

@@ -25,6 +25,7 @@ const Variant* variants_wide(int* n);        // 4 .. 32 lanes per sample
 const Variant* variants_narrow_ext(int* n);  // the same, with the optional terms
 const Variant* variants_wide_ext(int* n);
 const Variant* variants_latency(int* n);     // exact rows a lane, noise-warp shapes
+const Variant* variants_latency_ext(int* n); // the same with the optional terms (4 lanes)
 
 // Whether a launch with these constants needs the family with the optional terms.
 inline bool needs_ext(const KConst& k) { return k.coll || k.obs8 || k.abuf || k.discs || k.third || k.jerk; }

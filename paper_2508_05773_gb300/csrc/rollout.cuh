@@ -168,15 +168,20 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
 }
 
 // Two words -> two standard normals (Box-Muller). Uniform map
-// ((w >> 9) + 1/2) * 2^-23 lies in (0, 1) and is exact in binary32.
+// u = ((w >> 9) + 1/2) 2^-23 in (0, 1), exact in binary32.  It is formed
+// from bits, without an integer-to-float conversion: the float with
+// exponent 0 and mantissa w >> 9 is 1 + (w >> 9) 2^-23, and subtracting
+// 1 - 2^-24 from it is exact (Sterbenz: the operands are within a factor of
+// two); 2u the same way from exponent 1 and 2 - 2^-23.
 __device__ __forceinline__ void box_muller(uint32_t wa, uint32_t wb, float& n0, float& n1) {
-  const float ua = (static_cast<float>(wa >> 9) + 0.5f) * 1.1920928955078125e-07f;
-  const float ub = (static_cast<float>(wb >> 9) + 0.5f) * 1.1920928955078125e-07f;
-  // -2 ln ua lies in [1.2e-7, 33.3] (normal floats): x rsqrt(x), no slow path
-  const float r2 = -2.0f * logf(ua);
+  const float ua = __uint_as_float(0x3f800000u | (wa >> 9)) - 0.999999940395355224609375f;
+  const float ub2 = __uint_as_float(0x40000000u | (wb >> 9)) - 1.99999988079071044921875f;
+  // -2 ln ua lies in [1.2e-7, 33.3] (normal floats), taken without a
+  // branch (neg2_log_unit); the radius as x rsqrt(x), no slow path
+  const float r2 = neg2_log_unit(ua);
   const float radius = r2 * rsqrtf(r2);
   float sn, cs;
-  sincospif(2.0f * ub, &sn, &cs);
+  sincospif(ub2, &sn, &cs);
   n0 = radius * cs;
   n1 = radius * sn;
 }

@@ -1,10 +1,12 @@
-// trig.cuh -- branch-free sin / cos for the rollout step, host- and
+// trig.cuh -- branch-free sin / cos and log for the rollout step, host- and
 // device-callable (the host build serves the accuracy test).  A branch in
 // the step (such as the large-argument path of sincosf) splits it into
 // separate scheduling regions; these have none.
 #pragma once
 
 #include <cmath>
+#include <cstdint>
+#include <cstring>
 #include <cuda_runtime.h>
 
 namespace brmppi {
@@ -53,6 +55,48 @@ __host__ __device__ __forceinline__ void state_sincos(float x, float* s, float* 
   const float ss = odd ? cr : sr, cc = odd ? sr : cr;
   *s = (q & 2) ? -ss : ss;
   *c = ((q + 1) & 2) ? -cc : cc;
+}
+
+// -2 ln u for the Box-Muller uniforms u in [2^-24, 1), without branches.
+// Cody and Waite's reduction (1980): u = 2^e m with m in [sqrt(1/2),
+// sqrt(2)), so ln u = e ln 2 + ln m, and ln m = 2 atanh(s) with
+// s = (m - 1) / (m + 1), |s| <= 0.1716, whose odd series to s^9 truncates
+// below 2e-9 relative.  ln 2 is split into a 16-bit high part (e times it is
+// exact for |e| <= 24) and the float nearest the remainder.  The device
+// divides with the MUFU reciprocal (about 2 ulp).
+__host__ __device__ __forceinline__ float neg2_log_unit(float u) {
+  uint32_t b;
+#ifdef __CUDA_ARCH__
+  b = __float_as_uint(u);
+#else
+  std::memcpy(&b, &u, sizeof(b));
+#endif
+  // e = floor(log2(u / sqrt(1/2))): 0x3f800000 - 0x3f3504f3 (the bits of 1
+  // and of sqrt(1/2)) carries into the exponent field when the mantissa
+  // reaches sqrt(2); the sum stays positive for positive u
+  const int e = static_cast<int>((b + 0x004afb0du) >> 23) - 127;
+  const uint32_t mb = b - (static_cast<uint32_t>(e) << 23);  // m = u 2^-e
+  float m;
+#ifdef __CUDA_ARCH__
+  m = __uint_as_float(mb);
+#else
+  std::memcpy(&m, &mb, sizeof(m));
+#endif
+  const float f = m - 1.0f;
+#ifdef __CUDA_ARCH__
+  const float s = __fdividef(f, f + 2.0f);
+#else
+  const float s = f / (f + 2.0f);
+#endif
+  const float z = s * s;
+  // atanh s / s - 1 = z / 3 + z^2 / 5 + z^3 / 7 + z^4 / 9 + ...
+  const float q = z * fmaf(z, fmaf(z, fmaf(z, 0.1111111111111111f, 0.14285714285714285f), 0.2f),
+                           0.3333333333333333f);
+  const float t = -4.0f * s;
+  const float lm = fmaf(t, q, t);  // -2 ln m
+  const float ef = static_cast<float>(e);
+  // -2 ln 2 = -1.38629150390625 (high part, exact) - 2.8572136e-06
+  return fmaf(ef, -1.38629150390625f, fmaf(ef, -2.8572136406188344e-06f, lm));
 }
 
 }  // namespace brmppi

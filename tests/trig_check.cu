@@ -1,5 +1,6 @@
-// Host build of the rollout step's branch-free sin / cos (csrc/trig.cuh),
-// compared against the C library's double-precision sin / cos.  Prints one
+// Host build of the rollout step's branch-free sin / cos and of the
+// Box-Muller logarithm (csrc/trig.cuh), compared against the C library's
+// double-precision sin / cos / log.  Prints one
 // JSON line of maximum errors; tests/test_trig.py runs and judges it.
 #include <cmath>
 #include <cstdint>
@@ -49,12 +50,22 @@ int main() {
       brmppi::state_sincos(std::ldexp(1.0f + j * 9.5e-6f, i), &s, &c);
       far_abs = std::fmax(far_abs, std::fmax(std::fabs(s), std::fabs(c)));
     }
+  // -2 ln u on every Box-Muller uniform u = (k + 1/2) 2^-23, in ulp of the
+  // exact value
+  double log_ulp = 0;
+  for (uint32_t k = 0; k < (1u << 23); ++k) {
+    const float u = (static_cast<float>(k) + 0.5f) * 1.1920928955078125e-07f;
+    const double ex = -2.0 * std::log(static_cast<double>(u));
+    int ee;
+    std::frexp(ex, &ee);
+    log_ulp = std::fmax(log_ulp, std::fabs(brmppi::neg2_log_unit(u) - ex) / std::ldexp(1.0, ee - 24));
+  }
   float sn, cn;
   brmppi::state_sincos(NAN, &sn, &cn);
   std::printf(
       "{\"turn_sin_ulp\": %.4f, \"turn_cos_ulp\": %.4f, \"state_sin_ulp\": %.4f, \"state_cos_ulp\": %.4f, "
-      "\"state_sin_rel\": %.3e, \"far_max_abs\": %.4f, \"nan_propagates\": %d}\n",
+      "\"state_sin_rel\": %.3e, \"far_max_abs\": %.4f, \"nan_propagates\": %d, \"neg2_log_ulp\": %.4f}\n",
       turn_s / ulp1, turn_c / ulp1, state_s / ulp1, state_c / ulp1, state_rel, far_abs,
-      (std::isnan(sn) && std::isnan(cn)) ? 1 : 0);
+      (std::isnan(sn) && std::isnan(cn)) ? 1 : 0, log_ulp);
   return 0;
 }
