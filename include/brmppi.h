@@ -203,10 +203,12 @@ void brmppi_inject_alloc_failure(int32_t n);
    next call on the context. A NULL ctx gives the last create() failure. */
 const char *brmppi_last_error(const brmppi_ctx *ctx);
 
-/* One solve from HOST buffers: copies inputs to the device, runs the solve
-   and copies U* (H*3), and optionally the optimal trajectory ((H+1)*7) and
-   the per-sample costs (S), back; returns when they are in host memory.
-   n_obs in [0, max_obstacles], n_pts in [2, max_path_pts], ds > 0. */
+/* One solve from HOST buffers: copies the inputs to the device (one copy
+   from the context's pinned staging buffer), runs the solve, whose kernel
+   writes U* (H*3), the optimal trajectory ((H+1)*7) and its status straight
+   into a pinned host buffer of the context, and copies the per-sample costs
+   (S) back when asked for; returns when the outputs are in the caller's
+   buffers.  n_obs in [0, max_obstacles], n_pts in [2, max_path_pts], ds > 0. */
 brmppi_status brmppi_solve(brmppi_ctx *ctx, const double x0[7], const float *U_nom,
                            const float *obs, int32_t n_obs, const float *path, int32_t n_pts,
                            float ds, uint64_t seed, uint64_t counter, float *U_out,
@@ -431,10 +433,10 @@ brmppi_status brmppi_merge_tiles(brmppi_ctx *ctx, const brmppi_instance *q, cons
 brmppi_status brmppi_measure_pipe(int32_t pipe, int64_t iters, double *lane_ops_per_s, double *seconds,
                                   void *stream);
 
-/* Bytes the host entry point brmppi_solve copies per call for a solve with
+/* Bytes the host entry point brmppi_solve moves per call for a solve with
    n_obs obstacles and n_pts path rows: *h2d (inputs, one copy) and *d2h
-   (U*, trajectory and status, one copy; plus 4*S when costs are asked
-   for). */
+   (U*, trajectory and status, written by the kernel into pinned host
+   memory; plus 4*S when costs are asked for). */
 brmppi_status brmppi_transfer_bytes(brmppi_ctx *ctx, int32_t n_obs, int32_t n_pts, uint64_t *h2d,
                                     uint64_t *d2h);
 

@@ -731,13 +731,13 @@ brmppi_status brmppi_create(const brmppi_params* p, int device, brmppi_ctx** out
   if ((e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking)) != cudaSuccess)
     return bail(e, "cudaStreamCreate");
   if ((e = dev_alloc(&c->d_in, c->in_bytes)) != cudaSuccess) return bail(e, "cudaMalloc(in)");
-  if ((e = dev_alloc(&c->d_out, sizeof(float) * c->out_floats)) != cudaSuccess) return bail(e, "cudaMalloc(out)");
   if ((e = dev_alloc(&c->d_J, sizeof(float) * S)) != cudaSuccess) return bail(e, "cudaMalloc(J)");
   if ((e = dev_alloc(&c->d_part, sizeof(float) * c->part_stride * c->part_tiles)) != cudaSuccess)
     return bail(e, "cudaMalloc(partials)");
   if ((e = dev_alloc(&c->d_uh, sizeof(float) * c->uh_floats)) != cudaSuccess) return bail(e, "cudaMalloc(history)");
   if ((e = dev_alloc(&c->d_sync, sizeof(unsigned int) * 4)) != cudaSuccess) return bail(e, "cudaMalloc(sync)");
   if ((e = cudaMemset(c->d_sync, 0, sizeof(unsigned int) * 4)) != cudaSuccess) return bail(e, "cudaMemset");
+  if ((e = dev_alloc(&c->d_out, sizeof(float) * c->out_floats)) != cudaSuccess) return bail(e, "cudaMalloc(out)");
   if ((e = host_alloc(&c->h_in, c->in_bytes)) != cudaSuccess) return bail(e, "cudaMallocHost(in)");
   if ((e = host_alloc(&c->h_out, sizeof(float) * c->out_floats)) != cudaSuccess)
     return bail(e, "cudaMallocHost(out)");
@@ -768,13 +768,13 @@ brmppi_status brmppi_destroy(brmppi_ctx* c) {
   if (done) done = lane_free(c->batch, limit);
   if (done) {
     cudaFree(c->d_in);
-    cudaFree(c->d_out);
     cudaFree(c->d_J);
     cudaFree(c->d_part);
     cudaFree(c->d_uh);
     cudaFree(c->d_sync);
     cudaFreeHost(c->h_in);
     cudaFreeHost(c->h_out);
+    cudaFree(c->d_out);
   } else if (c->batch.stream) {
     cudaStreamDestroy(c->batch.stream);
   }
@@ -821,7 +821,10 @@ brmppi_status brmppi_solve(brmppi_ctx* c, const double x0[7], const float* U_nom
   const size_t in_used = c->off_path + sizeof(float) * 3 * n_pts;
   if ((e = cudaMemcpyAsync(c->d_in, c->h_in, in_used, cudaMemcpyHostToDevice, c->stream)) != cudaSuccess)
     return cuda_fail(c, e, "H2D copy");
-  float* dU = c->d_out;
+  // the kernel writes U*, the optimal trajectory and the status word
+  // straight into the pinned output buffer (mapped into the device's
+  // address space): no device-to-host copy follows the launch
+  float* dU = reinterpret_cast<float*>(c->h_out);
   float* dT = dU + 3 * H;
   int32_t* dS = reinterpret_cast<int32_t*>(dT + 7 * (H + 1));
   st = enqueue_plain(c, sh, reinterpret_cast<const double*>(c->d_in),
@@ -830,9 +833,6 @@ brmppi_status brmppi_solve(brmppi_ctx* c, const double x0[7], const float* U_nom
                      reinterpret_cast<const float*>(c->d_in + c->off_path), n_pts, ds, seed, counter, dU, dT,
                      J_out ? c->d_J : nullptr, nullptr, dS, c->stream);
   if (st != BRMPPI_OK) return st;
-  if ((e = cudaMemcpyAsync(c->h_out, c->d_out, sizeof(float) * c->out_floats, cudaMemcpyDeviceToHost,
-                           c->stream)) != cudaSuccess)
-    return cuda_fail(c, e, "D2H copy");
   if (J_out && (e = cudaMemcpyAsync(J_out, c->d_J, sizeof(float) * c->prm.S, cudaMemcpyDeviceToHost, c->stream)) !=
                    cudaSuccess)
     return cuda_fail(c, e, "D2H copy (J)");
@@ -1049,7 +1049,7 @@ brmppi_status brmppi_autotune(brmppi_ctx* c, const double* x0, const float* U_no
   cudaEventCreate(&e1);
   const int P = philox_blocks(rows_of(c->prm, n_obs));
   const int H = c->prm.H;
-  float* dU = c->d_out;
+  float* dU = c->d_out;  // device scratch: the timed launches' outputs are not read
   float* dT = dU + 3 * H;
   Shape best;
   float best_ms = 1e30f;

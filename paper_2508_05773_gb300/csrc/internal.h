@@ -85,13 +85,13 @@ struct brmppi_ctx {
   size_t smem_limit = 0;
   // plain solves
   unsigned char* d_in = nullptr;  // x0 | U_nom | obs | path
-  float* d_out = nullptr;         // U | traj | status
   float* d_J = nullptr;
   float* d_part = nullptr;
   unsigned int* d_sync = nullptr;  // finished tiles, error bits
   float* d_uh = nullptr;
   unsigned char* h_in = nullptr;
-  float* h_out = nullptr;
+  float* h_out = nullptr;          // U | traj | status of brmppi_solve (written by the kernel)
+  float* d_out = nullptr;          // the same on the device: the autotuner's scratch
   size_t off_unom = 0, off_obs = 0, off_path = 0, in_bytes = 0, out_floats = 0;
   size_t part_stride = 0, part_tiles = 0, uh_floats = 0;
   std::map<int, brmppi_host::Shape> tuned;  // obstacle count -> fastest plain shape

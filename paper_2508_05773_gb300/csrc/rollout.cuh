@@ -504,13 +504,24 @@ __device__ void run_tile(const KConst& k, const Inst& in, int tile, float* uh, c
     d[1] = (cy - fr.oy_h) - fr.oy_l;
     float so, co;
     sincosf(th, &so, &co);
-    d[2] = co;
-    d[3] = so;
     const float ix = 1.0f / (Ax * Ax), iy = 1.0f / (Ay * Ay);
-    d[4] = e4 ? -(ix * ix) : ix;
-    d[5] = e4 ? iy * iy : iy;
-    d[6] = co * vx + so * vy;
-    d[7] = co * vy - so * vx;
+    if constexpr (!EXT) {
+      // parked ellipses: h = d^T Q d - 1 with d the offset in world axes and
+      // Q = R^T diag(ix, iy) R (R the rotation into the obstacle's axes):
+      // (Qxx, Qxy) in place of (cos, sin), Qyy in slot 4
+      const float c2 = co * co, s2 = so * so;
+      d[2] = fmaf(c2, ix, s2 * iy);
+      d[3] = (co * so) * (ix - iy);
+      d[4] = fmaf(s2, ix, c2 * iy);
+      d[5] = d[6] = d[7] = 0.f;
+    } else {
+      d[2] = co;
+      d[3] = so;
+      d[4] = e4 ? -(ix * ix) : ix;
+      d[5] = e4 ? iy * iy : iy;
+      d[6] = co * vx + so * vy;
+      d[7] = co * vy - so * vx;
+    }
   };
   if (has_ob0) stage_obstacle(threadIdx.x, ob0[0], ob0[1], ob0[2], ob0[3], ob0[4], ob0[5], ob0[6], ob0[7]);
   for (int o = threadIdx.x + blockDim.x; o < in.n_obs; o += blockDim.x) {
@@ -865,31 +876,28 @@ __device__ void run_tile(const KConst& k, const Inst& in, int tile, float* uh, c
         a2w = -vv * k.k_hitch * cp * sec2 * k.inv_l2;
         a20 = vv * k.inv_l2 * (cp + k.k_hitch * tn * sp) * (th1dot - th2dot);
       }
-      // per-step factors of the parked-ellipse rows
-      const float cg_row = -2.f * k.Ts * vv, vth_row = vv * th1dot, vv2_row = vv * vv;
+      // per-step factors of the parked-ellipse rows (their rest term, below)
+      const float cg_row = -2.f * k.Ts * vv, vth_row = -k.Ts2 * vv * th1dot, vq_row = -k.Ts2 * vv * vv;
+      const float qxx_row = vq_row * c1 * c1, qyy_row = vq_row * s1 * s1, qxy_row = 2.f * vq_row * c1 * s1;
       auto obstacle_row = [&](int j, float n_alpha, int slot, float live) {
         float h, Aa, Aw = 0.f, brest;
         if constexpr (!EXT) {
+          // staged as (cx, cy, Qxx, Qxy, Qyy): h = d^T Q d - 1 in world axes
           const float4 o0 = *reinterpret_cast<const float4*>(S.obs + 8 * j);
-          const float2 o1 = *reinterpret_cast<const float2*>(S.obs + 8 * j + 4);
+          const float qyy = S.obs[8 * j + 4];
           const float dx = (px - o0.x) + pxl, dy = (py - o0.y) + pyl;
-          const float co = o0.z, so = o0.w, iax = o1.x, iay = o1.y;
-          const float xp = co * dx + so * dy;
-          const float yp = co * dy - so * dx;
-          // with (ax, ay) = grad h / 2 and the heading e1' = (dirx, diry):
-          // h = xp ax + yp ay - 1; hdot = 2 v g, g = grad h . e1' / 2;
+          // with (gx, gy) = grad h / 2 = Q d and the heading e1 = (c1, s1):
+          // h = d . (gx, gy) - 1; hdot = 2 v g, g = grad h . e1 / 2;
           // hddot (input part aside) = 2 v th1dot turn + 2 v^2 curv, turn =
-          // grad h . n1' / 2, curv = e1'^T (Hess h / 2) e1'; so the row's
-          // a-column Ts^2/2 dh/da = Ts^2 g and its rest
+          // grad h . n1 / 2, curv = e1^T (Hess h / 2) e1 = e1^T Q e1; so the
+          // row's a-column Ts^2/2 dh/da = Ts^2 g and its rest
           // -(Ts hdot + Ts^2/2 hddot0) = -2 Ts v g - Ts^2 (v th1dot turn + v^2 curv)
-          const float ax = xp * iax, ay = yp * iay;
-          h = fmaf(ax, xp, fmaf(ay, yp, -1.f));
-          const float dirx = co * c1 + so * s1, diry = co * s1 - so * c1;
-          const float g = fmaf(ax, dirx, ay * diry);
-          const float turn = fmaf(ay, dirx, -(ax * diry));
-          const float curv = fmaf(iax * dirx, dirx, iay * diry * diry);
+          const float gx = fmaf(o0.z, dx, o0.w * dy), gy = fmaf(o0.w, dx, qyy * dy);
+          h = fmaf(gx, dx, fmaf(gy, dy, -1.f));
+          const float g = fmaf(gx, c1, gy * s1);
+          const float turn = fmaf(gy, c1, -(gx * s1));
           Aa = k.Ts2 * g;
-          brest = fmaf(cg_row, g, -k.Ts2 * fmaf(vth_row, turn, vv2_row * curv));
+          brest = fmaf(cg_row, g, fmaf(vth_row, turn, fmaf(qxx_row, o0.z, fmaf(qxy_row, o0.w, qyy_row * qyy))));
         } else {
           // row j: obstacle o seen from footprint disc m (obstacle-major)
           const int o = (k.nd == 1) ? j : __float2int_rz((static_cast<float>(j) + 0.5f) * k.inv_nd);
