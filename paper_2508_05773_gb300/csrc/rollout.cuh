@@ -841,16 +841,25 @@ __device__ void run_tile(const KConst& k, const Inst& in, int tile, float* uh, c
         cw_h = hr.Aw * iht;
         cc_h = pam - rho;
         const float own = (lt == 0) ? 1.f : 0.f;  // the sums take the row once (lane 0)
-        const float ua_ = own * ca_h, uw_ = own * cw_h;
+        const float ua_ = own * ca_h;
         Saa = ua_ * ua_;
-        Saw = ua_ * uw_;
-        Sww = uw_ * uw_;
         ga = ua_ * rho;
-        gw = uw_ * rho;
+        if constexpr (EXT) {
+          const float uw_ = own * cw_h;
+          Saw = ua_ * uw_;
+          Sww = uw_ * uw_;
+          gw = uw_ * rho;
+        } else {
+          // the plain family's ellipse rows have no steer-rate column: these
+          // sums hold the hitch row's terms alone, the same on every lane of
+          // the team (no team reduction; the values it would give)
+          Saw = ca_h * cw_h;
+          Sww = cw_h * cw_h;
+          gw = cw_h * rho;
+        }
       }
 
-      // obstacle rows in the obstacle frame; the steer rate does not enter
-      // at second order.  Parked ellipses (e = 2): hdot shares dh/da's
+      // obstacle rows; the steer rate does not enter at second order.  Parked ellipses (e = 2): hdot shares dh/da's
       // direction term.  Moving or e = 4 rows (uniform branch): barrier of
       // the relative position at this step's time, relative velocity.
       // `live` = 0 turns a padding slot into a no-op without branching.
@@ -1035,10 +1044,16 @@ __device__ void run_tile(const KConst& k, const Inst& in, int tile, float* uh, c
       }
       if (EXT && k.abuf) acc2(Jh, Jl, team_sum<TPS>(cbuf));
       Saa = k.m_a * team_sum<TPS>(Saa) + k.m_u0;
-      Saw = k.m_a * team_sum<TPS>(Saw);
-      Sww = k.m_a * team_sum<TPS>(Sww) + k.m_u1;
       ga = k.m_a * team_sum<TPS>(ga);
-      gw = k.m_a * team_sum<TPS>(gw);
+      if constexpr (EXT) {
+        Saw = k.m_a * team_sum<TPS>(Saw);
+        Sww = k.m_a * team_sum<TPS>(Sww) + k.m_u1;
+        gw = k.m_a * team_sum<TPS>(gw);
+      } else {
+        Saw = k.m_a * Saw;
+        Sww = k.m_a * Sww + k.m_u1;
+        gw = k.m_a * gw;
+      }
       const float idet = __fdividef(1.f, Saa * Sww - Saw * Saw);  // SPD: det > 0
       const float ya = (Sww * ga - Saw * gw) * idet;
       const float yw = (Saa * gw - Saw * ga) * idet;
