@@ -52,18 +52,27 @@ L2_FLUSH_BYTES = 256 << 20
 # compensated sums and without team redundancy): every +, -, *, fma, min,
 # max, compare/select, integer mul.lo / mul.hi / xor / add / shift / convert
 # and every elementary function (sin, cos, tan, log, sqrt, exp, reciprocal)
-# counts one.  Tally per term:
-PHILOX_BLOCK_OPS = 132    # 10 rounds x 10 int ops, 4 uniform maps x 4, 2 Box-Muller pairs x 8
-STEP_BASE_OPS = 111       # z_des 9, state trig 13, p_u 6, 2x2 solve 14, clip 6, Euler 14, path + cost 49
-HITCH_OPS = 60            # row 27, projection terms 30, alpha update 3
-OBSTACLE_OPS = 64         # row 38, projection terms 24, alpha update 2
+# counts one; abs and negation are operand modifiers and count nothing.  The
+# tally follows the formulation the kernel evaluates (parked ellipses in
+# world axes through the staged quadratic form, shared per-step factors):
+PHILOX_BLOCK_OPS = 124    # 10 rounds x (2 mul.lo, 2 mul.hi, 4 xor, 2 key adds) less the last round's
+#                           dead key adds 98; 4 uniform maps x 3 (shift, or, subtract); 2 Box-Muller pairs x 7
+#                           (log, -2 scale, sqrt, sin, cos, 2 products)
+STEP_BASE_OPS = 115       # z_des 9, state trig 14, p_u 6, 2x2 solve 17, clip 6, Euler 14, path + cost 49
+ROW_FACTOR_OPS = 12       # per-step factors shared by the ellipse rows (-2 Ts v, -Ts^2 v th1dot, -Ts^2 v^2 x
+#                           (c1^2, 2 c1 s1, s1^2))
+HITCH_OPS = 51            # row 27, projection terms 21, alpha update 3
+OBSTACLE_OPS = 35         # offset 2, Q d 4, h 2, grad . e1 2, grad . n1 2, rest 5, a-column 1;
+#                           projection terms 15 (floor, sign, alpha sample 3, p_alpha, b, r 2, reciprocal,
+#                           u, rho, two sums, c); alpha update 2
 
 
 def ops_per_rollout_step(n_obs: int, proj: bool = True) -> int:
     if not proj:
-        return PHILOX_BLOCK_OPS + STEP_BASE_OPS - 6
+        return PHILOX_BLOCK_OPS + STEP_BASE_OPS - 6 - 17  # no p_u, no 2x2 solve
     P = (3 + 1 + n_obs + 3) // 4
-    return PHILOX_BLOCK_OPS * P + STEP_BASE_OPS + HITCH_OPS + OBSTACLE_OPS * n_obs
+    return (PHILOX_BLOCK_OPS * P + STEP_BASE_OPS + HITCH_OPS + OBSTACLE_OPS * n_obs +
+            (ROW_FACTOR_OPS if n_obs > 0 else 0))
 
 
 # Of those, the elementary functions the step evaluates on the XU (the

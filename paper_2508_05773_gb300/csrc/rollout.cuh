@@ -830,7 +830,7 @@ __device__ void run_tile(const KConst& k, const Inst& in, int tile, float* uh, c
           hr.Aa = -k.hTs2 * k.kappa;
         }
         const float hm = fmaxf(fabsf(hr.h), k.h_floor);
-        const float ht = hr.h >= 0.f ? hm : -hm;
+        const float ht = copysignf(hm, hr.h);  // h's sign (h = -0 does not arise: an exact zero rounds to +0)
         const float zda = clampf(k.sigma_alpha * n_h, k.ua_lo, k.ua_hi);
         const float pam = k.w_am * zda + k.pc_am;  // p_alpha / m_alpha
         const float b = -alpha_h * hr.h - hr.c0;
@@ -971,7 +971,7 @@ __device__ void run_tile(const KConst& k, const Inst& in, int tile, float* uh, c
           }
         }
         const float hm = fmaxf(fabsf(h), k.h_floor);
-        const float ht = h >= 0.f ? hm : -hm;
+        const float ht = copysignf(hm, h);
         const float zda = clampf(k.sigma_alpha * n_alpha, k.ua_lo, k.ua_hi);
         const float pam = k.w_am * zda + k.pc_am;  // p_alpha / m_alpha
         const float b = -alpha[slot] * h + brest;
