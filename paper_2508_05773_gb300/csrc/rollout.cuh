@@ -172,16 +172,16 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
 // from bits, without an integer-to-float conversion: the float with
 // exponent 0 and mantissa w >> 9 is 1 + (w >> 9) 2^-23, and subtracting
 // 1 - 2^-24 from it is exact (Sterbenz: the operands are within a factor of
-// two); 2u the same way from exponent 1 and 2 - 2^-23.
+// two).  The angle 2 pi u_b is reduced from the bits of w_b >> 9 too
+// (unit_turn_sincos).
 __device__ __forceinline__ void box_muller(uint32_t wa, uint32_t wb, float& n0, float& n1) {
   const float ua = __uint_as_float(0x3f800000u | (wa >> 9)) - 0.999999940395355224609375f;
-  const float ub2 = __uint_as_float(0x40000000u | (wb >> 9)) - 1.99999988079071044921875f;
   // -2 ln ua lies in [1.2e-7, 33.3] (normal floats), taken without a
   // branch (neg2_log_unit); the radius as x rsqrt(x), no slow path
   const float r2 = neg2_log_unit(ua);
   const float radius = r2 * rsqrtf(r2);
   float sn, cs;
-  sincospif(ub2, &sn, &cs);
+  unit_turn_sincos(wb >> 9, &sn, &cs);
   n0 = radius * cs;
   n1 = radius * sn;
 }

@@ -57,6 +57,32 @@ __host__ __device__ __forceinline__ void state_sincos(float x, float* s, float* 
   *c = ((q + 1) & 2) ? -cc : cc;
 }
 
+// sin and cos of 2 pi u for the Box-Muller uniforms u = (k + 1/2) 2^-23,
+// k < 2^23 (the top 23 bits of a Philox word), from k's bits: no
+// conversion, no branch.  4u = m + f with m = round(4u) = (k + 2^20) >> 21
+// the quadrant and f = (k' + 1/2) 2^-21 - 1/2, k' = (k + 2^20) mod 2^21;
+// f is the float 1 + k' 2^-21 (exponent 0, mantissa k' << 2) minus
+// 3/2 - 2^-22, exact (Sterbenz).  Then 2 pi u = m pi/2 + r with r = f pi/2,
+// |r| <= pi/4: the Taylor pair and the quadrant as in state_sincos.
+__host__ __device__ __forceinline__ void unit_turn_sincos(uint32_t k, float* s, float* c) {
+  const uint32_t kk = k + (1u << 20);
+  const uint32_t m = kk >> 21;
+  const uint32_t bits = 0x3f800000u | ((kk & 0x1fffffu) << 2);
+  float one_f;
+#ifdef __CUDA_ARCH__
+  one_f = __uint_as_float(bits);
+#else
+  std::memcpy(&one_f, &bits, sizeof(one_f));
+#endif
+  const float r = (one_f - 1.49999976158142089844f) * 1.57079632679489661923f;
+  float sr, cr;
+  turn_sincos(r, &sr, &cr);
+  const bool odd = m & 1u;
+  const float ss = odd ? cr : sr, cc = odd ? sr : cr;
+  *s = (m & 2u) ? -ss : ss;
+  *c = ((m + 1u) & 2u) ? -cc : cc;
+}
+
 // -2 ln u for the Box-Muller uniforms u in [2^-24, 1), without branches.
 // Cody and Waite's reduction (1980): u = 2^e m with m in [sqrt(1/2),
 // sqrt(2)), so ln u = e ln 2 + ln m, and ln m = 2 atanh(s) with

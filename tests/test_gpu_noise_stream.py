@@ -8,9 +8,10 @@ Bound on a normal: n = r (cos, sin)(2 pi u_b) with r = sqrt(-2 ln u_a).  The
 kernel takes -2 ln u_a without a branch (Cody-Waite reduction and the atanh
 series: within 2 ulp with an exact division, host test; about 3.5 ulp with
 the device's MUFU reciprocal), the radius as x rsqrt(x) (2 ulp for rsqrt,
-one rounding), sincospif (1 ulp) and one product: about 6 ulp of the radius
-in all, so |n_gpu - n_oracle| <= 2^-20 r (8 to 16 ulp of r); the uniform
-maps are exact on both sides."""
+one rounding), the sin / cos of 2 pi u_b from u_b's bits (within 0.75 ulp
+of 1, host test) and one product: about 6 ulp of the radius in all, so
+|n_gpu - n_oracle| <= 2^-20 r (8 to 16 ulp of r); the uniform maps are
+exact on both sides."""
 import numpy as np
 import pytest
 

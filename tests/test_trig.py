@@ -5,7 +5,9 @@ reduced state angle on [-2^16, 2^16] stay within 1.5 ulp of 1.0f, sin
 keeps its relative accuracy near zero, results stay in [-1, 1] up to 2^24
 and NaN propagates; -2 ln u is within 2 ulp of the exact value on all 2^23
 uniforms the noise maps to (the host divides exactly; the device's MUFU
-reciprocal adds about 2 ulp, bounded on the GPU by the noise-stream test)."""
+reciprocal adds about 2 ulp, bounded on the GPU by the noise-stream test),
+and sin / cos of 2 pi u from the uniform's bits within 1 ulp of 1.0f on
+all of them."""
 import json
 import os
 import shutil
@@ -53,3 +55,7 @@ def test_far_arguments_bounded_and_nan(errors):
 
 def test_box_muller_log_within_bound(errors):
     assert errors["neg2_log_ulp"] <= 2.0, errors
+
+
+def test_box_muller_angle_within_bound(errors):
+    assert errors["unit_sin_ulp"] <= 1.0 and errors["unit_cos_ulp"] <= 1.0, errors

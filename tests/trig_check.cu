@@ -1,5 +1,5 @@
 // Host build of the rollout step's branch-free sin / cos and of the
-// Box-Muller logarithm (csrc/trig.cuh), compared against the C library's
+// Box-Muller logarithm and angle (csrc/trig.cuh), compared against the C library's
 // double-precision sin / cos / log.  Prints one
 // JSON line of maximum errors; tests/test_trig.py runs and judges it.
 #include <cmath>
@@ -60,12 +60,21 @@ int main() {
     std::frexp(ex, &ee);
     log_ulp = std::fmax(log_ulp, std::fabs(brmppi::neg2_log_unit(u) - ex) / std::ldexp(1.0, ee - 24));
   }
+  // sin / cos of 2 pi u on every Box-Muller uniform, from the bits of k
+  double unit_s = 0, unit_c = 0;
+  for (uint32_t k = 0; k < (1u << 23); ++k) {
+    const double a = 6.283185307179586477 * ((k + 0.5) * std::ldexp(1.0, -23));
+    float s, c;
+    brmppi::unit_turn_sincos(k, &s, &c);
+    unit_s = std::fmax(unit_s, std::fabs(s - std::sin(a)));
+    unit_c = std::fmax(unit_c, std::fabs(c - std::cos(a)));
+  }
   float sn, cn;
   brmppi::state_sincos(NAN, &sn, &cn);
   std::printf(
       "{\"turn_sin_ulp\": %.4f, \"turn_cos_ulp\": %.4f, \"state_sin_ulp\": %.4f, \"state_cos_ulp\": %.4f, "
-      "\"state_sin_rel\": %.3e, \"far_max_abs\": %.4f, \"nan_propagates\": %d, \"neg2_log_ulp\": %.4f}\n",
+      "\"state_sin_rel\": %.3e, \"far_max_abs\": %.4f, \"nan_propagates\": %d, \"neg2_log_ulp\": %.4f, \"unit_sin_ulp\": %.4f, \"unit_cos_ulp\": %.4f}\n",
       turn_s / ulp1, turn_c / ulp1, state_s / ulp1, state_c / ulp1, state_rel, far_abs,
-      (std::isnan(sn) && std::isnan(cn)) ? 1 : 0, log_ulp);
+      (std::isnan(sn) && std::isnan(cn)) ? 1 : 0, log_ulp, unit_s / ulp1, unit_c / ulp1);
   return 0;
 }
