@@ -33,28 +33,35 @@ __host__ __device__ __forceinline__ void turn_sincos(float e, float* s, float* c
 // pi/2 (Cody and Waite, 1980): pi/2 split into the float nearest it and the
 // float nearest the remainder; x - k hi is exact for |x| < 2^24 pi/2, so r
 // carries one rounding; then turn_sincos on |r| <= pi/4 and the quadrant.
-// Within 1.5 ulp of the exact values for |x| <= 2^16 (host test against
-// FP64), within [-1, 1] up to |x| = 2^24, NaN for NaN or infinite x.
-// Beyond 2^24 rad the rounding of x 2/pi leaves r unbounded: only a rollout
-// whose steering came within ~1e-7 rad of +-pi/2 gets there, and the huge
-// or non-finite cost it then accrues carries zero weight in the softmin.
+// k = round(x 2/pi) by the shifter 1.5 * 2^23: adding it rounds the product
+// to an integer exactly as rintf does (ties to even) for |x 2/pi| < 2^22,
+// and the sum's low mantissa bits are k mod 4 -- no rounding or conversion
+// instruction on the steer angle's dependency chain.  Within 1.5 ulp of the
+// exact values for |x| <= 2^16 (host test against FP64); up to |x| = 2^24
+// the outputs stay within 4e-6 of [-1, 1] (beyond 2^22 pi/2 the shifted sum
+// loses integer resolution and |r| reaches pi/2, where the Taylor pair is
+// still within 3.6e-6); NaN for NaN or infinite x.  Beyond 2^24 rad the
+// outputs grow: only a rollout whose steering came within ~1e-7 rad of
+// +-pi/2 gets there, and the huge or non-finite cost it then accrues carries
+// zero weight in the softmin.
 __host__ __device__ __forceinline__ void state_sincos(float x, float* s, float* c) {
-  const float kf = rintf(x * 0.636619746685028f);  // 2 / pi
+  const float t = x * 0.636619746685028f + 12582912.0f;  // 2 / pi; 1.5 * 2^23
+  const float kf = t - 12582912.0f;
+  uint32_t tb;
 #ifdef __CUDA_ARCH__
-  const int q = static_cast<int>(kf);  // cvt.rzi: saturates, NaN -> 0
+  tb = __float_as_uint(t);
 #else
-  // the same in host C++, where the conversion of NaN or of |kf| >= 2^31 is
-  // undefined: clamp first (only q mod 4 is used), NaN -> 0
-  const int q = (kf == kf) ? static_cast<int>(fminf(fmaxf(kf, -1073741824.0f), 1073741824.0f)) : 0;
+  std::memcpy(&tb, &t, sizeof(tb));
 #endif
+  const uint32_t q = tb;  // k mod 4 in the low bits (the shifter is 0 mod 4)
   float r = fmaf(-kf, 1.5707963705062866f, x);
   r = fmaf(-kf, -4.371138828673793e-08f, r);
   float sr, cr;
   turn_sincos(r, &sr, &cr);
-  const bool odd = q & 1;  // x = r + q pi/2
+  const bool odd = q & 1u;  // x = r + k pi/2
   const float ss = odd ? cr : sr, cc = odd ? sr : cr;
-  *s = (q & 2) ? -ss : ss;
-  *c = ((q + 1) & 2) ? -cc : cc;
+  *s = (q & 2u) ? -ss : ss;
+  *c = ((q + 1u) & 2u) ? -cc : cc;
 }
 
 // sin and cos of 2 pi u for the Box-Muller uniforms u = (k + 1/2) 2^-23,
