@@ -189,9 +189,12 @@ __device__ __forceinline__ void box_muller(uint32_t wa, uint32_t wb, float& n0, 
 __device__ __forceinline__ float clampf(float v, float lo, float hi) { return fminf(fmaxf(v, lo), hi); }
 
 
-// into [-pi, pi]; only the square of the result is used
+// into [-pi, pi]; only the square of the result is used.  The turn count
+// is rounded by the 1.5 * 2^23 shifter (as rintf for |a| < 2^22 2 pi; no
+// rounding instruction)
 __device__ __forceinline__ float wrap_pi(float a) {
-  return a - 6.28318530717958647692f * rintf(a * 0.15915494309189533577f);
+  const float n = (a * 0.15915494309189533577f + 12582912.0f) - 12582912.0f;
+  return a - 6.28318530717958647692f * n;
 }
 
 template <int TPS>
@@ -977,15 +980,18 @@ __device__ void run_tile(const KConst& k, const Inst& in, int tile, float* uh, c
         const float b = -alpha[slot] * h + brest;
         float r = fmaf(Aa, q0, fmaf(ht, pam, -b));
         if constexpr (EXT) r = fmaf(Aw, q1, r);
-        const float iht = __fdividef(1.f, ht);  // MUFU reciprocal (~1 ulp)
-        const float u = live * (Aa * iht);
+        // MUFU reciprocal (~1 ulp); a padding slot (live = 0) gets 0: its
+        // u, w and rho vanish, so it adds nothing to the sums (its own rate
+        // drifts by p_alpha a step and is never read by a live row)
+        const float iht = live * __fdividef(1.f, ht);
+        const float u = Aa * iht;
         const float rho = r * iht;
         Saa += u * u;
         ga += u * rho;
         ca[slot] = u;
-        cc[slot] = live * (pam - rho);
+        cc[slot] = pam - rho;
         if constexpr (EXT) {
-          const float w = live * (Aw * iht);
+          const float w = Aw * iht;
           Saw += u * w;
           Sww += w * w;
           gw += w * rho;
