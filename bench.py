@@ -944,6 +944,7 @@ def run_ours(args, world, rank, local):
         kernel_s = total_ms * 1e-3 / args.steps
         roof = alu_roofline(ops, S * H * xu_ops_per_rollout_step(n_obs), kernel_s, "solve_kernel",
                             kernel_mhz=(clk or {}).get("sm_mhz"))
+        roof["ops_per_rollout_step"] = ops_per_rollout_step(n_obs)
         roof["traffic"] = _traffic_for_current_kernel()
         launch = solver.launch(n_obs)
         line = {
