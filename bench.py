@@ -859,7 +859,9 @@ def run_ours(args, world, rank, local):
     p = c["params"]
     S, H = int(p["S"]), int(p["H"])
     n_obs = int(c["obs"].shape[0])
-    solver = pkg.Solver(p, device=local, max_obstacles=max(16, n_obs), max_path_pts=1024)
+    pinned = args.tps > 0 and args.threads > 0  # a fixed launch shape in place of the autotuner's pick
+    shape = dict(threads_per_sample=args.tps, block_threads=args.threads) if pinned else {}
+    solver = pkg.Solver(p, device=local, max_obstacles=max(16, n_obs), max_path_pts=1024, **shape)
 
     # ---------------- device-resident inputs
     x0 = torch.tensor(c["x0"], dtype=torch.float64, device=dev)
@@ -874,7 +876,8 @@ def run_ours(args, world, rank, local):
 
     if rank == 0:
         pipe_peaks(local)  # the roofline denominators, measured before anything is timed
-    solver.autotune(x0, Ubuf[0], obs, path, c["ds"], reps=3, stream=stream)
+    if not pinned:
+        solver.autotune(x0, Ubuf[0], obs, path, c["ds"], reps=3, stream=stream)
 
     def solve(tick: int):
         rc = solver.solve_device(x0, Ubuf[tick % 2], obs, path, c["ds"], c["seed"], tick, U_out,
@@ -991,8 +994,10 @@ def main():
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--profile", choices=("solve", "batch", "stress", "stress_stored", "stabilizer"), default=None,
                     help="a few launches of one workload for ncu, no timing")
-    ap.add_argument("--tps", type=int, default=0, help="--profile: threads per sample")
-    ap.add_argument("--threads", type=int, default=0, help="--profile: threads per block")
+    ap.add_argument("--tps", type=int, default=0,
+                    help="threads per sample of the timed solve (with --threads: no autotuning; --profile too)")
+    ap.add_argument("--threads", type=int, default=0,
+                    help="threads per block of the timed solve (with --tps: no autotuning; --profile too)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
