@@ -384,9 +384,12 @@ __device__ __forceinline__ void make_frame_warp(const double* x0, double inv_ds,
 
 // Shared memory of a CTA (offsets into the dynamic buffer, floats).
 struct Smem {
-  float* obs;    // 8 per obstacle: cx, cy, cos, sin, kx, ky, vx', vy' with
-                 // k = 1/A^2 (e = 2) or 1/A^4 (e = 4, kx stored negated) and
-                 // the velocity in the obstacle frame (zero unless moving)
+  float* obs;    // 8 per obstacle.  Plain family (parked ellipses): cx, cy,
+                 // Qxx, Qxy, Qyy, 0, 0, 0 (the world-axis quadratic form of
+                 // h).  Family with the optional terms: cx, cy, cos, sin, kx,
+                 // ky, vx', vy' with k = 1/A^2 (e = 2) or 1/A^4 (e = 4, kx
+                 // stored negated) and the velocity in the obstacle frame
+                 // (zero unless moving)
   float* path;   // 3 per row: x, y, heading (relative frame)
   float* phead;  // 2 per row: cos, sin of the row's heading in world axes
   float* unom;   // 3H
