@@ -77,10 +77,11 @@ def ops_per_rollout_step(n_obs: int, proj: bool = True) -> int:
 
 # Of those, the elementary functions the step evaluates on the XU (the
 # special-function pipe, 16 lanes a clock per SM against 128 for FP32): per
-# Philox block the two Box-Muller logarithms and radii (reciprocal square
-# root); per constraint row one reciprocal (1 / h~); per step the steer
-# angle's tangent and the 2x2 determinant (one reciprocal each).  Box-Muller's
-# sin / cos of pi u and the state angles' sin / cos are FP32 polynomials.
+# Philox block the reciprocals of the two Box-Muller logarithms' reductions
+# and the two radii (reciprocal square root); per constraint row one
+# reciprocal (1 / h~); per step the steer angle's tangent and the 2x2
+# determinant (one reciprocal each).  The logarithms' series, Box-Muller's
+# sin / cos of 2 pi u and the state angles' sin / cos are FP32 polynomials.
 def xu_ops_per_rollout_step(n_obs: int, proj: bool = True) -> int:
     if not proj:
         return 4 + 1
